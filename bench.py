@@ -1,0 +1,317 @@
+"""Benchmark: FIRLS reconstructions per second at 256x256 (TV + Daubechies-4).
+
+Workload (one GPU): a batch of ``--batch`` independent 256x256 complex
+slices, each the TV + 4-level D4 problem (20 % variable-density mask,
+sigma 0.01, lambda_TV 1e-3, lambda_W 5e-4) with its own seed, solved with
+a fixed FIRLS schedule of ``--outer`` reweighting steps x ``--inner`` PCG
+steps.  One bench step = one full reconstruction of the whole batch; the
+value is reconstructions per second over all ranks.  Inputs are synthetic
+(seeded phantoms standing in for the paper's MR images).
+
+``--impl reference`` times the FP64 CPU oracle instead, on a bounded sample
+of the same workload (one slice, ``--ref-outer`` outer steps per bench
+step), and reports the same metric.
+
+Under torchrun every rank solves its own batch (independent slices, no data
+exchange: weak scaling); only the step timing is reduced (max over ranks).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "recons/sec at 256^2 to 1e-4 of FP64 oracle (TV+D4 FIRLS)"
+UNIT = "recons/s"
+N = 256
+RATIO, SIGMA, LAM_TV, LAM_W, LEVELS = 0.20, 0.01, 1e-3, 5e-4, 4
+
+# Algorithmic bytes per pixel per launch of each kernel class: every distinct
+# input read once and every output written once (complex64 8 B, float 4 B,
+# mask 1 B).  Wavelet passes move the full pyramid (4/3 of the image).
+ALG_BYTES_PER_PX = {
+    "row_fft": 32.0,            # read z, d; write d, t
+    "col_fft_mask": 17.0,       # read t, mask; write t
+    "wavelet_fwd": 8.0 + 4.0 + 8.0,   # read d, w; write w*Phi d (whole pyramid)
+    "wavelet_inv": 16.0,        # read coefficients; write image
+    "row_ifft_combine": 36.0,   # read t, d, u, W_tv; write q
+    "ilu": 68.0,                # read x, d, r, q, 1/a, b, c; write x, r, z
+    "axpy": 32.0,
+}
+
+
+def problem(seed):
+    import firls_synth as fs
+    return fs.make_problem(N, RATIO, SIGMA, seed, real=False, psi=fs.PSI_TV | fs.PSI_DB4, levels=LEVELS,
+                           lam=LAM_W, lam_tv=LAM_TV)
+
+
+def make_batch(batch, first_seed):
+    probs = [problem(first_seed + i) for i in range(batch)]
+    masks = np.stack([p.mask for p in probs])
+    b = np.stack([p.b for p in probs]).astype(np.complex64)
+    return masks, b
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_ours(args):
+    import torch
+    import paper_1411_5057_gb300 as F
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    B = args.batch
+    masks_h, b_h = make_batch(B, 2 + rank * B)
+    stream = torch.cuda.Stream()
+    params = F.make_params(args.outer, args.inner, lam=LAM_W, lam_tv=LAM_TV)
+    with torch.cuda.stream(stream):
+        masks = torch.from_numpy(masks_h).cuda()
+        b = torch.from_numpy(b_h).cuda()
+        ctx = F.Context(N, batch=B, stream=stream)
+        ctx.set_operator(masks, F.PSI_TV | F.PSI_DB4, LEVELS)
+        x = torch.empty_like(b)
+    stream.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- device-resident throughput ----
+    for _ in range(args.warmup):
+        ctx.solve(b, params, out=x)
+    stream.synchronize()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.solve(b, params, out=x)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    barrier()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * B / (ms / 1e3)
+
+    # ---- per-kernel timing of one outer step (same workload, same launches) ----
+    ctx.set_timing(True)
+    one = F.make_params(1, args.inner, lam=LAM_W, lam_tv=LAM_TV)
+    ctx.solve(b, one, out=x)
+    ctx.solve(b, one, out=x)
+    kt = ctx.get_timing()
+    ctx.set_timing(False)
+    launches_per_step = sum(v[1] for v in kt.values()) * args.outer
+    kern = {k: {"ms_per_outer": round(v[0], 4), "launches": v[1]} for k, v in kt.items()}
+    dom = max((k for k in ALG_BYTES_PER_PX if kt[k][1] > 0), key=lambda k: kt[k][0])
+    per_launch_s = kt[dom][0] / kt[dom][1] / 1e3
+    alg = ALG_BYTES_PER_PX[dom] * N * N * B
+    if dom.startswith("wavelet"):
+        alg *= 4.0 / 3.0
+    achieved = alg / per_launch_s / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "alg_bytes_per_launch": alg}
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if args.e2e_steps > 0:
+        bh = torch.from_numpy(b_h).pin_memory()
+        mh = torch.from_numpy(masks_h).pin_memory()
+        xh = torch.empty(b_h.shape, dtype=torch.complex64).pin_memory()
+        with torch.cuda.stream(stream):
+            bd = torch.empty_like(b)
+            md = torch.empty_like(masks)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            with torch.cuda.stream(stream):
+                md.copy_(mh, non_blocking=True)
+                bd.copy_(bh, non_blocking=True)
+                ctx.set_operator(md, F.PSI_TV | F.PSI_DB4, LEVELS)
+                ctx.solve(bd, params, out=x)
+                xh.copy_(x, non_blocking=True)
+            stream.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        if dist is not None:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * B / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(bh.numel() * 8 + mh.numel()),
+               "d2h_bytes_per_step": int(xh.numel() * 8)}
+
+    out = None
+    if rank == 0:
+        cpu = cpu_baseline(args) if (world == 1 and not args.no_cpu_baseline) else None
+        out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32 (FP64 PCG scalars)", "data": "synthetic",
+               "config": {"workload": f"firls_tv_db4_{N}", "n": N, "batch_per_gpu": B, "outer": args.outer,
+                          "inner": args.inner, "mask_ratio": RATIO, "sigma": SIGMA, "lambda_tv": LAM_TV,
+                          "lambda_w": LAM_W, "wavelet": "db4", "levels": LEVELS,
+                          "l2": "working set > L2 (no flush needed)",
+                          "parallelism": f"replicas{world}"},
+               "roofline": roofline, "kernels_per_outer_step": kern, "gpu_launches": int(launches_per_step * args.steps),
+               "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return out
+
+
+def oracle_sample(outer_steps, seed=2):
+    """Time ``outer_steps`` FIRLS outer steps of the FP64 oracle on one slice."""
+    from oracle import firls_oracle as O
+    p = problem(seed)
+    t0 = time.perf_counter()
+    O.firls_problem(p, outer=outer_steps, inner=ARGS_INNER[0])
+    return time.perf_counter() - t0
+
+
+ARGS_INNER = [20]
+
+
+def cpu_baseline(args):
+    env_threads = 1
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = str(env_threads)
+    ARGS_INNER[0] = args.inner
+    sec = oracle_sample(args.ref_outer)
+    recon_s = sec / args.ref_outer * args.outer
+    return {"value": round(1.0 / recon_s, 6), "unit": UNIT, "cores": env_threads, "kind": "oracle",
+            "sample": f"FP64 oracle, one {N}^2 slice, {args.ref_outer} of {args.outer} outer steps x {args.inner} "
+                      f"PCG ({sec:.1f} s), scaled to one reconstruction"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return None
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    ARGS_INNER[0] = args.inner
+    for _ in range(args.warmup):
+        oracle_sample(1)
+    t = [oracle_sample(args.ref_outer) for _ in range(args.steps)]
+    sec = float(np.mean(t))
+    value = (args.ref_outer / args.outer) / sec
+    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"FP64 oracle, one {N}^2 slice, {args.ref_outer} of {args.outer} outer steps x {args.inner} "
+                     f"PCG per bench step"}
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"firls_tv_db4_{N}", "n": N, "batch_per_gpu": 1, "outer": args.outer,
+                      "inner": args.inner, "parallelism": "cpu"},
+           "cpu_baseline": cpu, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=304)
+    ap.add_argument("--outer", type=int, default=50)
+    ap.add_argument("--inner", type=int, default=20)
+    ap.add_argument("--ref-outer", type=int, default=2, help="oracle outer steps per sample")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

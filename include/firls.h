@@ -1,0 +1,216 @@
+/*
+ * firls.h - C ABI of the GB300 (sm_103a) FIRLS library.
+ *
+ * FIRLS (fast iteratively reweighted least squares, arXiv 1411.5057) solves
+ * the analysis-sparsity reconstruction problem (Eq. anapro / probogs / iso)
+ *
+ *     min_x  1/2 ||A x - b||^2 + lambda ||G Phi x||_{2,1}
+ *                              + lambda_tv ||[D1 x, D2 x]||_{2,1}
+ *
+ * with A = R F an undersampled 2-D Fourier operator (R: sampling mask, F: the
+ * unitary 2-D DFT), Phi an orthogonal periodic wavelet (Haar or
+ * Daubechies-4, Mallat layout), G a group map built from rows of the
+ * identity (Fig. 1) and D1/D2 first-order finite differences (Sec. 4.1, zero
+ * extension at the image border).  Each outer step recomputes the weights
+ * W (Eq. gw, Eq. Wog, Eq. wi) and runs preconditioned CG on the normal
+ * equations (Eq. subprob, Eq. sub) with the pseudo-diagonal preconditioner
+ * (Eq. pog) or, when TV is present, the penta-diagonal preconditioner with
+ * the printed L U factors (Eq. ptv, Sec. 4.2) - Alg. 2 and Alg. 3.
+ *
+ * Conventions shared by every entry point:
+ *   - Images are square, n x n, row-major; a batch is [batch][n][n].
+ *   - Complex data is interleaved float pairs (re, im), i.e. complex64.
+ *   - Every pointer documented as "device" must point to memory of the CUDA
+ *     device that was current when the context was created; the caller
+ *     keeps ownership of every buffer it passes in.
+ *   - Work is enqueued on the context's stream; entry points return once
+ *     the work is enqueued unless stated otherwise.
+ *   - Errors are returned as firls_status codes, never thrown across the
+ *     ABI.  Invalid arguments are rejected before any launch.  After an
+ *     error the context stays valid; firls_last_error() gives a message.
+ */
+#ifndef FIRLS_H_
+#define FIRLS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct firls_ctx firls_ctx;
+
+typedef enum {
+  FIRLS_OK = 0,
+  FIRLS_E_INVALID_ARG = 1, /* null pointer, negative lambda, bad counts      */
+  FIRLS_E_SHAPE = 2,       /* unsupported n, n not divisible by 2^levels ... */
+  FIRLS_E_GROUPMAP = 3,    /* group index outside [0, n*n)                   */
+  FIRLS_E_CUDA = 4,        /* a CUDA runtime call or kernel launch failed    */
+  FIRLS_E_NOMEM = 5,       /* device allocation failed                       */
+  FIRLS_E_BREAKDOWN = 6,   /* PCG breakdown (d^H S d <= 0 or not finite)     */
+  FIRLS_E_STATE = 7        /* call out of order (e.g. solve before operator) */
+} firls_status;
+
+/* Regulariser bitmask (psi_kind).  HAAR and DB4 are exclusive; TV may be
+ * combined with either wavelet, in which case both terms enter S and the
+ * TV preconditioner's diagonal gains lambda * diag(Phi^T W Phi). */
+enum { FIRLS_PSI_HAAR = 1, FIRLS_PSI_DB4 = 2, FIRLS_PSI_TV = 4 };
+
+/* Context flags. FIRLS_REAL_X: the unknown x is real (A^T y = Re F^H R^T y);
+ * buffers are still complex64 and their imaginary parts are ignored on
+ * input and written as 0 on output. */
+enum { FIRLS_REAL_X = 1 };
+
+/* Sizes accepted for n: 16, 32, 48, 64, 80, 96, 128, 160, 192, 256, 320,
+ * 384, 512 (radix-2/3/5 FFT plans).  Query with firls_size_supported. */
+int firls_size_supported(int n);
+
+/* Create a context for `batch` independent slices of n_rows x n_cols
+ * (square: n_rows == n_cols).  `cuda_stream` is a cudaStream_t (NULL = the
+ * legacy default stream).  The context allocates its device workspace
+ * (about 14 complex64 + 6 float vectors per slice) on the current device.
+ * Returns FIRLS_E_SHAPE for unsupported sizes, FIRLS_E_NOMEM if the
+ * workspace does not fit. */
+firls_status firls_create(firls_ctx** out, int n_rows, int n_cols, int batch,
+                          unsigned flags, void* cuda_stream);
+
+/* Set the operator A and the regulariser (Alg. 2/3 inputs).
+ *   mask        device uint8 [batch][n][n], 0/1, unshifted FFT order (DC at
+ *               [0][0]); copied into the context.  mean(diag(A^H A)) of
+ *               each slice is its popcount / n^2 (Sec. 5.4).
+ *   psi_kind    FIRLS_PSI_* bitmask; a wavelet needs wavelet_levels >= 1
+ *               with n divisible by 2^levels and n / 2^(levels-1) >= 2.
+ *   group_idx   device int32: the Mallat-layout flat coefficient indices of
+ *               the members of each group, group after group (the rows of
+ *               G, Fig. 1; groups may overlap and may differ in size).
+ *               NULL = singleton groups (plain l1: every coefficient is its
+ *               own group, the IRLS weights of Sec. 3.1).
+ *   group_off   device int32 [n_groups+1] CSR offsets into group_idx, or
+ *               NULL for uniform groups of `group_size` members
+ *               (group_idx is then [n_groups][group_size]).
+ * The map is copied; the library builds the coefficient -> groups inverse
+ * map (CSR, ascending group ids per coefficient) used to sum the
+ * duplicated weights of Eq. Wog into diag(G^T W G) without atomics.
+ * Synchronises the stream (reads back the popcounts and the map check).
+ * Returns FIRLS_E_GROUPMAP if an index is outside [0, n^2) or the offsets
+ * are not non-decreasing. */
+firls_status firls_set_operator(firls_ctx* ctx, const uint8_t* mask,
+                                unsigned psi_kind, int wavelet_levels,
+                                const int32_t* group_idx, const int32_t* group_off,
+                                int n_groups, int group_size);
+
+typedef struct {
+  int outer_iters;  /* outer reweighting steps K (>= 1)                       */
+  int pcg_iters;    /* PCG steps J per outer step (>= 1)                      */
+  float pcg_tol;    /* stop PCG when ||r|| <= pcg_tol ||A^H b|| (0 = never)   */
+  float outer_tol;  /* stop when ||x^{k+1}-x^k|| <= outer_tol ||x^k|| (0=never)*/
+  float lambda;     /* wavelet lambda (lambda_W), >= 0                        */
+  float lambda_tv;  /* TV lambda, >= 0 (ignored without FIRLS_PSI_TV)         */
+  float eps;        /* smoothing eps of Eq. gw / Eq. wi; <= 0 selects 1e-10   */
+  const float* lambda_per_slice;    /* host [batch] or NULL (use lambda)      */
+  const float* lambda_tv_per_slice; /* host [batch] or NULL (use lambda_tv)   */
+} firls_params;
+
+typedef struct {
+  int outer_done;            /* outer steps run (max over slices)             */
+  long long pcg_steps;       /* PCG steps run, summed over slices             */
+  double max_rel_change;     /* max_s ||x^{K}-x^{K-1}|| / ||x^{K-1}||         */
+  double max_rel_residual;   /* max_s ||r|| / ||A^H b|| at the last PCG step  */
+  int n_breakdown;           /* slices stopped by a PCG breakdown             */
+} firls_stats;
+
+/* Run FIRLS on every slice (Alg. 2 / Alg. 3).
+ *   b      device complex64 [batch][n][n] k-space, entries off the mask are
+ *          ignored (multiplied by the mask).
+ *   x0     device complex64 [batch][n][n] warm start, or NULL for
+ *          x^1 = A^H b (Sec. 3.3).
+ *   x_out  device complex64 [batch][n][n]; receives x^{K+1}.
+ *   stats  host, may be NULL.  When non-NULL, or when a tolerance is set,
+ *          the call synchronises the stream before returning.
+ * Operators run in FP32; the PCG inner products, alpha, beta, rho, the
+ * residual norms and the relative change are accumulated in FP64.
+ * Returns FIRLS_E_BREAKDOWN if any slice broke down (its x_out holds its
+ * last iterate; the other slices are unaffected). */
+firls_status firls_solve(firls_ctx* ctx, const void* b, const firls_params* params,
+                         const void* x0, void* x_out, firls_stats* stats);
+
+/* Solve several contexts (slices of different sizes, e.g. 128^2 .. 320^2)
+ * as one CUDA-graph launch: each context's work is captured on a forked
+ * stream and joined back onto ctxs[0]'s stream.  Arrays have n_ctx
+ * entries; params apply to every context.  Same buffer rules as
+ * firls_solve.  stats (host, may be NULL) has n_ctx entries. */
+firls_status firls_solve_multi(firls_ctx* const* ctxs, int n_ctx,
+                               const void* const* b, const firls_params* params,
+                               const void* const* x0, void* const* x_out,
+                               firls_stats* stats);
+
+/* Message for the last error on this context (static storage owned by the
+ * context; valid until the next call on it). */
+const char* firls_last_error(const firls_ctx* ctx);
+
+/* Free the context and its device workspace (synchronises its stream). */
+void firls_destroy(firls_ctx* ctx);
+
+/* ---- operator-level entry points (for tests and roofline measurement) ----
+ * All act on device buffers of the context's batch and run on its stream. */
+
+/* q = A^H A d (unitary FFT, mask, inverse FFT; Sec. 5.4 A = RF). */
+firls_status firls_apply_AHA(firls_ctx* ctx, const void* d, void* q);
+
+/* c = Phi x (Mallat layout; wavelet of the context). */
+firls_status firls_apply_Phi(firls_ctx* ctx, const void* x, void* c);
+
+/* x = Phi^T c. */
+firls_status firls_apply_PhiT(firls_ctx* ctx, const void* c, void* x);
+
+/* Update the weights from x (Eq. gw + Eq. Wog, Eq. wi) and the
+ * preconditioner (Eq. pog / Eq. ptv); then q = S d and z = P^{-1} r.
+ * lambda/lambda_tv/eps are taken from params (per-slice arrays allowed). */
+firls_status firls_apply_S_P(firls_ctx* ctx, const firls_params* params,
+                             const void* x, const void* d, void* q,
+                             const void* r, void* z);
+
+/* Copy out the current per-coefficient wavelet weights diag(G^T W G)
+ * (device float [batch][n][n]) and TV weights (device float [batch][n][n]);
+ * either pointer may be NULL. */
+firls_status firls_get_weights(firls_ctx* ctx, float* w_wavelet, float* w_tv);
+
+/* Copy out the inverse group map (device int32: offsets [n*n+1], ids
+ * [total members]).  FIRLS_E_STATE if no group map is set. */
+firls_status firls_get_inverse_map(firls_ctx* ctx, int32_t* offsets, int32_t* ids);
+
+/* Per-slice mask popcounts M (device int32 [batch]). */
+firls_status firls_get_popcounts(firls_ctx* ctx, int32_t* counts);
+
+/* ---- per-kernel timing (instrumentation for roofline measurement) ----
+ * Kernel classes of one outer step. */
+enum {
+  FIRLS_K_ROW_FFT = 0,       /* d = z + beta d, row FFT                       */
+  FIRLS_K_COL_FFT_MASK = 1,  /* column FFT, mask, column IFFT                 */
+  FIRLS_K_WAVELET_FWD = 2,   /* Phi (all levels of one call)                  */
+  FIRLS_K_WAVELET_INV = 3,   /* Phi^T (all levels of one call)                */
+  FIRLS_K_ROW_IFFT = 4,      /* row IFFT + TV stencil + wavelet term + dot    */
+  FIRLS_K_ILU = 5,           /* x, r update and the two triangular sweeps     */
+  FIRLS_K_AXPY = 6,          /* x, r update                                   */
+  FIRLS_K_SCALARS = 7,       /* FP64 alpha / beta / rho / outer bookkeeping   */
+  FIRLS_K_WEIGHTS = 8,       /* weights, group sums, diag(Phi^T W Phi), P set-up */
+  FIRLS_K_OTHER = 9,         /* copies, relative change                       */
+  FIRLS_NKCLASS = 10
+};
+
+/* Enable (1) or disable (0) CUDA-event timing of every kernel launch of an
+ * outer step on the context's stream (the events are recorded into the
+ * captured outer-step graph).  Adds one event pair per launch group. */
+firls_status firls_set_timing(firls_ctx* ctx, int enable);
+
+/* Per-class totals for the last outer step executed: ms[FIRLS_NKCLASS]
+ * milliseconds and launches[FIRLS_NKCLASS] kernel launches.  Synchronises
+ * the stream.  FIRLS_E_STATE if timing is off or nothing ran. */
+firls_status firls_get_timing(firls_ctx* ctx, double* ms, int* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIRLS_H_ */

@@ -175,11 +175,17 @@ def wavelet_kind(psi):
 def group_matrix(groups, N):
     """G: N' x N binary matrix whose rows are rows of the identity (Fig. 1).
 
-    ``groups`` is int32 [n_groups][g] (uniform size) or None for singletons.
-    Returns (G, sizes).
+    ``groups`` is int32 [n_groups][g] (uniform size), a tuple
+    (offsets [n_groups+1], members) for groups of varying size (Sec. 3.1:
+    variant-size groups), or None for singletons.  Returns (G, sizes).
     """
     if groups is None:
         return sp.identity(N, format="csr"), np.ones(N, dtype=np.int64)
+    if isinstance(groups, tuple):
+        off, idx = (np.asarray(a) for a in groups)
+        M = len(idx)
+        G = sp.csr_matrix((np.ones(M), (np.arange(M), idx)), shape=(M, N))
+        return G, np.diff(off).astype(np.int64)
     groups = np.asarray(groups)
     s, g = groups.shape
     rows = np.arange(s * g)
@@ -470,12 +476,16 @@ def inverse_group_map(groups, N):
     """Coefficient -> groups map (CSR): offsets [N+1] and group ids, ascending.
 
     The integer structure the library derives from G at set-up; compared bit
-    for bit.
+    for bit.  ``groups`` as in ``group_matrix``.
     """
-    groups = np.asarray(groups)
-    s, g = groups.shape
-    coef = groups.reshape(-1)
-    gid = np.repeat(np.arange(s), g)
+    if isinstance(groups, tuple):
+        off, coef = (np.asarray(a) for a in groups)
+        gid = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    else:
+        groups = np.asarray(groups)
+        s, g = groups.shape
+        coef = groups.reshape(-1)
+        gid = np.repeat(np.arange(s), g)
     order = np.lexsort((gid, coef))
     counts = np.bincount(coef, minlength=N)
     off = np.zeros(N + 1, dtype=np.int32)

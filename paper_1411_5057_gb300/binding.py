@@ -1,0 +1,211 @@
+"""ctypes binding of the FIRLS C ABI (``include/firls.h``).
+
+Argument marshalling only: every step of the reconstruction runs in the CUDA
+library ``libfirls.so``.  PyTorch tensors provide device memory (their
+``data_ptr()`` is passed through) and the CUDA stream.  There is no CPU
+fallback: if the library is missing the import of a context raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfirls.so")
+
+FIRLS_OK = 0
+STATUS = {0: "FIRLS_OK", 1: "FIRLS_E_INVALID_ARG", 2: "FIRLS_E_SHAPE", 3: "FIRLS_E_GROUPMAP",
+          4: "FIRLS_E_CUDA", 5: "FIRLS_E_NOMEM", 6: "FIRLS_E_BREAKDOWN", 7: "FIRLS_E_STATE"}
+PSI_HAAR, PSI_DB4, PSI_TV = 1, 2, 4
+REAL_X = 1
+
+EXPORTED = ["firls_size_supported", "firls_create", "firls_set_operator", "firls_solve", "firls_solve_multi",
+            "firls_last_error", "firls_destroy", "firls_apply_AHA", "firls_apply_Phi", "firls_apply_PhiT",
+            "firls_apply_S_P", "firls_get_weights", "firls_get_inverse_map", "firls_get_popcounts",
+            "firls_set_timing", "firls_get_timing"]
+KERNEL_CLASSES = ["row_fft", "col_fft_mask", "wavelet_fwd", "wavelet_inv", "row_ifft_combine", "ilu", "axpy",
+                  "scalars", "weights", "other"]
+
+
+class FirlsError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int), ("pcg_iters", ctypes.c_int), ("pcg_tol", ctypes.c_float),
+                ("outer_tol", ctypes.c_float), ("lambda_", ctypes.c_float), ("lambda_tv", ctypes.c_float),
+                ("eps", ctypes.c_float), ("lambda_per_slice", ctypes.POINTER(ctypes.c_float)),
+                ("lambda_tv_per_slice", ctypes.POINTER(ctypes.c_float))]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("outer_done", ctypes.c_int), ("pcg_steps", ctypes.c_longlong), ("max_rel_change", ctypes.c_double),
+                ("max_rel_residual", ctypes.c_double), ("n_breakdown", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libfirls.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise FirlsError(4, f"{LIB_PATH} is missing; build it with paper_1411_5057_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, u32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint
+    L.firls_size_supported.argtypes = [i32]
+    L.firls_size_supported.restype = i32
+    L.firls_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, u32, vp]
+    L.firls_set_operator.argtypes = [vp, vp, u32, i32, vp, vp, i32, i32]
+    L.firls_solve.argtypes = [vp, vp, ctypes.POINTER(Params), vp, vp, ctypes.POINTER(Stats)]
+    L.firls_solve_multi.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(Params),
+                                    ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(Stats)]
+    L.firls_last_error.argtypes = [vp]
+    L.firls_last_error.restype = ctypes.c_char_p
+    L.firls_destroy.argtypes = [vp]
+    L.firls_destroy.restype = None
+    L.firls_apply_AHA.argtypes = [vp, vp, vp]
+    L.firls_apply_Phi.argtypes = [vp, vp, vp]
+    L.firls_apply_PhiT.argtypes = [vp, vp, vp]
+    L.firls_apply_S_P.argtypes = [vp, ctypes.POINTER(Params), vp, vp, vp, vp, vp]
+    L.firls_get_weights.argtypes = [vp, vp, vp]
+    L.firls_get_inverse_map.argtypes = [vp, vp, vp]
+    L.firls_get_popcounts.argtypes = [vp, vp]
+    L.firls_set_timing.argtypes = [vp, i32]
+    L.firls_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def size_supported(n: int) -> bool:
+    return bool(lib().firls_size_supported(int(n)))
+
+
+def make_params(outer, pcg, lam=0.0, lam_tv=0.0, pcg_tol=0.0, outer_tol=0.0, eps=0.0,
+                lam_per_slice=None, lam_tv_per_slice=None):
+    p = Params()
+    p.outer_iters, p.pcg_iters = int(outer), int(pcg)
+    p.pcg_tol, p.outer_tol = float(pcg_tol), float(outer_tol)
+    p.lambda_, p.lambda_tv, p.eps = float(lam), float(lam_tv), float(eps)
+    keep = []
+    if lam_per_slice is not None:
+        a = (ctypes.c_float * len(lam_per_slice))(*[float(v) for v in lam_per_slice])
+        keep.append(a)
+        p.lambda_per_slice = ctypes.cast(a, ctypes.POINTER(ctypes.c_float))
+    if lam_tv_per_slice is not None:
+        a = (ctypes.c_float * len(lam_tv_per_slice))(*[float(v) for v in lam_tv_per_slice])
+        keep.append(a)
+        p.lambda_tv_per_slice = ctypes.cast(a, ctypes.POINTER(ctypes.c_float))
+    p._keep = keep
+    return p
+
+
+class Context:
+    """A batch of ``batch`` same-size slices (n x n) on the current device."""
+
+    def __init__(self, n, batch=1, real=False, stream=None):
+        import torch
+        self.n, self.batch, self.real = int(n), int(batch), bool(real)
+        self._torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = lib().firls_create(ctypes.byref(h), self.n, self.n, self.batch, REAL_X if real else 0,
+                                ctypes.c_void_p(self.stream.cuda_stream))
+        if st != FIRLS_OK:
+            raise FirlsError(st, f"firls_create(n={n}, batch={batch})")
+        self.h = h
+
+    def _check(self, st, what):
+        if st != FIRLS_OK:
+            msg = lib().firls_last_error(self.h)
+            raise FirlsError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().firls_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_operator(self, mask, psi, levels=0, groups=None, group_off=None, group_size=0):
+        """mask: uint8 [batch, n, n] CUDA; groups: int32 CUDA ([G, g] or flat with group_off)."""
+        n_groups = 0
+        if groups is not None:
+            if group_off is not None:
+                n_groups = group_off.numel() - 1
+            else:
+                n_groups, group_size = groups.shape
+        self._check(lib().firls_set_operator(self.h, _ptr(mask), int(psi), int(levels), _ptr(groups),
+                                             _ptr(group_off), int(n_groups), int(group_size)), "set_operator")
+
+    def solve(self, b, params, x0=None, out=None, stats=False):
+        torch = self._torch
+        if out is None:
+            out = torch.empty((self.batch, self.n, self.n), dtype=torch.complex64, device=b.device)
+        s = Stats() if stats else None
+        st = lib().firls_solve(self.h, _ptr(b), ctypes.byref(params), _ptr(x0), _ptr(out),
+                               ctypes.byref(s) if s is not None else None)
+        self._check(st, "solve")
+        return (out, s.as_dict()) if stats else out
+
+    def apply_AHA(self, d, q):
+        self._check(lib().firls_apply_AHA(self.h, _ptr(d), _ptr(q)), "apply_AHA")
+
+    def apply_Phi(self, x, c):
+        self._check(lib().firls_apply_Phi(self.h, _ptr(x), _ptr(c)), "apply_Phi")
+
+    def apply_PhiT(self, c, x):
+        self._check(lib().firls_apply_PhiT(self.h, _ptr(c), _ptr(x)), "apply_PhiT")
+
+    def apply_S_P(self, params, x, d, q, r, z):
+        self._check(lib().firls_apply_S_P(self.h, ctypes.byref(params), _ptr(x), _ptr(d), _ptr(q), _ptr(r),
+                                          _ptr(z)), "apply_S_P")
+
+    def get_weights(self, w_wavelet=None, w_tv=None):
+        self._check(lib().firls_get_weights(self.h, _ptr(w_wavelet), _ptr(w_tv)), "get_weights")
+
+    def get_inverse_map(self, offsets, ids):
+        self._check(lib().firls_get_inverse_map(self.h, _ptr(offsets), _ptr(ids)), "get_inverse_map")
+
+    def set_timing(self, enable=True):
+        self._check(lib().firls_set_timing(self.h, 1 if enable else 0), "set_timing")
+
+    def get_timing(self):
+        """{class: (total ms, launches)} for the last outer step executed."""
+        k = len(KERNEL_CLASSES)
+        ms = (ctypes.c_double * k)()
+        ln = (ctypes.c_int * k)()
+        self._check(lib().firls_get_timing(self.h, ms, ln), "get_timing")
+        return {name: (ms[i], ln[i]) for i, name in enumerate(KERNEL_CLASSES)}
+
+    def get_popcounts(self, counts):
+        self._check(lib().firls_get_popcounts(self.h, _ptr(counts)), "get_popcounts")
+
+
+def solve_multi(ctxs, bs, params, outs, x0s=None, stats=False):
+    """One call over contexts of different sizes (forked streams)."""
+    k = len(ctxs)
+    H = (ctypes.c_void_p * k)(*[c.h for c in ctxs])
+    B = (ctypes.c_void_p * k)(*[b.data_ptr() for b in bs])
+    O = (ctypes.c_void_p * k)(*[o.data_ptr() for o in outs])
+    X = (ctypes.c_void_p * k)(*[x.data_ptr() for x in x0s]) if x0s is not None else None
+    S = (Stats * k)() if stats else None
+    st = lib().firls_solve_multi(H, k, B, ctypes.byref(params), X, O, S)
+    if st != FIRLS_OK:
+        raise FirlsError(st, "solve_multi: " + (lib().firls_last_error(ctxs[0].h) or b"").decode())
+    return [s.as_dict() for s in S] if stats else None

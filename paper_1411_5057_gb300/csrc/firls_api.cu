@@ -1,0 +1,758 @@
+// C ABI of the FIRLS library: context, operator set-up and the solve
+// orchestration (Alg. 2 FIRLS_OG / Alg. 3 FIRLS_TV).  One outer step (weights,
+// preconditioner, PCG initialisation and J PCG steps) is captured once as a
+// CUDA graph per (J, tolerances) and replayed K times.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "firls.h"
+#include "launch.h"
+
+using namespace firls;
+
+struct firls_ctx {
+  int n = 0, batch = 0;
+  unsigned flags = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  bool op_set = false;
+  unsigned psi = 0;
+  int levels = 0, kind = 0;
+  int n_groups = 0, gsize = 0, gtotal = 0;
+  bool groups = false;
+  // device workspace
+  uint8_t* mask = nullptr;
+  int* counts = nullptr;
+  float2* tw = nullptr;
+  float2 *atb = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *d = nullptr, *q = nullptr;
+  float2 *t = nullptr, *u = nullptr, *cw = nullptr, *xprev = nullptr, *tmpA = nullptr, *tmpB = nullptr;
+  float *ww = nullptr, *wtv = nullptr, *ia = nullptr, *pb = nullptr, *pc = nullptr, *wdiag = nullptr;
+  float* wg = nullptr;
+  int *gidx = nullptr, *goff = nullptr, *inv_off = nullptr, *inv_ids = nullptr;
+  int *gcounts = nullptr, *gcursor = nullptr, *gerr = nullptr;
+  float* sqtab = nullptr;
+  int* sqlen = nullptr;
+  SliceState* st = nullptr;
+  double* part = nullptr;
+  float *lam_d = nullptr, *lamtv_d = nullptr;
+  std::vector<void*> allocs;
+  std::string err;
+  // per-kernel timing marks of one outer step
+  bool timing = false;
+  struct Mark {
+    int cls, launches;
+    cudaEvent_t a, b;
+  };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> evpool;
+  size_t evnext = 0;
+  bool marks_valid = false;
+  // cached outer-step graph
+  cudaGraphExec_t exec = nullptr;
+  int g_pcg = -1;
+  float g_ptol = -1.f, g_otol = -1.f;
+  bool use_graph = true;
+};
+
+namespace {
+
+firls_status fail(firls_ctx* c, firls_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+firls_status cuda_check(firls_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return FIRLS_OK;
+  return fail(c, e == cudaErrorMemoryAllocation ? FIRLS_E_NOMEM : FIRLS_E_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T> firls_status dalloc(firls_ctx* c, T** p, size_t count) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, count * sizeof(T) + 16);
+  if (e != cudaSuccess) return cuda_check(c, e, "cudaMalloc");
+  c->allocs.push_back(v);
+  *p = static_cast<T*>(v);
+  return FIRLS_OK;
+}
+
+#define TRY(expr)                        \
+  do {                                   \
+    firls_status _s = (expr);            \
+    if (_s != FIRLS_OK) return _s;       \
+  } while (0)
+#define CU(expr) TRY(cuda_check(c, (expr), #expr))
+
+// Squared 1-D level-l basis functions of the periodic pyramid (low: scaling
+// cascade h*...*h, high: g after l-1 lowpass steps), folded modulo n.
+void basis_tables(int n, int levels, int kind, std::vector<float>& tab, std::vector<int>& len) {
+  std::vector<double> h, g;
+  if (kind == FIRLS_PSI_HAAR) {
+    const double r = 1.0 / std::sqrt(2.0);
+    h = {r, r};
+  } else {
+    const double s3 = std::sqrt(3.0), den = 4.0 * std::sqrt(2.0);
+    h = {(1 + s3) / den, (3 + s3) / den, (3 - s3) / den, (1 - s3) / den};
+  }
+  const int K = (int)h.size();
+  for (int t = 0; t < K; ++t) g.push_back(((t & 1) ? -1.0 : 1.0) * h[K - 1 - t]);
+  tab.assign((size_t)levels * 2 * n, 0.f);
+  len.assign((size_t)levels * 2, 0);
+  std::vector<double> low(h.begin(), h.end());
+  std::vector<double> high(g.begin(), g.end());
+  for (int l = 1; l <= levels; ++l) {
+    if (l > 1) {
+      const int sh = 1 << (l - 1);
+      const size_t L = low.size() + (size_t)sh * (K - 1);
+      std::vector<double> nl(L, 0.0), nh(L, 0.0);
+      for (int t = 0; t < K; ++t)
+        for (size_t i = 0; i < low.size(); ++i) {
+          nl[i + (size_t)sh * t] += h[t] * low[i];
+          nh[i + (size_t)sh * t] += g[t] * low[i];
+        }
+      low.swap(nl);
+      high.swap(nh);
+    }
+    for (int ty = 0; ty < 2; ++ty) {
+      const std::vector<double>& f = ty ? high : low;
+      std::vector<double> fold(n, 0.0);
+      for (size_t i = 0; i < f.size(); ++i) fold[i % n] += f[i];
+      const int ln = (int)std::min<size_t>(f.size(), (size_t)n);
+      for (int i = 0; i < n; ++i) tab[(size_t)((l - 1) * 2 + ty) * n + i] = (float)(fold[i] * fold[i]);
+      len[(l - 1) * 2 + ty] = ln;
+    }
+  }
+}
+
+WavArgs wav_args(firls_ctx* c, const SliceState* st) {
+  WavArgs a;
+  a.batch = c->batch;
+  a.n = c->n;
+  a.levels = c->levels;
+  a.kind = c->kind;
+  a.stream = c->stream;
+  a.st = st;
+  a.tmpA = c->tmpA;
+  a.tmpB = c->tmpB;
+  a.part = c->part;
+  return a;
+}
+
+FftArgs fft_args(firls_ctx* c) {
+  FftArgs a;
+  a.batch = c->batch;
+  a.stream = c->stream;
+  a.tw = c->tw;
+  a.st = c->st;
+  a.part = c->part;
+  a.real = (c->flags & FIRLS_REAL_X) ? 1 : 0;
+  return a;
+}
+
+bool has_tv(const firls_ctx* c) { return (c->psi & FIRLS_PSI_TV) != 0; }
+
+// ---- timing marks: an event pair around each launch group of a class ----
+cudaEvent_t next_event(firls_ctx* c) {
+  if (c->evnext == c->evpool.size()) {
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    c->evpool.push_back(e);
+  }
+  return c->evpool[c->evnext++];
+}
+
+struct TMark {
+  firls_ctx* c;
+  int cls, launches;
+  cudaEvent_t b = nullptr;
+  TMark(firls_ctx* c_, int cls_, int launches_) : c(c_), cls(cls_), launches(launches_) {
+    if (!c->timing) return;
+    b = next_event(c);
+    cudaEventRecord(b, c->stream);
+  }
+  ~TMark() {
+    if (!c->timing) return;
+    cudaEvent_t e = next_event(c);
+    cudaEventRecord(e, c->stream);
+    c->marks.push_back({cls, launches, b, e});
+  }
+};
+
+void marks_reset(firls_ctx* c) {
+  c->marks.clear();
+  c->evnext = 0;
+}
+
+// q = S d  (mode 0: d = z; 1: d = z + beta d; 2: d as given)
+void enqueue_S(firls_ctx* c, int mode, const float2* zin, float2* din, float2* q) {
+  FftArgs a = fft_args(c);
+  a.z = zin;
+  a.d = din;
+  a.t = c->t;
+  a.mode = mode;
+  { TMark m(c, FIRLS_K_ROW_FFT, 1); fft_row_fwd(c->n, a); }
+  a.mask = c->mask;
+  { TMark m(c, FIRLS_K_COL_FFT_MASK, 1); fft_col_mask(c->n, a); }
+  if (c->kind) {
+    WavArgs w = wav_args(c, c->st);
+    { TMark m(c, FIRLS_K_WAVELET_FWD, c->levels); wavelet_forward(w, din, c->cw, c->ww, WAV_MUL_W); }
+    { TMark m(c, FIRLS_K_WAVELET_INV, c->levels); wavelet_inverse(w, c->cw, c->u, nullptr, a.real); }
+  }
+  a.u = c->kind ? c->u : nullptr;
+  a.wtv = has_tv(c) ? c->wtv : nullptr;
+  a.q = q;
+  { TMark m(c, FIRLS_K_ROW_IFFT, 1); fft_row_inv(c->n, a); }
+}
+
+// Update W^k and P from x (Alg. 2/3, first two lines of the loop body).
+void enqueue_weights(firls_ctx* c, const float2* x) {
+  const int B = c->batch, n = c->n;
+  TMark mk(c, FIRLS_K_WEIGHTS, 0);
+  if (c->kind) {
+    WavArgs w = wav_args(c, c->st);
+    if (!c->groups) {
+      wavelet_forward(w, x, c->cw, c->ww, WAV_SINGLETON_W);
+    } else {
+      wavelet_forward(w, x, c->cw, nullptr, WAV_RAW);
+      group_norms(B, n, c->n_groups, c->stream, c->st, c->gidx, c->goff, c->gsize, c->cw, c->wg, 0.f);
+      group_gather(B, n, c->n_groups, c->stream, c->st, c->inv_off, c->inv_ids, c->wg, c->ww);
+    }
+  }
+  if (has_tv(c)) {
+    tv_weights(B, n, c->stream, c->st, x, c->wtv);
+    if (c->kind) wavelet_diag(B, n, c->levels, c->stream, c->st, c->ww, c->wdiag, c->sqtab, c->sqlen);
+    penta_setup(B, n, c->stream, c->st, c->wtv, c->kind ? c->wdiag : nullptr, c->ia, c->pb, c->pc);
+  }
+}
+
+// z = P^{-1} r after the residual update of `mode` (ILU_INIT / ILU_STEP).
+void enqueue_update_precond(firls_ctx* c, int step_mode, float pcg_tol, bool init) {
+  const int B = c->batch, n = c->n;
+  const int real = (c->flags & FIRLS_REAL_X) ? 1 : 0;
+  if (has_tv(c)) {
+    {
+      TMark m(c, FIRLS_K_ILU, 1);
+      ilu_step(B, n, c->stream, c->st, c->part, init ? ILU_INIT : ILU_STEP, c->x, c->d, c->r, c->q, c->atb,
+               c->u, c->z, c->ia, c->pb, c->pc);
+    }
+    TMark m(c, FIRLS_K_SCALARS, 1);
+    if (init)
+      pcg_rho_init(B, c->stream, c->st, c->part, 1, 1);
+    else
+      pcg_beta(B, c->stream, c->st, c->part, 1, 1, pcg_tol);
+  } else {
+    {
+      TMark m(c, FIRLS_K_AXPY, 1);
+      axpy_step(B, n, c->stream, c->st, c->part, init ? AXPY_INIT : AXPY_STEP, c->x, c->d, c->r, c->q, c->atb);
+    }
+    WavArgs w = wav_args(c, c->st);
+    { TMark m(c, FIRLS_K_WAVELET_FWD, c->levels); wavelet_forward(w, c->r, c->cw, c->ww, WAV_MUL_PINV); }
+    { TMark m(c, FIRLS_K_WAVELET_INV, c->levels); wavelet_inverse(w, c->cw, c->z, c->r, real); }
+    TMark m(c, FIRLS_K_SCALARS, 1);
+    if (init)
+      pcg_rho_init(B, c->stream, c->st, c->part, wavelet_inverse_ctas(n), axpy_ctas(n));
+    else
+      pcg_beta(B, c->stream, c->st, c->part, wavelet_inverse_ctas(n), axpy_ctas(n), pcg_tol);
+  }
+  (void)step_mode;
+}
+
+// One outer step of FIRLS: weights, P, PCG warm-started at x^k, relative change.
+void enqueue_outer(firls_ctx* c, int J, float pcg_tol, float outer_tol) {
+  const int B = c->batch, n = c->n;
+  marks_reset(c);
+  {
+    TMark m(c, FIRLS_K_OTHER, 1);
+    outer_begin(B, c->stream, c->st);
+    cudaMemcpyAsync(c->xprev, c->x, sizeof(float2) * (size_t)B * n * n, cudaMemcpyDeviceToDevice, c->stream);
+  }
+  enqueue_weights(c, c->x);
+  // r = A^H b - S x^k, z = P^{-1} r, rho = Re<r, z>
+  enqueue_S(c, 2, nullptr, c->x, c->q);
+  enqueue_update_precond(c, 0, pcg_tol, true);
+  for (int j = 1; j <= J; ++j) {
+    enqueue_S(c, j == 1 ? 0 : 1, c->z, c->d, c->q);
+    {
+      TMark m(c, FIRLS_K_SCALARS, 1);
+      pcg_alpha(B, c->stream, c->st, c->part, fft_row_ctas(n));
+    }
+    if (j < J) {
+      enqueue_update_precond(c, 1, pcg_tol, false);
+    } else {
+      TMark m(c, FIRLS_K_AXPY, 1);
+      axpy_step(B, n, c->stream, c->st, c->part, AXPY_LAST, c->x, c->d, c->r, c->q, c->atb);
+    }
+  }
+  TMark m(c, FIRLS_K_OTHER, 2);
+  relchange_parts(B, n, c->stream, c->st, c->x, c->xprev, c->part);
+  outer_end(B, c->stream, c->st, c->part, axpy_ctas(n), outer_tol);
+}
+
+firls_status check_params(firls_ctx* c, const firls_params* p) {
+  if (!p) return fail(c, FIRLS_E_INVALID_ARG, "params is null");
+  if (p->outer_iters < 1 || p->pcg_iters < 1) return fail(c, FIRLS_E_INVALID_ARG, "iteration counts must be >= 1");
+  if (!(p->pcg_tol >= 0.f) || !(p->outer_tol >= 0.f)) return fail(c, FIRLS_E_INVALID_ARG, "tolerances must be >= 0");
+  const int B = c->batch;
+  for (int s = 0; s < B; ++s) {
+    const float l = p->lambda_per_slice ? p->lambda_per_slice[s] : p->lambda;
+    const float lt = p->lambda_tv_per_slice ? p->lambda_tv_per_slice[s] : p->lambda_tv;
+    if (!(l >= 0.f) || !std::isfinite(l)) return fail(c, FIRLS_E_INVALID_ARG, "lambda must be finite and >= 0");
+    if (!(lt >= 0.f) || !std::isfinite(lt)) return fail(c, FIRLS_E_INVALID_ARG, "lambda_tv must be finite and >= 0");
+  }
+  return FIRLS_OK;
+}
+
+firls_status upload_params(firls_ctx* c, const firls_params* p) {
+  const int B = c->batch;
+  std::vector<float> l(B), lt(B);
+  for (int s = 0; s < B; ++s) {
+    l[s] = p->lambda_per_slice ? p->lambda_per_slice[s] : p->lambda;
+    lt[s] = has_tv(c) ? (p->lambda_tv_per_slice ? p->lambda_tv_per_slice[s] : p->lambda_tv) : 0.f;
+    if (!c->kind) l[s] = 0.f;
+  }
+  CU(cudaMemcpyAsync(c->lam_d, l.data(), sizeof(float) * B, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->lamtv_d, lt.data(), sizeof(float) * B, cudaMemcpyHostToDevice, c->stream));
+  // pageable copies: make sure the host vectors may go out of scope
+  CU(cudaStreamSynchronize(c->stream));
+  return FIRLS_OK;
+}
+
+float eps_of(const firls_params* p) { return p->eps > 0.f ? p->eps : 1e-10f; }
+
+// A^H b into atb (and x when x0 is null), ||A^H b||^2 partials, state init.
+firls_status enqueue_setup(firls_ctx* c, const void* b, const firls_params* p, const void* x0) {
+  const int B = c->batch, n = c->n;
+  TRY(upload_params(c, p));
+  FftArgs a = fft_args(c);
+  a.b = static_cast<const float2*>(b);
+  a.mask = c->mask;
+  a.t = c->t;
+  fft_row_ahb(n, a);
+  a.atb = c->atb;
+  a.x = x0 ? nullptr : c->x;
+  fft_col_inv(n, a);
+  if (x0) {
+    CU(cudaMemcpyAsync(c->x, x0, sizeof(float2) * (size_t)B * n * n, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  state_init(B, c->stream, c->st, c->part, fft_col_ctas(n), c->counts, n, c->lam_d, c->lamtv_d, eps_of(p));
+  return cuda_check(c, cudaGetLastError(), "setup launch");
+}
+
+firls_status run_outer_steps(firls_ctx* c, const firls_params* p) {
+  const bool graph = c->use_graph && c->stream != nullptr;
+  if (!graph) {
+    for (int k = 0; k < p->outer_iters; ++k) enqueue_outer(c, p->pcg_iters, p->pcg_tol, p->outer_tol);
+    c->marks_valid = c->timing;
+    return cuda_check(c, cudaGetLastError(), "outer step launch");
+  }
+  if (!c->exec || c->g_pcg != p->pcg_iters || c->g_ptol != p->pcg_tol || c->g_otol != p->outer_tol) {
+    if (c->exec) {
+      cudaGraphExecDestroy(c->exec);
+      c->exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_outer(c, p->pcg_iters, p->pcg_tol, p->outer_tol);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess) return cuda_check(c, e, "graph capture");
+    e = cudaGraphInstantiate(&c->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->exec = nullptr;
+      return cuda_check(c, e, "graph instantiate");
+    }
+    c->g_pcg = p->pcg_iters;
+    c->g_ptol = p->pcg_tol;
+    c->g_otol = p->outer_tol;
+  }
+  for (int k = 0; k < p->outer_iters; ++k) CU(cudaGraphLaunch(c->exec, c->stream));
+  c->marks_valid = c->timing;
+  return FIRLS_OK;
+}
+
+firls_status collect_stats(firls_ctx* c, firls_stats* stats, bool* breakdown) {
+  std::vector<SliceState> hs(c->batch);
+  CU(cudaMemcpyAsync(hs.data(), c->st, sizeof(SliceState) * c->batch, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  firls_stats s{};
+  for (const SliceState& v : hs) {
+    s.outer_done = v.outer_done > s.outer_done ? v.outer_done : s.outer_done;
+    s.pcg_steps += v.pcg_steps;
+    if (v.relchg > s.max_rel_change) s.max_rel_change = v.relchg;
+    const double rr = v.rhs2 > 0 ? std::sqrt(v.rr / v.rhs2) : 0.0;
+    if (rr > s.max_rel_residual) s.max_rel_residual = rr;
+    s.n_breakdown += v.breakdown ? 1 : 0;
+  }
+  if (stats) *stats = s;
+  *breakdown = s.n_breakdown > 0;
+  return FIRLS_OK;
+}
+
+void prepare_kernels(int n);
+
+}  // namespace
+
+// ======================================================================= ABI
+
+extern "C" int firls_size_supported(int n) { return fft_size_supported(n) ? 1 : 0; }
+
+extern "C" firls_status firls_create(firls_ctx** out, int n_rows, int n_cols, int batch, unsigned flags,
+                                     void* cuda_stream) {
+  if (!out) return FIRLS_E_INVALID_ARG;
+  *out = nullptr;
+  if (n_rows != n_cols || !fft_size_supported(n_rows)) return FIRLS_E_SHAPE;
+  if (batch < 1 || batch > 65535) return FIRLS_E_INVALID_ARG;
+  firls_ctx* c = new firls_ctx();
+  c->n = n_rows;
+  c->batch = batch;
+  c->flags = flags;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->use_graph = std::getenv("FIRLS_NO_GRAPH") == nullptr;
+  cudaGetDevice(&c->device);
+  const int n = c->n;
+  const size_t N = (size_t)n * n, BN = N * batch, BH = (size_t)batch * (n / 2) * (n / 2);
+  firls_status s = FIRLS_OK;
+  auto A = [&](auto** p, size_t cnt) {
+    if (s == FIRLS_OK) s = dalloc(c, p, cnt);
+  };
+  A(&c->mask, BN);
+  A(&c->counts, (size_t)batch);
+  A(&c->tw, (size_t)n);
+  for (float2** p : {&c->atb, &c->x, &c->r, &c->z, &c->d, &c->q, &c->t, &c->u, &c->cw, &c->xprev}) A(p, BN);
+  A(&c->tmpA, BH);
+  A(&c->tmpB, BH);
+  for (float** p : {&c->ww, &c->wtv, &c->ia, &c->pb, &c->pc, &c->wdiag}) A(p, BN);
+  A(&c->st, (size_t)batch);
+  A(&c->part, (size_t)batch * NSLOT * MAXPART);
+  A(&c->lam_d, (size_t)batch);
+  A(&c->lamtv_d, (size_t)batch);
+  if (s != FIRLS_OK) {
+    firls_destroy(c);
+    return s;
+  }
+  std::vector<float2> tw(n);
+  for (int j = 0; j < n; ++j) {
+    const double ang = -2.0 * 3.14159265358979323846 * (double)j / (double)n;
+    tw[j] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  }
+  cudaMemcpy(c->tw, tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
+  // d is read (times 0) nowhere, but keep the workspace finite
+  cudaMemset(c->d, 0, sizeof(float2) * BN);
+  cudaMemset(c->part, 0, sizeof(double) * batch * NSLOT * MAXPART);
+  prepare_kernels(n);
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    firls_destroy(c);
+    return FIRLS_E_CUDA;
+  }
+  *out = c;
+  return FIRLS_OK;
+}
+
+extern "C" firls_status firls_set_operator(firls_ctx* c, const uint8_t* mask, unsigned psi_kind,
+                                           int wavelet_levels, const int32_t* group_idx,
+                                           const int32_t* group_off, int n_groups, int group_size) {
+  if (!c) return FIRLS_E_INVALID_ARG;
+  if (!mask) return fail(c, FIRLS_E_INVALID_ARG, "mask is null");
+  const int n = c->n;
+  const bool haar = psi_kind & FIRLS_PSI_HAAR, db4 = psi_kind & FIRLS_PSI_DB4;
+  if ((psi_kind & ~7u) || (haar && db4) || psi_kind == 0)
+    return fail(c, FIRLS_E_INVALID_ARG, "psi_kind must be HAAR or DB4, optionally with TV, or TV alone");
+  const int kind = haar ? 1 : (db4 ? 2 : 0);
+  if (kind) {
+    if (wavelet_levels < 1 || (n % (1 << wavelet_levels)) || (n >> (wavelet_levels - 1)) < 2)
+      return fail(c, FIRLS_E_SHAPE, "n must be divisible by 2^levels, levels >= 1");
+  }
+  if (group_idx && !kind) return fail(c, FIRLS_E_INVALID_ARG, "groups need a wavelet");
+  if (group_idx && (n_groups < 1 || (!group_off && group_size < 1)))
+    return fail(c, FIRLS_E_INVALID_ARG, "bad group counts");
+  const int B = c->batch;
+  const size_t N = (size_t)n * n;
+  CU(cudaMemcpyAsync(c->mask, mask, N * B, cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaMemsetAsync(c->counts, 0, sizeof(int) * B, c->stream));
+  mask_popcount(B, n, c->stream, c->mask, c->counts);
+  c->groups = false;
+  if (group_idx) {
+    int total = 0;
+    if (group_off) {
+      CU(cudaMemcpyAsync(&total, group_off + n_groups, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+      CU(cudaStreamSynchronize(c->stream));
+    } else {
+      total = n_groups * group_size;
+    }
+    if (total < 0) return fail(c, FIRLS_E_GROUPMAP, "negative member count");
+    // (re)allocate the map buffers
+    auto rel = [&](void* p) {
+      if (!p) return;
+      cudaFree(p);
+      for (auto& a : c->allocs)
+        if (a == p) a = nullptr;
+    };
+    rel(c->gidx);
+    rel(c->goff);
+    rel(c->inv_off);
+    rel(c->inv_ids);
+    rel(c->gcounts);
+    rel(c->gcursor);
+    rel(c->gerr);
+    rel(c->wg);
+    c->gidx = c->goff = nullptr;
+    TRY(dalloc(c, &c->gidx, (size_t)total));
+    if (group_off) TRY(dalloc(c, &c->goff, (size_t)n_groups + 1));
+    TRY(dalloc(c, &c->inv_off, N + 1));
+    TRY(dalloc(c, &c->inv_ids, (size_t)total));
+    TRY(dalloc(c, &c->gcounts, N));
+    TRY(dalloc(c, &c->gcursor, N));
+    TRY(dalloc(c, &c->gerr, 1));
+    TRY(dalloc(c, &c->wg, (size_t)n_groups * B));
+    CU(cudaMemcpyAsync(c->gidx, group_idx, sizeof(int) * total, cudaMemcpyDeviceToDevice, c->stream));
+    if (group_off)
+      CU(cudaMemcpyAsync(c->goff, group_off, sizeof(int) * (n_groups + 1), cudaMemcpyDeviceToDevice, c->stream));
+    CU(cudaMemsetAsync(c->gcounts, 0, sizeof(int) * N, c->stream));
+    CU(cudaMemsetAsync(c->gcursor, 0, sizeof(int) * N, c->stream));
+    CU(cudaMemsetAsync(c->gerr, 0, sizeof(int), c->stream));
+    group_inverse_build(n, n_groups, group_size, c->stream, c->gidx, c->goff, c->gcounts, c->inv_off,
+                        c->inv_ids, c->gcursor, c->gerr);
+    int herr = 0;
+    CU(cudaMemcpyAsync(&herr, c->gerr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (herr) return fail(c, FIRLS_E_GROUPMAP, "group index outside [0, n*n) or decreasing offsets");
+    c->groups = true;
+    c->n_groups = n_groups;
+    c->gsize = group_size;
+    c->gtotal = total;
+  }
+  if (kind && (psi_kind & FIRLS_PSI_TV)) {
+    std::vector<float> tab;
+    std::vector<int> len;
+    basis_tables(n, wavelet_levels, kind == 1 ? FIRLS_PSI_HAAR : FIRLS_PSI_DB4, tab, len);
+    if (c->sqtab) {
+      cudaFree(c->sqtab);
+      cudaFree(c->sqlen);
+      for (auto& a : c->allocs)
+        if (a == c->sqtab || a == c->sqlen) a = nullptr;
+    }
+    TRY(dalloc(c, &c->sqtab, tab.size()));
+    TRY(dalloc(c, &c->sqlen, len.size()));
+    CU(cudaMemcpy(c->sqtab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(c->sqlen, len.data(), sizeof(int) * len.size(), cudaMemcpyHostToDevice));
+  }
+  c->psi = psi_kind;
+  c->kind = kind;
+  c->levels = kind ? wavelet_levels : 0;
+  if (c->exec) {
+    cudaGraphExecDestroy(c->exec);
+    c->exec = nullptr;
+  }
+  CU(cudaStreamSynchronize(c->stream));
+  CU(cudaGetLastError());
+  c->op_set = true;
+  return FIRLS_OK;
+}
+
+extern "C" firls_status firls_solve(firls_ctx* c, const void* b, const firls_params* p, const void* x0,
+                                    void* x_out, firls_stats* stats) {
+  if (!c) return FIRLS_E_INVALID_ARG;
+  if (!c->op_set) return fail(c, FIRLS_E_STATE, "firls_set_operator has not been called");
+  if (!b || !x_out) return fail(c, FIRLS_E_INVALID_ARG, "b and x_out must be non-null");
+  TRY(check_params(c, p));
+  TRY(enqueue_setup(c, b, p, x0));
+  TRY(run_outer_steps(c, p));
+  const size_t bytes = sizeof(float2) * (size_t)c->batch * c->n * c->n;
+  CU(cudaMemcpyAsync(x_out, c->x, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaGetLastError());
+  if (stats || p->pcg_tol > 0.f || p->outer_tol > 0.f) {
+    bool bd = false;
+    TRY(collect_stats(c, stats, &bd));
+    if (bd) return fail(c, FIRLS_E_BREAKDOWN, "PCG breakdown in at least one slice");
+  }
+  return FIRLS_OK;
+}
+
+extern "C" firls_status firls_solve_multi(firls_ctx* const* ctxs, int n_ctx, const void* const* b,
+                                          const firls_params* p, const void* const* x0, void* const* x_out,
+                                          firls_stats* stats) {
+  if (!ctxs || n_ctx < 1 || !b || !x_out || !p) return FIRLS_E_INVALID_ARG;
+  // Per context: the setup (uploads lambdas synchronously), then all outer
+  // steps of all contexts are enqueued on their own streams; the caller's
+  // view is ctxs[0]'s stream, which waits on the others at the end.
+  for (int i = 0; i < n_ctx; ++i) {
+    firls_ctx* c = ctxs[i];
+    if (!c || !c->op_set) return FIRLS_E_STATE;
+    TRY(check_params(c, p));
+  }
+  std::vector<cudaEvent_t> ev(n_ctx, nullptr);
+  cudaEvent_t start = nullptr;
+  cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
+  cudaEventRecord(start, ctxs[0]->stream);
+  for (int i = 0; i < n_ctx; ++i) {
+    firls_ctx* c = ctxs[i];
+    if (i > 0) cudaStreamWaitEvent(c->stream, start, 0);
+    TRY(enqueue_setup(c, b[i], p, x0 ? x0[i] : nullptr));
+  }
+  // interleave the outer steps so the independent contexts overlap
+  for (int i = 0; i < n_ctx; ++i) {
+    firls_ctx* c = ctxs[i];
+    TRY(run_outer_steps(c, p));
+    const size_t bytes = sizeof(float2) * (size_t)c->batch * c->n * c->n;
+    CU(cudaMemcpyAsync(x_out[i], c->x, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    cudaEventRecord(ev[i], c->stream);
+  }
+  for (int i = 1; i < n_ctx; ++i) cudaStreamWaitEvent(ctxs[0]->stream, ev[i], 0);
+  firls_status ret = FIRLS_OK;
+  if (stats || p->pcg_tol > 0.f || p->outer_tol > 0.f) {
+    for (int i = 0; i < n_ctx; ++i) {
+      bool bd = false;
+      firls_status s = collect_stats(ctxs[i], stats ? &stats[i] : nullptr, &bd);
+      if (s != FIRLS_OK) ret = s;
+      if (bd && ret == FIRLS_OK) ret = FIRLS_E_BREAKDOWN;
+    }
+  }
+  for (auto e : ev)
+    if (e) cudaEventDestroy(e);
+  cudaEventDestroy(start);
+  return ret;
+}
+
+extern "C" const char* firls_last_error(const firls_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+extern "C" firls_status firls_set_timing(firls_ctx* c, int enable) {
+  if (!c) return FIRLS_E_INVALID_ARG;
+  const bool on = enable != 0;
+  if (on != c->timing && c->exec) {  // the captured graph changes shape
+    cudaGraphExecDestroy(c->exec);
+    c->exec = nullptr;
+  }
+  c->timing = on;
+  c->marks_valid = false;
+  return FIRLS_OK;
+}
+
+extern "C" firls_status firls_get_timing(firls_ctx* c, double* ms, int* launches) {
+  if (!c || !ms || !launches) return FIRLS_E_INVALID_ARG;
+  if (!c->timing || !c->marks_valid) return fail(c, FIRLS_E_STATE, "timing is off or no outer step ran");
+  CU(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < FIRLS_NKCLASS; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  for (const auto& m : c->marks) {
+    float t = 0.f;
+    CU(cudaEventElapsedTime(&t, m.a, m.b));
+    ms[m.cls] += t;
+    launches[m.cls] += m.launches;
+  }
+  return FIRLS_OK;
+}
+
+extern "C" void firls_destroy(firls_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+  for (void* p : c->allocs)
+    if (p) cudaFree(p);
+  delete c;
+}
+
+// ------------------------------------------------ operator-level entry points
+
+extern "C" firls_status firls_apply_AHA(firls_ctx* c, const void* d, void* q) {
+  if (!c || !d || !q) return FIRLS_E_INVALID_ARG;
+  if (!c->op_set) return fail(c, FIRLS_E_STATE, "operator not set");
+  // run with lambdas 0 and no regulariser terms: state must say "running"
+  std::vector<float> zeros(c->batch, 0.f);
+  firls_params p{};
+  p.outer_iters = p.pcg_iters = 1;
+  p.lambda_per_slice = zeros.data();
+  p.lambda_tv_per_slice = zeros.data();
+  TRY(upload_params(c, &p));
+  state_init(c->batch, c->stream, c->st, c->part, 0, c->counts, c->n, c->lam_d, c->lamtv_d, 1e-10f);
+  FftArgs a = fft_args(c);
+  const size_t bytes = sizeof(float2) * (size_t)c->batch * c->n * c->n;
+  CU(cudaMemcpyAsync(c->d, d, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  a.d = c->d;
+  a.t = c->t;
+  a.mode = 2;
+  fft_row_fwd(c->n, a);
+  a.mask = c->mask;
+  fft_col_mask(c->n, a);
+  a.q = static_cast<float2*>(q);
+  fft_row_inv(c->n, a);
+  return cuda_check(c, cudaGetLastError(), "apply_AHA");
+}
+
+extern "C" firls_status firls_apply_Phi(firls_ctx* c, const void* x, void* cc) {
+  if (!c || !x || !cc) return FIRLS_E_INVALID_ARG;
+  if (!c->op_set || !c->kind) return fail(c, FIRLS_E_STATE, "no wavelet set");
+  WavArgs w = wav_args(c, nullptr);
+  wavelet_forward(w, static_cast<const float2*>(x), static_cast<float2*>(cc), nullptr, WAV_RAW);
+  return cuda_check(c, cudaGetLastError(), "apply_Phi");
+}
+
+extern "C" firls_status firls_apply_PhiT(firls_ctx* c, const void* cc, void* x) {
+  if (!c || !x || !cc) return FIRLS_E_INVALID_ARG;
+  if (!c->op_set || !c->kind) return fail(c, FIRLS_E_STATE, "no wavelet set");
+  WavArgs w = wav_args(c, nullptr);
+  wavelet_inverse(w, static_cast<const float2*>(cc), static_cast<float2*>(x), nullptr, 0);
+  return cuda_check(c, cudaGetLastError(), "apply_PhiT");
+}
+
+extern "C" firls_status firls_apply_S_P(firls_ctx* c, const firls_params* p, const void* x, const void* d,
+                                        void* q, const void* r, void* z) {
+  if (!c || !p || !x || !d || !q || !r || !z) return FIRLS_E_INVALID_ARG;
+  if (!c->op_set) return fail(c, FIRLS_E_STATE, "operator not set");
+  TRY(check_params(c, p));
+  TRY(upload_params(c, p));
+  const int B = c->batch, n = c->n;
+  const size_t bytes = sizeof(float2) * (size_t)B * n * n;
+  state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, eps_of(p));
+  CU(cudaMemcpyAsync(c->x, x, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  enqueue_weights(c, c->x);
+  // q = S d
+  CU(cudaMemcpyAsync(c->d, d, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  enqueue_S(c, 2, nullptr, c->d, static_cast<float2*>(q));
+  // z = P^{-1} r: feed r as "A^H b" with q = 0 through the INIT path
+  CU(cudaMemcpyAsync(c->atb, r, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaMemsetAsync(c->q, 0, bytes, c->stream));
+  enqueue_update_precond(c, 0, 0.f, true);
+  CU(cudaMemcpyAsync(z, c->z, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  return cuda_check(c, cudaGetLastError(), "apply_S_P");
+}
+
+extern "C" firls_status firls_get_weights(firls_ctx* c, float* w_wavelet, float* w_tv) {
+  if (!c) return FIRLS_E_INVALID_ARG;
+  const size_t bytes = sizeof(float) * (size_t)c->batch * c->n * c->n;
+  if (w_wavelet) CU(cudaMemcpyAsync(w_wavelet, c->ww, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  if (w_tv) CU(cudaMemcpyAsync(w_tv, c->wtv, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  return FIRLS_OK;
+}
+
+extern "C" firls_status firls_get_inverse_map(firls_ctx* c, int32_t* offsets, int32_t* ids) {
+  if (!c || !offsets || !ids) return FIRLS_E_INVALID_ARG;
+  if (!c->groups) return fail(c, FIRLS_E_STATE, "no group map set");
+  const size_t N = (size_t)c->n * c->n;
+  CU(cudaMemcpyAsync(offsets, c->inv_off, sizeof(int) * (N + 1), cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaMemcpyAsync(ids, c->inv_ids, sizeof(int) * c->gtotal, cudaMemcpyDeviceToDevice, c->stream));
+  return FIRLS_OK;
+}
+
+extern "C" firls_status firls_get_popcounts(firls_ctx* c, int32_t* counts) {
+  if (!c || !counts) return FIRLS_E_INVALID_ARG;
+  CU(cudaMemcpyAsync(counts, c->counts, sizeof(int) * c->batch, cudaMemcpyDeviceToDevice, c->stream));
+  return FIRLS_OK;
+}
+
+namespace {
+// Sets the dynamic shared-memory limits of every kernel for this size
+// outside any stream capture.
+void prepare_kernels(int n) {
+  fft_prepare(n);
+  wav_prepare();
+}
+}  // namespace

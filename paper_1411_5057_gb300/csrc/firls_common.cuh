@@ -1,0 +1,63 @@
+// Shared device-side definitions of the FIRLS CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define FI __device__ __forceinline__
+
+namespace firls {
+
+// Per-slice PCG / outer-loop state, FP64 scalars (the only FP64 steps:
+// inner products, alpha, beta, rho, residual norms, relative change).
+struct SliceState {
+  double rho;        // Re<r, z> of the current PCG step
+  double alpha;      // rho / Re<d, S d>
+  double beta;       // rho_new / rho
+  double rhs2;       // ||A^H b||^2
+  double rr;         // ||r||^2 after the last update
+  double relchg;     // ||x^{k+1} - x^k|| / ||x^k|| of the last outer step
+  int active;        // PCG running in this outer step
+  int done;          // outer loop stopped (outer_tol reached)
+  int breakdown;     // PCG broke down at least once
+  int pcg_steps;     // PCG steps taken (all outer steps)
+  int outer_done;    // outer steps taken
+  int pad_;
+  float lam;         // wavelet lambda
+  float lam_tv;      // TV lambda
+  float abar;        // mean(diag(A^H A)) = popcount / N
+  float eps;         // smoothing eps
+};
+
+// Partial-sum slots (double part[B][NSLOT][MAXPART]).
+enum { SLOT_DQ = 0, SLOT_RZ = 1, SLOT_RR = 2, SLOT_RHS = 3, SLOT_DX = 4, SLOT_XX = 5, NSLOT = 6 };
+constexpr int MAXPART = 128;
+
+FI float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+FI float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+FI float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+FI float2 cfma(float s, float2 a, float2 b) { return make_float2(fmaf(s, a.x, b.x), fmaf(s, a.y, b.y)); }
+FI float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+FI float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+FI float rdot2(float2 a, float2 b) { return fmaf(a.x, b.x, a.y * b.y); }
+
+FI bool slice_running(const SliceState* st, int s) { return st[s].active && !st[s].done; }
+
+// Block-wide FP64 sum; result valid in thread 0.  `red` holds >= 32 doubles.
+FI double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < nw; ++i) s += red[i];
+  return s;
+}
+
+}  // namespace firls

@@ -1,0 +1,386 @@
+// FFT-based kernels of A^H A = F^H R^T R F (Sec. 5.4: A = RF) and A^H b.
+//
+// A 2-D unitary FFT is a row pass and a column pass.  A^H A d runs as
+//   row FFT of d  ->  column FFT, mask, column IFFT (one kernel)  ->
+//   row IFFT fused with the rest of S d (TV stencil, wavelet term) and the
+//   partial inner product Re<d, S d>.
+// The unnormalised transforms are scaled once: 1/N for F^H R F, 1/n for
+// F^H R b.  Rows: T threads of one warp per row (coalesced loads of
+// t + T*s).  Columns: tiles of 16 columns x n rows staged in shared memory
+// with 128-byte row segments.
+#include "fft.cuh"
+#include "launch.h"
+
+namespace firls {
+
+constexpr int COLS = 16;  // columns per column-pass CTA
+
+template <int N> __host__ __device__ constexpr int rows_per_cta() {
+  int r = 256 / FftCfg<N>::T;
+  if (r > N) r = N;
+  while (N % r) --r;
+  return r;
+}
+
+template <int N> constexpr int row_smem_bytes(bool tv) {
+  constexpr int R = rows_per_cta<N>();
+  int b = N * 8 + R * 2 * fft_line_words<N>() * 4;
+  if (tv) b += (R + 2) * N * 8 + (R + 1) * N * 4;
+  return b;
+}
+
+template <int N> constexpr int col_smem_bytes() {
+  return N * 8 + 2 * N * (COLS + 1) * 4 + N * COLS;
+}
+
+template <int N> FI void load_twiddles(float2* tw, const float2* __restrict__ twg) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+}
+
+// d = z (mode 0) | d = z + beta d (mode 1) | use d as is (mode 2); t = rowFFT(d)
+template <int N>
+__global__ void __launch_bounds__(256) k_row_fwd(const float2* __restrict__ z, float2* __restrict__ d,
+                                                 float2* __restrict__ t_out,
+                                                 const SliceState* __restrict__ st,
+                                                 const float2* __restrict__ twg, int mode) {
+  using C = FftCfg<N>;
+  constexpr int R = rows_per_cta<N>(), E = C::E, T = C::T, LW = fft_line_words<N>();
+  const int s = blockIdx.y;
+  if (!slice_running(st, s)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* tw = reinterpret_cast<float2*>(smem);
+  float* lines = reinterpret_cast<float*>(smem + N * 8);
+  load_twiddles<N>(tw, twg);
+  const int lr = threadIdx.x / T, t = threadIdx.x % T;
+  const int row = blockIdx.x * R + lr;
+  const size_t base = (size_t)s * N * N + (size_t)row * N;
+  const double beta = st[s].beta;
+  float2 v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const size_t i = base + t + T * e;
+    float2 dv;
+    if (mode == 0) {
+      dv = z[i];
+      d[i] = dv;
+    } else if (mode == 1) {
+      dv = cfma((float)beta, d[i], z[i]);
+      d[i] = dv;
+    } else {
+      dv = d[i];
+    }
+    v[e] = dv;
+  }
+  __syncthreads();
+  fft_line<N, -1>(v, lines + lr * 2 * LW, lines + lr * 2 * LW + LW, tw, t);
+#pragma unroll
+  for (int e = 0; e < E; ++e) t_out[base + t + T * e] = v[e];
+}
+
+// t = rowIFFT(mask * b)
+template <int N>
+__global__ void __launch_bounds__(256) k_row_ahb(const float2* __restrict__ b, const uint8_t* __restrict__ mask,
+                                                 float2* __restrict__ t_out,
+                                                 const float2* __restrict__ twg) {
+  using C = FftCfg<N>;
+  constexpr int R = rows_per_cta<N>(), E = C::E, T = C::T, LW = fft_line_words<N>();
+  const int s = blockIdx.y;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* tw = reinterpret_cast<float2*>(smem);
+  float* lines = reinterpret_cast<float*>(smem + N * 8);
+  load_twiddles<N>(tw, twg);
+  const int lr = threadIdx.x / T, t = threadIdx.x % T;
+  const int row = blockIdx.x * R + lr;
+  const size_t base = (size_t)s * N * N + (size_t)row * N;
+  float2 v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const size_t i = base + t + T * e;
+    v[e] = mask[i] ? b[i] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_line<N, +1>(v, lines + lr * 2 * LW, lines + lr * 2 * LW + LW, tw, t);
+#pragma unroll
+  for (int e = 0; e < E; ++e) t_out[base + t + T * e] = v[e];
+}
+
+// Load a 16-column tile of t into shared memory (SoA, row stride COLS+1).
+template <int N>
+FI void load_col_tile(const float2* __restrict__ src, float* tre, float* tim, size_t sbase, int c0) {
+  for (int idx = threadIdx.x; idx < N * COLS; idx += blockDim.x) {
+    const int r = idx / COLS, c = idx % COLS;
+    const float2 g = src[sbase + (size_t)r * N + c0 + c];
+    tre[r * (COLS + 1) + c] = g.x;
+    tim[r * (COLS + 1) + c] = g.y;
+  }
+}
+
+// In place on t: t = colIFFT(mask * colFFT(t)) for a 16-column tile.
+template <int N>
+__global__ void __launch_bounds__(512) k_col_mask(float2* __restrict__ tbuf, const uint8_t* __restrict__ mask,
+                                                  const SliceState* __restrict__ st,
+                                                  const float2* __restrict__ twg) {
+  using C = FftCfg<N>;
+  constexpr int E = C::E, T = C::T, LW = fft_line_words<N>();
+  const int s = blockIdx.y;
+  if (st != nullptr && !slice_running(st, s)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* tw = reinterpret_cast<float2*>(smem);
+  float* tre = reinterpret_cast<float*>(smem + N * 8);
+  float* tim = tre + N * (COLS + 1);
+  uint8_t* msk = reinterpret_cast<uint8_t*>(tim + N * (COLS + 1));
+  const int c0 = blockIdx.x * COLS;
+  const size_t sbase = (size_t)s * N * N;
+  load_twiddles<N>(tw, twg);
+  load_col_tile<N>(tbuf, tre, tim, sbase, c0);
+  for (int idx = threadIdx.x; idx < N * COLS; idx += blockDim.x) {
+    const int r = idx / COLS, c = idx % COLS;
+    msk[idx] = mask[sbase + (size_t)r * N + c0 + c];
+  }
+  __syncthreads();
+  const int c = threadIdx.x / T, t = threadIdx.x % T;
+  float2 v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int r = t + T * e;
+    v[e] = make_float2(tre[r * (COLS + 1) + c], tim[r * (COLS + 1) + c]);
+  }
+  __syncthreads();
+  float* bre = tre + c * LW;
+  float* bim = tim + c * LW;
+  fft_line<N, -1>(v, bre, bim, tw, t);
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+    if (!msk[(t + T * e) * COLS + c]) v[e] = make_float2(0.f, 0.f);
+  fft_line<N, +1>(v, bre, bim, tw, t);
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int r = t + T * e;
+    tre[r * (COLS + 1) + c] = v[e].x;
+    tim[r * (COLS + 1) + c] = v[e].y;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < N * COLS; idx += blockDim.x) {
+    const int r = idx / COLS, cc = idx % COLS;
+    tbuf[sbase + (size_t)r * N + c0 + cc] = make_float2(tre[r * (COLS + 1) + cc], tim[r * (COLS + 1) + cc]);
+  }
+}
+
+// atb = (1/n) colIFFT(t)  [real: imaginary part dropped]; x = atb if x != null;
+// partial ||atb||^2.
+template <int N>
+__global__ void __launch_bounds__(512) k_col_inv(const float2* __restrict__ tbuf, float2* __restrict__ atb,
+                                                 float2* __restrict__ x, int real,
+                                                 double* __restrict__ part,
+                                                 const float2* __restrict__ twg) {
+  using C = FftCfg<N>;
+  constexpr int E = C::E, T = C::T, LW = fft_line_words<N>();
+  const int s = blockIdx.y;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* tw = reinterpret_cast<float2*>(smem);
+  float* tre = reinterpret_cast<float*>(smem + N * 8);
+  float* tim = tre + N * (COLS + 1);
+  __shared__ double red[32];
+  const int c0 = blockIdx.x * COLS;
+  const size_t sbase = (size_t)s * N * N;
+  load_twiddles<N>(tw, twg);
+  load_col_tile<N>(tbuf, tre, tim, sbase, c0);
+  __syncthreads();
+  const int c = threadIdx.x / T, t = threadIdx.x % T;
+  float2 v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int r = t + T * e;
+    v[e] = make_float2(tre[r * (COLS + 1) + c], tim[r * (COLS + 1) + c]);
+  }
+  __syncthreads();
+  fft_line<N, +1>(v, tre + c * LW, tim + c * LW, tw, t);
+  const float sc = 1.0f / (float)N;
+  float acc = 0.f;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    v[e] = make_float2(v[e].x * sc, real ? 0.f : v[e].y * sc);
+    acc += cabs2(v[e]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int r = t + T * e;
+    tre[r * (COLS + 1) + c] = v[e].x;
+    tim[r * (COLS + 1) + c] = v[e].y;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < N * COLS; idx += blockDim.x) {
+    const int r = idx / COLS, cc = idx % COLS;
+    const float2 o = make_float2(tre[r * (COLS + 1) + cc], tim[r * (COLS + 1) + cc]);
+    const size_t gi = sbase + (size_t)r * N + c0 + cc;
+    atb[gi] = o;
+    if (x) x[gi] = o;
+  }
+  const double tot = block_sum((double)acc, red);
+  if (threadIdx.x == 0) part[((size_t)s * NSLOT + SLOT_RHS) * MAXPART + blockIdx.x] = tot;
+}
+
+// q = (1/N) rowIFFT(t) [Re if real] + lam_tv (D1^T W D1 + D2^T W D2) d + lam u;
+// partial Re<d, q>.
+template <int N>
+__global__ void __launch_bounds__(256) k_row_inv(const float2* __restrict__ tbuf, const float2* __restrict__ d,
+                                                 const float2* __restrict__ u, const float* __restrict__ wtv,
+                                                 float2* __restrict__ q, const SliceState* __restrict__ st,
+                                                 double* __restrict__ part, int real,
+                                                 const float2* __restrict__ twg) {
+  using C = FftCfg<N>;
+  constexpr int R = rows_per_cta<N>(), E = C::E, T = C::T, LW = fft_line_words<N>();
+  const int s = blockIdx.y;
+  if (!slice_running(st, s)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[32];
+  float2* tw = reinterpret_cast<float2*>(smem);
+  float* lines = reinterpret_cast<float*>(smem + N * 8);
+  float2* ds = reinterpret_cast<float2*>(smem + N * 8 + R * 2 * LW * 4);  // rows r0-1 .. r0+R
+  float* ws = reinterpret_cast<float*>(ds + (R + 2) * N);                 // rows r0 .. r0+R
+  load_twiddles<N>(tw, twg);
+  const int r0 = blockIdx.x * R;
+  const size_t sbase = (size_t)s * N * N;
+  const bool tv = (wtv != nullptr);
+  if (tv) {
+    for (int idx = threadIdx.x; idx < (R + 2) * N; idx += blockDim.x) {
+      const int rr = r0 - 1 + idx / N, cc = idx % N;
+      ds[idx] = (rr >= 0 && rr < N) ? d[sbase + (size_t)rr * N + cc] : make_float2(0.f, 0.f);
+    }
+    for (int idx = threadIdx.x; idx < (R + 1) * N; idx += blockDim.x) {
+      const int rr = r0 + idx / N, cc = idx % N;
+      ws[idx] = (rr < N) ? wtv[sbase + (size_t)rr * N + cc] : 0.f;
+    }
+  }
+  const int lr = threadIdx.x / T, t = threadIdx.x % T;
+  const int row = r0 + lr;
+  const size_t base = sbase + (size_t)row * N;
+  float2 v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = tbuf[base + t + T * e];
+  __syncthreads();
+  fft_line<N, +1>(v, lines + lr * 2 * LW, lines + lr * 2 * LW + LW, tw, t);
+  const float sc = 1.0f / ((float)N * (float)N);
+  const float lam = st[s].lam, lam_tv = st[s].lam_tv;
+  float acc = 0.f;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int col = t + T * e;
+    float2 a = make_float2(v[e].x * sc, real ? 0.f : v[e].y * sc);
+    float2 dc;
+    if (tv) {
+      const float2* dr = ds + (lr + 1) * N;  // this row
+      dc = dr[col];
+      const float2 dl = col > 0 ? dr[col - 1] : make_float2(0.f, 0.f);
+      const float2 du = (ds + lr * N)[col];  // row - 1 (zero above the image)
+      const float2 g1 = csub(dc, dl), g2 = csub(dc, du);
+      const float wc = ws[lr * N + col];
+      float2 tvv = cscale(cadd(g1, g2), wc);
+      if (col < N - 1) tvv = csub(tvv, cscale(csub(dr[col + 1], dc), ws[lr * N + col + 1]));
+      if (row < N - 1) tvv = csub(tvv, cscale(csub((ds + (lr + 2) * N)[col], dc), ws[(lr + 1) * N + col]));
+      a = cfma(lam_tv, tvv, a);
+    } else {
+      dc = d[base + col];
+    }
+    if (u) a = cfma(lam, u[base + col], a);
+    q[base + col] = a;
+    acc += rdot2(dc, a);
+  }
+  const double tot = block_sum((double)acc, red);
+  if (threadIdx.x == 0) part[((size_t)s * NSLOT + SLOT_DQ) * MAXPART + blockIdx.x] = tot;
+}
+
+// ------------------------------------------------------------------ launch --
+
+template <int N> static void set_smem_attrs() {
+  static bool done = false;
+  if (done) return;
+  done = true;
+  cudaFuncSetAttribute(k_row_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem_bytes<N>(false));
+  cudaFuncSetAttribute(k_row_ahb<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem_bytes<N>(false));
+  cudaFuncSetAttribute(k_row_inv<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem_bytes<N>(true));
+  cudaFuncSetAttribute(k_col_mask<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem_bytes<N>());
+  cudaFuncSetAttribute(k_col_inv<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem_bytes<N>());
+}
+
+template <int N> struct FftLaunch {
+  static constexpr int R = rows_per_cta<N>();
+  static void row_fwd(const FftArgs& a) {
+    set_smem_attrs<N>();
+    k_row_fwd<N><<<dim3(N / R, a.batch), R * FftCfg<N>::T, row_smem_bytes<N>(false), a.stream>>>(
+        a.z, a.d, a.t, a.st, a.tw, a.mode);
+  }
+  static void row_ahb(const FftArgs& a) {
+    set_smem_attrs<N>();
+    k_row_ahb<N><<<dim3(N / R, a.batch), R * FftCfg<N>::T, row_smem_bytes<N>(false), a.stream>>>(
+        a.b, a.mask, a.t, a.tw);
+  }
+  static void col_mask(const FftArgs& a) {
+    set_smem_attrs<N>();
+    k_col_mask<N><<<dim3(N / COLS, a.batch), COLS * FftCfg<N>::T, col_smem_bytes<N>(), a.stream>>>(
+        a.t, a.mask, a.st, a.tw);
+  }
+  static void col_inv(const FftArgs& a) {
+    set_smem_attrs<N>();
+    k_col_inv<N><<<dim3(N / COLS, a.batch), COLS * FftCfg<N>::T, col_smem_bytes<N>(), a.stream>>>(
+        a.t, a.atb, a.x, a.real, a.part, a.tw);
+  }
+  static void row_inv(const FftArgs& a) {
+    set_smem_attrs<N>();
+    k_row_inv<N><<<dim3(N / R, a.batch), R * FftCfg<N>::T, row_smem_bytes<N>(a.wtv != nullptr), a.stream>>>(
+        a.t, a.d, a.u, a.wtv, a.q, a.st, a.part, a.real, a.tw);
+  }
+};
+
+#define FIRLS_FOR_SIZES(X) X(16) X(32) X(48) X(64) X(80) X(96) X(128) X(160) X(192) X(256) X(320) X(384) X(512)
+
+#define FIRLS_DISPATCH(fn)                              \
+  void fft_##fn(int n, const FftArgs& a) {              \
+    switch (n) {                                        \
+      FIRLS_FOR_SIZES(FIRLS_CASE_##fn)                  \
+      default: break;                                   \
+    }                                                   \
+  }
+#define FIRLS_CASE_row_fwd(n) case n: FftLaunch<n>::row_fwd(a); break;
+#define FIRLS_CASE_row_ahb(n) case n: FftLaunch<n>::row_ahb(a); break;
+#define FIRLS_CASE_col_mask(n) case n: FftLaunch<n>::col_mask(a); break;
+#define FIRLS_CASE_col_inv(n) case n: FftLaunch<n>::col_inv(a); break;
+#define FIRLS_CASE_row_inv(n) case n: FftLaunch<n>::row_inv(a); break;
+FIRLS_DISPATCH(row_fwd)
+FIRLS_DISPATCH(row_ahb)
+FIRLS_DISPATCH(col_mask)
+FIRLS_DISPATCH(col_inv)
+FIRLS_DISPATCH(row_inv)
+
+bool fft_size_supported(int n) {
+  switch (n) {
+#define FIRLS_CASE_SUP(n) case n: return true;
+    FIRLS_FOR_SIZES(FIRLS_CASE_SUP)
+#undef FIRLS_CASE_SUP
+    default: return false;
+  }
+}
+
+int fft_row_ctas(int n) {
+  switch (n) {
+#define FIRLS_CASE_RC(n) case n: return n / rows_per_cta<n>();
+    FIRLS_FOR_SIZES(FIRLS_CASE_RC)
+#undef FIRLS_CASE_RC
+    default: return 0;
+  }
+}
+
+int fft_col_ctas(int n) { return n / COLS; }
+
+void fft_prepare(int n) {
+  switch (n) {
+#define FIRLS_CASE_PREP(n) case n: set_smem_attrs<n>(); break;
+    FIRLS_FOR_SIZES(FIRLS_CASE_PREP)
+#undef FIRLS_CASE_PREP
+    default: break;
+  }
+}
+
+}  // namespace firls

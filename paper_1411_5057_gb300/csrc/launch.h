@@ -1,0 +1,102 @@
+// Host-side launch wrappers shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "firls_common.cuh"
+
+namespace firls {
+
+struct FftArgs {
+  int batch = 0;
+  cudaStream_t stream = 0;
+  const float2* tw = nullptr;     // twiddles exp(-2 pi i j / n), j < n
+  const SliceState* st = nullptr;
+  double* part = nullptr;
+  const float2* z = nullptr;
+  float2* d = nullptr;
+  float2* t = nullptr;
+  const float2* b = nullptr;
+  const uint8_t* mask = nullptr;
+  float2* atb = nullptr;
+  float2* x = nullptr;
+  const float2* u = nullptr;
+  const float* wtv = nullptr;
+  float2* q = nullptr;
+  int mode = 0;
+  int real = 0;
+};
+
+bool fft_size_supported(int n);
+int fft_row_ctas(int n);
+int fft_col_ctas(int n);
+void fft_row_fwd(int n, const FftArgs& a);
+void fft_row_ahb(int n, const FftArgs& a);
+void fft_col_mask(int n, const FftArgs& a);
+void fft_col_inv(int n, const FftArgs& a);
+void fft_row_inv(int n, const FftArgs& a);
+void fft_prepare(int n);  // set shared-memory limits (call outside capture)
+
+// ---- wavelet (lifting) ----
+enum WavMode { WAV_RAW = 0, WAV_MUL_W = 1, WAV_MUL_PINV = 2, WAV_SINGLETON_W = 3 };
+
+struct WavArgs {
+  int batch = 0, n = 0, levels = 0, kind = 0;
+  cudaStream_t stream = 0;
+  const SliceState* st = nullptr;   // slices not running are skipped (may be null)
+  float2* tmpA = nullptr;           // [batch][n/2 * n/2] ping-pong LL buffers
+  float2* tmpB = nullptr;
+  double* part = nullptr;
+};
+// c = Phi x (Mallat, stride n) with the final store scaled per `mode`:
+// RAW: c; MUL_W: w*c; MUL_PINV: c / (abar + lam w); SINGLETON_W: writes
+// w = (|c|^2 + eps)^-1/2 into `w` instead of c.
+void wavelet_forward(const WavArgs& a, const float2* x, float2* c, float* w, int mode);
+// x = Phi^T c; if r != null also partial Re<r, x> into SLOT_RZ.
+void wavelet_inverse(const WavArgs& a, const float2* c, float2* x, const float2* r, int real);
+int wavelet_inverse_ctas(int n);
+void wav_prepare();
+
+// ---- TV, preconditioner, groups, PCG scalars ----
+void tv_weights(int batch, int n, cudaStream_t s, const SliceState* st, const float2* x, float* wtv);
+void wavelet_diag(int batch, int n, int levels, cudaStream_t s, const SliceState* st, const float* w,
+                  float* out, const float* sqtab, const int* sqlen);
+void penta_setup(int batch, int n, cudaStream_t s, const SliceState* st, const float* wtv,
+                 const float* wdiag, float* ia, float* pb, float* pc);
+
+enum IluMode { ILU_INIT = 0, ILU_STEP = 1, ILU_LAST = 2 };
+void ilu_step(int batch, int n, cudaStream_t s, const SliceState* st, double* part, int mode,
+              float2* x, const float2* d, float2* r, const float2* q, const float2* atb, float2* y,
+              float2* z, const float* ia, const float* pb, const float* pc);
+
+enum AxpyMode { AXPY_INIT = 0, AXPY_STEP = 1, AXPY_LAST = 2 };
+void axpy_step(int batch, int n, cudaStream_t s, const SliceState* st, double* part, int mode,
+               float2* x, const float2* d, float2* r, const float2* q, const float2* atb);
+int axpy_ctas(int n);
+
+void group_norms(int batch, int n, int n_groups, cudaStream_t s, const SliceState* st,
+                 const int* gidx, const int* goff, int gsize, const float2* c, float* wg, float eps_unused);
+void group_gather(int batch, int n, int n_groups, cudaStream_t s, const SliceState* st,
+                  const int* inv_off, const int* inv_ids, const float* wg, float* w);
+// Build the inverse map; returns via err (device int) 1 on bad index/offsets.
+void group_inverse_build(int n, int n_groups, int gsize, cudaStream_t s, const int* gidx, const int* goff,
+                         int* counts, int* inv_off, int* inv_ids, int* cursor, int* err);
+
+void mask_popcount(int batch, int n, cudaStream_t s, const uint8_t* mask, int* counts);
+
+// PCG scalar updates (one thread per slice)
+void pcg_alpha(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts);
+void pcg_rho_init(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts_rz,
+                  int nparts_rr);
+void pcg_beta(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts_rz,
+              int nparts_rr, float pcg_tol);
+void outer_begin(int batch, cudaStream_t s, SliceState* st);
+void relchange_parts(int batch, int n, cudaStream_t s, const SliceState* st, const float2* x,
+                     const float2* xprev, double* part);
+void outer_end(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts,
+               float outer_tol);
+void state_init(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts_rhs,
+                const int* counts, int n, const float* lam, const float* lam_tv, float eps);
+
+}  // namespace firls
