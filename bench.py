@@ -171,6 +171,7 @@ def run_ours(args):
         ms = float(t.item())
     value = world * B / (ms / 1e3)
 
+    print(f"[bench] {B} slices, {args.outer}x{args.inner}: {ms:.1f} ms/step", file=sys.stderr, flush=True)
     # ---- per-kernel timing of one outer step (same workload, same launches) ----
     ctx.set_timing(True)
     one = F.make_params(1, args.inner, lam=LAM_W, lam_tv=LAM_TV)
@@ -178,6 +179,8 @@ def run_ours(args):
     ctx.solve(b, one, out=x)
     kt = ctx.get_timing()
     ctx.set_timing(False)
+    print("[bench] per outer step: " + ", ".join(f"{k} {v[0]:.2f} ms/{v[1]}" for k, v in kt.items()),
+          file=sys.stderr, flush=True)
     launches_per_step = sum(v[1] for v in kt.values()) * args.outer
     kern = {k: {"ms_per_outer": round(v[0], 4), "launches": v[1]} for k, v in kt.items()}
     dom = max((k for k in ALG_BYTES_PER_PX if kt[k][1] > 0), key=lambda k: kt[k][0])

@@ -172,12 +172,12 @@ struct TMark {
   TMark(firls_ctx* c_, int cls_, int launches_) : c(c_), cls(cls_), launches(launches_) {
     if (!c->timing) return;
     b = next_event(c);
-    cudaEventRecord(b, c->stream);
+    cudaEventRecordWithFlags(b, c->stream, cudaEventRecordExternal);
   }
   ~TMark() {
     if (!c->timing) return;
     cudaEvent_t e = next_event(c);
-    cudaEventRecord(e, c->stream);
+    cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal);
     c->marks.push_back({cls, launches, b, e});
   }
 };
@@ -369,7 +369,21 @@ firls_status run_outer_steps(firls_ctx* c, const firls_params* p) {
     c->g_ptol = p->pcg_tol;
     c->g_otol = p->outer_tol;
   }
-  for (int k = 0; k < p->outer_iters; ++k) CU(cudaGraphLaunch(c->exec, c->stream));
+  // With an outer tolerance, poll the per-slice done flags every
+  // kPoll replays and stop launching once every slice has stopped.
+  const int kPoll = 16;
+  std::vector<SliceState> hs;
+  for (int k = 0; k < p->outer_iters; ++k) {
+    CU(cudaGraphLaunch(c->exec, c->stream));
+    if (p->outer_tol > 0.f && (k + 1) % kPoll == 0 && k + 1 < p->outer_iters) {
+      hs.resize(c->batch);
+      CU(cudaMemcpyAsync(hs.data(), c->st, sizeof(SliceState) * c->batch, cudaMemcpyDeviceToHost, c->stream));
+      CU(cudaStreamSynchronize(c->stream));
+      bool all = true;
+      for (const SliceState& v : hs) all = all && v.done;
+      if (all) break;
+    }
+  }
   c->marks_valid = c->timing;
   return FIRLS_OK;
 }
