@@ -41,8 +41,7 @@ RATIO, SIGMA, LAM_TV, LAM_W, LEVELS = 0.20, 0.01, 1e-3, 5e-4, 4
 ALG_BYTES_PER_PX = {
     "row_fft": 32.0,            # read z, d; write d, t
     "col_fft_mask": 17.0,       # read t, mask; write t
-    "wavelet_fwd": 8.0 + 4.0 + 8.0,   # read d, w; write w*Phi d (whole pyramid)
-    "wavelet_inv": 16.0,        # read coefficients; write image
+    "wavelet_S": 8.0 + 4.0 + 8.0,     # read d and w, write u = Phi^T (w o Phi d)
     "row_ifft_combine": 36.0,   # read t, d, u, W_tv; write q
     "ilu": 68.0,                # read x, d, r, q, 1/a, b, c; write x, r, z
     "axpy": 32.0,
@@ -186,8 +185,6 @@ def run_ours(args):
     dom = max((k for k in ALG_BYTES_PER_PX if kt[k][1] > 0), key=lambda k: kt[k][0])
     per_launch_s = kt[dom][0] / kt[dom][1] / 1e3
     alg = ALG_BYTES_PER_PX[dom] * N * N * B
-    if dom.startswith("wavelet"):
-        alg *= 4.0 / 3.0
     achieved = alg / per_launch_s / 1e9
     peaks = {}
     try:

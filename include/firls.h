@@ -188,8 +188,8 @@ firls_status firls_get_popcounts(firls_ctx* ctx, int32_t* counts);
 enum {
   FIRLS_K_ROW_FFT = 0,       /* d = z + beta d, row FFT                       */
   FIRLS_K_COL_FFT_MASK = 1,  /* column FFT, mask, column IFFT                 */
-  FIRLS_K_WAVELET_FWD = 2,   /* Phi (all levels of one call)                  */
-  FIRLS_K_WAVELET_INV = 3,   /* Phi^T (all levels of one call)                */
+  FIRLS_K_WAVELET_S = 2,     /* Phi^T (w o Phi d), the wavelet term of S      */
+  FIRLS_K_WAVELET_P = 3,     /* Phi^T (pinv o Phi r), the wavelet P^{-1}      */
   FIRLS_K_ROW_IFFT = 4,      /* row IFFT + TV stencil + wavelet term + dot    */
   FIRLS_K_ILU = 5,           /* x, r update and the two triangular sweeps     */
   FIRLS_K_AXPY = 6,          /* x, r update                                   */

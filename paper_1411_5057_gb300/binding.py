@@ -23,7 +23,7 @@ EXPORTED = ["firls_size_supported", "firls_create", "firls_set_operator", "firls
             "firls_last_error", "firls_destroy", "firls_apply_AHA", "firls_apply_Phi", "firls_apply_PhiT",
             "firls_apply_S_P", "firls_get_weights", "firls_get_inverse_map", "firls_get_popcounts",
             "firls_set_timing", "firls_get_timing"]
-KERNEL_CLASSES = ["row_fft", "col_fft_mask", "wavelet_fwd", "wavelet_inv", "row_ifft_combine", "ilu", "axpy",
+KERNEL_CLASSES = ["row_fft", "col_fft_mask", "wavelet_S", "wavelet_Pinv", "row_ifft_combine", "ilu", "axpy",
                   "scalars", "weights", "other"]
 
 

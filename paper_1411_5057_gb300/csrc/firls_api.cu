@@ -199,8 +199,8 @@ void enqueue_S(firls_ctx* c, int mode, const float2* zin, float2* din, float2* q
   { TMark m(c, FIRLS_K_COL_FFT_MASK, 1); fft_col_mask(c->n, a); }
   if (c->kind) {
     WavArgs w = wav_args(c, c->st);
-    { TMark m(c, FIRLS_K_WAVELET_FWD, c->levels); wavelet_forward(w, din, c->cw, c->ww, WAV_MUL_W); }
-    { TMark m(c, FIRLS_K_WAVELET_INV, c->levels); wavelet_inverse(w, c->cw, c->u, nullptr, a.real); }
+    TMark m(c, FIRLS_K_WAVELET_S, wavelet_apply_launches(c->n, c->levels));
+    wavelet_apply(w, din, c->cw, c->ww, WAV_MUL_W, c->u, nullptr, a.real);
   }
   a.u = c->kind ? c->u : nullptr;
   a.wtv = has_tv(c) ? c->wtv : nullptr;
@@ -250,13 +250,16 @@ void enqueue_update_precond(firls_ctx* c, int step_mode, float pcg_tol, bool ini
       axpy_step(B, n, c->stream, c->st, c->part, init ? AXPY_INIT : AXPY_STEP, c->x, c->d, c->r, c->q, c->atb);
     }
     WavArgs w = wav_args(c, c->st);
-    { TMark m(c, FIRLS_K_WAVELET_FWD, c->levels); wavelet_forward(w, c->r, c->cw, c->ww, WAV_MUL_PINV); }
-    { TMark m(c, FIRLS_K_WAVELET_INV, c->levels); wavelet_inverse(w, c->cw, c->z, c->r, real); }
+    {
+      TMark m(c, FIRLS_K_WAVELET_P, wavelet_apply_launches(n, c->levels));
+      wavelet_apply(w, c->r, c->cw, c->ww, WAV_MUL_PINV, c->z, c->r, real);
+    }
     TMark m(c, FIRLS_K_SCALARS, 1);
+    const int np = wavelet_inverse_ctas(n, c->levels);
     if (init)
-      pcg_rho_init(B, c->stream, c->st, c->part, wavelet_inverse_ctas(n), axpy_ctas(n));
+      pcg_rho_init(B, c->stream, c->st, c->part, np, axpy_ctas(n));
     else
-      pcg_beta(B, c->stream, c->st, c->part, wavelet_inverse_ctas(n), axpy_ctas(n), pcg_tol);
+      pcg_beta(B, c->stream, c->st, c->part, np, axpy_ctas(n), pcg_tol);
   }
   (void)step_mode;
 }

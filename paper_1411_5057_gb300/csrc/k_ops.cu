@@ -52,27 +52,16 @@ FI void inv_haar(float2 a, float2 d, float2& x0, float2& x1) {
 }
 }  // namespace lift
 
-constexpr int WAV_SMEM = 96 * 1024;
 constexpr int WAV_THREADS = 256;
+constexpr int WAV_RB = 8;            // output row pairs per CTA of a tiled level
+constexpr int COARSE_MAX = 128;      // largest block kept whole in shared memory
+constexpr int COARSE_THREADS = 512;
 
-static int wav_fwd_rb(int m) {
-  int half = m / 2;
-  int rb = (WAV_SMEM / (m * 16) - 2) / 2;
-  if (rb > 8) rb = 8;
-  if (rb < 1) rb = 1;
-  if (rb > half) rb = half;
-  return rb;
-}
-static int wav_inv_rb(int m) {
-  int half = m / 2;
-  int rb = (WAV_SMEM / (m * 8) - 2) / 4;
-  if (rb > 8) rb = 8;
-  if (rb < 1) rb = 1;
-  if (rb > half) rb = half;
-  return rb;
-}
+static int wav_rb(int m) { return m / 2 < WAV_RB ? m / 2 : WAV_RB; }
 
-// One analysis level on the m x m block `in` (row stride ld_in).
+// One tiled analysis level on the m x m block `in` (row stride ld_in).  The
+// horizontal step reads the input rows straight from global memory (16-byte
+// pairs), the vertical step works from shared memory.
 __global__ void __launch_bounds__(WAV_THREADS)
 k_wav_fwd(const float2* __restrict__ in, size_t in_ss, int ld_in, float2* __restrict__ llo, size_t ll_ss,
           int ld_ll, float2* __restrict__ c, float* __restrict__ w, int n, int m, int rb, int kind,
@@ -83,30 +72,24 @@ k_wav_fwd(const float2* __restrict__ in, size_t in_ss, int ld_in, float2* __rest
   const int half = m / 2;
   const int k0 = blockIdx.x * rb;
   const int nrow = 2 * rb + (kind == 2 ? 2 : 0);
-  float2* xs = reinterpret_cast<float2*>(smem);  // [nrow][m] input rows
-  float2* rt = xs + nrow * m;                    // [nrow][m] row-transformed
+  float2* rt = reinterpret_cast<float2*>(smem);  // [nrow][m] row-transformed
   const float2* src = in + (size_t)s * in_ss;
-  for (int idx = threadIdx.x; idx < nrow * m; idx += blockDim.x) {
-    const int i = idx / m, col = idx % m;
-    const int gr = (2 * k0 + i) % m;
-    xs[idx] = src[(size_t)gr * ld_in + col];
-  }
-  __syncthreads();
-  // horizontal step: [lo | hi] per row
   for (int idx = threadIdx.x; idx < nrow * half; idx += blockDim.x) {
     const int i = idx / half, k = idx % half;
-    const float2* xr = xs + i * m;
+    const float4* xr = reinterpret_cast<const float4*>(src + (size_t)((2 * k0 + i) % m) * ld_in);
+    const float4 p0 = xr[k];
     float2 a, d;
     if (kind == 2) {
-      lift::fwd_db4(xr[2 * k], xr[2 * k + 1], xr[(2 * k + 2) % m], xr[(2 * k + 3) % m], a, d);
+      const float4 p1 = xr[k + 1 < half ? k + 1 : 0];
+      lift::fwd_db4(make_float2(p0.x, p0.y), make_float2(p0.z, p0.w), make_float2(p1.x, p1.y),
+                    make_float2(p1.z, p1.w), a, d);
     } else {
-      lift::fwd_haar(xr[2 * k], xr[2 * k + 1], a, d);
+      lift::fwd_haar(make_float2(p0.x, p0.y), make_float2(p0.z, p0.w), a, d);
     }
     rt[i * m + k] = a;
     rt[i * m + half + k] = d;
   }
   __syncthreads();
-  // vertical step and store
   const float lam = st ? st[s].lam : 0.f, abar = st ? st[s].abar : 0.f, eps = st ? st[s].eps : 1e-10f;
   float2* cs = c + (size_t)s * n * n;
   float* ws = w ? w + (size_t)s * n * n : nullptr;
@@ -126,7 +109,7 @@ k_wav_fwd(const float2* __restrict__ in, size_t in_ss, int ld_in, float2* __rest
     for (int h = 0; h < 2; ++h) {
       const int orow = h ? half + row : row;
       const float2 v = h ? d : a;
-      if (!h && j < half && !last) {  // intermediate LL: raw, to the ping-pong buffer
+      if (!h && j < half && !last) {  // LL of a non-final level: raw, to the ping-pong buffer
         lls[(size_t)row * ld_ll + j] = v;
         continue;
       }
@@ -144,8 +127,9 @@ k_wav_fwd(const float2* __restrict__ in, size_t in_ss, int ld_in, float2* __rest
   }
 }
 
-// One synthesis level: coefficients of the m x m block (LL from ll_in,
-// details from c at stride n) to the m x m output block.
+// One tiled synthesis level: LL from `lli` (row stride ld_ll), details from c
+// (stride n) to the m x m output block.  Vertical step from global memory,
+// horizontal step from shared memory; optional partial Re<r, out>.
 __global__ void __launch_bounds__(WAV_THREADS)
 k_wav_inv(const float2* __restrict__ lli, size_t ll_ss, int ld_ll, const float2* __restrict__ c,
           float2* __restrict__ out, size_t out_ss, int ld_out, int n, int m, int rb, int kind,
@@ -158,25 +142,22 @@ k_wav_inv(const float2* __restrict__ lli, size_t ll_ss, int ld_ll, const float2*
   const int half = m / 2;
   const int k0 = blockIdx.x * rb;
   const int nout = min(rb, half - k0);
-  float2* lo = reinterpret_cast<float2*>(smem);  // [rb+1][m]: [LL | LH] rows k0-1 .. k0+rb-1
-  float2* hi = lo + (rb + 1) * m;                // [rb+1][m]: [HL | HH]
-  float2* vs = hi + (rb + 1) * m;                // [2 rb][m]
+  float2* vs = reinterpret_cast<float2*>(smem);  // [2 rb][m]
   const float2* cs = c + (size_t)s * n * n;
   const float2* ls = lli + (size_t)s * ll_ss;
-  for (int idx = threadIdx.x; idx < (nout + 1) * m; idx += blockDim.x) {
-    const int i = idx / m, j = idx % m;
-    const int kr = (k0 - 1 + i + half) % half;
-    lo[idx] = j < half ? ls[(size_t)kr * ld_ll + j] : cs[(size_t)kr * n + j];
-    hi[idx] = cs[(size_t)(half + kr) * n + j];
-  }
-  __syncthreads();
   for (int idx = threadIdx.x; idx < nout * m; idx += blockDim.x) {
     const int kk = idx / m, j = idx % m;
+    const int k = k0 + kk;
+    const float2 al = j < half ? ls[(size_t)k * ld_ll + j] : cs[(size_t)k * n + j];
+    const float2 dl = cs[(size_t)(half + k) * n + j];
     float2 x0, x1;
     if (kind == 2) {
-      lift::inv_db4(lo[kk * m + j], hi[kk * m + j], lo[(kk + 1) * m + j], hi[(kk + 1) * m + j], x0, x1);
+      const int km = (k - 1 + half) % half;
+      const float2 am = j < half ? ls[(size_t)km * ld_ll + j] : cs[(size_t)km * n + j];
+      const float2 dm = cs[(size_t)(half + km) * n + j];
+      lift::inv_db4(am, dm, al, dl, x0, x1);
     } else {
-      lift::inv_haar(lo[(kk + 1) * m + j], hi[(kk + 1) * m + j], x0, x1);
+      lift::inv_haar(al, dl, x0, x1);
     }
     vs[(2 * kk) * m + j] = x0;
     vs[(2 * kk + 1) * m + j] = x1;
@@ -200,10 +181,11 @@ k_wav_inv(const float2* __restrict__ lli, size_t ll_ss, int ld_ll, const float2*
       x1.y = 0.f;
     }
     const int orow = 2 * k0 + i;
-    const size_t p = (size_t)orow * ld_out + 2 * l;
-    os[p] = x0;
-    os[p + 1] = x1;
-    if (rs) acc += rdot2(rs[(size_t)orow * n + 2 * l], x0) + rdot2(rs[(size_t)orow * n + 2 * l + 1], x1);
+    reinterpret_cast<float4*>(os + (size_t)orow * ld_out)[l] = make_float4(x0.x, x0.y, x1.x, x1.y);
+    if (rs) {
+      const float4 rv = reinterpret_cast<const float4*>(rs + (size_t)orow * n)[l];
+      acc += rdot2(make_float2(rv.x, rv.y), x0) + rdot2(make_float2(rv.z, rv.w), x1);
+    }
   }
   if (part) {
     const double tot = block_sum((double)acc, red);
@@ -211,67 +193,296 @@ k_wav_inv(const float2* __restrict__ lli, size_t ll_ss, int ld_ll, const float2*
   }
 }
 
+// ---- coarse levels of one slice in shared memory ----
+// In-place one-level analysis of the top-left m x m block of S (row stride
+// ls): every lane reads the inputs of its pairs, the warp syncs, then writes
+// [lo | hi].  m <= COARSE_MAX, so a lane holds at most two pairs.
+FI void smem_fwd_level(float2* S, int ls, int m, int kind) {
+  const int half = m / 2, lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int pass = 0; pass < 2; ++pass) {  // 0: rows, 1: columns
+    const int es = pass ? ls : 1;         // element stride along the line
+    for (int line = wid; line < m; line += nw) {
+      float2* L = pass ? S + line : S + (size_t)line * ls;
+      float2 a[2], d[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int k = lane + 32 * u;
+        if (k < half) {
+          if (kind == 2) {
+            lift::fwd_db4(L[(2 * k) * es], L[(2 * k + 1) * es], L[((2 * k + 2) % m) * es],
+                          L[((2 * k + 3) % m) * es], a[u], d[u]);
+          } else {
+            lift::fwd_haar(L[(2 * k) * es], L[(2 * k + 1) * es], a[u], d[u]);
+          }
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int k = lane + 32 * u;
+        if (k < half) {
+          L[k * es] = a[u];
+          L[(half + k) * es] = d[u];
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+}
+
+// In-place inverse of smem_fwd_level (columns first, then rows).
+FI void smem_inv_level(float2* S, int ls, int m, int kind) {
+  const int half = m / 2, lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int pass = 0; pass < 2; ++pass) {  // 0: columns, 1: rows
+    const int es = pass ? 1 : ls;
+    for (int line = wid; line < m; line += nw) {
+      float2* L = pass ? S + (size_t)line * ls : S + line;
+      float2 x0[2], x1[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int l = lane + 32 * u;
+        if (l < half) {
+          if (kind == 2) {
+            const int lm = (l - 1 + half) % half;
+            lift::inv_db4(L[lm * es], L[(half + lm) * es], L[l * es], L[(half + l) * es], x0[u], x1[u]);
+          } else {
+            lift::inv_haar(L[l * es], L[(half + l) * es], x0[u], x1[u]);
+          }
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int l = lane + 32 * u;
+        if (l < half) {
+          L[(2 * l) * es] = x0[u];
+          L[(2 * l + 1) * es] = x1[u];
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+}
+
+enum { COARSE_FWD = 1, COARSE_INV = 2 };
+
+// Levels l0..L of one slice on the m0 x m0 block (m0 <= COARSE_MAX) held in
+// shared memory.  FWD: analysis of `src`; without INV the coefficients are
+// stored per `mode` at their Mallat positions (top-left block of c / w).
+// FWD|INV: analysis, per-coefficient scaling (MUL_W or MUL_PINV), synthesis;
+// the coarse coefficients never leave shared memory.  INV alone: synthesis
+// of the coefficients read from c.  The synthesised block goes to `dst`.
+__global__ void __launch_bounds__(COARSE_THREADS)
+k_wav_coarse(const float2* __restrict__ src, size_t src_ss, int src_ld, float2* __restrict__ dst, size_t dst_ss,
+             int dst_ld, float2* __restrict__ c, float* __restrict__ w, int n, int m0, int nlev, int kind,
+             int mode, int flags, const float2* __restrict__ r, double* __restrict__ part, int real,
+             const SliceState* __restrict__ st) {
+  const int s = blockIdx.x;
+  if (st != nullptr && !slice_running(st, s)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[32];
+  float2* S = reinterpret_cast<float2*>(smem);
+  const int ls = m0 + 1;
+  const size_t nn = (size_t)n * n;
+  float2* cs = c + (size_t)s * nn;
+  float* ws = w ? w + (size_t)s * nn : nullptr;
+  const int cnt = m0 * m0;
+  if (flags & COARSE_FWD) {
+    const float2* sp = src + (size_t)s * src_ss;
+    for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
+      const int rr = idx / m0, cc = idx % m0;
+      S[rr * ls + cc] = sp[(size_t)rr * src_ld + cc];
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
+      const int rr = idx / m0, cc = idx % m0;
+      S[rr * ls + cc] = cs[(size_t)rr * n + cc];
+    }
+  }
+  __syncthreads();
+  if (flags & COARSE_FWD) {
+    for (int lev = 0; lev < nlev; ++lev) smem_fwd_level(S, ls, m0 >> lev, kind);
+    const float lam = st ? st[s].lam : 0.f, abar = st ? st[s].abar : 0.f, eps = st ? st[s].eps : 1e-10f;
+    for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
+      const int rr = idx / m0, cc = idx % m0;
+      const size_t p = (size_t)rr * n + cc;
+      float2& v = S[rr * ls + cc];
+      if (flags & COARSE_INV) {
+        v = cscale(v, mode == WAV_MUL_W ? ws[p] : 1.0f / (abar + lam * ws[p]));
+      } else if (mode == WAV_RAW) {
+        cs[p] = v;
+      } else if (mode == WAV_MUL_W) {
+        cs[p] = cscale(v, ws[p]);
+      } else if (mode == WAV_MUL_PINV) {
+        cs[p] = cscale(v, 1.0f / (abar + lam * ws[p]));
+      } else {
+        ws[p] = rsqrtf(cabs2(v) + eps);
+      }
+    }
+    __syncthreads();
+  }
+  if (!(flags & COARSE_INV)) return;
+  for (int lev = nlev - 1; lev >= 0; --lev) smem_inv_level(S, ls, m0 >> lev, kind);
+  float2* dp = dst + (size_t)s * dst_ss;
+  const float2* rs = r ? r + (size_t)s * nn : nullptr;
+  float acc = 0.f;
+  for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
+    const int rr = idx / m0, cc = idx % m0;
+    float2 v = S[rr * ls + cc];
+    if (real) v.y = 0.f;
+    dp[(size_t)rr * dst_ld + cc] = v;
+    if (rs) acc += rdot2(rs[(size_t)rr * n + cc], v);
+  }
+  if (part) {
+    const double tot = block_sum((double)acc, red);
+    if (threadIdx.x == 0) part[((size_t)s * NSLOT + SLOT_RZ) * MAXPART] = tot;
+  }
+}
+
+static int coarse_smem(int m0) { return m0 * (m0 + 1) * 8; }
+
 static void set_wav_attrs() {
   static bool done = false;
   if (done) return;
   done = true;
-  cudaFuncSetAttribute(k_wav_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, WAV_SMEM);
-  cudaFuncSetAttribute(k_wav_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, WAV_SMEM);
+  cudaFuncSetAttribute(k_wav_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 20 * 512 * 8);
+  cudaFuncSetAttribute(k_wav_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * WAV_RB * 512 * 8);
+  cudaFuncSetAttribute(k_wav_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, coarse_smem(COARSE_MAX));
 }
 
-void wav_prepare() { set_wav_attrs(); }
-
-void wavelet_forward(const WavArgs& a, const float2* x, float2* c, float* w, int mode) {
+void ilu_prepare();
+void wav_prepare() {
   set_wav_attrs();
+  ilu_prepare();
+}
+
+// First level handled by the coarse kernel: its input side m <= COARSE_MAX.
+static int coarse_first_level(int n, int levels) {
+  int l0 = 1;
+  while (l0 <= levels && (n >> (l0 - 1)) > COARSE_MAX) ++l0;
+  return l0;  // levels + 1 when no level fits
+}
+
+// Tiled analysis of levels 1 .. lend; returns the buffer holding LL_lend.
+static const float2* tiled_forward(const WavArgs& a, const float2* x, float2* c, float* w, int mode, int lend,
+                                   bool ll_final_to_c, size_t* ss, int* ld) {
   const int n = a.n;
   const size_t hh = (size_t)(n / 2) * (n / 2);
   const float2* src = x;
   size_t src_ss = (size_t)n * n;
   int src_ld = n;
-  for (int l = 1; l <= a.levels; ++l) {
+  for (int l = 1; l <= lend; ++l) {
     const int m = n >> (l - 1), half = m / 2;
-    const bool last = (l == a.levels);
-    float2* dst = last ? c : ((l & 1) ? a.tmpA : a.tmpB);
-    const size_t dst_ss = last ? (size_t)n * n : hh;
-    const int dst_ld = last ? n : half;
-    const int rb = wav_fwd_rb(m);
-    const int nrow = 2 * rb + (a.kind == 2 ? 2 : 0);
-    const int smem = 2 * nrow * m * 8;
+    const bool to_c = ll_final_to_c && l == lend;
+    float2* dst = to_c ? c : ((l & 1) ? a.tmpA : a.tmpB);
+    const size_t dst_ss = to_c ? (size_t)n * n : hh;
+    const int dst_ld = to_c ? n : half;
+    const int rb = wav_rb(m);
+    const int smem = (2 * rb + (a.kind == 2 ? 2 : 0)) * m * 8;
     k_wav_fwd<<<dim3((half + rb - 1) / rb, a.batch), WAV_THREADS, smem, a.stream>>>(
-        src, src_ss, src_ld, dst, dst_ss, dst_ld, c, w, n, m, rb, a.kind, mode, last ? 1 : 0, a.st);
+        src, src_ss, src_ld, dst, dst_ss, dst_ld, c, w, n, m, rb, a.kind, mode, to_c ? 1 : 0, a.st);
     src = dst;
     src_ss = dst_ss;
     src_ld = dst_ld;
   }
+  *ss = src_ss;
+  *ld = src_ld;
+  return src;
 }
 
-int wavelet_inverse_ctas(int n) {
-  const int rb = wav_inv_rb(n);
-  return (n / 2 + rb - 1) / rb;
-}
-
-void wavelet_inverse(const WavArgs& a, const float2* c, float2* x, const float2* r, int real) {
-  set_wav_attrs();
+// Tiled synthesis of levels lstart .. 1 with LL_lstart in (lli, ll_ss, ll_ld).
+static void tiled_inverse(const WavArgs& a, const float2* lli, size_t ll_ss, int ll_ld, const float2* c,
+                          float2* x, int lstart, const float2* r, int real) {
   const int n = a.n;
   const size_t hh = (size_t)(n / 2) * (n / 2);
-  const float2* lli = c;
-  size_t ll_ss = (size_t)n * n;
-  int ll_ld = n;
-  for (int l = a.levels; l >= 1; --l) {
+  for (int l = lstart; l >= 1; --l) {
     const int m = n >> (l - 1), half = m / 2;
     const bool final_level = (l == 1);
-    float2* out = final_level ? x : ((l & 1) ? a.tmpA : a.tmpB);
+    // write into the ping-pong buffer the input does not occupy
+    float2* out = final_level ? x : (lli == a.tmpA ? a.tmpB : a.tmpA);
     const size_t out_ss = final_level ? (size_t)n * n : hh;
     const int out_ld = final_level ? n : m;
-    const int rb = wav_inv_rb(m);
-    const int smem = (4 * rb + 2) * m * 8;
-    k_wav_inv<<<dim3((half + rb - 1) / rb, a.batch), WAV_THREADS, smem, a.stream>>>(
+    const int rb = wav_rb(m);
+    k_wav_inv<<<dim3((half + rb - 1) / rb, a.batch), WAV_THREADS, 2 * rb * m * 8, a.stream>>>(
         lli, ll_ss, ll_ld, c, out, out_ss, out_ld, n, m, rb, a.kind, final_level ? r : nullptr,
         final_level && r ? a.part : nullptr, real, a.st);
     lli = out;
     ll_ss = out_ss;
     ll_ld = out_ld;
   }
+}
+
+void wavelet_forward(const WavArgs& a, const float2* x, float2* c, float* w, int mode) {
+  set_wav_attrs();
+  const int n = a.n, L = a.levels;
+  const int l0 = coarse_first_level(n, L);
+  size_t ss;
+  int ld;
+  const float2* ll = tiled_forward(a, x, c, w, mode, l0 - 1, l0 > L, &ss, &ld);
+  if (l0 <= L) {
+    const int m0 = n >> (l0 - 1);
+    k_wav_coarse<<<a.batch, COARSE_THREADS, coarse_smem(m0), a.stream>>>(
+        ll, ss, ld, nullptr, 0, 0, c, w, n, m0, L - l0 + 1, a.kind, mode, COARSE_FWD, nullptr, nullptr, 0, a.st);
+  }
+}
+
+void wavelet_inverse(const WavArgs& a, const float2* c, float2* x, const float2* r, int real) {
+  set_wav_attrs();
+  const int n = a.n, L = a.levels;
+  const int l0 = coarse_first_level(n, L);
+  if (l0 <= L) {
+    const int m0 = n >> (l0 - 1);
+    const bool final_coarse = (l0 == 1);
+    float2* dst = final_coarse ? x : ((l0 - 1) & 1 ? a.tmpA : a.tmpB);
+    const size_t dss = final_coarse ? (size_t)n * n : (size_t)(n / 2) * (n / 2);
+    const int dld = final_coarse ? n : m0;
+    k_wav_coarse<<<a.batch, COARSE_THREADS, coarse_smem(m0), a.stream>>>(
+        nullptr, 0, 0, dst, dss, dld, const_cast<float2*>(c), nullptr, n, m0, L - l0 + 1, a.kind, WAV_RAW,
+        COARSE_INV, final_coarse ? r : nullptr, final_coarse && r ? a.part : nullptr, real, a.st);
+    if (!final_coarse) tiled_inverse(a, dst, dss, dld, c, x, l0 - 1, r, real);
+  } else {
+    tiled_inverse(a, c, (size_t)n * n, n, c, x, L, r, real);
+  }
+}
+
+// u = Phi^T (s o Phi x) with s = w (MUL_W) or 1/(abar + lam w) (MUL_PINV).
+void wavelet_apply(const WavArgs& a, const float2* x, float2* c, float* w, int mode, float2* u,
+                   const float2* r, int real) {
+  set_wav_attrs();
+  const int n = a.n, L = a.levels;
+  const int l0 = coarse_first_level(n, L);
+  if (l0 > L) {
+    wavelet_forward(a, x, c, w, mode);
+    wavelet_inverse(a, c, u, r, real);
+    return;
+  }
+  size_t ss;
+  int ld;
+  const float2* ll = tiled_forward(a, x, c, w, mode, l0 - 1, false, &ss, &ld);
+  const int m0 = n >> (l0 - 1);
+  const bool final_coarse = (l0 == 1);
+  float2* dst = final_coarse ? u : const_cast<float2*>(ll);  // LL' overwrites LL in place
+  const size_t dss = final_coarse ? (size_t)n * n : ss;
+  const int dld = final_coarse ? n : ld;
+  k_wav_coarse<<<a.batch, COARSE_THREADS, coarse_smem(m0), a.stream>>>(
+      ll, ss, ld, dst, dss, dld, c, w, n, m0, L - l0 + 1, a.kind, mode, COARSE_FWD | COARSE_INV,
+      final_coarse ? r : nullptr, final_coarse && r ? a.part : nullptr, real, a.st);
+  if (!final_coarse) tiled_inverse(a, dst, dss, dld, c, u, l0 - 1, r, real);
+}
+
+// Partial-sum count of the stage that computes Re<r, Phi^T ...>.
+int wavelet_inverse_ctas(int n, int levels) {
+  if (coarse_first_level(n, levels) == 1) return 1;
+  return (n / 2 + wav_rb(n) - 1) / wav_rb(n);
+}
+
+// Launches per wavelet_apply call (for the launch count).
+int wavelet_apply_launches(int n, int levels) {
+  const int l0 = coarse_first_level(n, levels);
+  if (l0 > levels) return 2 * levels;
+  return 2 * (l0 - 1) + 1;
 }
 
 // ================================================================== TV =====
@@ -301,18 +512,19 @@ void tv_weights(int batch, int n, cudaStream_t s, const SliceState* st, const fl
 // Exact diag(Phi^T diag(w) Phi): each 2-D basis function is an outer product
 // of 1-D level-l functions f_{l,type}(i - 2^l p) whose squares are tabulated
 // (sqtab[(l-1)*2 + type][0..len)), so the diagonal is a separable sum.
-__global__ void k_wavelet_diag(int n, int levels, const SliceState* __restrict__ st,
-                               const float* __restrict__ w, float* __restrict__ out,
-                               const float* __restrict__ sqtab, const int* __restrict__ sqlen) {
+__global__ void __launch_bounds__(256) k_wavelet_diag(int n, int levels, const SliceState* __restrict__ st,
+                                                      const float* __restrict__ w, float* __restrict__ out,
+                                                      const float* __restrict__ sqtab,
+                                                      const int* __restrict__ sqlen) {
   const int s = blockIdx.y;
   if (!slice_running(st, s)) return;
+  const int r = blockIdx.x;  // one image row per CTA: the row taps are uniform
   const size_t base = (size_t)s * n * n;
   const float* ws = w + base;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * n; i += gridDim.x * blockDim.x) {
-    const int r = i / n, c = i % n;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
     float acc = 0.f;
     for (int l = 1; l <= levels; ++l) {
-      const int h = n >> l, step = 1 << l;
+      const int h = n >> l, msk = (1 << l) - 1, step = 1 << l;
       const int nb = (l == levels) ? 4 : 3;
       for (int b = 0; b < nb; ++b) {
         // bands: (0,1) low/high, (1,0) high/low, (1,1) high/high, (0,0) low/low
@@ -321,30 +533,30 @@ __global__ void k_wavelet_diag(int n, int levels, const SliceState* __restrict__
         const float* fr = sqtab + (size_t)((l - 1) * 2 + br) * n;
         const float* fc = sqtab + (size_t)((l - 1) * 2 + bc) * n;
         const int lr = sqlen[(l - 1) * 2 + br], lc = sqlen[(l - 1) * 2 + bc];
-        for (int sr = r & (step - 1); sr < lr; sr += step) {
-          const int p = ((r - sr + n) % n) >> l;
+        for (int sr = r & msk; sr < lr; sr += step) {
+          int pr = r - sr;
+          if (pr < 0) pr += n;
           const float vr = fr[sr];
-          const float* wrow = ws + (size_t)(br * h + p) * n + bc * h;
-          for (int sc = c & (step - 1); sc < lc; sc += step) {
-            const int qq = ((c - sc + n) % n) >> l;
-            acc = fmaf(vr * fc[sc], wrow[qq], acc);
+          const float* wrow = ws + (size_t)(br * h + (pr >> l)) * n + bc * h;
+          for (int sc = c & msk; sc < lc; sc += step) {
+            int pc = c - sc;
+            if (pc < 0) pc += n;
+            acc = fmaf(vr * fc[sc], wrow[pc >> l], acc);
           }
         }
       }
     }
-    out[base + i] = acc;
+    out[base + (size_t)r * n + c] = acc;
   }
 }
 
 void wavelet_diag(int batch, int n, int levels, cudaStream_t s, const SliceState* st, const float* w,
                   float* out, const float* sqtab, const int* sqlen) {
-  const int N = n * n;
-  const int blocks = (N + 255) / 256 < 256 ? (N + 255) / 256 : 256;
-  k_wavelet_diag<<<dim3(blocks, batch), 256, 0, s>>>(n, levels, st, w, out, sqtab, sqlen);
+  k_wavelet_diag<<<dim3(n, batch), n < 256 ? n : 256, 0, s>>>(n, levels, st, w, out, sqtab, sqlen);
 }
 
 // P = abar I + lam_tv (D1^T W D1 + D2^T W D2) [+ lam diag(Phi^T W Phi)] (Eq. ptv):
-// ia = 1/a_i, pb = b_i (coupling i, i+1), pc = c_i (coupling i, i+n).
+// ia = 1/a_i, pb = b_i / a_i (b couples i, i+1), pc = c_i / a_i (c couples i, i+n).
 __global__ void k_penta(int n, const SliceState* __restrict__ st, const float* __restrict__ wtv,
                         const float* __restrict__ wdiag, float* __restrict__ ia, float* __restrict__ pb,
                         float* __restrict__ pc) {
@@ -359,9 +571,10 @@ __global__ void k_penta(int n, const SliceState* __restrict__ st, const float* _
     const float wd = r < n - 1 ? wtv[base + i + n] : 0.f;
     float a = abar + lt * (2.f * wc + wr + wd);
     if (wdiag) a = fmaf(lw, wdiag[base + i], a);
-    ia[base + i] = 1.0f / a;
-    pb[base + i] = -lt * wr;
-    pc[base + i] = -lt * wd;
+    const float inv = 1.0f / a;
+    ia[base + i] = inv;
+    pb[base + i] = -lt * wr * inv;  // b_i / a_i
+    pc[base + i] = -lt * wd * inv;  // c_i / a_i
   }
 }
 
@@ -373,172 +586,254 @@ void penta_setup(int batch, int n, cudaStream_t s, const SliceState* st, const f
 }
 
 // ------------------------------------------------ ILU solves (Sec. 4.2) -----
-// z = U^{-1} L^{-1} r with L = I + L_P diag(a)^{-1}, U = diag(a) + U_P:
-//   forward  y_i = r_i - (b_{i-1}/a_{i-1}) y_{i-1} - (c_{i-n}/a_{i-n}) y_{i-n}
-//   backward z_i = (y_i - b_i z_{i+1} - c_i z_{i+n}) / a_i
+// z = U^{-1} L^{-1} r with L = I + L_P diag(a)^{-1}, U = diag(a) + U_P.  With
+// ia = 1/a, ib = b/a, ic = c/a (b couples i, i+1; c couples i, i+n):
+//   forward  y_i = r_i - ib_{i-1} y_{i-1} - ic_{i-n} y_{i-n}
+//   backward z_i = ia_i y_i - ib_i z_{i+1} - ic_i z_{i+n}
+// P is symmetric, so U = diag(a) L^T and Re<r, z> = sum_i ia_i |y_i|^2,
+// which the forward sweep accumulates (the backward sweep need not reread r).
 // One CTA per slice sweeps the rows; within a row the first-order
-// recurrence is an affine scan across threads (4 columns per thread).
+// recurrence is an affine scan across threads (4 columns per thread).  Rows
+// are prefetched ILU_D - 1 ahead through a cp.async ring in shared memory
+// (each thread copies and later reads only its own 16-byte chunks).
 
-// Inclusive scan of affine maps y -> A y + B in thread order (forward) or
-// reverse thread order; returns, per thread, B of the exclusive prefix
-// (the value entering this thread's segment when the boundary value is 0).
+FI unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+FI void cp_async16(void* s, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(s)), "l"(g) : "memory");
+}
+FI void cp_async4(void* s, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(s)), "l"(g) : "memory");
+}
+FI void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K> FI void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
+
+// Exclusive scan of affine maps y -> A y + B in logical thread order
+// (forward: thread order; REV: reversed).  Returns B of the exclusive
+// prefix, i.e. the value entering this thread's segment for a zero boundary.
+// One barrier; sA/sB hold two 32-entry buffers alternated by `par`.
 template <bool REV>
-FI float2 affine_exclusive(float A, float2 B, float* sA, float2* sB) {
-  const int nt = blockDim.x;
-  const int t = REV ? (nt - 1 - (int)threadIdx.x) : (int)threadIdx.x;  // logical index
-  const int lane = threadIdx.x & 31;
-  // warp-level inclusive scan in logical order
+FI float2 affine_exclusive(float A, float2 B, float* sA, float2* sB, int par) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
     const float Ap = REV ? __shfl_down_sync(0xffffffffu, A, off) : __shfl_up_sync(0xffffffffu, A, off);
     const float bx = REV ? __shfl_down_sync(0xffffffffu, B.x, off) : __shfl_up_sync(0xffffffffu, B.x, off);
     const float by = REV ? __shfl_down_sync(0xffffffffu, B.y, off) : __shfl_up_sync(0xffffffffu, B.y, off);
-    const bool ok = REV ? (lane + off < 32) : (lane >= off);
-    if (ok) {
+    if (REV ? (lane + off < 32) : (lane >= off)) {
       B = make_float2(fmaf(A, bx, B.x), fmaf(A, by, B.y));
       A = A * Ap;
     }
   }
-  // warp totals: physical warp w holds logical block (REV: reversed)
-  const int w = threadIdx.x >> 5, nw = nt >> 5;
-  const bool tail = REV ? (lane == 0) : (lane == 31);
-  if (tail) {
-    sA[w] = A;
-    sB[w] = B;
+  float* sa = sA + par * 32;
+  float2* sb = sB + par * 32;
+  if (lane == (REV ? 0 : 31)) {
+    sa[w] = A;
+    sb[w] = B;
   }
   __syncthreads();
-  // prefix of the logically preceding warps
-  float Ap = 1.f;
   float2 Bp = make_float2(0.f, 0.f);
   if (!REV) {
-    for (int v = 0; v < w; ++v) {
-      Bp = make_float2(fmaf(sA[v], Bp.x, sB[v].x), fmaf(sA[v], Bp.y, sB[v].y));
-      Ap *= sA[v];
-    }
+    for (int v = 0; v < w; ++v) Bp = make_float2(fmaf(sa[v], Bp.x, sb[v].x), fmaf(sa[v], Bp.y, sb[v].y));
   } else {
-    for (int v = nw - 1; v > w; --v) {
-      Bp = make_float2(fmaf(sA[v], Bp.x, sB[v].x), fmaf(sA[v], Bp.y, sB[v].y));
-      Ap *= sA[v];
-    }
+    for (int v = nw - 1; v > w; --v) Bp = make_float2(fmaf(sa[v], Bp.x, sb[v].x), fmaf(sa[v], Bp.y, sb[v].y));
   }
-  // inclusive value of this thread including earlier warps (boundary 0)
-  const float2 inc = make_float2(fmaf(A, Bp.x, B.x), fmaf(A, Bp.y, B.y));
-  __syncthreads();
-  sB[32 + t] = inc;  // indexed by logical position
-  __syncthreads();
-  const float2 ex = t > 0 ? sB[32 + t - 1] : make_float2(0.f, 0.f);
-  __syncthreads();
-  (void)Ap;
-  return ex;
+  // inclusive value of the logically preceding lane, then the warp prefix
+  const float Ai = REV ? __shfl_down_sync(0xffffffffu, A, 1) : __shfl_up_sync(0xffffffffu, A, 1);
+  const float bix = REV ? __shfl_down_sync(0xffffffffu, B.x, 1) : __shfl_up_sync(0xffffffffu, B.x, 1);
+  const float biy = REV ? __shfl_down_sync(0xffffffffu, B.y, 1) : __shfl_up_sync(0xffffffffu, B.y, 1);
+  if (lane == (REV ? 31 : 0)) return Bp;
+  return make_float2(fmaf(Ai, Bp.x, bix), fmaf(Ai, Bp.y, biy));
 }
 
 constexpr int ILU_E = 4;
+constexpr int ILU_D = 4;  // ring stages (rows in flight: ILU_D - 1 ahead)
+// 16-byte chunk slots per thread and stage
+enum { FC_R0 = 0, FC_R1, FC_Q0, FC_Q1, FC_X0, FC_X1, FC_D0, FC_D1, FC_IA, FC_IB, FC_IC, FC_IBL, FCH };
+enum { BC_Y0 = 0, BC_Y1, BC_IA, BC_IB, BC_IC };
 
-__global__ void __launch_bounds__(512) k_ilu(int n, int mode, const SliceState* __restrict__ st,
+static int ilu_threads(int n) { return (n / ILU_E + 31) / 32 * 32; }
+static int ilu_smem(int n) { return ILU_D * FCH * ilu_threads(n) * 16; }
+
+__global__ void __launch_bounds__(128) k_ilu(int n, int mode, const SliceState* __restrict__ st,
                                              double* __restrict__ part, float2* __restrict__ x,
                                              const float2* __restrict__ d, float2* __restrict__ r,
                                              const float2* __restrict__ q, const float2* __restrict__ atb,
                                              float2* __restrict__ y, float2* __restrict__ z,
-                                             const float* __restrict__ ia, const float* __restrict__ pb,
-                                             const float* __restrict__ pc) {
+                                             const float* __restrict__ ia, const float* __restrict__ ib,
+                                             const float* __restrict__ ic) {
   const int s = blockIdx.x;
   if (!slice_running(st, s)) return;
-  __shared__ float sA[32];
-  __shared__ float2 sB[32 + 512];
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* ring = reinterpret_cast<float4*>(smem);
+  __shared__ float sA[64];
+  __shared__ float2 sB[64];
   __shared__ double red[32];
-  const int t = threadIdx.x;
+  const int T = blockDim.x, t = threadIdx.x;
   const int c0 = ILU_E * t;
   const bool own = c0 < n;
   const float alpha = (float)st[s].alpha;
   const size_t base = (size_t)s * n * n;
+  auto slot = [&](int stage, int ch) -> float4* { return ring + ((size_t)stage * FCH + ch) * T + t; };
+  const float2* rsrc = (mode == ILU_INIT) ? atb : r;
+
+  auto issue_fwd = [&](int row) {
+    if (row < n && own) {
+      const int stg = row % ILU_D;
+      const size_t g = base + (size_t)row * n + c0;
+      cp_async16(slot(stg, FC_R0), rsrc + g);
+      cp_async16(slot(stg, FC_R1), rsrc + g + 2);
+      cp_async16(slot(stg, FC_Q0), q + g);
+      cp_async16(slot(stg, FC_Q1), q + g + 2);
+      if (mode != ILU_INIT) {
+        cp_async16(slot(stg, FC_X0), x + g);
+        cp_async16(slot(stg, FC_X1), x + g + 2);
+        cp_async16(slot(stg, FC_D0), d + g);
+        cp_async16(slot(stg, FC_D1), d + g + 2);
+      }
+      cp_async16(slot(stg, FC_IA), ia + g);
+      cp_async16(slot(stg, FC_IB), ib + g);
+      cp_async16(slot(stg, FC_IC), ic + g);
+      if (c0 > 0) cp_async4(slot(stg, FC_IBL), ib + g - 1);
+    }
+    cp_async_commit();
+  };
+
   float2 yprev[ILU_E];
-  float mprev[ILU_E];
+  float icprev[ILU_E];
 #pragma unroll
   for (int e = 0; e < ILU_E; ++e) {
     yprev[e] = make_float2(0.f, 0.f);
-    mprev[e] = 0.f;
+    icprev[e] = 0.f;
   }
-  float rr = 0.f;
+  float rr = 0.f, rho = 0.f;
+  for (int k = 0; k < ILU_D - 1; ++k) issue_fwd(k);
   for (int row = 0; row < n; ++row) {
-    const size_t i0 = base + (size_t)row * n + c0;
+    issue_fwd(row + ILU_D - 1);
+    cp_async_wait<ILU_D - 1>();
+    const int stg = row % ILU_D;
     float A = 1.f;
     float2 B = make_float2(0.f, 0.f);
     float2 tv[ILU_E];
-    float iav[ILU_E], pbv[ILU_E], pcv[ILU_E];
+    float iav[ILU_E], ibv[ILU_E], icv[ILU_E], ibl = 0.f;
+    const size_t g = base + (size_t)row * n + c0;
     if (own) {
+      const float4 r0 = *slot(stg, FC_R0), r1 = *slot(stg, FC_R1);
+      const float4 q0 = *slot(stg, FC_Q0), q1 = *slot(stg, FC_Q1);
+      const float4 fa = *slot(stg, FC_IA), fb = *slot(stg, FC_IB), fc = *slot(stg, FC_IC);
+      if (c0 > 0) ibl = slot(stg, FC_IBL)->x;
+      float2 rv[ILU_E] = {make_float2(r0.x, r0.y), make_float2(r0.z, r0.w), make_float2(r1.x, r1.y),
+                          make_float2(r1.z, r1.w)};
+      const float2 qv[ILU_E] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y),
+                                make_float2(q1.z, q1.w)};
+      iav[0] = fa.x; iav[1] = fa.y; iav[2] = fa.z; iav[3] = fa.w;
+      ibv[0] = fb.x; ibv[1] = fb.y; ibv[2] = fb.z; ibv[3] = fb.w;
+      icv[0] = fc.x; icv[1] = fc.y; icv[2] = fc.z; icv[3] = fc.w;
+      if (mode == ILU_INIT) {
 #pragma unroll
-      for (int e = 0; e < ILU_E; ++e) {
-        float2 rv;
-        if (mode == ILU_INIT) {
-          rv = csub(atb[i0 + e], q[i0 + e]);
-        } else {
-          rv = cfma(-alpha, q[i0 + e], r[i0 + e]);
-          x[i0 + e] = cfma(alpha, d[i0 + e], x[i0 + e]);
+        for (int e = 0; e < ILU_E; ++e) rv[e] = csub(rv[e], qv[e]);
+      } else {
+        const float4 x0 = *slot(stg, FC_X0), x1 = *slot(stg, FC_X1);
+        const float4 d0 = *slot(stg, FC_D0), d1 = *slot(stg, FC_D1);
+        const float2 xv[ILU_E] = {make_float2(x0.x, x0.y), make_float2(x0.z, x0.w), make_float2(x1.x, x1.y),
+                                  make_float2(x1.z, x1.w)};
+        const float2 dv[ILU_E] = {make_float2(d0.x, d0.y), make_float2(d0.z, d0.w), make_float2(d1.x, d1.y),
+                                  make_float2(d1.z, d1.w)};
+        float2 xn[ILU_E];
+#pragma unroll
+        for (int e = 0; e < ILU_E; ++e) {
+          rv[e] = cfma(-alpha, qv[e], rv[e]);
+          xn[e] = cfma(alpha, dv[e], xv[e]);
         }
-        r[i0 + e] = rv;
-        rr += cabs2(rv);
-        iav[e] = ia[i0 + e];
-        pbv[e] = pb[i0 + e];
-        pcv[e] = pc[i0 + e];
-        tv[e] = cfma(-mprev[e], yprev[e], rv);
+        reinterpret_cast<float4*>(x + g)[0] = make_float4(xn[0].x, xn[0].y, xn[1].x, xn[1].y);
+        reinterpret_cast<float4*>(x + g)[1] = make_float4(xn[2].x, xn[2].y, xn[3].x, xn[3].y);
       }
-      float l = c0 > 0 ? pb[i0 - 1] * ia[i0 - 1] : 0.f;
+      reinterpret_cast<float4*>(r + g)[0] = make_float4(rv[0].x, rv[0].y, rv[1].x, rv[1].y);
+      reinterpret_cast<float4*>(r + g)[1] = make_float4(rv[2].x, rv[2].y, rv[3].x, rv[3].y);
 #pragma unroll
       for (int e = 0; e < ILU_E; ++e) {
-        if (e > 0) l = pbv[e - 1] * iav[e - 1];
+        rr += cabs2(rv[e]);
+        tv[e] = cfma(-icprev[e], yprev[e], rv[e]);
+        const float l = e == 0 ? ibl : ibv[e - 1];
         B = cfma(-l, B, tv[e]);
         A = -l * A;
       }
     }
-    float2 yin = affine_exclusive<false>(A, B, sA, sB);
+    float2 yin = affine_exclusive<false>(A, B, sA, sB, row & 1);
     if (own) {
-      float l = c0 > 0 ? pb[i0 - 1] * ia[i0 - 1] : 0.f;
+      float2 yv[ILU_E];
 #pragma unroll
       for (int e = 0; e < ILU_E; ++e) {
-        if (e > 0) l = pbv[e - 1] * iav[e - 1];
+        const float l = e == 0 ? ibl : ibv[e - 1];
         yin = cfma(-l, yin, tv[e]);
-        y[i0 + e] = yin;
+        yv[e] = yin;
+        rho = fmaf(iav[e], cabs2(yin), rho);
         yprev[e] = yin;
-        mprev[e] = pcv[e] * iav[e];
+        icprev[e] = icv[e];
       }
+      reinterpret_cast<float4*>(y + g)[0] = make_float4(yv[0].x, yv[0].y, yv[1].x, yv[1].y);
+      reinterpret_cast<float4*>(y + g)[1] = make_float4(yv[2].x, yv[2].y, yv[3].x, yv[3].y);
     }
   }
+  cp_async_wait<0>();
+  __syncthreads();
+
+  auto issue_bwd = [&](int k) {  // k-th row of the backward sweep: row n-1-k
+    if (k < n && own) {
+      const int row = n - 1 - k;
+      const int stg = k % ILU_D;
+      const size_t g = base + (size_t)row * n + c0;
+      cp_async16(slot(stg, BC_Y0), y + g);
+      cp_async16(slot(stg, BC_Y1), y + g + 2);
+      cp_async16(slot(stg, BC_IA), ia + g);
+      cp_async16(slot(stg, BC_IB), ib + g);
+      cp_async16(slot(stg, BC_IC), ic + g);
+    }
+    cp_async_commit();
+  };
   float2 znext[ILU_E];
 #pragma unroll
   for (int e = 0; e < ILU_E; ++e) znext[e] = make_float2(0.f, 0.f);
-  float rz = 0.f;
-  for (int row = n - 1; row >= 0; --row) {
-    const size_t i0 = base + (size_t)row * n + c0;
+  for (int k = 0; k < ILU_D - 1; ++k) issue_bwd(k);
+  for (int k = 0; k < n; ++k) {
+    issue_bwd(k + ILU_D - 1);
+    cp_async_wait<ILU_D - 1>();
+    const int stg = k % ILU_D;
+    const int row = n - 1 - k;
+    const size_t g = base + (size_t)row * n + c0;
     float A = 1.f;
     float2 B = make_float2(0.f, 0.f);
     float2 tv[ILU_E];
-    float iav[ILU_E], pbv[ILU_E];
+    float iav[ILU_E], ibv[ILU_E];
     if (own) {
-#pragma unroll
-      for (int e = 0; e < ILU_E; ++e) {
-        iav[e] = ia[i0 + e];
-        pbv[e] = pb[i0 + e];
-        tv[e] = cfma(-pc[i0 + e], znext[e], y[i0 + e]);
-      }
+      const float4 y0 = *slot(stg, BC_Y0), y1 = *slot(stg, BC_Y1);  // y of row n-1-k
+      const float4 fa = *slot(stg, BC_IA), fb = *slot(stg, BC_IB), fc = *slot(stg, BC_IC);
+      const float2 yv[ILU_E] = {make_float2(y0.x, y0.y), make_float2(y0.z, y0.w), make_float2(y1.x, y1.y),
+                                make_float2(y1.z, y1.w)};
+      const float icv[ILU_E] = {fc.x, fc.y, fc.z, fc.w};
+      iav[0] = fa.x; iav[1] = fa.y; iav[2] = fa.z; iav[3] = fa.w;
+      ibv[0] = fb.x; ibv[1] = fb.y; ibv[2] = fb.z; ibv[3] = fb.w;
 #pragma unroll
       for (int e = ILU_E - 1; e >= 0; --e) {
-        const float Ae = -iav[e] * pbv[e];
-        B = cfma(Ae, B, cscale(tv[e], iav[e]));
-        A = Ae * A;
+        tv[e] = cfma(-icv[e], znext[e], cscale(yv[e], iav[e]));  // ia y - ic z_{i+n}
+        B = cfma(-ibv[e], B, tv[e]);
+        A = -ibv[e] * A;
       }
     }
-    float2 zr = affine_exclusive<true>(A, B, sA, sB);
+    float2 zr = affine_exclusive<true>(A, B, sA, sB, k & 1);
     if (own) {
+      float2 zv[ILU_E];
 #pragma unroll
       for (int e = ILU_E - 1; e >= 0; --e) {
-        zr = cfma(-iav[e] * pbv[e], zr, cscale(tv[e], iav[e]));
-        z[i0 + e] = zr;
+        zr = cfma(-ibv[e], zr, tv[e]);
+        zv[e] = zr;
         znext[e] = zr;
-        rz += rdot2(r[i0 + e], zr);
       }
+      reinterpret_cast<float4*>(z + g)[0] = make_float4(zv[0].x, zv[0].y, zv[1].x, zv[1].y);
+      reinterpret_cast<float4*>(z + g)[1] = make_float4(zv[2].x, zv[2].y, zv[3].x, zv[3].y);
     }
   }
-  const double trz = block_sum((double)rz, red);
+  cp_async_wait<0>();
+  const double trz = block_sum((double)rho, red);
   __syncthreads();
   const double trr = block_sum((double)rr, red);
   if (threadIdx.x == 0) {
@@ -547,11 +842,14 @@ __global__ void __launch_bounds__(512) k_ilu(int n, int mode, const SliceState* 
   }
 }
 
+void ilu_prepare() {
+  cudaFuncSetAttribute(k_ilu, cudaFuncAttributeMaxDynamicSharedMemorySize, ILU_D * FCH * 128 * 16);
+}
+
 void ilu_step(int batch, int n, cudaStream_t s, const SliceState* st, double* part, int mode, float2* x,
               const float2* d, float2* r, const float2* q, const float2* atb, float2* y, float2* z,
-              const float* ia, const float* pb, const float* pc) {
-  int threads = (n / ILU_E + 31) / 32 * 32;
-  k_ilu<<<batch, threads, 0, s>>>(n, mode, st, part, x, d, r, q, atb, y, z, ia, pb, pc);
+              const float* ia, const float* ib, const float* ic) {
+  k_ilu<<<batch, ilu_threads(n), ilu_smem(n), s>>>(n, mode, st, part, x, d, r, q, atb, y, z, ia, ib, ic);
 }
 
 // =========================================================== PCG vectors ==

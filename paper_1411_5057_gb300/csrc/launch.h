@@ -55,7 +55,13 @@ struct WavArgs {
 void wavelet_forward(const WavArgs& a, const float2* x, float2* c, float* w, int mode);
 // x = Phi^T c; if r != null also partial Re<r, x> into SLOT_RZ.
 void wavelet_inverse(const WavArgs& a, const float2* c, float2* x, const float2* r, int real);
-int wavelet_inverse_ctas(int n);
+// u = Phi^T (s o Phi x), s = w (MUL_W) or 1/(abar + lam w) (MUL_PINV); levels
+// that fit in shared memory are fused (their coefficients stay on chip); the
+// fine levels' scaled details go through c.  Optional partial Re<r, u>.
+void wavelet_apply(const WavArgs& a, const float2* x, float2* c, float* w, int mode, float2* u,
+                   const float2* r, int real);
+int wavelet_inverse_ctas(int n, int levels);
+int wavelet_apply_launches(int n, int levels);
 void wav_prepare();
 
 // ---- TV, preconditioner, groups, PCG scalars ----
