@@ -209,6 +209,38 @@ firls_status firls_set_timing(firls_ctx* ctx, int enable);
  * the stream.  FIRLS_E_STATE if timing is off or nothing ran. */
 firls_status firls_get_timing(firls_ctx* ctx, double* ms, int* launches);
 
+/* ---- allocation-free A^H A (no counterpart in the paper) ----
+ * For callers that must not allocate device memory (code running inside
+ * another framework's memory pool or a real-time loop, where cudaMalloc /
+ * cudaFree would synchronise the device or break a fixed memory budget, and
+ * plug-ins that are handed only their input and output buffers).
+ *
+ * q = A^H A d for `batch` slices of n x n (same operation and kernels as
+ * firls_apply_AHA, without a context): mask device uint8 [batch][n][n],
+ * d and q device complex64 [batch][n][n], caller-owned; runs on the given
+ * stream (NULL = legacy default stream).
+ *
+ * Scratch: instead of allocating, the library keeps fixed-size __device__
+ * arrays (FFT intermediate of FIRLS_NOALLOC_MAX_ELEMS complex values, a
+ * twiddle table, per-slice state and partial sums: about 8.4 MB) that every
+ * GPU loading the library holds until the process exits.  Limits:
+ * batch * n * n <= FIRLS_NOALLOC_MAX_ELEMS and batch <= FIRLS_NOALLOC_MAX_BATCH;
+ * larger requests return FIRLS_E_SHAPE, as do unsupported n.  Null pointers
+ * return FIRLS_E_INVALID_ARG; a failed CUDA call FIRLS_E_CUDA.
+ *
+ * The first call on a device (it looks up the arrays' device addresses),
+ * and every call whose n differs from the previous call's on that device
+ * (it rewrites the twiddle table from a host buffer and synchronises the
+ * stream), must be made outside stream capture.  All calls share the same
+ * arrays, which keep the last call's contents; each call rewrites what it
+ * reads before reading it.  Calls that overlap on the GPU (different
+ * streams, or different host threads) race on the arrays: serialise them.
+ * No cudaMalloc, cudaFree or allocating library routine is called. */
+#define FIRLS_NOALLOC_MAX_ELEMS (1 << 20)
+#define FIRLS_NOALLOC_MAX_BATCH 64
+firls_status firls_apply_AHA_noalloc(int n, int batch, const uint8_t* mask, const void* d, void* q,
+                                     void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,7 @@ REAL_X = 1
 EXPORTED = ["firls_size_supported", "firls_create", "firls_set_operator", "firls_solve", "firls_solve_multi",
             "firls_last_error", "firls_destroy", "firls_apply_AHA", "firls_apply_Phi", "firls_apply_PhiT",
             "firls_apply_S_P", "firls_get_weights", "firls_get_inverse_map", "firls_get_popcounts",
-            "firls_set_timing", "firls_get_timing"]
+            "firls_set_timing", "firls_get_timing", "firls_apply_AHA_noalloc"]
 KERNEL_CLASSES = ["row_fft", "col_fft_mask", "wavelet_S", "wavelet_Pinv", "row_ifft_combine", "ilu", "axpy",
                   "scalars", "weights", "other"]
 
@@ -78,6 +78,7 @@ def lib():
     L.firls_get_weights.argtypes = [vp, vp, vp]
     L.firls_get_inverse_map.argtypes = [vp, vp, vp]
     L.firls_get_popcounts.argtypes = [vp, vp]
+    L.firls_apply_AHA_noalloc.argtypes = [i32, i32, vp, vp, vp, vp]
     L.firls_set_timing.argtypes = [vp, i32]
     L.firls_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
     _lib = L
