@@ -1,4 +1,4 @@
-// Mixed-radix (2/3/4/5/8) Stockham FFT of one length-N line held by T
+// Mixed-radix (2/3/4/5/8/16) Stockham FFT of one length-N line held by T
 // threads of one warp, E = N / T elements per thread in registers.
 //
 // Thread t holds elements t + T*s (s = 0..E-1) on entry and exit (natural
@@ -28,13 +28,13 @@ template <int N> struct FftCfg;
 FIRLS_FFT_CFG(16, 4, 2, 4, 4, 1, 1, 1)
 FIRLS_FFT_CFG(32, 4, 3, 2, 4, 4, 1, 1)
 FIRLS_FFT_CFG(48, 12, 3, 3, 4, 4, 1, 1)
-FIRLS_FFT_CFG(64, 4, 3, 4, 4, 4, 1, 1)
+FIRLS_FFT_CFG(64, 8, 2, 8, 8, 1, 1, 1)
 FIRLS_FFT_CFG(80, 20, 3, 5, 4, 4, 1, 1)
 FIRLS_FFT_CFG(96, 12, 4, 3, 4, 4, 2, 1)
-FIRLS_FFT_CFG(128, 8, 3, 8, 4, 4, 1, 1)
+FIRLS_FFT_CFG(128, 16, 2, 16, 8, 1, 1, 1)
 FIRLS_FFT_CFG(160, 20, 4, 5, 4, 4, 2, 1)
 FIRLS_FFT_CFG(192, 12, 4, 3, 4, 4, 4, 1)
-FIRLS_FFT_CFG(256, 8, 3, 8, 8, 4, 1, 1)
+FIRLS_FFT_CFG(256, 16, 2, 16, 16, 1, 1, 1)
 FIRLS_FFT_CFG(320, 20, 4, 5, 4, 4, 4, 1)
 FIRLS_FFT_CFG(384, 12, 5, 3, 4, 4, 4, 2)
 FIRLS_FFT_CFG(512, 16, 3, 8, 8, 8, 1, 1)
@@ -125,6 +125,43 @@ template <int DIR> struct Dft<5, DIR> {
     a[4] = csub(b1, ig1);
     a[2] = cadd(b2, ig2);
     a[3] = csub(b2, ig2);
+  }
+};
+
+// 16 = 4 x 4: four 4-point DFTs over n1 (stride 4), twiddles w16^(n2 k1),
+// four 4-point DFTs over n2; output k1 + 4 k2.
+template <int DIR> struct Dft<16, DIR> {
+  static FI void run(float2* a) {
+    const float c1 = 0.92387953251128674f;  // cos(pi/8)
+    const float s1 = 0.38268343236508977f;  // sin(pi/8)
+    const float h = 0.70710678118654752f;
+    float2 b[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      float2 t[4] = {a[n2], a[4 + n2], a[8 + n2], a[12 + n2]};
+      Dft<4, DIR>::run(t);
+#pragma unroll
+      for (int k1 = 0; k1 < 4; ++k1) b[n2][k1] = t[k1];
+    }
+    // w16^j = (cos(2 pi j/16), DIR sin(2 pi j/16)) for j = n2 * k1
+    const float2 w1 = make_float2(c1, DIR * s1), w2 = make_float2(h, DIR * h), w3 = make_float2(s1, DIR * c1);
+    const float2 w6 = make_float2(-h, DIR * h), w9 = make_float2(-c1, -DIR * s1);
+    b[1][1] = cmul(b[1][1], w1);
+    b[1][2] = cmul(b[1][2], w2);
+    b[1][3] = cmul(b[1][3], w3);
+    b[2][1] = cmul(b[2][1], w2);
+    b[2][2] = mul_i<DIR>(b[2][2]);  // w16^4 = DIR i
+    b[2][3] = cmul(b[2][3], w6);
+    b[3][1] = cmul(b[3][1], w3);
+    b[3][2] = cmul(b[3][2], w6);
+    b[3][3] = cmul(b[3][3], w9);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      float2 t[4] = {b[0][k1], b[1][k1], b[2][k1], b[3][k1]};
+      Dft<4, DIR>::run(t);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) a[k1 + 4 * k2] = t[k2];
+    }
   }
 };
 

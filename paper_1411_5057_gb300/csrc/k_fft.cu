@@ -257,9 +257,13 @@ __global__ void __launch_bounds__(256) k_row_inv(const float2* __restrict__ tbuf
   const int lr = threadIdx.x / T, t = threadIdx.x % T;
   const int row = r0 + lr;
   const size_t base = sbase + (size_t)row * N;
-  float2 v[E];
+  float2 v[E], uv[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) v[e] = tbuf[base + t + T * e];
+  if (u) {  // in flight during the FFT
+#pragma unroll
+    for (int e = 0; e < E; ++e) uv[e] = u[base + t + T * e];
+  }
   __syncthreads();
   fft_line<N, +1>(v, lines + lr * 2 * LW, lines + lr * 2 * LW + LW, tw, t);
   const float sc = 1.0f / ((float)N * (float)N);
@@ -284,7 +288,7 @@ __global__ void __launch_bounds__(256) k_row_inv(const float2* __restrict__ tbuf
     } else {
       dc = d[base + col];
     }
-    if (u) a = cfma(lam, u[base + col], a);
+    if (u) a = cfma(lam, uv[e], a);
     q[base + col] = a;
     acc += rdot2(dc, a);
   }

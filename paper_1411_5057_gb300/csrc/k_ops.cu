@@ -54,8 +54,8 @@ FI void inv_haar(float2 a, float2 d, float2& x0, float2& x1) {
 
 constexpr int WAV_THREADS = 256;
 constexpr int WAV_RB = 8;            // output row pairs per CTA of a tiled level
-constexpr int COARSE_MAX = 128;      // largest block kept whole in shared memory
-constexpr int COARSE_THREADS = 512;
+constexpr int COARSE_MAX = 64;       // largest block kept whole in shared memory
+constexpr int COARSE_THREADS = 256;
 
 static int wav_rb(int m) { return m / 2 < WAV_RB ? m / 2 : WAV_RB; }
 
