@@ -246,6 +246,21 @@ def test_firls_tv_db4_converged_parity(F):
     assert rel(x, x_star) < TOL_SOLVE
 
 
+def test_bench_workload_reaches_converged_oracle(F):
+    """The bench workload (256^2 TV + D4, seed 2) at the bench schedule lands
+    within 1e-4 of the FP64 oracle's converged minimiser x*.
+
+    x* is stored as a strided sample (every 4th row and column) written by
+    tests/golden/make_xstar.py, which calls only the oracle.
+    """
+    import os
+    import bench
+    xs = np.load(os.path.join(os.path.dirname(__file__), "golden", "xstar_tv_db4_256_seed2_stride4.npy"))
+    p = bench.problem(2)
+    x = _gpu_solve(F, [p], bench.OUTER, bench.INNER)[0]
+    assert rel(x[::4, ::4], xs) < TOL_SOLVE, rel(x[::4, ::4], xs)
+
+
 def test_batch_slices_independent(F):
     """A batch of different slices gives each slice's single-slice result exactly."""
     probs = [fs.make_problem(64, r, 0.01, s, real=False, psi=6, levels=3, lam=3e-4, lam_tv=8e-4)
