@@ -217,3 +217,32 @@ def uneven_batch(first_seed: int = 1000, per_size: int = 16) -> list[Problem]:
                                     lam=lam_tv / 2, lam_tv=lam_tv))
             s += 1
     return out
+
+
+# --- learned warm start: architecture and seeded initial weights ------------
+
+CNN_CHANNELS = (3, 32, 32, 32, 32, 32, 2)   # input: Re A^H b, Im A^H b, mask
+
+
+def cnn_init_weights(seed: int = 0):
+    """He-normal initial weights of the 6-layer 3x3 CNN, float32.
+
+    Returns a list of (w [3][3][c_in][c_out], b [c_out]); the last layer starts
+    at zero so that the untrained network returns A^H b unchanged.
+    """
+    rng = _rng(seed, PARAMS + 1)
+    out = []
+    layers = len(CNN_CHANNELS) - 1
+    for l in range(layers):
+        cin, cout = CNN_CHANNELS[l], CNN_CHANNELS[l + 1]
+        std = math.sqrt(2.0 / (9 * cin))
+        w = (rng.standard_normal((3, 3, cin, cout)) * std).astype(np.float32)
+        if l == layers - 1:
+            w[:] = 0.0
+        out.append((w, np.zeros(cout, dtype=np.float32)))
+    return out
+
+
+def cnn_input(atb: np.ndarray, mask: np.ndarray) -> np.ndarray:
+    """Network input [n][n][3]: Re A^H b, Im A^H b, mask (as float)."""
+    return np.stack([atb.real, atb.imag, mask.astype(np.float64)], axis=-1)

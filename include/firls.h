@@ -209,6 +209,42 @@ firls_status firls_set_timing(firls_ctx* ctx, int enable);
  * the stream.  FIRLS_E_STATE if timing is off or nothing ran. */
 firls_status firls_get_timing(firls_ctx* ctx, double* ms, int* launches);
 
+/* ---- learned warm start (not in the paper; workload of the learned variant) ----
+ * A 6-layer 3x3 CNN (3 -> 32 -> 32 -> 32 -> 32 -> 32 -> 2 channels, ReLU between
+ * layers, zero padding) maps [Re A^H b, Im A^H b, mask] to a correction:
+ * x1 = A^H b + CNN(.), used as the FIRLS warm start (firls_solve's x0).  BF16
+ * weights and activations (NHWC), FP32 accumulation on the tensor cores, FP32
+ * master weights with Adam (beta 0.9 / 0.999, eps 1e-8).  Loss: sum |x1 - x*|^2. */
+typedef struct firls_cnn firls_cnn;
+
+/* Network for `batch` images of n x n (n a multiple of 32); allocates
+ * weights, optimiser state and activations on the current device.  The
+ * parameters are undefined until firls_cnn_set_params. */
+firls_status firls_cnn_create(firls_cnn** out, int n, int batch, void* cuda_stream);
+
+/* Set the FP32 parameters (host arrays, one per layer): w[l] is
+ * [3][3][c_in][c_out] (row tap, column tap, input, output channel), b[l]
+ * [c_out].  Resets the Adam state.  Synchronises the stream. */
+firls_status firls_cnn_set_params(firls_cnn* net, const float* const* w, const float* const* b);
+
+/* Copy the FP32 parameters / the last step's gradients to host arrays
+ * (same layout; NULL entries are skipped).  Synchronise the stream. */
+firls_status firls_cnn_get_params(firls_cnn* net, float* const* w, float* const* b);
+firls_status firls_cnn_get_grads(firls_cnn* net, float* const* dw, float* const* db);
+
+/* x1 = A^H b + CNN([Re A^H b, Im A^H b, mask]) for the batch: atb and x1
+ * device complex64 [batch][n][n], mask device uint8 [batch][n][n]. */
+firls_status firls_cnn_forward(firls_cnn* net, const void* atb, const uint8_t* mask, void* x1);
+
+/* One training step on the batch: forward (x1 written), loss
+ * sum |x1 - target|^2, backward, Adam update with learning rate lr.
+ * target device complex64 [batch][n][n]; loss (host, may be NULL) receives
+ * the loss before the update (synchronises when non-NULL). */
+firls_status firls_cnn_train_step(firls_cnn* net, const void* atb, const uint8_t* mask, const void* target,
+                                  void* x1, float lr, double* loss);
+
+void firls_cnn_destroy(firls_cnn* net);
+
 /* ---- allocation-free A^H A (no counterpart in the paper) ----
  * For callers that must not allocate device memory (code running inside
  * another framework's memory pool or a real-time loop, where cudaMalloc /

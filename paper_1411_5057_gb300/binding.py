@@ -22,7 +22,9 @@ REAL_X = 1
 EXPORTED = ["firls_size_supported", "firls_create", "firls_set_operator", "firls_solve", "firls_solve_multi",
             "firls_last_error", "firls_destroy", "firls_apply_AHA", "firls_apply_Phi", "firls_apply_PhiT",
             "firls_apply_S_P", "firls_get_weights", "firls_get_inverse_map", "firls_get_popcounts",
-            "firls_set_timing", "firls_get_timing", "firls_apply_AHA_noalloc"]
+            "firls_set_timing", "firls_get_timing", "firls_apply_AHA_noalloc",
+            "firls_cnn_create", "firls_cnn_set_params", "firls_cnn_get_params", "firls_cnn_get_grads",
+            "firls_cnn_forward", "firls_cnn_train_step", "firls_cnn_destroy"]
 KERNEL_CLASSES = ["row_fft", "col_fft_mask", "wavelet_S", "wavelet_Pinv", "row_ifft_combine", "ilu", "axpy",
                   "scalars", "weights", "other"]
 
@@ -79,6 +81,15 @@ def lib():
     L.firls_get_inverse_map.argtypes = [vp, vp, vp]
     L.firls_get_popcounts.argtypes = [vp, vp]
     L.firls_apply_AHA_noalloc.argtypes = [i32, i32, vp, vp, vp, vp]
+    fpp = ctypes.POINTER(ctypes.c_void_p)
+    L.firls_cnn_create.argtypes = [ctypes.POINTER(vp), i32, i32, vp]
+    L.firls_cnn_set_params.argtypes = [vp, fpp, fpp]
+    L.firls_cnn_get_params.argtypes = [vp, fpp, fpp]
+    L.firls_cnn_get_grads.argtypes = [vp, fpp, fpp]
+    L.firls_cnn_forward.argtypes = [vp, vp, vp, vp]
+    L.firls_cnn_train_step.argtypes = [vp, vp, vp, vp, vp, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
+    L.firls_cnn_destroy.argtypes = [vp]
+    L.firls_cnn_destroy.restype = None
     L.firls_set_timing.argtypes = [vp, i32]
     L.firls_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
     _lib = L
@@ -210,3 +221,79 @@ def solve_multi(ctxs, bs, params, outs, x0s=None, stats=False):
     if st != FIRLS_OK:
         raise FirlsError(st, "solve_multi: " + (lib().firls_last_error(ctxs[0].h) or b"").decode())
     return [s.as_dict() for s in S] if stats else None
+
+
+CNN_CHANNELS = (3, 32, 32, 32, 32, 32, 2)
+
+
+class Cnn:
+    """The learned warm start: x1 = A^H b + CNN([Re A^H b, Im A^H b, mask])."""
+
+    def __init__(self, n, batch, stream=None):
+        import torch
+        self._torch = torch
+        self.n, self.batch = int(n), int(batch)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = lib().firls_cnn_create(ctypes.byref(h), self.n, self.batch, ctypes.c_void_p(self.stream.cuda_stream))
+        if st != FIRLS_OK:
+            raise FirlsError(st, f"firls_cnn_create(n={n}, batch={batch})")
+        self.h = h
+
+    def _arrays(self, arrs):
+        import numpy as np
+        keep = [np.ascontiguousarray(a, dtype=np.float32) for a in arrs]
+        ptrs = (ctypes.c_void_p * len(keep))(*[a.ctypes.data for a in keep])
+        return keep, ptrs
+
+    def set_params(self, params):
+        """params: list of (w [3][3][cin][cout], b [cout]) float arrays."""
+        kw, pw = self._arrays([w for w, _ in params])
+        kb, pb = self._arrays([b for _, b in params])
+        st = lib().firls_cnn_set_params(self.h, pw, pb)
+        if st != FIRLS_OK:
+            raise FirlsError(st, "firls_cnn_set_params")
+
+    def _get(self, fn):
+        import numpy as np
+        ws = [np.zeros((3, 3, CNN_CHANNELS[l], CNN_CHANNELS[l + 1]), np.float32) for l in range(6)]
+        bs = [np.zeros(CNN_CHANNELS[l + 1], np.float32) for l in range(6)]
+        pw = (ctypes.c_void_p * 6)(*[a.ctypes.data for a in ws])
+        pb = (ctypes.c_void_p * 6)(*[a.ctypes.data for a in bs])
+        st = fn(self.h, pw, pb)
+        if st != FIRLS_OK:
+            raise FirlsError(st, "firls_cnn_get")
+        return list(zip(ws, bs))
+
+    def get_params(self):
+        return self._get(lib().firls_cnn_get_params)
+
+    def get_grads(self):
+        return self._get(lib().firls_cnn_get_grads)
+
+    def forward(self, atb, mask, out=None):
+        out = self._torch.empty_like(atb) if out is None else out
+        st = lib().firls_cnn_forward(self.h, _ptr(atb), _ptr(mask), _ptr(out))
+        if st != FIRLS_OK:
+            raise FirlsError(st, "firls_cnn_forward")
+        return out
+
+    def train_step(self, atb, mask, target, lr, out=None, want_loss=True):
+        out = self._torch.empty_like(atb) if out is None else out
+        loss = ctypes.c_double()
+        st = lib().firls_cnn_train_step(self.h, _ptr(atb), _ptr(mask), _ptr(target), _ptr(out), ctypes.c_float(lr),
+                                        ctypes.byref(loss) if want_loss else None)
+        if st != FIRLS_OK:
+            raise FirlsError(st, "firls_cnn_train_step")
+        return loss.value if want_loss else None
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().firls_cnn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
