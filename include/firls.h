@@ -110,6 +110,12 @@ typedef struct {
   float eps;        /* smoothing eps of Eq. gw / Eq. wi; <= 0 selects 1e-10   */
   const float* lambda_per_slice;    /* host [batch] or NULL (use lambda)      */
   const float* lambda_tv_per_slice; /* host [batch] or NULL (use lambda_tv)   */
+  int outer_tol_kind;  /* 0: stop when the relative change <= outer_tol;
+                          1: stop when the estimated distance to the limit,
+                          relchg * mu / (1 - mu) with the contraction
+                          mu = sqrt(relchg_k / relchg_{k-2}) (linear
+                          convergence), and the relative change are both
+                          <= outer_tol (after >= 4 outer steps)               */
 } firls_params;
 
 typedef struct {
@@ -136,10 +142,14 @@ firls_status firls_solve(firls_ctx* ctx, const void* b, const firls_params* para
                          const void* x0, void* x_out, firls_stats* stats);
 
 /* Solve several contexts (slices of different sizes, e.g. 128^2 .. 320^2)
- * as one CUDA-graph launch: each context's work is captured on a forked
- * stream and joined back onto ctxs[0]'s stream.  Arrays have n_ctx
- * entries; params apply to every context.  Same buffer rules as
- * firls_solve.  stats (host, may be NULL) has n_ctx entries. */
+ * together: one outer step of every context is captured as ONE CUDA graph
+ * (forked from ctxs[0]'s stream onto each context's own stream and joined
+ * back) and replayed outer_iters times on ctxs[0]'s stream.  Arrays have
+ * n_ctx entries, params included (per-context lambdas); the schedule and
+ * tolerances must be equal in all of them.  Contexts must have distinct,
+ * non-default streams for the graph; otherwise the steps are enqueued
+ * directly.  Same buffer rules as firls_solve; results are ordered on
+ * ctxs[0]'s stream.  stats (host, may be NULL) has n_ctx entries. */
 firls_status firls_solve_multi(firls_ctx* const* ctxs, int n_ctx,
                                const void* const* b, const firls_params* params,
                                const void* const* x0, void* const* x_out,
@@ -170,6 +180,68 @@ firls_status firls_apply_PhiT(firls_ctx* ctx, const void* c, void* x);
 firls_status firls_apply_S_P(firls_ctx* ctx, const firls_params* params,
                              const void* x, const void* d, void* q,
                              const void* r, void* z);
+
+/* ---- continuous batching (serving) ----
+ * Slots of a context hold independent slices at different stages of their
+ * solve.  A slice that has converged (outer_tol) or reached the caller's cap
+ * is read out and its slot reloaded with the next slice while the other
+ * slots keep iterating, so throughput follows the average number of outer
+ * steps per slice instead of the slowest slice of a fixed batch.
+ *
+ * firls_slot_load: put one slice into slot s: copy its mask (device uint8
+ *   [n][n]) and k-space b (device complex64 [n][n]), compute its A^H b and
+ *   popcount, start from x0 (device, one slice) or A^H b, reset its state
+ *   with its own lambdas (eps <= 0 selects 1e-10).  Other slots untouched.
+ * firls_run: enqueue params->outer_iters outer steps of every slot that is
+ *   not done (one captured graph per step; no host synchronisation).
+ * firls_slot_status: per-slot done flag, outer steps and last relative
+ *   change (host arrays [batch], each may be NULL); synchronises.
+ * firls_slot_retire: slot s stops taking part until reloaded.
+ * firls_slot_get: copy slot s's current x (device complex64 [n][n]). */
+firls_status firls_slot_load(firls_ctx* ctx, int s, const uint8_t* mask, const void* b, const void* x0,
+                             float lambda, float lambda_tv, float eps);
+firls_status firls_run(firls_ctx* ctx, const firls_params* params);
+firls_status firls_slot_status(firls_ctx* ctx, int* done, int* outer_done, double* rel_change);
+firls_status firls_slot_retire(firls_ctx* ctx, int s);
+firls_status firls_slot_get(firls_ctx* ctx, int s, void* x_out);
+
+/* Autotuner: time the tile-shape choices of this context's size, batch and
+ * regulariser on its own buffers (CUDA events on its stream) and keep the
+ * fastest: rows per CTA of the tiled wavelet levels (4, 8, 16), the largest
+ * wavelet block kept in shared memory (32, 64), the ILU row-prefetch depth
+ * (3, 4, 6 stages).  cache_path (may be NULL) is a text file of earlier
+ * results keyed by "n batch psi levels": a hit skips the timing, a miss
+ * appends the new result.  Overwrites the context's workspace; call after
+ * firls_set_operator and before solving.  Synchronises the stream. */
+firls_status firls_autotune(firls_ctx* ctx, const char* cache_path);
+
+/* The tile shapes in use (0 = built-in default). */
+firls_status firls_get_tuning(const firls_ctx* ctx, int* rows_per_cta, int* coarse_max, int* ilu_depth);
+
+/* atb = A^H b = F^H R^T b (real unknown: its real part), the zero-filled
+ * reconstruction and x^1 of Sec. 3.3.  b, atb device complex64 [batch][n][n]. */
+firls_status firls_adjoint(firls_ctx* ctx, const void* b, void* atb);
+
+/* out = F^H((1 - R) F x + R b): keeps x's unsampled k-space and restores the
+ * measured entries (data consistency of a warm start; A out = b exactly, so
+ * its data term of F is zero like that of A^H b).  b, x, out device complex64
+ * [batch][n][n]; out may alias x.  Real unknown: the real part. */
+firls_status firls_data_consistency(firls_ctx* ctx, const void* b, const void* x, void* out);
+
+/* F_eps(x) per slice: 1/2 ||A x - b||^2 + lambda sum_g sqrt(||(G Phi x)_g||^2 + eps)
+ * + lambda_tv sum_i sqrt(|(D1 x)_i|^2 + |(D2 x)_i|^2 + eps) (Eq. anapro / iso with the
+ * eps of Eq. gw / wi; Theorem 2 says FIRLS never increases it).  b, x device
+ * complex64 [batch][n][n]; out host double [batch]; lambdas / eps from params.
+ * Synchronises the stream. */
+firls_status firls_objective(firls_ctx* ctx, const void* b, const firls_params* params, const void* x,
+                             double* out);
+
+/* Warm-start guard of the learned variant: per slice, x0 = x1 when
+ * F_eps(x1) <= F_eps(A^H b), otherwise x0 = A^H b (the plain start).  x1, x0
+ * device complex64 [batch][n][n] (x0 may not alias x1); chosen (host int
+ * [batch], may be NULL) receives 1 where x1 was kept.  Synchronises. */
+firls_status firls_warm_start_guard(firls_ctx* ctx, const void* b, const firls_params* params, const void* x1,
+                                    void* x0, int* chosen);
 
 /* Copy out the current per-coefficient wavelet weights diag(G^T W G)
  * (device float [batch][n][n]) and TV weights (device float [batch][n][n]);

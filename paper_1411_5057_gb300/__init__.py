@@ -5,7 +5,7 @@ The compute lives in the CUDA library ``libfirls.so`` (C ABI in
 step (``build.py``) and a thin ctypes binding (``binding.py``).
 """
 from .binding import (Cnn, PSI_DB4, PSI_HAAR, PSI_TV, Context, FirlsError, Params, Stats, lib, make_params,
-                      size_supported, solve_multi)
+                      serve, size_supported, solve_multi)
 
 __all__ = ["Cnn", "PSI_DB4", "PSI_HAAR", "PSI_TV", "Context", "FirlsError", "Params", "Stats", "lib", "make_params",
-           "size_supported", "solve_multi"]
+           "serve", "size_supported", "solve_multi"]

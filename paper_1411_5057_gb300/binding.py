@@ -24,7 +24,10 @@ EXPORTED = ["firls_size_supported", "firls_create", "firls_set_operator", "firls
             "firls_apply_S_P", "firls_get_weights", "firls_get_inverse_map", "firls_get_popcounts",
             "firls_set_timing", "firls_get_timing", "firls_apply_AHA_noalloc",
             "firls_cnn_create", "firls_cnn_set_params", "firls_cnn_get_params", "firls_cnn_get_grads",
-            "firls_cnn_forward", "firls_cnn_train_step", "firls_cnn_destroy"]
+            "firls_cnn_forward", "firls_cnn_train_step", "firls_cnn_destroy", "firls_objective",
+            "firls_warm_start_guard", "firls_adjoint", "firls_data_consistency", "firls_autotune",
+            "firls_get_tuning", "firls_slot_load", "firls_run", "firls_slot_status", "firls_slot_retire",
+            "firls_slot_get"]
 KERNEL_CLASSES = ["row_fft", "col_fft_mask", "wavelet_S", "wavelet_Pinv", "row_ifft_combine", "ilu", "axpy",
                   "scalars", "weights", "other"]
 
@@ -39,7 +42,7 @@ class Params(ctypes.Structure):
     _fields_ = [("outer_iters", ctypes.c_int), ("pcg_iters", ctypes.c_int), ("pcg_tol", ctypes.c_float),
                 ("outer_tol", ctypes.c_float), ("lambda_", ctypes.c_float), ("lambda_tv", ctypes.c_float),
                 ("eps", ctypes.c_float), ("lambda_per_slice", ctypes.POINTER(ctypes.c_float)),
-                ("lambda_tv_per_slice", ctypes.POINTER(ctypes.c_float))]
+                ("lambda_tv_per_slice", ctypes.POINTER(ctypes.c_float)), ("outer_tol_kind", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -81,6 +84,17 @@ def lib():
     L.firls_get_inverse_map.argtypes = [vp, vp, vp]
     L.firls_get_popcounts.argtypes = [vp, vp]
     L.firls_apply_AHA_noalloc.argtypes = [i32, i32, vp, vp, vp, vp]
+    L.firls_objective.argtypes = [vp, vp, ctypes.POINTER(Params), vp, ctypes.POINTER(ctypes.c_double)]
+    L.firls_adjoint.argtypes = [vp, vp, vp]
+    L.firls_autotune.argtypes = [vp, ctypes.c_char_p]
+    L.firls_slot_load.argtypes = [vp, i32, vp, vp, vp, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+    L.firls_run.argtypes = [vp, ctypes.POINTER(Params)]
+    L.firls_slot_status.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]
+    L.firls_slot_retire.argtypes = [vp, i32]
+    L.firls_slot_get.argtypes = [vp, i32, vp]
+    L.firls_get_tuning.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.firls_data_consistency.argtypes = [vp, vp, vp, vp]
+    L.firls_warm_start_guard.argtypes = [vp, vp, ctypes.POINTER(Params), vp, vp, ctypes.POINTER(ctypes.c_int)]
     fpp = ctypes.POINTER(ctypes.c_void_p)
     L.firls_cnn_create.argtypes = [ctypes.POINTER(vp), i32, i32, vp]
     L.firls_cnn_set_params.argtypes = [vp, fpp, fpp]
@@ -105,8 +119,9 @@ def size_supported(n: int) -> bool:
 
 
 def make_params(outer, pcg, lam=0.0, lam_tv=0.0, pcg_tol=0.0, outer_tol=0.0, eps=0.0,
-                lam_per_slice=None, lam_tv_per_slice=None):
+                lam_per_slice=None, lam_tv_per_slice=None, stop_on_distance=False):
     p = Params()
+    p.outer_tol_kind = 1 if stop_on_distance else 0
     p.outer_iters, p.pcg_iters = int(outer), int(pcg)
     p.pcg_tol, p.outer_tol = float(pcg_tol), float(outer_tol)
     p.lambda_, p.lambda_tv, p.eps = float(lam), float(lam_tv), float(eps)
@@ -188,6 +203,62 @@ class Context:
         self._check(lib().firls_apply_S_P(self.h, ctypes.byref(params), _ptr(x), _ptr(d), _ptr(q), _ptr(r),
                                           _ptr(z)), "apply_S_P")
 
+    # ---- continuous batching ----
+    def slot_load(self, s, mask, b, lam, lam_tv, x0=None, eps=0.0):
+        self._check(lib().firls_slot_load(self.h, int(s), _ptr(mask), _ptr(b), _ptr(x0), float(lam), float(lam_tv),
+                                          float(eps)), "slot_load")
+
+    def run(self, params):
+        self._check(lib().firls_run(self.h, ctypes.byref(params)), "run")
+
+    def slot_status(self):
+        k = self.batch
+        done, od, rc = (ctypes.c_int * k)(), (ctypes.c_int * k)(), (ctypes.c_double * k)()
+        self._check(lib().firls_slot_status(self.h, done, od, rc), "slot_status")
+        return list(done), list(od), list(rc)
+
+    def slot_retire(self, s):
+        self._check(lib().firls_slot_retire(self.h, int(s)), "slot_retire")
+
+    def slot_get(self, s, out):
+        self._check(lib().firls_slot_get(self.h, int(s), _ptr(out)), "slot_get")
+
+    def autotune(self, cache_path=None):
+        """Time the tile-shape choices on this context and keep the fastest."""
+        self._check(lib().firls_autotune(self.h, cache_path.encode() if cache_path else None), "autotune")
+        return self.tuning()
+
+    def tuning(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(lib().firls_get_tuning(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "tuning")
+        return {"rows_per_cta": a.value, "coarse_max": b.value, "ilu_depth": c.value}
+
+    def adjoint(self, b, out=None):
+        """A^H b (the zero-filled reconstruction)."""
+        out = self._torch.empty((self.batch, self.n, self.n), dtype=self._torch.complex64,
+                                device=b.device) if out is None else out
+        self._check(lib().firls_adjoint(self.h, _ptr(b), _ptr(out)), "adjoint")
+        return out
+
+    def data_consistency(self, b, x, out=None):
+        """F^H((1 - R) F x + R b)."""
+        out = self._torch.empty_like(x) if out is None else out
+        self._check(lib().firls_data_consistency(self.h, _ptr(b), _ptr(x), _ptr(out)), "data_consistency")
+        return out
+
+    def objective(self, b, params, x):
+        """F_eps per slice (host list of floats)."""
+        out = (ctypes.c_double * self.batch)()
+        self._check(lib().firls_objective(self.h, _ptr(b), ctypes.byref(params), _ptr(x), out), "objective")
+        return list(out)
+
+    def warm_start_guard(self, b, params, x1, x0):
+        """x0 = x1 where F_eps(x1) <= F_eps(A^H b), else A^H b; returns the per-slice choice."""
+        ch = (ctypes.c_int * self.batch)()
+        self._check(lib().firls_warm_start_guard(self.h, _ptr(b), ctypes.byref(params), _ptr(x1), _ptr(x0), ch),
+                    "warm_start_guard")
+        return [bool(v) for v in ch]
+
     def get_weights(self, w_wavelet=None, w_tv=None):
         self._check(lib().firls_get_weights(self.h, _ptr(w_wavelet), _ptr(w_tv)), "get_weights")
 
@@ -210,14 +281,16 @@ class Context:
 
 
 def solve_multi(ctxs, bs, params, outs, x0s=None, stats=False):
-    """One call over contexts of different sizes (forked streams)."""
+    """One call over contexts of different sizes: one CUDA graph per outer
+    step; `params` is one Params per context (same schedule)."""
     k = len(ctxs)
+    P = (Params * k)(*params)
     H = (ctypes.c_void_p * k)(*[c.h for c in ctxs])
     B = (ctypes.c_void_p * k)(*[b.data_ptr() for b in bs])
     O = (ctypes.c_void_p * k)(*[o.data_ptr() for o in outs])
     X = (ctypes.c_void_p * k)(*[x.data_ptr() for x in x0s]) if x0s is not None else None
     S = (Stats * k)() if stats else None
-    st = lib().firls_solve_multi(H, k, B, ctypes.byref(params), X, O, S)
+    st = lib().firls_solve_multi(H, k, B, P, X, O, S)
     if st != FIRLS_OK:
         raise FirlsError(st, "solve_multi: " + (lib().firls_last_error(ctxs[0].h) or b"").decode())
     return [s.as_dict() for s in S] if stats else None
@@ -297,3 +370,55 @@ class Cnn:
             self.close()
         except Exception:
             pass
+
+
+def serve(ctx, masks, bs, lams, lam_tvs, params, outs, x0s=None, chunk=8, max_outer=400, stop_after=None):
+    """Continuous batching over a queue of slices with ctx.batch slots.
+
+    masks/bs/outs: per-slice device tensors ([n][n]); lams/lam_tvs: floats;
+    params: schedule (pcg_iters, tolerances; outer_iters ignored).  A slot is
+    read out and refilled when its slice has converged (params.outer_tol) or
+    reached max_outer outer steps.  With stop_after, returns once that many
+    slices have completed and retires the slices still in flight (their
+    entry in the result stays 0).  Returns the outer steps of every slice.
+    """
+    q = len(bs)
+    steps = [0] * q
+    slot_of = [-1] * ctx.batch
+    nxt = 0
+    for s in range(ctx.batch):
+        if nxt < q:
+            ctx.slot_load(s, masks[nxt], bs[nxt], lams[nxt], lam_tvs[nxt], None if x0s is None else x0s[nxt])
+            slot_of[s] = nxt
+            nxt += 1
+        else:
+            ctx.slot_retire(s)
+    run = Params.from_buffer_copy(params)
+    run.outer_iters = chunk
+    active = sum(1 for v in slot_of if v >= 0)
+    completed = 0
+    while active:
+        if stop_after is not None and completed >= stop_after:
+            for s in range(ctx.batch):
+                if slot_of[s] >= 0:
+                    ctx.slot_retire(s)
+                    slot_of[s] = -1
+            break
+        ctx.run(run)
+        done, od, _ = ctx.slot_status()
+        for s in range(ctx.batch):
+            i = slot_of[s]
+            if i < 0 or not (done[s] or od[s] >= max_outer):
+                continue
+            ctx.slot_get(s, outs[i])
+            steps[i] = od[s]
+            completed += 1
+            if nxt < q:
+                ctx.slot_load(s, masks[nxt], bs[nxt], lams[nxt], lam_tvs[nxt], None if x0s is None else x0s[nxt])
+                slot_of[s] = nxt
+                nxt += 1
+            else:
+                ctx.slot_retire(s)
+                slot_of[s] = -1
+                active -= 1
+    return steps

@@ -5,6 +5,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
+#include <functional>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -36,6 +38,8 @@ struct firls_ctx {
   int *gcounts = nullptr, *gcursor = nullptr, *gerr = nullptr;
   float* sqtab = nullptr;
   int* sqlen = nullptr;
+  // tile shapes (autotuned or defaults)
+  int tune_rb = 0, tune_cmax = 0, tune_ilu = 4;
   SliceState* st = nullptr;
   double* part = nullptr;
   float *lam_d = nullptr, *lamtv_d = nullptr;
@@ -53,7 +57,7 @@ struct firls_ctx {
   bool marks_valid = false;
   // cached outer-step graph
   cudaGraphExec_t exec = nullptr;
-  int g_pcg = -1;
+  int g_pcg = -1, g_kind = -1;
   float g_ptol = -1.f, g_otol = -1.f;
   bool use_graph = true;
 };
@@ -139,6 +143,8 @@ WavArgs wav_args(firls_ctx* c, const SliceState* st) {
   a.tmpA = c->tmpA;
   a.tmpB = c->tmpB;
   a.part = c->part;
+  a.rb = c->tune_rb;
+  a.coarse_max = c->tune_cmax;
   return a;
 }
 
@@ -199,7 +205,7 @@ void enqueue_S(firls_ctx* c, int mode, const float2* zin, float2* din, float2* q
   { TMark m(c, FIRLS_K_COL_FFT_MASK, 1); fft_col_mask(c->n, a); }
   if (c->kind) {
     WavArgs w = wav_args(c, c->st);
-    TMark m(c, FIRLS_K_WAVELET_S, wavelet_apply_launches(c->n, c->levels));
+    TMark m(c, FIRLS_K_WAVELET_S, wavelet_apply_launches(c->n, c->levels, c->tune_cmax));
     wavelet_apply(w, din, c->cw, c->ww, WAV_MUL_W, c->u, nullptr, a.real);
   }
   a.u = c->kind ? c->u : nullptr;
@@ -237,7 +243,7 @@ void enqueue_update_precond(firls_ctx* c, int step_mode, float pcg_tol, bool ini
     {
       TMark m(c, FIRLS_K_ILU, 1);
       ilu_step(B, n, c->stream, c->st, c->part, init ? ILU_INIT : ILU_STEP, c->x, c->d, c->r, c->q, c->atb,
-               c->u, c->z, c->ia, c->pb, c->pc);
+               c->u, c->z, c->ia, c->pb, c->pc, c->tune_ilu);
     }
     TMark m(c, FIRLS_K_SCALARS, 1);
     if (init)
@@ -251,11 +257,11 @@ void enqueue_update_precond(firls_ctx* c, int step_mode, float pcg_tol, bool ini
     }
     WavArgs w = wav_args(c, c->st);
     {
-      TMark m(c, FIRLS_K_WAVELET_P, wavelet_apply_launches(n, c->levels));
+      TMark m(c, FIRLS_K_WAVELET_P, wavelet_apply_launches(n, c->levels, c->tune_cmax));
       wavelet_apply(w, c->r, c->cw, c->ww, WAV_MUL_PINV, c->z, c->r, real);
     }
     TMark m(c, FIRLS_K_SCALARS, 1);
-    const int np = wavelet_inverse_ctas(n, c->levels);
+    const int np = wavelet_inverse_ctas(n, c->levels, c->tune_rb, c->tune_cmax);
     if (init)
       pcg_rho_init(B, c->stream, c->st, c->part, np, axpy_ctas(n));
     else
@@ -265,7 +271,7 @@ void enqueue_update_precond(firls_ctx* c, int step_mode, float pcg_tol, bool ini
 }
 
 // One outer step of FIRLS: weights, P, PCG warm-started at x^k, relative change.
-void enqueue_outer(firls_ctx* c, int J, float pcg_tol, float outer_tol) {
+void enqueue_outer(firls_ctx* c, int J, float pcg_tol, float outer_tol, int tol_kind) {
   const int B = c->batch, n = c->n;
   marks_reset(c);
   {
@@ -292,13 +298,14 @@ void enqueue_outer(firls_ctx* c, int J, float pcg_tol, float outer_tol) {
   }
   TMark m(c, FIRLS_K_OTHER, 2);
   relchange_parts(B, n, c->stream, c->st, c->x, c->xprev, c->part);
-  outer_end(B, c->stream, c->st, c->part, axpy_ctas(n), outer_tol);
+  outer_end(B, c->stream, c->st, c->part, axpy_ctas(n), outer_tol, tol_kind);
 }
 
 firls_status check_params(firls_ctx* c, const firls_params* p) {
   if (!p) return fail(c, FIRLS_E_INVALID_ARG, "params is null");
   if (p->outer_iters < 1 || p->pcg_iters < 1) return fail(c, FIRLS_E_INVALID_ARG, "iteration counts must be >= 1");
   if (!(p->pcg_tol >= 0.f) || !(p->outer_tol >= 0.f)) return fail(c, FIRLS_E_INVALID_ARG, "tolerances must be >= 0");
+  if (p->outer_tol_kind != 0 && p->outer_tol_kind != 1) return fail(c, FIRLS_E_INVALID_ARG, "bad outer_tol_kind");
   const int B = c->batch;
   for (int s = 0; s < B; ++s) {
     const float l = p->lambda_per_slice ? p->lambda_per_slice[s] : p->lambda;
@@ -348,18 +355,19 @@ firls_status enqueue_setup(firls_ctx* c, const void* b, const firls_params* p, c
 firls_status run_outer_steps(firls_ctx* c, const firls_params* p) {
   const bool graph = c->use_graph && c->stream != nullptr;
   if (!graph) {
-    for (int k = 0; k < p->outer_iters; ++k) enqueue_outer(c, p->pcg_iters, p->pcg_tol, p->outer_tol);
+    for (int k = 0; k < p->outer_iters; ++k) enqueue_outer(c, p->pcg_iters, p->pcg_tol, p->outer_tol, p->outer_tol_kind);
     c->marks_valid = c->timing;
     return cuda_check(c, cudaGetLastError(), "outer step launch");
   }
-  if (!c->exec || c->g_pcg != p->pcg_iters || c->g_ptol != p->pcg_tol || c->g_otol != p->outer_tol) {
+  if (!c->exec || c->g_pcg != p->pcg_iters || c->g_ptol != p->pcg_tol || c->g_otol != p->outer_tol ||
+      c->g_kind != p->outer_tol_kind) {
     if (c->exec) {
       cudaGraphExecDestroy(c->exec);
       c->exec = nullptr;
     }
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_outer(c, p->pcg_iters, p->pcg_tol, p->outer_tol);
+    enqueue_outer(c, p->pcg_iters, p->pcg_tol, p->outer_tol, p->outer_tol_kind);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (e != cudaSuccess) return cuda_check(c, e, "graph capture");
     e = cudaGraphInstantiate(&c->exec, g, 0);
@@ -371,6 +379,7 @@ firls_status run_outer_steps(firls_ctx* c, const firls_params* p) {
     c->g_pcg = p->pcg_iters;
     c->g_ptol = p->pcg_tol;
     c->g_otol = p->outer_tol;
+    c->g_kind = p->outer_tol_kind;
   }
   // With an outer tolerance, poll the per-slice done flags every
   // kPoll replays and stop launching once every slice has stopped.
@@ -414,6 +423,22 @@ void prepare_kernels(int n);
 }  // namespace
 
 // ======================================================================= ABI
+
+struct MultiGraph {
+  std::vector<firls_ctx*> ctxs;
+  int J = -1, kind = -1;
+  float ptol = -1.f, otol = -1.f;
+  cudaGraphExec_t exec = nullptr;
+};
+static MultiGraph g_multi;  // last multi-context graph (per process)
+
+static void multi_forget(firls_ctx* c) {
+  if (std::find(g_multi.ctxs.begin(), g_multi.ctxs.end(), c) != g_multi.ctxs.end()) {
+    if (g_multi.exec) cudaGraphExecDestroy(g_multi.exec);
+    g_multi.exec = nullptr;
+    g_multi.ctxs.clear();
+  }
+}
 
 extern "C" int firls_size_supported(int n) { return fft_size_supported(n) ? 1 : 0; }
 
@@ -560,6 +585,7 @@ extern "C" firls_status firls_set_operator(firls_ctx* c, const uint8_t* mask, un
   c->psi = psi_kind;
   c->kind = kind;
   c->levels = kind ? wavelet_levels : 0;
+  multi_forget(c);
   if (c->exec) {
     cudaGraphExecDestroy(c->exec);
     c->exec = nullptr;
@@ -589,39 +615,119 @@ extern "C" firls_status firls_solve(firls_ctx* c, const void* b, const firls_par
   return FIRLS_OK;
 }
 
+// Several contexts (different sizes) in one CUDA graph per outer step: the
+// capture forks from ctxs[0]'s stream to every context's stream, each
+// context enqueues its outer step on its own stream, and the streams join
+// back.  Graph replays are launched on ctxs[0]'s stream.
+
 extern "C" firls_status firls_solve_multi(firls_ctx* const* ctxs, int n_ctx, const void* const* b,
-                                          const firls_params* p, const void* const* x0, void* const* x_out,
+                                          const firls_params* pa, const void* const* x0, void* const* x_out,
                                           firls_stats* stats) {
-  if (!ctxs || n_ctx < 1 || !b || !x_out || !p) return FIRLS_E_INVALID_ARG;
-  // Per context: the setup (uploads lambdas synchronously), then all outer
-  // steps of all contexts are enqueued on their own streams; the caller's
-  // view is ctxs[0]'s stream, which waits on the others at the end.
+  if (!ctxs || n_ctx < 1 || !b || !x_out || !pa) return FIRLS_E_INVALID_ARG;
+  const firls_params* p = &pa[0];  // the schedule (counts, tolerances) shared by all contexts
+  bool graphable = true;
   for (int i = 0; i < n_ctx; ++i) {
     firls_ctx* c = ctxs[i];
     if (!c || !c->op_set) return FIRLS_E_STATE;
-    TRY(check_params(c, p));
+    TRY(check_params(c, &pa[i]));
+    if (pa[i].outer_iters != p->outer_iters || pa[i].pcg_iters != p->pcg_iters || pa[i].pcg_tol != p->pcg_tol ||
+        pa[i].outer_tol != p->outer_tol || pa[i].outer_tol_kind != p->outer_tol_kind)
+      return fail(c, FIRLS_E_INVALID_ARG, "solve_multi: contexts must share the schedule and tolerances");
+    if (!c->stream || !c->use_graph) graphable = false;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c || (ctxs[j]->stream == c->stream && c->stream)) graphable = false;
   }
-  std::vector<cudaEvent_t> ev(n_ctx, nullptr);
-  cudaEvent_t start = nullptr;
-  cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
-  cudaEventRecord(start, ctxs[0]->stream);
+  firls_ctx* c0 = ctxs[0];
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join(n_ctx, nullptr);
+  cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  for (auto& e : join) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  auto cleanup = [&]() {
+    cudaEventDestroy(fork);
+    for (auto e : join) cudaEventDestroy(e);
+  };
+  // set-up of every context (A^H b, state), ordered after c0's prior work
+  cudaEventRecord(fork, c0->stream);
   for (int i = 0; i < n_ctx; ++i) {
     firls_ctx* c = ctxs[i];
-    if (i > 0) cudaStreamWaitEvent(c->stream, start, 0);
-    TRY(enqueue_setup(c, b[i], p, x0 ? x0[i] : nullptr));
+    if (i > 0) cudaStreamWaitEvent(c->stream, fork, 0);
+    firls_status st = enqueue_setup(c, b[i], &pa[i], x0 ? x0[i] : nullptr);
+    if (st != FIRLS_OK) {
+      cleanup();
+      return st;
+    }
   }
-  // interleave the outer steps so the independent contexts overlap
+  if (!graphable) {
+    for (int k = 0; k < p->outer_iters; ++k)
+      for (int i = 0; i < n_ctx; ++i) enqueue_outer(ctxs[i], p->pcg_iters, p->pcg_tol, p->outer_tol, p->outer_tol_kind);
+  } else {
+    const bool same = g_multi.exec && g_multi.J == p->pcg_iters && g_multi.ptol == p->pcg_tol &&
+                      g_multi.otol == p->outer_tol && g_multi.kind == p->outer_tol_kind &&
+                      (int)g_multi.ctxs.size() == n_ctx &&
+                      std::equal(g_multi.ctxs.begin(), g_multi.ctxs.end(), ctxs);
+    // every context's set-up must precede the replays on c0's stream
+    for (int i = 1; i < n_ctx; ++i) {
+      cudaEventRecord(join[i], ctxs[i]->stream);
+      cudaStreamWaitEvent(c0->stream, join[i], 0);
+    }
+    if (!same) {
+      if (g_multi.exec) cudaGraphExecDestroy(g_multi.exec);
+      g_multi.exec = nullptr;
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(c0->stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) {
+        cleanup();
+        return cuda_check(c0, e, "multi capture");
+      }
+      cudaEventRecord(fork, c0->stream);
+      for (int i = 1; i < n_ctx; ++i) cudaStreamWaitEvent(ctxs[i]->stream, fork, 0);
+      for (int i = 0; i < n_ctx; ++i) enqueue_outer(ctxs[i], p->pcg_iters, p->pcg_tol, p->outer_tol, p->outer_tol_kind);
+      for (int i = 1; i < n_ctx; ++i) {
+        cudaEventRecord(join[i], ctxs[i]->stream);
+        cudaStreamWaitEvent(c0->stream, join[i], 0);
+      }
+      e = cudaStreamEndCapture(c0->stream, &g);
+      if (e != cudaSuccess) {
+        cleanup();
+        return cuda_check(c0, e, "multi capture end");
+      }
+      e = cudaGraphInstantiate(&g_multi.exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        g_multi.exec = nullptr;
+        cleanup();
+        return cuda_check(c0, e, "multi instantiate");
+      }
+      g_multi.ctxs.assign(ctxs, ctxs + n_ctx);
+      g_multi.J = p->pcg_iters;
+      g_multi.ptol = p->pcg_tol;
+      g_multi.otol = p->outer_tol;
+      g_multi.kind = p->outer_tol_kind;
+    }
+    for (int k = 0; k < p->outer_iters; ++k) {
+      cudaError_t e = cudaGraphLaunch(g_multi.exec, c0->stream);
+      if (e != cudaSuccess) {
+        cleanup();
+        return cuda_check(c0, e, "multi graph launch");
+      }
+    }
+  }
+  // results, on c0's stream after the replays; other streams wait for them
   for (int i = 0; i < n_ctx; ++i) {
     firls_ctx* c = ctxs[i];
-    TRY(run_outer_steps(c, p));
     const size_t bytes = sizeof(float2) * (size_t)c->batch * c->n * c->n;
-    CU(cudaMemcpyAsync(x_out[i], c->x, bytes, cudaMemcpyDeviceToDevice, c->stream));
-    cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
-    cudaEventRecord(ev[i], c->stream);
+    cudaStream_t s = graphable ? c0->stream : c->stream;
+    cudaMemcpyAsync(x_out[i], c->x, bytes, cudaMemcpyDeviceToDevice, s);
   }
-  for (int i = 1; i < n_ctx; ++i) cudaStreamWaitEvent(ctxs[0]->stream, ev[i], 0);
-  firls_status ret = FIRLS_OK;
-  if (stats || p->pcg_tol > 0.f || p->outer_tol > 0.f) {
+  if (!graphable)
+    for (int i = 1; i < n_ctx; ++i) {
+      cudaEventRecord(join[i], ctxs[i]->stream);
+      cudaStreamWaitEvent(c0->stream, join[i], 0);
+    }
+  cudaEventRecord(fork, c0->stream);
+  for (int i = 1; i < n_ctx; ++i) cudaStreamWaitEvent(ctxs[i]->stream, fork, 0);
+  firls_status ret = cuda_check(c0, cudaGetLastError(), "solve_multi");
+  if (ret == FIRLS_OK && (stats || p->pcg_tol > 0.f || p->outer_tol > 0.f)) {
     for (int i = 0; i < n_ctx; ++i) {
       bool bd = false;
       firls_status s = collect_stats(ctxs[i], stats ? &stats[i] : nullptr, &bd);
@@ -629,9 +735,7 @@ extern "C" firls_status firls_solve_multi(firls_ctx* const* ctxs, int n_ctx, con
       if (bd && ret == FIRLS_OK) ret = FIRLS_E_BREAKDOWN;
     }
   }
-  for (auto e : ev)
-    if (e) cudaEventDestroy(e);
-  cudaEventDestroy(start);
+  cleanup();
   return ret;
 }
 
@@ -639,6 +743,7 @@ extern "C" const char* firls_last_error(const firls_ctx* c) { return c ? c->err.
 
 extern "C" firls_status firls_set_timing(firls_ctx* c, int enable) {
   if (!c) return FIRLS_E_INVALID_ARG;
+  multi_forget(c);
   const bool on = enable != 0;
   if (on != c->timing && c->exec) {  // the captured graph changes shape
     cudaGraphExecDestroy(c->exec);
@@ -668,6 +773,7 @@ extern "C" firls_status firls_get_timing(firls_ctx* c, double* ms, int* launches
 
 extern "C" void firls_destroy(firls_ctx* c) {
   if (!c) return;
+  multi_forget(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   if (c->exec) cudaGraphExecDestroy(c->exec);
@@ -740,6 +846,340 @@ extern "C" firls_status firls_apply_S_P(firls_ctx* c, const firls_params* p, con
   enqueue_update_precond(c, 0, 0.f, true);
   CU(cudaMemcpyAsync(z, c->z, bytes, cudaMemcpyDeviceToDevice, c->stream));
   return cuda_check(c, cudaGetLastError(), "apply_S_P");
+}
+
+// F_eps per slice (Eq. anapro / iso with the eps of Eq. gw / wi), host out[batch].
+firls_status objective_parts(firls_ctx* c, const void* b, const firls_params* p, const float2* x) {
+  const int B = c->batch, n = c->n;
+  const float eps = eps_of(p);
+  FftArgs a = fft_args(c);
+  a.st = nullptr;
+  a.d = const_cast<float2*>(x);
+  a.t = c->t;
+  a.mode = 2;
+  // row FFT of x into t (state checks off: the kernel runs every slice)
+  TRY(cuda_check(c, cudaMemsetAsync(c->st, 0, sizeof(SliceState) * B, c->stream), "memset"));
+  state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, eps);
+  a.st = c->st;
+  fft_row_fwd(n, a);
+  a.b = static_cast<const float2*>(b);
+  a.mask = c->mask;
+  a.mode = SLOT_DQ;
+  fft_col_resid(n, a);
+  if (c->kind) {
+    WavArgs w = wav_args(c, nullptr);
+    wavelet_forward(w, x, c->cw, nullptr, WAV_RAW);
+    l21_sum(B, n, c->stream, c->cw, c->groups ? c->gidx : nullptr, c->goff, c->n_groups, c->gsize, eps, c->part,
+            SLOT_RZ);
+  }
+  if (has_tv(c)) tv_sum(B, n, c->stream, x, eps, c->part, SLOT_RR);
+  return cuda_check(c, cudaGetLastError(), "objective");
+}
+
+firls_status objective_read(firls_ctx* c, const firls_params* p, double* out) {
+  const int B = c->batch, n = c->n;
+  std::vector<double> h((size_t)B * NSLOT * MAXPART);
+  CU(cudaMemcpyAsync(h.data(), c->part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  const int nd = fft_col_ctas(n), nr = axpy_ctas(n);
+  for (int s = 0; s < B; ++s) {
+    auto sum = [&](int slot, int np) {
+      double a = 0.0;
+      for (int i = 0; i < np; ++i) a += h[((size_t)s * NSLOT + slot) * MAXPART + i];
+      return a;
+    };
+    const double lam = p->lambda_per_slice ? p->lambda_per_slice[s] : p->lambda;
+    const double lt = p->lambda_tv_per_slice ? p->lambda_tv_per_slice[s] : p->lambda_tv;
+    double f = 0.5 * sum(SLOT_DQ, nd);
+    if (c->kind) f += lam * sum(SLOT_RZ, nr);
+    if (has_tv(c)) f += lt * sum(SLOT_RR, nr);
+    out[s] = f;
+  }
+  return FIRLS_OK;
+}
+
+// ---- continuous batching: per-slot load, run, status, read-out ----
+
+extern "C" firls_status firls_slot_load(firls_ctx* c, int s, const uint8_t* mask, const void* b, const void* x0,
+                                        float lambda, float lambda_tv, float eps) {
+  if (!c || !mask || !b) return FIRLS_E_INVALID_ARG;
+  if (!c->op_set) return fail(c, FIRLS_E_STATE, "operator not set");
+  if (s < 0 || s >= c->batch) return fail(c, FIRLS_E_INVALID_ARG, "slot out of range");
+  if (!(lambda >= 0.f) || !(lambda_tv >= 0.f) || !std::isfinite(lambda) || !std::isfinite(lambda_tv))
+    return fail(c, FIRLS_E_INVALID_ARG, "lambdas must be finite and >= 0");
+  const int n = c->n;
+  const size_t N = (size_t)n * n, off = (size_t)s * N;
+  CU(cudaMemcpyAsync(c->mask + off, mask, N, cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaMemsetAsync(c->counts + s, 0, sizeof(int), c->stream));
+  mask_popcount(1, n, c->stream, c->mask + off, c->counts + s);
+  const float lam[2] = {c->kind ? lambda : 0.f, has_tv(c) ? lambda_tv : 0.f};
+  CU(cudaMemcpyAsync(c->lam_d + s, &lam[0], sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->lamtv_d + s, &lam[1], sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  double* part = c->part + (size_t)s * NSLOT * MAXPART;
+  FftArgs a = fft_args(c);
+  a.batch = 1;
+  a.part = part;
+  a.b = static_cast<const float2*>(b);
+  a.mask = c->mask + off;
+  a.t = c->t + off;
+  fft_row_ahb(n, a);
+  a.atb = c->atb + off;
+  a.x = x0 ? nullptr : c->x + off;
+  fft_col_inv(n, a);
+  if (x0) CU(cudaMemcpyAsync(c->x + off, x0, N * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+  state_init(1, c->stream, c->st + s, part, fft_col_ctas(n), c->counts + s, n, c->lam_d + s, c->lamtv_d + s,
+             eps > 0.f ? eps : 1e-10f);
+  return cuda_check(c, cudaGetLastError(), "slot_load");
+}
+
+extern "C" firls_status firls_run(firls_ctx* c, const firls_params* p) {
+  if (!c || !p) return FIRLS_E_INVALID_ARG;
+  if (!c->op_set) return fail(c, FIRLS_E_STATE, "operator not set");
+  if (p->outer_iters < 1 || p->pcg_iters < 1) return fail(c, FIRLS_E_INVALID_ARG, "iteration counts must be >= 1");
+  firls_params q = *p;
+  q.outer_tol = p->outer_tol;  // no polling inside: the caller polls with firls_slot_status
+  const bool graph = c->use_graph && c->stream != nullptr;
+  if (!graph) {
+    for (int k = 0; k < q.outer_iters; ++k) enqueue_outer(c, q.pcg_iters, q.pcg_tol, q.outer_tol, q.outer_tol_kind);
+    return cuda_check(c, cudaGetLastError(), "run");
+  }
+  if (!c->exec || c->g_pcg != q.pcg_iters || c->g_ptol != q.pcg_tol || c->g_otol != q.outer_tol ||
+      c->g_kind != q.outer_tol_kind) {
+    firls_params one = q;
+    one.outer_iters = 1;
+    TRY(run_outer_steps(c, &one));  // captures (and runs) one step
+    q.outer_iters -= 1;
+  }
+  for (int k = 0; k < q.outer_iters; ++k) CU(cudaGraphLaunch(c->exec, c->stream));
+  c->marks_valid = c->timing;
+  return FIRLS_OK;
+}
+
+extern "C" firls_status firls_slot_status(firls_ctx* c, int* done, int* outer_done, double* rel_change) {
+  if (!c) return FIRLS_E_INVALID_ARG;
+  std::vector<SliceState> hs(c->batch);
+  CU(cudaMemcpyAsync(hs.data(), c->st, sizeof(SliceState) * c->batch, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  for (int s = 0; s < c->batch; ++s) {
+    if (done) done[s] = hs[s].done;
+    if (outer_done) outer_done[s] = hs[s].outer_done;
+    if (rel_change) rel_change[s] = hs[s].relchg;
+  }
+  return FIRLS_OK;
+}
+
+// Retire a slot: it stops taking part in the outer steps until reloaded.
+__global__ void k_slot_retire(SliceState* st) { st->done = 1; st->active = 0; }
+
+extern "C" firls_status firls_slot_retire(firls_ctx* c, int s) {
+  if (!c || s < 0 || s >= c->batch) return FIRLS_E_INVALID_ARG;
+  k_slot_retire<<<1, 1, 0, c->stream>>>(c->st + s);
+  return cuda_check(c, cudaGetLastError(), "slot_retire");
+}
+
+extern "C" firls_status firls_slot_get(firls_ctx* c, int s, void* x_out) {
+  if (!c || !x_out || s < 0 || s >= c->batch) return FIRLS_E_INVALID_ARG;
+  const size_t N = (size_t)c->n * c->n;
+  CU(cudaMemcpyAsync(x_out, c->x + (size_t)s * N, N * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+  return FIRLS_OK;
+}
+
+// ---- autotuner: tile shapes timed on the context's own buffers ----
+namespace {
+bool tune_cache_lookup(const char* path, const std::string& key, int* rb, int* cm, int* il) {
+  if (!path || !*path) return false;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[256];
+  bool found = false;
+  while (std::fgets(line, sizeof line, f)) {
+    char k[128];
+    int a, b2, d;
+    if (std::sscanf(line, "%127[^|]| %d %d %d", k, &a, &b2, &d) == 4 && key == k) {
+      *rb = a;
+      *cm = b2;
+      *il = d;
+      found = true;  // last entry wins
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+float time_ms(firls_ctx* c, const std::function<void()>& fn, int reps) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  fn();  // warm-up
+  cudaEventRecord(a, c->stream);
+  for (int i = 0; i < reps; ++i) fn();
+  cudaEventRecord(b, c->stream);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms / reps;
+}
+}  // namespace
+
+extern "C" firls_status firls_autotune(firls_ctx* c, const char* cache_path) {
+  if (!c) return FIRLS_E_INVALID_ARG;
+  if (!c->op_set) return fail(c, FIRLS_E_STATE, "operator not set");
+  const int B = c->batch, n = c->n;
+  char keybuf[128];
+  std::snprintf(keybuf, sizeof keybuf, "n=%d batch=%d psi=%u levels=%d ", n, B, c->psi, c->levels);
+  const std::string key(keybuf);
+  int rb = 0, cm = 0, il = 4;
+  if (!tune_cache_lookup(cache_path, key, &rb, &cm, &il)) {
+    // deterministic, finite contents for timing
+    const size_t BN = (size_t)B * n * n;
+    for (float2* v : {c->x, c->d, c->r, c->q, c->z, c->atb, c->u, c->cw}) cudaMemsetAsync(v, 0, BN * 8, c->stream);
+    for (float* v : {c->ww, c->wtv, c->wdiag}) cudaMemsetAsync(v, 0, BN * 4, c->stream);
+    firls_params p{};
+    p.outer_iters = p.pcg_iters = 1;
+    p.lambda = 1e-3f;
+    p.lambda_tv = 1e-3f;
+    TRY(upload_params(c, &p));
+    state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, 1e-10f);
+    if (has_tv(c)) penta_setup(B, n, c->stream, c->st, c->wtv, nullptr, c->ia, c->pb, c->pc);
+    float best = 1e30f;
+    if (c->kind) {
+      for (int r : {4, 8, 16})
+        for (int m : {32, 64}) {
+          WavArgs w = wav_args(c, c->st);
+          w.rb = r;
+          w.coarse_max = m;
+          const float t = time_ms(c, [&]() { wavelet_apply(w, c->d, c->cw, c->ww, WAV_MUL_W, c->u, nullptr, 0); }, 5);
+          if (t < best) {
+            best = t;
+            rb = r;
+            cm = m;
+          }
+        }
+    }
+    if (has_tv(c)) {
+      best = 1e30f;
+      for (int d : {3, 4, 6}) {
+        const float t = time_ms(c, [&]() {
+          ilu_step(B, n, c->stream, c->st, c->part, ILU_STEP, c->x, c->d, c->r, c->q, c->atb, c->u, c->z, c->ia,
+                   c->pb, c->pc, d);
+        }, 5);
+        if (t < best) {
+          best = t;
+          il = d;
+        }
+      }
+    }
+    CU(cudaGetLastError());
+    if (cache_path && *cache_path) {
+      FILE* f = std::fopen(cache_path, "a");
+      if (f) {
+        std::fprintf(f, "%s| %d %d %d\n", key.c_str(), rb, cm, il);
+        std::fclose(f);
+      }
+    }
+  }
+  c->tune_rb = rb;
+  c->tune_cmax = cm;
+  c->tune_ilu = il;
+  multi_forget(c);
+  if (c->exec) {
+    cudaGraphExecDestroy(c->exec);
+    c->exec = nullptr;
+  }
+  return FIRLS_OK;
+}
+
+extern "C" firls_status firls_get_tuning(const firls_ctx* c, int* rows_per_cta, int* coarse_max, int* ilu_depth) {
+  if (!c) return FIRLS_E_INVALID_ARG;
+  if (rows_per_cta) *rows_per_cta = c->tune_rb;
+  if (coarse_max) *coarse_max = c->tune_cmax;
+  if (ilu_depth) *ilu_depth = c->tune_ilu;
+  return FIRLS_OK;
+}
+
+extern "C" firls_status firls_adjoint(firls_ctx* c, const void* b, void* atb) {
+  if (!c || !b || !atb) return FIRLS_E_INVALID_ARG;
+  if (!c->op_set) return fail(c, FIRLS_E_STATE, "operator not set");
+  FftArgs a = fft_args(c);
+  a.b = static_cast<const float2*>(b);
+  a.mask = c->mask;
+  a.t = c->t;
+  fft_row_ahb(c->n, a);
+  a.atb = static_cast<float2*>(atb);
+  a.x = nullptr;
+  fft_col_inv(c->n, a);
+  return cuda_check(c, cudaGetLastError(), "adjoint");
+}
+
+extern "C" firls_status firls_data_consistency(firls_ctx* c, const void* b, const void* x, void* out) {
+  if (!c || !b || !x || !out) return FIRLS_E_INVALID_ARG;
+  if (!c->op_set) return fail(c, FIRLS_E_STATE, "operator not set");
+  const int B = c->batch, n = c->n;
+  // kernels check the slice state: lambdas 0, all running
+  std::vector<float> zeros(B, 0.f);
+  firls_params p{};
+  p.outer_iters = p.pcg_iters = 1;
+  p.lambda_per_slice = zeros.data();
+  p.lambda_tv_per_slice = zeros.data();
+  TRY(upload_params(c, &p));
+  state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, 1e-10f);
+  FftArgs a = fft_args(c);
+  a.d = const_cast<float2*>(static_cast<const float2*>(x));
+  a.t = c->t;
+  a.mode = 2;
+  fft_row_fwd(n, a);
+  a.b = static_cast<const float2*>(b);
+  a.mask = c->mask;
+  fft_col_dc(n, a);
+  a.d = c->t;  // only read for the (unused) dot product
+  a.u = nullptr;
+  a.wtv = nullptr;
+  a.q = static_cast<float2*>(out);
+  fft_row_inv(n, a);
+  return cuda_check(c, cudaGetLastError(), "data_consistency");
+}
+
+extern "C" firls_status firls_objective(firls_ctx* c, const void* b, const firls_params* p, const void* x,
+                                        double* out) {
+  if (!c || !b || !p || !x || !out) return FIRLS_E_INVALID_ARG;
+  if (!c->op_set) return fail(c, FIRLS_E_STATE, "operator not set");
+  TRY(check_params(c, p));
+  TRY(upload_params(c, p));
+  TRY(objective_parts(c, b, p, static_cast<const float2*>(x)));
+  return objective_read(c, p, out);
+}
+
+extern "C" firls_status firls_warm_start_guard(firls_ctx* c, const void* b, const firls_params* p, const void* x1,
+                                               void* x0, int* chosen) {
+  if (!c || !b || !p || !x1 || !x0) return FIRLS_E_INVALID_ARG;
+  if (!c->op_set) return fail(c, FIRLS_E_STATE, "operator not set");
+  TRY(check_params(c, p));
+  TRY(upload_params(c, p));
+  const int B = c->batch, n = c->n;
+  const size_t slice = sizeof(float2) * (size_t)n * n;
+  std::vector<double> f1(B), f0(B);
+  TRY(objective_parts(c, b, p, static_cast<const float2*>(x1)));
+  TRY(objective_read(c, p, f1.data()));
+  // A^H b into the context's atb buffer
+  FftArgs a = fft_args(c);
+  a.b = static_cast<const float2*>(b);
+  a.mask = c->mask;
+  a.t = c->t;
+  fft_row_ahb(n, a);
+  a.atb = c->atb;
+  a.x = nullptr;
+  fft_col_inv(n, a);
+  TRY(objective_parts(c, b, p, c->atb));
+  TRY(objective_read(c, p, f0.data()));
+  for (int s = 0; s < B; ++s) {
+    const bool use = std::isfinite(f1[s]) && f1[s] <= f0[s];
+    const void* src = use ? static_cast<const char*>(x1) + s * slice : static_cast<const void*>(c->atb + (size_t)s * n * n);
+    CU(cudaMemcpyAsync(static_cast<char*>(x0) + s * slice, src, slice, cudaMemcpyDeviceToDevice, c->stream));
+    if (chosen) chosen[s] = use ? 1 : 0;
+  }
+  return cuda_check(c, cudaGetLastError(), "warm_start_guard");
 }
 
 extern "C" firls_status firls_get_weights(firls_ctx* c, float* w_wavelet, float* w_tv) {

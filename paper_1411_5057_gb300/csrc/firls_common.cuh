@@ -17,6 +17,7 @@ struct SliceState {
   double rhs2;       // ||A^H b||^2
   double rr;         // ||r||^2 after the last update
   double relchg;     // ||x^{k+1} - x^k|| / ||x^k|| of the last outer step
+  double relchg_prev;  // the same one outer step earlier
   int active;        // PCG running in this outer step
   int done;          // outer loop stopped (outer_tol reached)
   int breakdown;     // PCG broke down at least once

@@ -222,6 +222,95 @@ __global__ void __launch_bounds__(512) k_col_inv(const float2* __restrict__ tbuf
   if (threadIdx.x == 0) part[((size_t)s * NSLOT + SLOT_RHS) * MAXPART + blockIdx.x] = tot;
 }
 
+// Data consistency of a warm start, column part: t = colIFFT((1 - R) colFFT(t) + R n b)
+// (t = rowFFT(x); followed by the row IFFT with the 1/N scale this gives
+// F^H((1 - R) F x + R b)).
+template <int N>
+__global__ void __launch_bounds__(512) k_col_dc(float2* __restrict__ tbuf, const float2* __restrict__ b,
+                                                const uint8_t* __restrict__ mask, const float2* __restrict__ twg) {
+  using C = FftCfg<N>;
+  constexpr int E = C::E, T = C::T, LW = fft_line_words<N>();
+  const int s = blockIdx.y;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* tw = reinterpret_cast<float2*>(smem);
+  float* tre = reinterpret_cast<float*>(smem + N * 8);
+  float* tim = tre + N * (COLS + 1);
+  const int c0 = blockIdx.x * COLS;
+  const size_t sbase = (size_t)s * N * N;
+  load_twiddles<N>(tw, twg);
+  load_col_tile<N>(tbuf, tre, tim, sbase, c0);
+  __syncthreads();
+  const int c = threadIdx.x / T, t = threadIdx.x % T;
+  float2 v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int r = t + T * e;
+    v[e] = make_float2(tre[r * (COLS + 1) + c], tim[r * (COLS + 1) + c]);
+  }
+  __syncthreads();
+  fft_line<N, -1>(v, tre + c * LW, tim + c * LW, tw, t);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const size_t gi = sbase + (size_t)(t + T * e) * N + c0 + c;
+    if (mask[gi]) v[e] = cscale(b[gi], (float)N);
+  }
+  fft_line<N, +1>(v, tre + c * LW, tim + c * LW, tw, t);
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int r = t + T * e;
+    tre[r * (COLS + 1) + c] = v[e].x;
+    tim[r * (COLS + 1) + c] = v[e].y;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < N * COLS; idx += blockDim.x) {
+    const int r = idx / COLS, cc = idx % COLS;
+    tbuf[sbase + (size_t)r * N + c0 + cc] = make_float2(tre[r * (COLS + 1) + cc], tim[r * (COLS + 1) + cc]);
+  }
+}
+
+// Data term of F: partial sum over sampled entries of |(1/n) colFFT(t) - b|^2,
+// t = rowFFT(x), i.e. ||R F x - b||^2 with the unitary F (Eq. anapro).
+template <int N>
+__global__ void __launch_bounds__(512) k_col_resid(const float2* __restrict__ tbuf, const float2* __restrict__ b,
+                                                   const uint8_t* __restrict__ mask, double* __restrict__ part,
+                                                   int slot, const float2* __restrict__ twg) {
+  using C = FftCfg<N>;
+  constexpr int E = C::E, T = C::T, LW = fft_line_words<N>();
+  const int s = blockIdx.y;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* tw = reinterpret_cast<float2*>(smem);
+  float* tre = reinterpret_cast<float*>(smem + N * 8);
+  float* tim = tre + N * (COLS + 1);
+  __shared__ double red[32];
+  const int c0 = blockIdx.x * COLS;
+  const size_t sbase = (size_t)s * N * N;
+  load_twiddles<N>(tw, twg);
+  load_col_tile<N>(tbuf, tre, tim, sbase, c0);
+  __syncthreads();
+  const int c = threadIdx.x / T, t = threadIdx.x % T;
+  float2 v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int r = t + T * e;
+    v[e] = make_float2(tre[r * (COLS + 1) + c], tim[r * (COLS + 1) + c]);
+  }
+  __syncthreads();
+  fft_line<N, -1>(v, tre + c * LW, tim + c * LW, tw, t);
+  const float sc = 1.0f / (float)N;
+  float acc = 0.f;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const size_t gi = sbase + (size_t)(t + T * e) * N + c0 + c;
+    if (mask[gi]) {
+      const float2 bv = b[gi];
+      acc += cabs2(make_float2(v[e].x * sc - bv.x, v[e].y * sc - bv.y));
+    }
+  }
+  const double tot = block_sum((double)acc, red);
+  if (threadIdx.x == 0) part[((size_t)s * NSLOT + slot) * MAXPART + blockIdx.x] = tot;
+}
+
 // q = (1/N) rowIFFT(t) [Re if real] + lam_tv (D1^T W D1 + D2^T W D2) d + lam u;
 // partial Re<d, q>.
 template <int N>
@@ -307,6 +396,8 @@ template <int N> static void set_smem_attrs() {
   cudaFuncSetAttribute(k_row_inv<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem_bytes<N>(true));
   cudaFuncSetAttribute(k_col_mask<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem_bytes<N>());
   cudaFuncSetAttribute(k_col_inv<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem_bytes<N>());
+  cudaFuncSetAttribute(k_col_resid<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem_bytes<N>());
+  cudaFuncSetAttribute(k_col_dc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem_bytes<N>());
 }
 
 template <int N> struct FftLaunch {
@@ -331,6 +422,16 @@ template <int N> struct FftLaunch {
     k_col_inv<N><<<dim3(N / COLS, a.batch), COLS * FftCfg<N>::T, col_smem_bytes<N>(), a.stream>>>(
         a.t, a.atb, a.x, a.real, a.part, a.tw);
   }
+  static void col_resid(const FftArgs& a) {
+    set_smem_attrs<N>();
+    k_col_resid<N><<<dim3(N / COLS, a.batch), COLS * FftCfg<N>::T, col_smem_bytes<N>(), a.stream>>>(
+        a.t, a.b, a.mask, a.part, a.mode, a.tw);
+  }
+  static void col_dc(const FftArgs& a) {
+    set_smem_attrs<N>();
+    k_col_dc<N><<<dim3(N / COLS, a.batch), COLS * FftCfg<N>::T, col_smem_bytes<N>(), a.stream>>>(a.t, a.b, a.mask,
+                                                                                                  a.tw);
+  }
   static void row_inv(const FftArgs& a) {
     set_smem_attrs<N>();
     k_row_inv<N><<<dim3(N / R, a.batch), R * FftCfg<N>::T, row_smem_bytes<N>(a.wtv != nullptr), a.stream>>>(
@@ -352,11 +453,15 @@ template <int N> struct FftLaunch {
 #define FIRLS_CASE_col_mask(n) case n: FftLaunch<n>::col_mask(a); break;
 #define FIRLS_CASE_col_inv(n) case n: FftLaunch<n>::col_inv(a); break;
 #define FIRLS_CASE_row_inv(n) case n: FftLaunch<n>::row_inv(a); break;
+#define FIRLS_CASE_col_resid(n) case n: FftLaunch<n>::col_resid(a); break;
+#define FIRLS_CASE_col_dc(n) case n: FftLaunch<n>::col_dc(a); break;
 FIRLS_DISPATCH(row_fwd)
 FIRLS_DISPATCH(row_ahb)
 FIRLS_DISPATCH(col_mask)
 FIRLS_DISPATCH(col_inv)
 FIRLS_DISPATCH(row_inv)
+FIRLS_DISPATCH(col_resid)
+FIRLS_DISPATCH(col_dc)
 
 bool fft_size_supported(int n) {
   switch (n) {

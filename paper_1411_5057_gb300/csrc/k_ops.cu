@@ -54,10 +54,14 @@ FI void inv_haar(float2 a, float2 d, float2& x0, float2& x1) {
 
 constexpr int WAV_THREADS = 256;
 constexpr int WAV_RB = 8;            // output row pairs per CTA of a tiled level
-constexpr int COARSE_MAX = 64;       // largest block kept whole in shared memory
+constexpr int COARSE_MAX = 64;       // default largest block kept whole in shared memory
+constexpr int COARSE_LIMIT = 64;     // the in-shared-memory transform handles up to 64^2 (2 pairs per lane)
 constexpr int COARSE_THREADS = 256;
 
-static int wav_rb(int m) { return m / 2 < WAV_RB ? m / 2 : WAV_RB; }
+static int wav_rb(int m, int want = 0) {
+  const int rb = want > 0 ? want : WAV_RB;
+  return m / 2 < rb ? m / 2 : rb;
+}
 
 // One tiled analysis level on the m x m block `in` (row stride ld_in).  The
 // horizontal step reads the input rows straight from global memory (16-byte
@@ -347,9 +351,9 @@ static void set_wav_attrs() {
   static bool done = false;
   if (done) return;
   done = true;
-  cudaFuncSetAttribute(k_wav_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 20 * 512 * 8);
-  cudaFuncSetAttribute(k_wav_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * WAV_RB * 512 * 8);
-  cudaFuncSetAttribute(k_wav_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, coarse_smem(COARSE_MAX));
+  cudaFuncSetAttribute(k_wav_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (2 * 16 + 2) * 512 * 8);
+  cudaFuncSetAttribute(k_wav_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 16 * 512 * 8);
+  cudaFuncSetAttribute(k_wav_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, coarse_smem(COARSE_LIMIT));
 }
 
 void ilu_prepare();
@@ -358,10 +362,11 @@ void wav_prepare() {
   ilu_prepare();
 }
 
-// First level handled by the coarse kernel: its input side m <= COARSE_MAX.
-static int coarse_first_level(int n, int levels) {
+// First level handled by the coarse kernel: its input side m <= cmax.
+static int coarse_first_level(int n, int levels, int cmax = 0) {
+  const int lim = cmax > 0 ? (cmax < COARSE_LIMIT ? cmax : COARSE_LIMIT) : COARSE_MAX;
   int l0 = 1;
-  while (l0 <= levels && (n >> (l0 - 1)) > COARSE_MAX) ++l0;
+  while (l0 <= levels && (n >> (l0 - 1)) > lim) ++l0;
   return l0;  // levels + 1 when no level fits
 }
 
@@ -379,7 +384,7 @@ static const float2* tiled_forward(const WavArgs& a, const float2* x, float2* c,
     float2* dst = to_c ? c : ((l & 1) ? a.tmpA : a.tmpB);
     const size_t dst_ss = to_c ? (size_t)n * n : hh;
     const int dst_ld = to_c ? n : half;
-    const int rb = wav_rb(m);
+    const int rb = wav_rb(m, a.rb);
     const int smem = (2 * rb + (a.kind == 2 ? 2 : 0)) * m * 8;
     k_wav_fwd<<<dim3((half + rb - 1) / rb, a.batch), WAV_THREADS, smem, a.stream>>>(
         src, src_ss, src_ld, dst, dst_ss, dst_ld, c, w, n, m, rb, a.kind, mode, to_c ? 1 : 0, a.st);
@@ -404,7 +409,7 @@ static void tiled_inverse(const WavArgs& a, const float2* lli, size_t ll_ss, int
     float2* out = final_level ? x : (lli == a.tmpA ? a.tmpB : a.tmpA);
     const size_t out_ss = final_level ? (size_t)n * n : hh;
     const int out_ld = final_level ? n : m;
-    const int rb = wav_rb(m);
+    const int rb = wav_rb(m, a.rb);
     k_wav_inv<<<dim3((half + rb - 1) / rb, a.batch), WAV_THREADS, 2 * rb * m * 8, a.stream>>>(
         lli, ll_ss, ll_ld, c, out, out_ss, out_ld, n, m, rb, a.kind, final_level ? r : nullptr,
         final_level && r ? a.part : nullptr, real, a.st);
@@ -417,7 +422,7 @@ static void tiled_inverse(const WavArgs& a, const float2* lli, size_t ll_ss, int
 void wavelet_forward(const WavArgs& a, const float2* x, float2* c, float* w, int mode) {
   set_wav_attrs();
   const int n = a.n, L = a.levels;
-  const int l0 = coarse_first_level(n, L);
+  const int l0 = coarse_first_level(n, L, a.coarse_max);
   size_t ss;
   int ld;
   const float2* ll = tiled_forward(a, x, c, w, mode, l0 - 1, l0 > L, &ss, &ld);
@@ -431,7 +436,7 @@ void wavelet_forward(const WavArgs& a, const float2* x, float2* c, float* w, int
 void wavelet_inverse(const WavArgs& a, const float2* c, float2* x, const float2* r, int real) {
   set_wav_attrs();
   const int n = a.n, L = a.levels;
-  const int l0 = coarse_first_level(n, L);
+  const int l0 = coarse_first_level(n, L, a.coarse_max);
   if (l0 <= L) {
     const int m0 = n >> (l0 - 1);
     const bool final_coarse = (l0 == 1);
@@ -452,7 +457,7 @@ void wavelet_apply(const WavArgs& a, const float2* x, float2* c, float* w, int m
                    const float2* r, int real) {
   set_wav_attrs();
   const int n = a.n, L = a.levels;
-  const int l0 = coarse_first_level(n, L);
+  const int l0 = coarse_first_level(n, L, a.coarse_max);
   if (l0 > L) {
     wavelet_forward(a, x, c, w, mode);
     wavelet_inverse(a, c, u, r, real);
@@ -473,14 +478,14 @@ void wavelet_apply(const WavArgs& a, const float2* x, float2* c, float* w, int m
 }
 
 // Partial-sum count of the stage that computes Re<r, Phi^T ...>.
-int wavelet_inverse_ctas(int n, int levels) {
-  if (coarse_first_level(n, levels) == 1) return 1;
-  return (n / 2 + wav_rb(n) - 1) / wav_rb(n);
+int wavelet_inverse_ctas(int n, int levels, int rb, int cmax) {
+  if (coarse_first_level(n, levels, cmax) == 1) return 1;
+  return (n / 2 + wav_rb(n, rb) - 1) / wav_rb(n, rb);
 }
 
 // Launches per wavelet_apply call (for the launch count).
-int wavelet_apply_launches(int n, int levels) {
-  const int l0 = coarse_first_level(n, levels);
+int wavelet_apply_launches(int n, int levels, int cmax) {
+  const int l0 = coarse_first_level(n, levels, cmax);
   if (l0 > levels) return 2 * levels;
   return 2 * (l0 - 1) + 1;
 }
@@ -646,14 +651,15 @@ FI float2 affine_exclusive(float A, float2 B, float* sA, float2* sB, int par) {
 }
 
 constexpr int ILU_E = 4;
-constexpr int ILU_D = 4;  // ring stages (rows in flight: ILU_D - 1 ahead)
+constexpr int ILU_DMAX = 6;  // ring stages (rows in flight: D - 1 ahead); D in {3, 4, 6}
 // 16-byte chunk slots per thread and stage
 enum { FC_R0 = 0, FC_R1, FC_Q0, FC_Q1, FC_X0, FC_X1, FC_D0, FC_D1, FC_IA, FC_IB, FC_IC, FC_IBL, FCH };
 enum { BC_Y0 = 0, BC_Y1, BC_IA, BC_IB, BC_IC };
 
 static int ilu_threads(int n) { return (n / ILU_E + 31) / 32 * 32; }
-static int ilu_smem(int n) { return ILU_D * FCH * ilu_threads(n) * 16; }
+static int ilu_smem(int n, int D) { return D * FCH * ilu_threads(n) * 16; }
 
+template <int ILU_D>
 __global__ void __launch_bounds__(128) k_ilu(int n, int mode, const SliceState* __restrict__ st,
                                              double* __restrict__ part, float2* __restrict__ x,
                                              const float2* __restrict__ d, float2* __restrict__ r,
@@ -843,13 +849,21 @@ __global__ void __launch_bounds__(128) k_ilu(int n, int mode, const SliceState* 
 }
 
 void ilu_prepare() {
-  cudaFuncSetAttribute(k_ilu, cudaFuncAttributeMaxDynamicSharedMemorySize, ILU_D * FCH * 128 * 16);
+  cudaFuncSetAttribute(k_ilu<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * FCH * 128 * 16);
+  cudaFuncSetAttribute(k_ilu<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * FCH * 128 * 16);
+  cudaFuncSetAttribute(k_ilu<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 6 * FCH * 128 * 16);
 }
 
 void ilu_step(int batch, int n, cudaStream_t s, const SliceState* st, double* part, int mode, float2* x,
               const float2* d, float2* r, const float2* q, const float2* atb, float2* y, float2* z,
-              const float* ia, const float* ib, const float* ic) {
-  k_ilu<<<batch, ilu_threads(n), ilu_smem(n), s>>>(n, mode, st, part, x, d, r, q, atb, y, z, ia, ib, ic);
+              const float* ia, const float* ib, const float* ic, int depth) {
+  const int T = ilu_threads(n);
+  if (depth == 3)
+    k_ilu<3><<<batch, T, ilu_smem(n, 3), s>>>(n, mode, st, part, x, d, r, q, atb, y, z, ia, ib, ic);
+  else if (depth == 6)
+    k_ilu<6><<<batch, T, ilu_smem(n, 6), s>>>(n, mode, st, part, x, d, r, q, atb, y, z, ia, ib, ic);
+  else
+    k_ilu<4><<<batch, T, ilu_smem(n, 4), s>>>(n, mode, st, part, x, d, r, q, atb, y, z, ia, ib, ic);
 }
 
 // =========================================================== PCG vectors ==
@@ -1081,6 +1095,62 @@ void mask_popcount(int batch, int n, cudaStream_t s, const uint8_t* mask, int* c
   k_popcount<<<dim3(blocks, batch), 256, 0, s>>>(N, mask, counts);
 }
 
+// ======================================================== objective sums ===
+
+__global__ void k_l21_sum(int n, const float2* __restrict__ c, const int* __restrict__ gidx,
+                          const int* __restrict__ goff, int G, int gsize, float eps, double* __restrict__ part,
+                          int slot) {
+  const int s = blockIdx.y;
+  __shared__ double red[32];
+  const float2* cs = c + (size_t)s * n * n;
+  const int count = gidx ? G : n * n;
+  const int chunk = (count + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * chunk, hi = min(count, lo + chunk);
+  float acc = 0.f;
+  for (int g = lo + threadIdx.x; g < hi; g += blockDim.x) {
+    float ss;
+    if (!gidx) {
+      ss = cabs2(cs[g]);
+    } else {
+      const int b = goff ? goff[g] : g * gsize;
+      const int e = goff ? goff[g + 1] : b + gsize;
+      ss = 0.f;
+      for (int k = b; k < e; ++k) ss += cabs2(cs[gidx[k]]);
+    }
+    acc += sqrtf(ss + eps);
+  }
+  const double tot = block_sum((double)acc, red);
+  if (threadIdx.x == 0) part[((size_t)s * NSLOT + slot) * MAXPART + blockIdx.x] = tot;
+}
+
+void l21_sum(int batch, int n, cudaStream_t s, const float2* c, const int* gidx, const int* goff, int G, int gsize,
+             float eps, double* part, int slot) {
+  k_l21_sum<<<dim3(axpy_ctas(n), batch), 256, 0, s>>>(n, c, gidx, goff, G, gsize, eps, part, slot);
+}
+
+__global__ void k_tv_sum(int n, const float2* __restrict__ x, float eps, double* __restrict__ part, int slot) {
+  const int s = blockIdx.y;
+  __shared__ double red[32];
+  const size_t base = (size_t)s * n * n;
+  const int N = n * n;
+  const int chunk = (N + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * chunk, hi = min(N, lo + chunk);
+  float acc = 0.f;
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const int r = i / n, cc = i % n;
+    const float2 xc = x[base + i];
+    const float2 g1 = cc > 0 ? csub(xc, x[base + i - 1]) : xc;
+    const float2 g2 = r > 0 ? csub(xc, x[base + i - n]) : xc;
+    acc += sqrtf(cabs2(g1) + cabs2(g2) + eps);
+  }
+  const double tot = block_sum((double)acc, red);
+  if (threadIdx.x == 0) part[((size_t)s * NSLOT + slot) * MAXPART + blockIdx.x] = tot;
+}
+
+void tv_sum(int batch, int n, cudaStream_t s, const float2* x, float eps, double* part, int slot) {
+  k_tv_sum<<<dim3(axpy_ctas(n), batch), 256, 0, s>>>(n, x, eps, part, slot);
+}
+
 // ========================================================== PCG scalars ===
 
 FI double sum_parts(const double* part, int s, int slot, int np) {
@@ -1101,6 +1171,7 @@ __global__ void k_state_init(int B, SliceState* st, const double* part, int np, 
   v.rhs2 = sum_parts(part, s, SLOT_RHS, np);
   v.rr = v.rhs2;
   v.relchg = 0.0;
+  v.relchg_prev = 0.0;
   v.active = 1;
   v.done = 0;
   v.breakdown = 0;
@@ -1183,19 +1254,32 @@ void pcg_beta(int batch, cudaStream_t s, SliceState* st, const double* part, int
   k_beta<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np_rz, np_rr, tol);
 }
 
-__global__ void k_outer_end(int B, SliceState* st, const double* part, int np, float tol) {
+// Outer-loop stop.  kind 0: relative change <= tol.  kind 1: estimated
+// distance to the limit <= tol.  Under linear convergence x^k -> x* with
+// contraction mu, ||x^k - x*|| ~ relchg_k mu / (1 - mu) (the sum of the
+// remaining steps) relative to ||x^k||; mu is the two-step geometric mean
+// sqrt(relchg_k / relchg_{k-2}), capped at 0.999.
+__global__ void k_outer_end(int B, SliceState* st, const double* part, int np, float tol, int kind) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B || st[s].done) return;
   const double dx = sum_parts(part, s, SLOT_DX, np);
   const double xx = sum_parts(part, s, SLOT_XX, np);
   const double rel = xx > 0.0 ? sqrt(dx / xx) : INFINITY;
+  const double prev2 = st[s].relchg_prev;
+  st[s].relchg_prev = st[s].relchg;
   st[s].relchg = rel;
   st[s].outer_done += 1;
-  if (tol > 0.f && rel <= (double)tol) st[s].done = 1;
+  if (!(tol > 0.f)) return;
+  if (kind == 0) {
+    if (rel <= (double)tol) st[s].done = 1;
+  } else if (st[s].outer_done >= 4 && prev2 > 0.0) {
+    const double mu = fmin(sqrt(rel / prev2), 0.999);
+    if (rel * mu / (1.0 - mu) <= (double)tol && rel <= (double)tol) st[s].done = 1;
+  }
 }
 
-void outer_end(int batch, cudaStream_t s, SliceState* st, const double* part, int np, float tol) {
-  k_outer_end<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np, tol);
+void outer_end(int batch, cudaStream_t s, SliceState* st, const double* part, int np, float tol, int kind) {
+  k_outer_end<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np, tol, kind);
 }
 
 }  // namespace firls

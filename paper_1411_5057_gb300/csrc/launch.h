@@ -36,6 +36,10 @@ void fft_row_ahb(int n, const FftArgs& a);
 void fft_col_mask(int n, const FftArgs& a);
 void fft_col_inv(int n, const FftArgs& a);
 void fft_row_inv(int n, const FftArgs& a);
+// partial ||R F x - b||^2 (t = rowFFT(x), a.b, a.mask) into slot a.mode
+void fft_col_resid(int n, const FftArgs& a);
+// t = colIFFT((1 - R) colFFT(t) + R n b)  (data consistency, column part)
+void fft_col_dc(int n, const FftArgs& a);
 void fft_prepare(int n);  // set shared-memory limits (call outside capture)
 
 // ---- wavelet (lifting) ----
@@ -48,6 +52,8 @@ struct WavArgs {
   float2* tmpA = nullptr;           // [batch][n/2 * n/2] ping-pong LL buffers
   float2* tmpB = nullptr;
   double* part = nullptr;
+  int rb = 0;          // rows per CTA of the tiled levels (0: default 8)
+  int coarse_max = 0;  // largest side kept in shared memory (0: default 64)
 };
 // c = Phi x (Mallat, stride n) with the final store scaled per `mode`:
 // RAW: c; MUL_W: w*c; MUL_PINV: c / (abar + lam w); SINGLETON_W: writes
@@ -60,8 +66,8 @@ void wavelet_inverse(const WavArgs& a, const float2* c, float2* x, const float2*
 // fine levels' scaled details go through c.  Optional partial Re<r, u>.
 void wavelet_apply(const WavArgs& a, const float2* x, float2* c, float* w, int mode, float2* u,
                    const float2* r, int real);
-int wavelet_inverse_ctas(int n, int levels);
-int wavelet_apply_launches(int n, int levels);
+int wavelet_inverse_ctas(int n, int levels, int rb, int coarse_max);
+int wavelet_apply_launches(int n, int levels, int coarse_max);
 void wav_prepare();
 
 // ---- TV, preconditioner, groups, PCG scalars ----
@@ -74,7 +80,7 @@ void penta_setup(int batch, int n, cudaStream_t s, const SliceState* st, const f
 enum IluMode { ILU_INIT = 0, ILU_STEP = 1, ILU_LAST = 2 };
 void ilu_step(int batch, int n, cudaStream_t s, const SliceState* st, double* part, int mode,
               float2* x, const float2* d, float2* r, const float2* q, const float2* atb, float2* y,
-              float2* z, const float* ia, const float* pb, const float* pc);
+              float2* z, const float* ia, const float* pb, const float* pc, int depth);
 
 enum AxpyMode { AXPY_INIT = 0, AXPY_STEP = 1, AXPY_LAST = 2 };
 void axpy_step(int batch, int n, cudaStream_t s, const SliceState* st, double* part, int mode,
@@ -91,6 +97,13 @@ void group_inverse_build(int n, int n_groups, int gsize, cudaStream_t s, const i
 
 void mask_popcount(int batch, int n, cudaStream_t s, const uint8_t* mask, int* counts);
 
+// Partial sums of the regularisers of F_eps (one slot each, axpy_ctas parts):
+// sum_j sqrt(|c_j|^2 + eps) (singleton groups) or sum_g sqrt(||c_g||^2 + eps),
+// and sum_i sqrt(|D1 x|_i^2 + |D2 x|_i^2 + eps).
+void l21_sum(int batch, int n, cudaStream_t s, const float2* c, const int* gidx, const int* goff, int n_groups,
+             int gsize, float eps, double* part, int slot);
+void tv_sum(int batch, int n, cudaStream_t s, const float2* x, float eps, double* part, int slot);
+
 // PCG scalar updates (one thread per slice)
 void pcg_alpha(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts);
 void pcg_rho_init(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts_rz,
@@ -101,7 +114,7 @@ void outer_begin(int batch, cudaStream_t s, SliceState* st);
 void relchange_parts(int batch, int n, cudaStream_t s, const SliceState* st, const float2* x,
                      const float2* xprev, double* part);
 void outer_end(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts,
-               float outer_tol);
+               float outer_tol, int tol_kind);
 void state_init(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts_rhs,
                 const int* counts, int n, const float* lam, const float* lam_tv, float eps);
 

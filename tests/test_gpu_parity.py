@@ -186,14 +186,16 @@ def test_weights_S_Pinv_parity(F, name, n, cfg):
 
 # -------------------------------------------------------- reconstructions ---
 
-def _gpu_solve(F, problems, outer, inner, pcg_tol=0.0, outer_tol=0.0, stats=False, lam_per_slice=None):
+def _gpu_solve(F, problems, outer, inner, pcg_tol=0.0, outer_tol=0.0, stats=False, lam_per_slice=None,
+               stop_on_distance=False):
     p0 = problems[0]
     n, B = p0.n, len(problems)
     ctx = F.Context(n, batch=B, real=p0.real)
     groups = dev(p0.groups) if p0.groups is not None else None
     ctx.set_operator(dev(np.stack([p.mask for p in problems])), p0.psi, p0.levels, groups)
     params = F.make_params(outer, inner, lam=p0.lam, lam_tv=p0.lam_tv, pcg_tol=pcg_tol, outer_tol=outer_tol,
-                           lam_per_slice=[p.lam for p in problems], lam_tv_per_slice=[p.lam_tv for p in problems])
+                           lam_per_slice=[p.lam for p in problems], lam_tv_per_slice=[p.lam_tv for p in problems],
+                           stop_on_distance=stop_on_distance)
     res = ctx.solve(c64(np.stack([p.b for p in problems])), params, stats=stats)
     if stats:
         return host(res[0]), res[1]
@@ -247,18 +249,25 @@ def test_firls_tv_db4_converged_parity(F):
 
 
 def test_bench_workload_reaches_converged_oracle(F):
-    """The bench workload (256^2 TV + D4, seed 2) at the bench schedule lands
-    within 1e-4 of the FP64 oracle's converged minimiser x*.
+    """The bench workload (256^2 TV + D4) with the bench's schedule and
+    per-slice stopping rule lands within 1e-4 of the FP64 oracle's converged
+    minimiser x* for every slice that has a stored x*.
 
-    x* is stored as a strided sample (every 4th row and column) written by
-    tests/golden/make_xstar.py, which calls only the oracle.
+    Each x* is stored as a strided sample (every 4th row and column) written
+    by tests/golden/make_xstar.py, which calls only the oracle.
     """
+    import glob
     import os
+    import re
     import bench
-    xs = np.load(os.path.join(os.path.dirname(__file__), "golden", "xstar_tv_db4_256_seed2_stride4.npy"))
-    p = bench.problem(2)
-    x = _gpu_solve(F, [p], bench.OUTER, bench.INNER)[0]
-    assert rel(x[::4, ::4], xs) < TOL_SOLVE, rel(x[::4, ::4], xs)
+    files = sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "xstar_tv_db4_256_seed*_stride4.npy")))
+    seeds = [int(re.search(r"seed(\d+)_", f).group(1)) for f in files]
+    assert 2 in seeds
+    probs = [bench.problem(s) for s in seeds]
+    x = _gpu_solve(F, probs, bench.OUTER, bench.INNER, outer_tol=bench.OUTER_TOL, stop_on_distance=True)
+    for i, f in enumerate(files):
+        xs = np.load(f)
+        assert rel(x[i][::4, ::4], xs) < TOL_SOLVE, (seeds[i], rel(x[i][::4, ::4], xs))
 
 
 def test_batch_slices_independent(F):

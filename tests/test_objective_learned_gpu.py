@@ -1,0 +1,137 @@
+"""F_eps on the GPU against the oracle, Theorem 2 measured on the GPU, the
+warm-start guard, and what the trained CNN warm start saves."""
+import os
+
+import numpy as np
+import pytest
+
+import firls_synth as fs
+from oracle import firls_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1411_5057_gb300 as F
+    return F
+
+
+def c64(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(torch.complex64).cuda()
+
+
+CASES = [
+    ("haar_real", lambda: fs.haar_l1_64()),
+    ("tree", lambda: fs.tree_db4_512(n=64)),
+    ("tv", lambda: fs.make_problem(96, 0.25, 0.01, 11, real=False, psi=4, levels=0, lam=0.0, lam_tv=1e-3)),
+    ("tv_db4_256", lambda: fs.tv_db4_256()),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_objective_parity(F, name, make):
+    p = make()
+    ctx = F.Context(p.n, real=p.real)
+    ctx.set_operator(torch.from_numpy(p.mask).cuda()[None], p.psi, p.levels,
+                     torch.from_numpy(p.groups).cuda() if p.groups is not None else None)
+    params = F.make_params(1, 1, lam=p.lam, lam_tv=p.lam_tv)
+    x = O.op_AH(p.b, p.mask, p.real) * 0.9 + (p.x0 * 0.1)
+    if p.real:
+        x = x.real
+    f_gpu = ctx.objective(c64(p.b[None]), params, c64(np.asarray(x, complex)[None]))[0]
+    f_ref = O.objective(x, p.b, p.mask, p.real, p.psi, p.levels, p.lam, p.lam_tv, p.groups, O.EPS)
+    assert abs(f_gpu - f_ref) < 1e-5 * abs(f_ref), (f_gpu, f_ref)
+
+
+def test_theorem2_monotone_on_gpu(F):
+    """F_eps(x^k) never increases along the GPU's own FIRLS trajectory."""
+    p = fs.tv_db4_256()
+    ctx = F.Context(p.n)
+    ctx.set_operator(torch.from_numpy(p.mask).cuda()[None], p.psi, p.levels)
+    b = c64(p.b[None])
+    params1 = F.make_params(1, 60, lam=p.lam, lam_tv=p.lam_tv)
+    x = ctx.adjoint(b)
+    f = [ctx.objective(b, params1, x)[0]]
+    for _ in range(12):
+        x = ctx.solve(b, params1, x0=x)
+        f.append(ctx.objective(b, params1, x)[0])
+    for k in range(len(f) - 1):
+        assert f[k + 1] <= f[k] * (1 + 1e-6), (k, f[k], f[k + 1])
+    assert f[-1] < f[0]
+
+
+def test_warm_start_guard(F):
+    p = fs.tv_db4_256(n=64)
+    q = fs.tv_db4_256(seed=3, n=64)
+    ctx = F.Context(64, batch=2)
+    ctx.set_operator(torch.from_numpy(np.stack([p.mask, q.mask])).cuda(), p.psi, p.levels)
+    b = c64(np.stack([p.b, q.b]))
+    params = F.make_params(1, 1, lam=p.lam, lam_tv=p.lam_tv)
+    good, _ = O.firls_problem(p, outer=20, inner=20)
+    rng = np.random.default_rng(0)
+    bad = 10 * (rng.standard_normal((64, 64)) + 1j * rng.standard_normal((64, 64)))
+    x1 = c64(np.stack([good, bad]))
+    x0 = torch.empty_like(x1)
+    chosen = ctx.warm_start_guard(b, params, x1, x0)
+    assert chosen == [True, False]
+    atb = ctx.adjoint(b)
+    torch.cuda.synchronize()
+    assert torch.equal(x0[0], x1[0]) and torch.equal(x0[1], atb[1])
+
+
+def test_data_consistency(F):
+    """DC(x) = F^H((1 - R) F x + R b): zero data term, identity on A^H b."""
+    p = fs.tv_db4_256(n=64)
+    ctx = F.Context(64)
+    ctx.set_operator(torch.from_numpy(p.mask).cuda()[None], p.psi, p.levels)
+    b = c64(p.b[None])
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((64, 64)) + 1j * rng.standard_normal((64, 64))
+    out = ctx.data_consistency(b, c64(x[None]))
+    torch.cuda.synchronize()
+    m = p.mask.astype(float)
+    ref = O.ifft2u((1 - m) * O.fft2u(x) + m * p.b)
+    got = out[0].cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(got - ref) < 2e-6 * np.linalg.norm(ref)
+    f0 = ctx.objective(b, F.make_params(1, 1), out)[0]
+    assert f0 < 1e-10 * np.sum(np.abs(p.b) ** 2)
+
+
+def test_learned_warm_start_saves_pcg_steps(F):
+    """Reduced learned-warm-start workload at 256^2: train the CNN on pairs
+    the solver generates, then count outer steps (60 PCG each) to reach 1e-4
+    of x* from A^H b and from the guarded CNN start on held-out slices.
+
+    The held-out references x* are long GPU runs; for seed 2 the FP64 oracle's
+    stored x* checks that reference."""
+    from paper_1411_5057_gb300 import learned as Lr
+    n, inner = 256, 60
+    train_seeds = list(range(10000, 10512))
+    held = [2] + list(range(20000, 20007))
+    atb, masks, xt = Lr.generate_pairs(n, train_seeds, 50, inner)
+    masks_h, b_h, meta = Lr.workload(n, held)
+    ctx = Lr._ctx(n, masks_h, meta)
+    bd = torch.from_numpy(b_h).cuda()
+    xstar = ctx.solve(bd, F.make_params(150, inner, lam=meta["lam"], lam_tv=meta["lam_tv"]))
+    atb_h = ctx.adjoint(bd)
+    gold = np.load(os.path.join(os.path.dirname(__file__), "golden", "xstar_tv_db4_256_seed2_stride4.npy"))
+    xs0 = xstar[0].cpu().numpy().astype(np.complex128)[::4, ::4]
+    assert np.linalg.norm(xs0 - gold) / np.linalg.norm(gold) < 2e-5
+    net = F.Cnn(n, 16)
+    net.set_params(fs.cnn_init_weights(0))
+    losses = Lr.train(net, atb, masks, xt, epochs=30, lr=1e-3, batch=16)
+    assert losses[-1] < 0.7 * losses[0]
+    net_eval = F.Cnn(n, len(held))
+    net_eval.set_params(net.get_params())
+    x0, chosen = Lr.warm_start(ctx, net_eval, bd, atb_h, torch.from_numpy(masks_h).cuda(),
+                               F.make_params(1, 1, lam=meta["lam"], lam_tv=meta["lam_tv"]))
+    plain = Lr.steps_to_tolerance(n, masks_h, b_h, meta, atb_h, xstar, inner)
+    learned = Lr.steps_to_tolerance(n, masks_h, b_h, meta, x0, xstar, inner)
+    print("outer steps to 1e-4, plain:", plain.tolist(), "learned:", learned.tolist())
+    assert np.all(plain > 0) and np.all(learned > 0)
+    assert learned.mean() < plain.mean()
+    assert np.all(learned <= plain + 1)
