@@ -49,7 +49,9 @@ typedef enum {
   FIRLS_E_CUDA = 4,        /* a CUDA runtime call or kernel launch failed    */
   FIRLS_E_NOMEM = 5,       /* device allocation failed                       */
   FIRLS_E_BREAKDOWN = 6,   /* PCG breakdown (d^H S d <= 0 or not finite)     */
-  FIRLS_E_STATE = 7        /* call out of order (e.g. solve before operator) */
+  FIRLS_E_STATE = 7,       /* call out of order (e.g. solve before operator) */
+  FIRLS_E_DEVICE_TIMEOUT = 8 /* a bounded wait inside a kernel ran out; the
+                                 slices it names hold invalid results        */
 } firls_status;
 
 /* Regulariser bitmask (psi_kind).  HAAR and DB4 are exclusive; TV may be
@@ -208,8 +210,9 @@ firls_status firls_slot_get(firls_ctx* ctx, int s, void* x_out);
 /* Autotuner: time the tile-shape choices of this context's size, batch and
  * regulariser on its own buffers (CUDA events on its stream) and keep the
  * fastest: rows per CTA of the tiled wavelet levels (4, 8, 16), the largest
- * wavelet block kept in shared memory (32, 64), the ILU row-prefetch depth
- * (3, 4, 6 stages).  cache_path (may be NULL) is a text file of earlier
+ * wavelet block kept in shared memory (32, 64), the ILU shared-memory ring
+ * shape (10 * rows per stage + stages: 42, 43, 44, 22, 23, 24, as far as
+ * they fit).  cache_path (may be NULL) is a text file of earlier
  * results keyed by "n batch psi levels": a hit skips the timing, a miss
  * appends the new result.  Overwrites the context's workspace; call after
  * firls_set_operator and before solving.  Synchronises the stream. */

@@ -32,14 +32,14 @@ struct firls_ctx {
   float2* tw = nullptr;
   float2 *atb = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *d = nullptr, *q = nullptr;
   float2 *t = nullptr, *u = nullptr, *cw = nullptr, *xprev = nullptr, *tmpA = nullptr, *tmpB = nullptr;
-  float *ww = nullptr, *wtv = nullptr, *ia = nullptr, *pb = nullptr, *pc = nullptr, *wdiag = nullptr;
+  float *ww = nullptr, *wtv = nullptr, *ia = nullptr, *wdiag = nullptr;
   float* wg = nullptr;
   int *gidx = nullptr, *goff = nullptr, *inv_off = nullptr, *inv_ids = nullptr;
   int *gcounts = nullptr, *gcursor = nullptr, *gerr = nullptr;
   float* sqtab = nullptr;
   int* sqlen = nullptr;
   // tile shapes (autotuned or defaults)
-  int tune_rb = 0, tune_cmax = 0, tune_ilu = 4;
+  int tune_rb = 0, tune_cmax = 0, tune_ilu = 0;  // 0: ILU ring shape chosen from n and batch
   SliceState* st = nullptr;
   double* part = nullptr;
   float *lam_d = nullptr, *lamtv_d = nullptr;
@@ -171,6 +171,17 @@ cudaEvent_t next_event(firls_ctx* c) {
   return c->evpool[c->evnext++];
 }
 
+// Inside a stream capture the events become external event-record nodes of
+// the graph (recorded at every replay); outside one they are plain records.
+void record_mark(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (s != nullptr) cudaStreamIsCapturing(s, &cs);
+  if (cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, s);
+}
+
 struct TMark {
   firls_ctx* c;
   int cls, launches;
@@ -178,12 +189,12 @@ struct TMark {
   TMark(firls_ctx* c_, int cls_, int launches_) : c(c_), cls(cls_), launches(launches_) {
     if (!c->timing) return;
     b = next_event(c);
-    cudaEventRecordWithFlags(b, c->stream, cudaEventRecordExternal);
+    record_mark(b, c->stream);
   }
   ~TMark() {
     if (!c->timing) return;
     cudaEvent_t e = next_event(c);
-    cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal);
+    record_mark(e, c->stream);
     c->marks.push_back({cls, launches, b, e});
   }
 };
@@ -231,7 +242,7 @@ void enqueue_weights(firls_ctx* c, const float2* x) {
   if (has_tv(c)) {
     tv_weights(B, n, c->stream, c->st, x, c->wtv);
     if (c->kind) wavelet_diag(B, n, c->levels, c->stream, c->st, c->ww, c->wdiag, c->sqtab, c->sqlen);
-    penta_setup(B, n, c->stream, c->st, c->wtv, c->kind ? c->wdiag : nullptr, c->ia, c->pb, c->pc);
+    penta_setup(B, n, c->stream, c->st, c->wtv, c->kind ? c->wdiag : nullptr, c->ia);
   }
 }
 
@@ -243,7 +254,7 @@ void enqueue_update_precond(firls_ctx* c, int step_mode, float pcg_tol, bool ini
     {
       TMark m(c, FIRLS_K_ILU, 1);
       ilu_step(B, n, c->stream, c->st, c->part, init ? ILU_INIT : ILU_STEP, c->x, c->d, c->r, c->q, c->atb,
-               c->u, c->z, c->ia, c->pb, c->pc, c->tune_ilu);
+               c->u, c->z, c->ia, c->wtv, c->tune_ilu);
     }
     TMark m(c, FIRLS_K_SCALARS, 1);
     if (init)
@@ -405,6 +416,7 @@ firls_status collect_stats(firls_ctx* c, firls_stats* stats, bool* breakdown) {
   CU(cudaMemcpyAsync(hs.data(), c->st, sizeof(SliceState) * c->batch, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
   firls_stats s{};
+  int faults = 0;
   for (const SliceState& v : hs) {
     s.outer_done = v.outer_done > s.outer_done ? v.outer_done : s.outer_done;
     s.pcg_steps += v.pcg_steps;
@@ -412,9 +424,12 @@ firls_status collect_stats(firls_ctx* c, firls_stats* stats, bool* breakdown) {
     const double rr = v.rhs2 > 0 ? std::sqrt(v.rr / v.rhs2) : 0.0;
     if (rr > s.max_rel_residual) s.max_rel_residual = rr;
     s.n_breakdown += v.breakdown ? 1 : 0;
+    faults += v.fault ? 1 : 0;
   }
   if (stats) *stats = s;
   *breakdown = s.n_breakdown > 0;
+  if (faults) return fail(c, FIRLS_E_DEVICE_TIMEOUT, "a bounded device wait ran out in " + std::to_string(faults) +
+                                                         " slice(s); their results are invalid");
   return FIRLS_OK;
 }
 
@@ -467,7 +482,7 @@ extern "C" firls_status firls_create(firls_ctx** out, int n_rows, int n_cols, in
   for (float2** p : {&c->atb, &c->x, &c->r, &c->z, &c->d, &c->q, &c->t, &c->u, &c->cw, &c->xprev}) A(p, BN);
   A(&c->tmpA, BH);
   A(&c->tmpB, BH);
-  for (float** p : {&c->ww, &c->wtv, &c->ia, &c->pb, &c->pc, &c->wdiag}) A(p, BN);
+  for (float** p : {&c->ww, &c->wtv, &c->ia, &c->wdiag}) A(p, BN);
   A(&c->st, (size_t)batch);
   A(&c->part, (size_t)batch * NSLOT * MAXPART);
   A(&c->lam_d, (size_t)batch);
@@ -1030,7 +1045,7 @@ extern "C" firls_status firls_autotune(firls_ctx* c, const char* cache_path) {
   char keybuf[128];
   std::snprintf(keybuf, sizeof keybuf, "n=%d batch=%d psi=%u levels=%d ", n, B, c->psi, c->levels);
   const std::string key(keybuf);
-  int rb = 0, cm = 0, il = 4;
+  int rb = 0, cm = 0, il = 0;
   if (!tune_cache_lookup(cache_path, key, &rb, &cm, &il)) {
     // deterministic, finite contents for timing
     const size_t BN = (size_t)B * n * n;
@@ -1042,7 +1057,7 @@ extern "C" firls_status firls_autotune(firls_ctx* c, const char* cache_path) {
     p.lambda_tv = 1e-3f;
     TRY(upload_params(c, &p));
     state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, 1e-10f);
-    if (has_tv(c)) penta_setup(B, n, c->stream, c->st, c->wtv, nullptr, c->ia, c->pb, c->pc);
+    if (has_tv(c)) penta_setup(B, n, c->stream, c->st, c->wtv, nullptr, c->ia);
     float best = 1e30f;
     if (c->kind) {
       for (int r : {4, 8, 16})
@@ -1060,14 +1075,15 @@ extern "C" firls_status firls_autotune(firls_ctx* c, const char* cache_path) {
     }
     if (has_tv(c)) {
       best = 1e30f;
-      for (int d : {3, 4, 6}) {
+      for (int shape : {42, 43, 44, 22, 23, 24}) {
+        if (!ilu_shape_fits(n, shape)) continue;
         const float t = time_ms(c, [&]() {
           ilu_step(B, n, c->stream, c->st, c->part, ILU_STEP, c->x, c->d, c->r, c->q, c->atb, c->u, c->z, c->ia,
-                   c->pb, c->pc, d);
+                   c->wtv, shape);
         }, 5);
         if (t < best) {
           best = t;
-          il = d;
+          il = shape;
         }
       }
     }

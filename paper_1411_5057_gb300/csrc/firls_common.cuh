@@ -23,7 +23,7 @@ struct SliceState {
   int breakdown;     // PCG broke down at least once
   int pcg_steps;     // PCG steps taken (all outer steps)
   int outer_done;    // outer steps taken
-  int pad_;
+  int fault;         // a bounded device wait ran out (results invalid)
   float lam;         // wavelet lambda
   float lam_tv;      // TV lambda
   float abar;        // mean(diag(A^H A)) = popcount / N

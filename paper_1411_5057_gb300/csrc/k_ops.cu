@@ -561,10 +561,10 @@ void wavelet_diag(int batch, int n, int levels, cudaStream_t s, const SliceState
 }
 
 // P = abar I + lam_tv (D1^T W D1 + D2^T W D2) [+ lam diag(Phi^T W Phi)] (Eq. ptv):
-// ia = 1/a_i, pb = b_i / a_i (b couples i, i+1), pc = c_i / a_i (c couples i, i+n).
+// ia = 1 / a_i, the inverse diagonal.  The off-diagonals (-lam_tv W_{i+1},
+// -lam_tv W_{i+n}) are formed from W inside the ILU sweeps.
 __global__ void k_penta(int n, const SliceState* __restrict__ st, const float* __restrict__ wtv,
-                        const float* __restrict__ wdiag, float* __restrict__ ia, float* __restrict__ pb,
-                        float* __restrict__ pc) {
+                        const float* __restrict__ wdiag, float* __restrict__ ia) {
   const int s = blockIdx.y;
   if (!slice_running(st, s)) return;
   const float abar = st[s].abar, lt = st[s].lam_tv, lw = st[s].lam;
@@ -576,49 +576,119 @@ __global__ void k_penta(int n, const SliceState* __restrict__ st, const float* _
     const float wd = r < n - 1 ? wtv[base + i + n] : 0.f;
     float a = abar + lt * (2.f * wc + wr + wd);
     if (wdiag) a = fmaf(lw, wdiag[base + i], a);
-    const float inv = 1.0f / a;
-    ia[base + i] = inv;
-    pb[base + i] = -lt * wr * inv;  // b_i / a_i
-    pc[base + i] = -lt * wd * inv;  // c_i / a_i
+    ia[base + i] = 1.0f / a;
   }
 }
 
 void penta_setup(int batch, int n, cudaStream_t s, const SliceState* st, const float* wtv,
-                 const float* wdiag, float* ia, float* pb, float* pc) {
+                 const float* wdiag, float* ia) {
   const int N = n * n;
   const int blocks = (N + 255) / 256 < 64 ? (N + 255) / 256 : 64;
-  k_penta<<<dim3(blocks, batch), 256, 0, s>>>(n, st, wtv, wdiag, ia, pb, pc);
+  k_penta<<<dim3(blocks, batch), 256, 0, s>>>(n, st, wtv, wdiag, ia);
 }
 
 // ------------------------------------------------ ILU solves (Sec. 4.2) -----
-// z = U^{-1} L^{-1} r with L = I + L_P diag(a)^{-1}, U = diag(a) + U_P.  With
-// ia = 1/a, ib = b/a, ic = c/a (b couples i, i+1; c couples i, i+n):
-//   forward  y_i = r_i - ib_{i-1} y_{i-1} - ic_{i-n} y_{i-n}
-//   backward z_i = ia_i y_i - ib_i z_{i+1} - ic_i z_{i+n}
-// P is symmetric, so U = diag(a) L^T and Re<r, z> = sum_i ia_i |y_i|^2,
-// which the forward sweep accumulates (the backward sweep need not reread r).
-// One CTA per slice sweeps the rows; within a row the first-order
-// recurrence is an affine scan across threads (4 columns per thread).  Rows
-// are prefetched ILU_D - 1 ahead through a cp.async ring in shared memory
-// (each thread copies and later reads only its own 16-byte chunks).
+// z = U^{-1} L^{-1} r with L = I + L_P diag(a)^{-1}, U = diag(a) + U_P, where
+// P = diag(a) + L_P + U_P is the TV penta-diagonal matrix.  Its off-diagonal
+// entries are b_i = -lam_tv W_{i+1} (couples i, i+1; zero at a row end) and
+// c_i = -lam_tv W_{i+n} (couples i, i+n; zero in the last row), so with
+// ia = 1/a the sweeps need only W and ia:
+//   forward  y_i = r_i + g_i y_{i-1} + h_i y_{i-n},
+//            g_i = lam W_i ia_{i-1} [col > 0],  h_i = lam W_i ia_{i-n} [row > 0]
+//   backward z_i = ia_i y_i + g_i z_{i+1} + h_i z_{i+n},
+//            g_i = lam ia_i W_{i+1} [col < n-1],  h_i = lam ia_i W_{i+n} [row < n-1]
+// P is symmetric, so U = diag(a) L^T and Re<r, z> = sum_i ia_i |y_i|^2.
+//
+// Kernel layout: one CTA per slice, five warps.
+//  * Warp 1 (scan warp) runs only the row recurrences: a row is E columns
+//    per lane, composed as affine maps and combined by a warp shuffle scan
+//    (no block barrier); it stores y (z) itself.
+//  * Warps 2-4 (helpers) own two-column chunks and process G rows at a time
+//    (independent rows, so their latencies overlap): the residual update
+//    r -= alpha q, x += alpha d, and per column (t, h, g) in the scan warp's
+//    lane-major layout.
+//  * Warp 0 (producer, one lane) fills a ring of S stages of G rows with
+//    1-D bulk copies (TMA), one copy per array and stage.
+// Handover per stage, with mbarriers: `full` (bytes landed), `empty`
+// (helpers done with the natural rows), `ready` (helpers wrote the group's
+// coefficients), `consumed` (scan warp done with them).  The scan warp waits
+// once per group of G rows and prefetches the next row of the group while
+// it scans the current one.  Every wait is bounded; a wait that runs out
+// marks the slice faulted and the CTA finishes without hanging.
 
 FI unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-FI void cp_async16(void* s, const void* g) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(s)), "l"(g) : "memory");
-}
-FI void cp_async4(void* s, const void* g) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(s)), "l"(g) : "memory");
-}
-FI void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int K> FI void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
 
-// Exclusive scan of affine maps y -> A y + B in logical thread order
-// (forward: thread order; REV: reversed).  Returns B of the exclusive
-// prefix, i.e. the value entering this thread's segment for a zero boundary.
-// One barrier; sA/sB hold two 32-entry buffers alternated by `par`.
+FI void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+FI void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+FI void mbar_arrive_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+FI bool mbar_test(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// try_wait suspends the thread until the phase completes or the hint
+// (nanoseconds) runs out; the loop bounds the whole wait to about a second.
+FI bool mbar_try(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(100000u)
+      : "memory");
+  return ok != 0;
+}
+FI bool mbar_wait(uint64_t* bar, unsigned parity) {
+  if (mbar_test(bar, parity)) return true;
+  for (int it = 0; it < 10000; ++it)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+// 1-D bulk copy global -> shared (16-byte aligned, size a multiple of 16),
+// completion counted in bytes on `bar`.
+FI void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+FI void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;\n" ::: "memory"); }
+FI int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared.b32 %0, [%1];\n" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+  return v;
+}
+FI void st_release(int* p, int v) {
+  asm volatile("st.release.cta.shared.b32 [%0], %1;\n" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+// Bounded poll until *p >= want (about a second at most); returns the value
+// seen, or -1 when the wait ran out.
+FI int poll_at_least(const int* p, int want) {
+  for (int it = 0; it < (1 << 24); ++it) {
+    const int v = ld_acquire(p);
+    if (v >= want) return v;
+    if (it >= 256) __nanosleep(32);
+  }
+  return -1;
+}
+
+// Warp-wide exclusive scan of affine maps v -> A v + B in lane order
+// (REV: from lane 31 down).  Returns the value entering this lane's segment
+// for a zero value entering the row.
 template <bool REV>
-FI float2 affine_exclusive(float A, float2 B, float* sA, float2* sB, int par) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+FI float2 warp_affine_exclusive(float A, float2 B) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
     const float Ap = REV ? __shfl_down_sync(0xffffffffu, A, off) : __shfl_up_sync(0xffffffffu, A, off);
@@ -629,241 +699,415 @@ FI float2 affine_exclusive(float A, float2 B, float* sA, float2* sB, int par) {
       A = A * Ap;
     }
   }
-  float* sa = sA + par * 32;
-  float2* sb = sB + par * 32;
-  if (lane == (REV ? 0 : 31)) {
-    sa[w] = A;
-    sb[w] = B;
-  }
-  __syncthreads();
-  float2 Bp = make_float2(0.f, 0.f);
-  if (!REV) {
-    for (int v = 0; v < w; ++v) Bp = make_float2(fmaf(sa[v], Bp.x, sb[v].x), fmaf(sa[v], Bp.y, sb[v].y));
-  } else {
-    for (int v = nw - 1; v > w; --v) Bp = make_float2(fmaf(sa[v], Bp.x, sb[v].x), fmaf(sa[v], Bp.y, sb[v].y));
-  }
-  // inclusive value of the logically preceding lane, then the warp prefix
-  const float Ai = REV ? __shfl_down_sync(0xffffffffu, A, 1) : __shfl_up_sync(0xffffffffu, A, 1);
-  const float bix = REV ? __shfl_down_sync(0xffffffffu, B.x, 1) : __shfl_up_sync(0xffffffffu, B.x, 1);
-  const float biy = REV ? __shfl_down_sync(0xffffffffu, B.y, 1) : __shfl_up_sync(0xffffffffu, B.y, 1);
-  if (lane == (REV ? 31 : 0)) return Bp;
-  return make_float2(fmaf(Ai, Bp.x, bix), fmaf(Ai, Bp.y, biy));
+  const float bx = REV ? __shfl_down_sync(0xffffffffu, B.x, 1) : __shfl_up_sync(0xffffffffu, B.x, 1);
+  const float by = REV ? __shfl_down_sync(0xffffffffu, B.y, 1) : __shfl_up_sync(0xffffffffu, B.y, 1);
+  if (lane == (REV ? 31 : 0)) return make_float2(0.f, 0.f);
+  return make_float2(bx, by);
 }
 
-constexpr int ILU_E = 4;
-constexpr int ILU_DMAX = 6;  // ring stages (rows in flight: D - 1 ahead); D in {3, 4, 6}
-// 16-byte chunk slots per thread and stage
-enum { FC_R0 = 0, FC_R1, FC_Q0, FC_Q1, FC_X0, FC_X1, FC_D0, FC_D1, FC_IA, FC_IB, FC_IC, FC_IBL, FCH };
-enum { BC_Y0 = 0, BC_Y1, BC_IA, BC_IB, BC_IC };
+// Store E consecutive complex values of one lane (columns c0 .. c0+E-1 < n).
+template <int E>
+FI void store_lane_row(float2* dst, int c0, int n, const float2 (&v)[E]) {
+  if ((E & 1) == 0 && c0 + E <= n) {
+#pragma unroll
+    for (int e = 0; e < E; e += 2)
+      *reinterpret_cast<float4*>(dst + c0 + e) = make_float4(v[e].x, v[e].y, v[e + 1].x, v[e + 1].y);
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (c0 + e < n) dst[c0 + e] = v[e];
+  }
+}
 
-static int ilu_threads(int n) { return (n / ILU_E + 31) / 32 * 32; }
-static int ilu_smem(int n, int D) { return D * FCH * ilu_threads(n) * 16; }
+constexpr int IW_HWARPS = 3;                   // helper warps (warps 2-4)
+constexpr int IW_HELPERS = 32 * IW_HWARPS;
+constexpr int IW_THREADS = 32 + IW_HELPERS + 32;
+constexpr int IW_MAXCH = 3;                    // chunks of two columns per helper thread (n <= 512)
+constexpr int IW_MAXSTAGES = 8;
 
-template <int ILU_D>
-__global__ void __launch_bounds__(128) k_ilu(int n, int mode, const SliceState* __restrict__ st,
-                                             double* __restrict__ part, float2* __restrict__ x,
-                                             const float2* __restrict__ d, float2* __restrict__ r,
-                                             const float2* __restrict__ q, const float2* __restrict__ atb,
-                                             float2* __restrict__ y, float2* __restrict__ z,
-                                             const float* __restrict__ ia, const float* __restrict__ ib,
-                                             const float* __restrict__ ic) {
+static int iw_cols_per_lane(int n) { return (n + 31) / 32; }
+// Stage of G rows (bytes): R, Q, X, D (8nG each), W, IA (4nG each), then
+// SC: per row, float4 (t.x, t.y, h, g) per lane-major column slot.
+struct IwLayout {
+  int n, G, ns, oQ, oX, oD, oW, oIA, oSC, bytes;
+};
+static IwLayout iw_layout(int n, int G) {
+  IwLayout L;
+  L.n = n;
+  L.G = G;
+  L.ns = 32 * iw_cols_per_lane(n);
+  L.oQ = 8 * n * G;
+  L.oX = 16 * n * G;
+  L.oD = 24 * n * G;
+  L.oW = 32 * n * G;
+  L.oIA = 36 * n * G;
+  L.oSC = 40 * n * G;
+  L.bytes = (L.oSC + 16 * L.ns * G + 127) / 128 * 128;
+  return L;
+}
+
+// Ring position: stage index and the parity of its current use.
+struct RingPos {
+  int s;
+  unsigned ph;
+  FI void next(int S) {
+    if (++s == S) {
+      s = 0;
+      ph ^= 1u;
+    }
+  }
+};
+
+// Groups: forward group g holds rows gG .. gG+G-1; backward group g (after
+// the NG = n/G forward ones) holds rows n-(g'+1)G .. n-g'G-1, g' = g - NG,
+// processed from the bottom row up.  Row uses: forward row k is use k,
+// backward step k (row n-1-k) is use n + k; use u sits in group u / G at
+// row slot u % G.
+template <int E, int G>
+__global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
+    k_ilu(int n, int mode, int S, IwLayout lay, SliceState* __restrict__ st, double* __restrict__ part,
+          float2* __restrict__ x, const float2* __restrict__ d, float2* __restrict__ r,
+          const float2* __restrict__ q, const float2* __restrict__ atb, float2* __restrict__ y,
+          float2* __restrict__ z, const float* __restrict__ ia, const float* __restrict__ wtv) {
   const int s = blockIdx.x;
   if (!slice_running(st, s)) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  float4* ring = reinterpret_cast<float4*>(smem);
-  __shared__ float sA[64];
-  __shared__ float2 sB[64];
+  __shared__ __align__(8) uint64_t bar_full[IW_MAXSTAGES], bar_empty[IW_MAXSTAGES];
+  __shared__ __align__(8) uint64_t bar_ready[IW_MAXSTAGES], bar_used[IW_MAXSTAGES];
+  __shared__ int y_stored;  // 1 once every y row is stored and fenced
+  __shared__ volatile int abort_flag;
   __shared__ double red[32];
-  const int T = blockDim.x, t = threadIdx.x;
-  const int c0 = ILU_E * t;
-  const bool own = c0 < n;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int NCH = n >> 1;
+  const int NG = n / G;
+  const float lam = st[s].lam_tv;
   const float alpha = (float)st[s].alpha;
   const size_t base = (size_t)s * n * n;
-  auto slot = [&](int stage, int ch) -> float4* { return ring + ((size_t)stage * FCH + ch) * T + t; };
-  const float2* rsrc = (mode == ILU_INIT) ? atb : r;
-
-  auto issue_fwd = [&](int row) {
-    if (row < n && own) {
-      const int stg = row % ILU_D;
-      const size_t g = base + (size_t)row * n + c0;
-      cp_async16(slot(stg, FC_R0), rsrc + g);
-      cp_async16(slot(stg, FC_R1), rsrc + g + 2);
-      cp_async16(slot(stg, FC_Q0), q + g);
-      cp_async16(slot(stg, FC_Q1), q + g + 2);
-      if (mode != ILU_INIT) {
-        cp_async16(slot(stg, FC_X0), x + g);
-        cp_async16(slot(stg, FC_X1), x + g + 2);
-        cp_async16(slot(stg, FC_D0), d + g);
-        cp_async16(slot(stg, FC_D1), d + g + 2);
-      }
-      cp_async16(slot(stg, FC_IA), ia + g);
-      cp_async16(slot(stg, FC_IB), ib + g);
-      cp_async16(slot(stg, FC_IC), ic + g);
-      if (c0 > 0) cp_async4(slot(stg, FC_IBL), ib + g - 1);
+  if (t == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&bar_full[i], 1);
+      mbar_init(&bar_empty[i], IW_HWARPS);
+      mbar_init(&bar_ready[i], IW_HWARPS);
+      mbar_init(&bar_used[i], 1);
     }
-    cp_async_commit();
-  };
-
-  float2 yprev[ILU_E];
-  float icprev[ILU_E];
-#pragma unroll
-  for (int e = 0; e < ILU_E; ++e) {
-    yprev[e] = make_float2(0.f, 0.f);
-    icprev[e] = 0.f;
+    y_stored = 0;
+    abort_flag = 0;
   }
-  float rr = 0.f, rho = 0.f;
-  for (int k = 0; k < ILU_D - 1; ++k) issue_fwd(k);
-  for (int row = 0; row < n; ++row) {
-    issue_fwd(row + ILU_D - 1);
-    cp_async_wait<ILU_D - 1>();
-    const int stg = row % ILU_D;
-    float A = 1.f;
-    float2 B = make_float2(0.f, 0.f);
-    float2 tv[ILU_E];
-    float iav[ILU_E], ibv[ILU_E], icv[ILU_E], ibl = 0.f;
-    const size_t g = base + (size_t)row * n + c0;
-    if (own) {
-      const float4 r0 = *slot(stg, FC_R0), r1 = *slot(stg, FC_R1);
-      const float4 q0 = *slot(stg, FC_Q0), q1 = *slot(stg, FC_Q1);
-      const float4 fa = *slot(stg, FC_IA), fb = *slot(stg, FC_IB), fc = *slot(stg, FC_IC);
-      if (c0 > 0) ibl = slot(stg, FC_IBL)->x;
-      float2 rv[ILU_E] = {make_float2(r0.x, r0.y), make_float2(r0.z, r0.w), make_float2(r1.x, r1.y),
-                          make_float2(r1.z, r1.w)};
-      const float2 qv[ILU_E] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y),
-                                make_float2(q1.z, q1.w)};
-      iav[0] = fa.x; iav[1] = fa.y; iav[2] = fa.z; iav[3] = fa.w;
-      ibv[0] = fb.x; ibv[1] = fb.y; ibv[2] = fb.z; ibv[3] = fb.w;
-      icv[0] = fc.x; icv[1] = fc.y; icv[2] = fc.z; icv[3] = fc.w;
-      if (mode == ILU_INIT) {
-#pragma unroll
-        for (int e = 0; e < ILU_E; ++e) rv[e] = csub(rv[e], qv[e]);
-      } else {
-        const float4 x0 = *slot(stg, FC_X0), x1 = *slot(stg, FC_X1);
-        const float4 d0 = *slot(stg, FC_D0), d1 = *slot(stg, FC_D1);
-        const float2 xv[ILU_E] = {make_float2(x0.x, x0.y), make_float2(x0.z, x0.w), make_float2(x1.x, x1.y),
-                                  make_float2(x1.z, x1.w)};
-        const float2 dv[ILU_E] = {make_float2(d0.x, d0.y), make_float2(d0.z, d0.w), make_float2(d1.x, d1.y),
-                                  make_float2(d1.z, d1.w)};
-        float2 xn[ILU_E];
-#pragma unroll
-        for (int e = 0; e < ILU_E; ++e) {
-          rv[e] = cfma(-alpha, qv[e], rv[e]);
-          xn[e] = cfma(alpha, dv[e], xv[e]);
-        }
-        reinterpret_cast<float4*>(x + g)[0] = make_float4(xn[0].x, xn[0].y, xn[1].x, xn[1].y);
-        reinterpret_cast<float4*>(x + g)[1] = make_float4(xn[2].x, xn[2].y, xn[3].x, xn[3].y);
-      }
-      reinterpret_cast<float4*>(r + g)[0] = make_float4(rv[0].x, rv[0].y, rv[1].x, rv[1].y);
-      reinterpret_cast<float4*>(r + g)[1] = make_float4(rv[2].x, rv[2].y, rv[3].x, rv[3].y);
-#pragma unroll
-      for (int e = 0; e < ILU_E; ++e) {
-        rr += cabs2(rv[e]);
-        tv[e] = cfma(-icprev[e], yprev[e], rv[e]);
-        const float l = e == 0 ? ibl : ibv[e - 1];
-        B = cfma(-l, B, tv[e]);
-        A = -l * A;
-      }
-    }
-    float2 yin = affine_exclusive<false>(A, B, sA, sB, row & 1);
-    if (own) {
-      float2 yv[ILU_E];
-#pragma unroll
-      for (int e = 0; e < ILU_E; ++e) {
-        const float l = e == 0 ? ibl : ibv[e - 1];
-        yin = cfma(-l, yin, tv[e]);
-        yv[e] = yin;
-        rho = fmaf(iav[e], cabs2(yin), rho);
-        yprev[e] = yin;
-        icprev[e] = icv[e];
-      }
-      reinterpret_cast<float4*>(y + g)[0] = make_float4(yv[0].x, yv[0].y, yv[1].x, yv[1].y);
-      reinterpret_cast<float4*>(y + g)[1] = make_float4(yv[2].x, yv[2].y, yv[3].x, yv[3].y);
+  if (lay.ns > n) {  // slots of columns >= n are never written: make them zero, not garbage
+    for (int i = t; i < S * G * lay.ns; i += IW_THREADS) {
+      const int row = i / lay.ns;
+      unsigned char* sp = smem + (size_t)(row / G) * lay.bytes + lay.oSC + (size_t)(row % G) * 16 * lay.ns;
+      reinterpret_cast<float4*>(sp)[i % lay.ns] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
-  cp_async_wait<0>();
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   __syncthreads();
-
-  auto issue_bwd = [&](int k) {  // k-th row of the backward sweep: row n-1-k
-    if (k < n && own) {
-      const int row = n - 1 - k;
-      const int stg = k % ILU_D;
-      const size_t g = base + (size_t)row * n + c0;
-      cp_async16(slot(stg, BC_Y0), y + g);
-      cp_async16(slot(stg, BC_Y1), y + g + 2);
-      cp_async16(slot(stg, BC_IA), ia + g);
-      cp_async16(slot(stg, BC_IB), ib + g);
-      cp_async16(slot(stg, BC_IC), ic + g);
-    }
-    cp_async_commit();
+  auto fault = [&]() {
+    abort_flag = 1;
+    st[s].fault = 1;
   };
-  float2 znext[ILU_E];
+  // lane-major slot of column c (lane c / E, element c % E), XOR-swizzled so
+  // that helper stores of neighbouring columns hit different banks
+  auto slot_of = [&](int c) -> int {
+    const int e = c % E;
+    return e * 32 + ((c / E) ^ (e & 31));
+  };
+  auto sc_row = [&](int stg, int slot) -> float4* {
+    return reinterpret_cast<float4*>(smem + (size_t)stg * lay.bytes + lay.oSC + (size_t)slot * 16 * lay.ns);
+  };
+
+  float rr = 0.f, rho = 0.f;
+
+  if (warp == 1) {
+    // ============================================================ scan warp
+    // (alone on its SM sub-partition: of the five warps, 0 and 4 share one)
+    float2 vab[E];  // y of the row above (forward) / z of the row below (backward)
+    RingPos pos{0, 0u};
+    bool ok = true;
+    for (int sweep = 0; sweep < 2 && ok; ++sweep) {
+      if (sweep == 1) {
+        // y goes back to global memory and is re-read by bulk copies, so
+        // order the generic stores before the async proxy
+        fence_proxy_async_global();
+        __syncwarp();
+        if (lane == 0) st_release(&y_stored, 1);
+      }
 #pragma unroll
-  for (int e = 0; e < ILU_E; ++e) znext[e] = make_float2(0.f, 0.f);
-  for (int k = 0; k < ILU_D - 1; ++k) issue_bwd(k);
-  for (int k = 0; k < n; ++k) {
-    issue_bwd(k + ILU_D - 1);
-    cp_async_wait<ILU_D - 1>();
-    const int stg = k % ILU_D;
-    const int row = n - 1 - k;
-    const size_t g = base + (size_t)row * n + c0;
-    float A = 1.f;
-    float2 B = make_float2(0.f, 0.f);
-    float2 tv[ILU_E];
-    float iav[ILU_E], ibv[ILU_E];
-    if (own) {
-      const float4 y0 = *slot(stg, BC_Y0), y1 = *slot(stg, BC_Y1);  // y of row n-1-k
-      const float4 fa = *slot(stg, BC_IA), fb = *slot(stg, BC_IB), fc = *slot(stg, BC_IC);
-      const float2 yv[ILU_E] = {make_float2(y0.x, y0.y), make_float2(y0.z, y0.w), make_float2(y1.x, y1.y),
-                                make_float2(y1.z, y1.w)};
-      const float icv[ILU_E] = {fc.x, fc.y, fc.z, fc.w};
-      iav[0] = fa.x; iav[1] = fa.y; iav[2] = fa.z; iav[3] = fa.w;
-      ibv[0] = fb.x; ibv[1] = fb.y; ibv[2] = fb.z; ibv[3] = fb.w;
+      for (int e = 0; e < E; ++e) vab[e] = make_float2(0.f, 0.f);
+      for (int gg = 0; gg < NG; ++gg) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&bar_ready[pos.s], pos.ph))) {
+          ok = false;
+          break;
+        }
+        float4 cA[E], cB[E];
+        {
+          const float4* sc = sc_row(pos.s, 0);
 #pragma unroll
-      for (int e = ILU_E - 1; e >= 0; --e) {
-        tv[e] = cfma(-icv[e], znext[e], cscale(yv[e], iav[e]));  // ia y - ic z_{i+n}
-        B = cfma(-ibv[e], B, tv[e]);
-        A = -ibv[e] * A;
+          for (int e = 0; e < E; ++e) cA[e] = sc[e * 32 + (lane ^ (e & 31))];
+        }
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+          float4(&cur)[E] = (i & 1) ? cB : cA;
+          float4(&nxt)[E] = (i & 1) ? cA : cB;
+          if (i + 1 < G) {  // the next row of this group, while this one is scanned
+            const float4* sc = sc_row(pos.s, i + 1);
+#pragma unroll
+            for (int e = 0; e < E; ++e) nxt[e] = sc[e * 32 + (lane ^ (e & 31))];
+          } else {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar_used[pos.s]);
+          }
+          float2 tv[E];
+          float A = 1.f;
+          float2 B = make_float2(0.f, 0.f);
+          if (sweep == 0) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              tv[e] = make_float2(fmaf(cur[e].z, vab[e].x, cur[e].x), fmaf(cur[e].z, vab[e].y, cur[e].y));
+              B = make_float2(fmaf(cur[e].w, B.x, tv[e].x), fmaf(cur[e].w, B.y, tv[e].y));
+              A *= cur[e].w;
+            }
+            float2 v = warp_affine_exclusive<false>(A, B);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              v = make_float2(fmaf(cur[e].w, v.x, tv[e].x), fmaf(cur[e].w, v.y, tv[e].y));
+              vab[e] = v;
+            }
+            store_lane_row<E>(y + base + (size_t)(gg * G + i) * n, E * lane, n, vab);
+          } else {
+#pragma unroll
+            for (int e = E - 1; e >= 0; --e) {
+              tv[e] = make_float2(fmaf(cur[e].z, vab[e].x, cur[e].x), fmaf(cur[e].z, vab[e].y, cur[e].y));
+              B = make_float2(fmaf(cur[e].w, B.x, tv[e].x), fmaf(cur[e].w, B.y, tv[e].y));
+              A *= cur[e].w;
+            }
+            float2 v = warp_affine_exclusive<true>(A, B);
+#pragma unroll
+            for (int e = E - 1; e >= 0; --e) {
+              v = make_float2(fmaf(cur[e].w, v.x, tv[e].x), fmaf(cur[e].w, v.y, tv[e].y));
+              vab[e] = v;
+            }
+            store_lane_row<E>(z + base + (size_t)(n - 1 - gg * G - i) * n, E * lane, n, vab);
+          }
+        }
+        pos.next(S);
       }
     }
-    float2 zr = affine_exclusive<true>(A, B, sA, sB, k & 1);
-    if (own) {
-      float2 zv[ILU_E];
-#pragma unroll
-      for (int e = ILU_E - 1; e >= 0; --e) {
-        zr = cfma(-ibv[e], zr, tv[e]);
-        zv[e] = zr;
-        znext[e] = zr;
+    if (!ok) fault();
+  } else if (warp == 0) {
+    // ============================================================= producer
+    if (lane == 0) {
+      const float2* rsrc = (mode == ILU_INIT) ? atb : r;
+      const bool init = mode == ILU_INIT;
+      const unsigned c8 = 8u * n * G, c4 = 4u * n * G;
+      RingPos pos{0, 0u};
+      bool ok = true;
+      for (int g = 0; g < 2 * NG && ok; ++g) {
+        if (abort_flag) break;
+        // the stage's previous group (g - S) has been left by every helper
+        if (g >= S && !mbar_wait(&bar_empty[pos.s], pos.ph ^ 1u)) {
+          ok = false;
+          break;
+        }
+        if (g == NG && poll_at_least(&y_stored, 1) < 1) {  // backward copies read y
+          ok = false;
+          break;
+        }
+        unsigned char* sp = smem + (size_t)pos.s * lay.bytes;
+        uint64_t* bar = &bar_full[pos.s];
+        if (g < NG) {
+          const size_t go = base + (size_t)g * G * n;
+          mbar_arrive_tx(bar, init ? 2 * c8 + 2 * c4 : 4 * c8 + 2 * c4);
+          bulk_g2s(sp, rsrc + go, c8, bar);
+          bulk_g2s(sp + lay.oQ, q + go, c8, bar);
+          if (!init) {
+            bulk_g2s(sp + lay.oX, x + go, c8, bar);
+            bulk_g2s(sp + lay.oD, d + go, c8, bar);
+          }
+          bulk_g2s(sp + lay.oW, wtv + go, c4, bar);
+          bulk_g2s(sp + lay.oIA, ia + go, c4, bar);
+        } else {
+          const size_t go = base + (size_t)(n - (g - NG + 1) * G) * n;
+          mbar_arrive_tx(bar, c8 + 2 * c4);
+          bulk_g2s(sp, y + go, c8, bar);
+          bulk_g2s(sp + lay.oW, wtv + go, c4, bar);
+          bulk_g2s(sp + lay.oIA, ia + go, c4, bar);
+        }
+        pos.next(S);
       }
-      reinterpret_cast<float4*>(z + g)[0] = make_float4(zv[0].x, zv[0].y, zv[1].x, zv[1].y);
-      reinterpret_cast<float4*>(z + g)[1] = make_float4(zv[2].x, zv[2].y, zv[3].x, zv[3].y);
+      if (!ok) fault();
     }
+  } else {
+    // ============================================================== helpers
+    const int hh = t - 64;
+    float2 prev[IW_MAXCH];  // ia of the row above (forward) / W of the row below (backward)
+#pragma unroll
+    for (int c = 0; c < IW_MAXCH; ++c) prev[c] = make_float2(0.f, 0.f);
+    bool ok = true;
+    RingPos pos{0, 0u};
+    const size_t nG4 = (size_t)4 * n;  // bytes per float row
+    for (int g = 0; g < 2 * NG && ok; ++g) {
+      if (__any_sync(0xffffffffu, abort_flag != 0)) break;
+      if (g == NG) {
+#pragma unroll
+        for (int c = 0; c < IW_MAXCH; ++c) prev[c] = make_float2(0.f, 0.f);
+      }
+      unsigned char* sp = smem + (size_t)pos.s * lay.bytes;
+      bool got = mbar_wait(&bar_full[pos.s], pos.ph);
+      if (g >= S) got = got && mbar_wait(&bar_used[pos.s], pos.ph ^ 1u);  // scan warp left group g - S
+      if (!__all_sync(0xffffffffu, got)) {
+        ok = false;
+        break;
+      }
+      if (g < NG) {
+#pragma unroll
+        for (int ch = 0; ch < IW_MAXCH; ++ch) {
+          const int j = hh + IW_HELPERS * ch;
+          if (j < NCH) {
+            const int c = 2 * j;
+#pragma unroll
+            for (int i = 0; i < G; ++i) {
+              const size_t g0 = base + (size_t)(g * G + i) * n + c;
+              const unsigned char* rowp = sp + (size_t)i * 8 * n;
+              const float4 r4 = *reinterpret_cast<const float4*>(rowp + 16 * j);
+              const float4 q4 = *reinterpret_cast<const float4*>(rowp + lay.oQ + 16 * j);
+              float4 rn;
+              if (mode == ILU_INIT) {
+                rn = make_float4(r4.x - q4.x, r4.y - q4.y, r4.z - q4.z, r4.w - q4.w);
+              } else {
+                const float4 x4 = *reinterpret_cast<const float4*>(rowp + lay.oX + 16 * j);
+                const float4 d4 = *reinterpret_cast<const float4*>(rowp + lay.oD + 16 * j);
+                rn = make_float4(fmaf(-alpha, q4.x, r4.x), fmaf(-alpha, q4.y, r4.y), fmaf(-alpha, q4.z, r4.z),
+                                 fmaf(-alpha, q4.w, r4.w));
+                *reinterpret_cast<float4*>(x + g0) =
+                    make_float4(fmaf(alpha, d4.x, x4.x), fmaf(alpha, d4.y, x4.y), fmaf(alpha, d4.z, x4.z),
+                                fmaf(alpha, d4.w, x4.w));
+              }
+              *reinterpret_cast<float4*>(r + g0) = rn;
+              rr += rn.x * rn.x + rn.y * rn.y + rn.z * rn.z + rn.w * rn.w;
+              const float* wrow = reinterpret_cast<const float*>(sp + lay.oW + i * nG4);
+              const float* arow = reinterpret_cast<const float*>(sp + lay.oIA + i * nG4);
+              const float2 w2 = *reinterpret_cast<const float2*>(wrow + c);
+              const float2 a2 = *reinterpret_cast<const float2*>(arow + c);
+              const float ial = c > 0 ? arow[c - 1] : 0.f;
+              const float2 aab = prev[ch];  // ia of the row above
+              const float lw0 = lam * w2.x, lw1 = lam * w2.y;
+              float4* sc = sc_row(pos.s, i);
+              sc[slot_of(c)] = make_float4(rn.x, rn.y, lw0 * aab.x, lw0 * ial);
+              sc[slot_of(c + 1)] = make_float4(rn.z, rn.w, lw1 * aab.y, lw1 * a2.x);
+              prev[ch] = a2;
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int ch = 0; ch < IW_MAXCH; ++ch) {
+          const int j = hh + IW_HELPERS * ch;
+          if (j < NCH) {
+            const int c = 2 * j;
+#pragma unroll
+            for (int i = 0; i < G; ++i) {
+              const int o = G - 1 - i;  // memory row of processing slot i
+              const float4 y4 = *reinterpret_cast<const float4*>(sp + (size_t)o * 8 * n + 16 * j);
+              const float* wrow = reinterpret_cast<const float*>(sp + lay.oW + o * nG4);
+              const float* arow = reinterpret_cast<const float*>(sp + lay.oIA + o * nG4);
+              const float2 w2 = *reinterpret_cast<const float2*>(wrow + c);
+              const float2 a2 = *reinterpret_cast<const float2*>(arow + c);
+              const float w3 = c + 2 < n ? wrow[c + 2] : 0.f;
+              const float2 wbl = prev[ch];  // W of the row below
+              const float la0 = lam * a2.x, la1 = lam * a2.y;
+              const float2 t0 = make_float2(a2.x * y4.x, a2.x * y4.y), t1 = make_float2(a2.y * y4.z, a2.y * y4.w);
+              rho = fmaf(t0.x, y4.x, fmaf(t0.y, y4.y, rho));
+              rho = fmaf(t1.x, y4.z, fmaf(t1.y, y4.w, rho));
+              float4* sc = sc_row(pos.s, i);
+              sc[slot_of(c)] = make_float4(t0.x, t0.y, la0 * wbl.x, la0 * w2.y);
+              sc[slot_of(c + 1)] = make_float4(t1.x, t1.y, la1 * wbl.y, la1 * w3);
+              prev[ch] = w2;
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&bar_empty[pos.s]);
+        mbar_arrive(&bar_ready[pos.s]);
+      }
+      pos.next(S);
+    }
+    if (!ok) fault();
   }
-  cp_async_wait<0>();
+  __syncthreads();
   const double trz = block_sum((double)rho, red);
   __syncthreads();
   const double trr = block_sum((double)rr, red);
-  if (threadIdx.x == 0) {
+  if (t == 0) {
     part[((size_t)s * NSLOT + SLOT_RZ) * MAXPART] = trz;
     part[((size_t)s * NSLOT + SLOT_RR) * MAXPART] = trr;
   }
 }
 
-void ilu_prepare() {
-  cudaFuncSetAttribute(k_ilu<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * FCH * 128 * 16);
-  cudaFuncSetAttribute(k_ilu<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * FCH * 128 * 16);
-  cudaFuncSetAttribute(k_ilu<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 6 * FCH * 128 * 16);
+typedef void (*IluKernel)(int, int, int, IwLayout, SliceState*, double*, float2*, const float2*, float2*,
+                          const float2*, const float2*, float2*, float2*, const float*, const float*);
+template <int G>
+static IluKernel ilu_kernel_g(int E) {
+  switch (E) {
+    case 1: return k_ilu<1, G>;
+    case 2: return k_ilu<2, G>;
+    case 3: return k_ilu<3, G>;
+    case 4: return k_ilu<4, G>;
+    case 5: return k_ilu<5, G>;
+    case 6: return k_ilu<6, G>;
+    case 8: return k_ilu<8, G>;
+    case 10: return k_ilu<10, G>;
+    case 12: return k_ilu<12, G>;
+    case 16: return k_ilu<16, G>;
+    default: return nullptr;
+  }
+}
+static IluKernel ilu_kernel(int n, int G) {
+  const int E = iw_cols_per_lane(n);
+  return G == 4 ? ilu_kernel_g<4>(E) : ilu_kernel_g<2>(E);
 }
 
-void ilu_step(int batch, int n, cudaStream_t s, const SliceState* st, double* part, int mode, float2* x,
+static constexpr int ILU_SMEM_MAX = 200 * 1024;
+
+void ilu_prepare() {
+  for (int e : {1, 2, 3, 4, 5, 6, 8, 10, 12, 16})
+    for (int G : {2, 4})
+      cudaFuncSetAttribute(ilu_kernel(32 * e, G), cudaFuncAttributeMaxDynamicSharedMemorySize, ILU_SMEM_MAX);
+}
+
+// Ring shape, encoded 10 * G + S: G rows per stage and S stages.  With one
+// CTA per SM (batch <= 152) the ring takes 4-row stages, three of them as
+// long as they fit; with more CTAs per SM, 2-row stages in the shared
+// memory each CTA gets.
+int ilu_default_shape(int n, int batch) {
+  int per_sm = (batch + 151) / 152;
+  if (per_sm > 3) per_sm = 3;
+  const int budget = per_sm == 1 ? ILU_SMEM_MAX : (224 * 1024) / per_sm - 2048;
+  for (int G : {4, 2}) {
+    if (per_sm > 1 && G == 4) continue;
+    int S = budget / iw_layout(n, G).bytes;
+    if (S > 4) S = 4;
+    if (S >= 2) return 10 * G + S;
+  }
+  return 10 * 2 + 2;
+}
+
+bool ilu_shape_fits(int n, int shape) {
+  const int G = shape / 10, S = shape % 10;
+  if ((G != 2 && G != 4) || S < 2 || S > IW_MAXSTAGES || n % G) return false;
+  return (long)S * iw_layout(n, G).bytes <= ILU_SMEM_MAX;
+}
+
+void ilu_step(int batch, int n, cudaStream_t s, SliceState* st, double* part, int mode, float2* x,
               const float2* d, float2* r, const float2* q, const float2* atb, float2* y, float2* z,
-              const float* ia, const float* ib, const float* ic, int depth) {
-  const int T = ilu_threads(n);
-  if (depth == 3)
-    k_ilu<3><<<batch, T, ilu_smem(n, 3), s>>>(n, mode, st, part, x, d, r, q, atb, y, z, ia, ib, ic);
-  else if (depth == 6)
-    k_ilu<6><<<batch, T, ilu_smem(n, 6), s>>>(n, mode, st, part, x, d, r, q, atb, y, z, ia, ib, ic);
-  else
-    k_ilu<4><<<batch, T, ilu_smem(n, 4), s>>>(n, mode, st, part, x, d, r, q, atb, y, z, ia, ib, ic);
+              const float* ia, const float* wtv, int shape) {
+  if (shape <= 0 || !ilu_shape_fits(n, shape)) shape = ilu_default_shape(n, batch);
+  const int G = shape / 10, S = shape % 10;
+  const IwLayout lay = iw_layout(n, G);
+  ilu_kernel(n, G)<<<batch, IW_THREADS, (size_t)S * lay.bytes, s>>>(n, mode, S, lay, st, part, x, d, r, q, atb, y,
+                                                                     z, ia, wtv);
 }
 
 // =========================================================== PCG vectors ==
@@ -1177,7 +1421,7 @@ __global__ void k_state_init(int B, SliceState* st, const double* part, int np, 
   v.breakdown = 0;
   v.pcg_steps = 0;
   v.outer_done = 0;
-  v.pad_ = 0;
+  v.fault = 0;
   v.lam = lam[s];
   v.lam_tv = lam_tv[s];
   v.abar = (float)((double)counts[s] / (double)N);

@@ -75,12 +75,15 @@ void tv_weights(int batch, int n, cudaStream_t s, const SliceState* st, const fl
 void wavelet_diag(int batch, int n, int levels, cudaStream_t s, const SliceState* st, const float* w,
                   float* out, const float* sqtab, const int* sqlen);
 void penta_setup(int batch, int n, cudaStream_t s, const SliceState* st, const float* wtv,
-                 const float* wdiag, float* ia, float* pb, float* pc);
+                 const float* wdiag, float* ia);
 
 enum IluMode { ILU_INIT = 0, ILU_STEP = 1, ILU_LAST = 2 };
-void ilu_step(int batch, int n, cudaStream_t s, const SliceState* st, double* part, int mode,
+// shape: shared-memory ring, 10 * rows per stage + stages (0: chosen from n and batch)
+void ilu_step(int batch, int n, cudaStream_t s, SliceState* st, double* part, int mode,
               float2* x, const float2* d, float2* r, const float2* q, const float2* atb, float2* y,
-              float2* z, const float* ia, const float* pb, const float* pc, int depth);
+              float2* z, const float* ia, const float* wtv, int shape);
+int ilu_default_shape(int n, int batch);
+bool ilu_shape_fits(int n, int shape);
 
 enum AxpyMode { AXPY_INIT = 0, AXPY_STEP = 1, AXPY_LAST = 2 };
 void axpy_step(int batch, int n, cudaStream_t s, const SliceState* st, double* part, int mode,

@@ -7,6 +7,7 @@ within the relative l2 error 1e-4 that the method's FP32 operators with FP64
 PCG scalars are required to reach.  Integer structures (mask popcounts,
 inverse group maps) are compared bit for bit.
 """
+import contextlib
 import math
 
 import numpy as np
@@ -367,6 +368,30 @@ def test_tolerances_and_stats(F):
     assert abs(st["outer_done"] - info["outer_done"]) <= 1
     assert abs(st["pcg_steps"] - sum(info["pcg_steps"])) <= 0.1 * sum(info["pcg_steps"])
     assert rel(x.real, x_ref) < 1e-3
+
+
+@pytest.mark.parametrize("own_stream", [True, False], ids=["graph", "default_stream"])
+def test_kernel_timing_does_not_change_the_result(F, own_stream):
+    """Per-kernel-class timing works both in a captured graph (own stream) and
+    with eager launches (the legacy default stream), counts the launches of
+    one outer step, and leaves the computed iterate bit-identical."""
+    p = fs.tv_db4_256(n=64)
+    J = 7
+    stream = torch.cuda.Stream() if own_stream else None
+    ctx = F.Context(64, stream=stream)
+    ctx.set_operator(dev(p.mask[None]), p.psi, p.levels)
+    b = c64(p.b[None])
+    params = F.make_params(2, J, lam=p.lam, lam_tv=p.lam_tv)
+    with torch.cuda.stream(stream) if own_stream else contextlib.nullcontext():
+        x0 = ctx.solve(b, params)
+        ctx.set_timing(True)
+        x1 = ctx.solve(b, params)
+        kt = ctx.get_timing()
+        ctx.set_timing(False)
+    torch.cuda.synchronize()
+    assert torch.equal(x0, x1)
+    assert kt["ilu"][1] == J and kt["row_fft"][1] == J + 1
+    assert all(v[0] >= 0.0 for v in kt.values()) and kt["ilu"][0] > 0.0
 
 
 def test_errors_are_status_codes(F):
