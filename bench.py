@@ -61,7 +61,7 @@ ALG_BYTES_PER_PX = {
     "col_fft_mask": 17.0,       # read t, mask; write t
     "wavelet_S": 8.0 + 4.0 + 8.0,     # read d and w, write u = Phi^T (w o Phi d)
     "row_ifft_combine": 36.0,   # read t, d, u, W_tv; write q
-    "ilu": 68.0,                # read x, d, r, q, 1/a, b, c; write x, r, z
+    "ilu": 64.0,                # read x, d, r, q, W_tv, 1/a; write x, r, z
     "axpy": 32.0,
 }
 

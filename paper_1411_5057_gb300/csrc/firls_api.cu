@@ -253,14 +253,10 @@ void enqueue_update_precond(firls_ctx* c, int step_mode, float pcg_tol, bool ini
   if (has_tv(c)) {
     {
       TMark m(c, FIRLS_K_ILU, 1);
+      // the ILU CTA finishes rho (and beta) from its own sums
       ilu_step(B, n, c->stream, c->st, c->part, init ? ILU_INIT : ILU_STEP, c->x, c->d, c->r, c->q, c->atb,
-               c->u, c->z, c->ia, c->wtv, c->tune_ilu);
+               c->u, c->z, c->ia, c->wtv, c->tune_ilu, 1, pcg_tol);
     }
-    TMark m(c, FIRLS_K_SCALARS, 1);
-    if (init)
-      pcg_rho_init(B, c->stream, c->st, c->part, 1, 1);
-    else
-      pcg_beta(B, c->stream, c->st, c->part, 1, 1, pcg_tol);
   } else {
     {
       TMark m(c, FIRLS_K_AXPY, 1);

@@ -46,6 +46,42 @@ FI float rdot2(float2 a, float2 b) { return fmaf(a.x, b.x, a.y * b.y); }
 
 FI bool slice_running(const SliceState* st, int s) { return st[s].active && !st[s].done; }
 
+// PCG scalar updates of one slice (FP64), shared by the scalar kernels and
+// the kernels that finish them in place.
+// alpha = rho / <d, S d>; a non-positive or non-finite <d, S d> is a breakdown.
+FI void pcg_alpha_from(SliceState* v, double dq) {
+  const double rho = v->rho;
+  if (rho == 0.0) {  // exact solution reached: nothing left to do
+    v->alpha = 0.0;
+    v->active = 0;
+    return;
+  }
+  if (!(dq > 0.0) || !isfinite(dq) || !isfinite(rho)) {
+    v->active = 0;
+    v->breakdown = 1;
+    return;
+  }
+  v->alpha = rho / dq;
+  v->pcg_steps += 1;
+}
+// First residual: rho = Re<r, z>, rr = ||r||^2, no previous direction.
+FI void pcg_rho_init_from(SliceState* v, double rz, double rr) {
+  v->rho = rz;
+  v->rr = rr;
+  v->beta = 0.0;
+}
+// After the residual update: stop on ||r|| <= tol ||A^H b||, else
+// beta = rho_new / rho.
+FI void pcg_beta_from(SliceState* v, double rz, double rr, float tol) {
+  v->rr = rr;
+  if (tol > 0.f && sqrt(rr) <= (double)tol * sqrt(v->rhs2)) {
+    v->active = 0;
+    return;
+  }
+  v->beta = rz / v->rho;
+  v->rho = rz;
+}
+
 // Block-wide FP64 sum; result valid in thread 0.  `red` holds >= 32 doubles.
 FI double block_sum(double v, double* red) {
 #pragma unroll

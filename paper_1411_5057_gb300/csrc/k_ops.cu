@@ -768,7 +768,8 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
     k_ilu(int n, int mode, int S, IwLayout lay, SliceState* __restrict__ st, double* __restrict__ part,
           float2* __restrict__ x, const float2* __restrict__ d, float2* __restrict__ r,
           const float2* __restrict__ q, const float2* __restrict__ atb, float2* __restrict__ y,
-          float2* __restrict__ z, const float* __restrict__ ia, const float* __restrict__ wtv) {
+          float2* __restrict__ z, const float* __restrict__ ia, const float* __restrict__ wtv, int fuse,
+          float pcg_tol) {
   const int s = blockIdx.x;
   if (!slice_running(st, s)) return;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1043,11 +1044,17 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
   if (t == 0) {
     part[((size_t)s * NSLOT + SLOT_RZ) * MAXPART] = trz;
     part[((size_t)s * NSLOT + SLOT_RR) * MAXPART] = trr;
+    if (fuse && !abort_flag) {
+      if (mode == ILU_INIT)
+        pcg_rho_init_from(st + s, 0.0 + trz, 0.0 + trr);
+      else
+        pcg_beta_from(st + s, 0.0 + trz, 0.0 + trr, pcg_tol);
+    }
   }
 }
 
 typedef void (*IluKernel)(int, int, int, IwLayout, SliceState*, double*, float2*, const float2*, float2*,
-                          const float2*, const float2*, float2*, float2*, const float*, const float*);
+                          const float2*, const float2*, float2*, float2*, const float*, const float*, int, float);
 template <int G>
 static IluKernel ilu_kernel_g(int E) {
   switch (E) {
@@ -1102,12 +1109,12 @@ bool ilu_shape_fits(int n, int shape) {
 
 void ilu_step(int batch, int n, cudaStream_t s, SliceState* st, double* part, int mode, float2* x,
               const float2* d, float2* r, const float2* q, const float2* atb, float2* y, float2* z,
-              const float* ia, const float* wtv, int shape) {
+              const float* ia, const float* wtv, int shape, int fuse_scalars, float pcg_tol) {
   if (shape <= 0 || !ilu_shape_fits(n, shape)) shape = ilu_default_shape(n, batch);
   const int G = shape / 10, S = shape % 10;
   const IwLayout lay = iw_layout(n, G);
   ilu_kernel(n, G)<<<batch, IW_THREADS, (size_t)S * lay.bytes, s>>>(n, mode, S, lay, st, part, x, d, r, q, atb, y,
-                                                                     z, ia, wtv);
+                                                                     z, ia, wtv, fuse_scalars, pcg_tol);
 }
 
 // =========================================================== PCG vectors ==
@@ -1447,20 +1454,7 @@ void outer_begin(int batch, cudaStream_t s, SliceState* st) {
 __global__ void k_alpha(int B, SliceState* st, const double* part, int np) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B || !slice_running(st, s)) return;
-  const double dq = sum_parts(part, s, SLOT_DQ, np);
-  const double rho = st[s].rho;
-  if (rho == 0.0) {  // exact solution reached: nothing left to do
-    st[s].alpha = 0.0;
-    st[s].active = 0;
-    return;
-  }
-  if (!(dq > 0.0) || !isfinite(dq) || !isfinite(rho)) {
-    st[s].active = 0;
-    st[s].breakdown = 1;
-    return;
-  }
-  st[s].alpha = rho / dq;
-  st[s].pcg_steps += 1;
+  pcg_alpha_from(st + s, sum_parts(part, s, SLOT_DQ, np));
 }
 
 void pcg_alpha(int batch, cudaStream_t s, SliceState* st, const double* part, int np) {
@@ -1470,9 +1464,7 @@ void pcg_alpha(int batch, cudaStream_t s, SliceState* st, const double* part, in
 __global__ void k_rho_init(int B, SliceState* st, const double* part, int np_rz, int np_rr) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B || !slice_running(st, s)) return;
-  st[s].rho = sum_parts(part, s, SLOT_RZ, np_rz);
-  st[s].rr = sum_parts(part, s, SLOT_RR, np_rr);
-  st[s].beta = 0.0;
+  pcg_rho_init_from(st + s, sum_parts(part, s, SLOT_RZ, np_rz), sum_parts(part, s, SLOT_RR, np_rr));
 }
 
 void pcg_rho_init(int batch, cudaStream_t s, SliceState* st, const double* part, int np_rz, int np_rr) {
@@ -1482,15 +1474,7 @@ void pcg_rho_init(int batch, cudaStream_t s, SliceState* st, const double* part,
 __global__ void k_beta(int B, SliceState* st, const double* part, int np_rz, int np_rr, float tol) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B || !slice_running(st, s)) return;
-  const double rz = sum_parts(part, s, SLOT_RZ, np_rz);
-  const double rr = sum_parts(part, s, SLOT_RR, np_rr);
-  st[s].rr = rr;
-  if (tol > 0.f && sqrt(rr) <= (double)tol * sqrt(st[s].rhs2)) {
-    st[s].active = 0;
-    return;
-  }
-  st[s].beta = rz / st[s].rho;
-  st[s].rho = rz;
+  pcg_beta_from(st + s, sum_parts(part, s, SLOT_RZ, np_rz), sum_parts(part, s, SLOT_RR, np_rr), tol);
 }
 
 void pcg_beta(int batch, cudaStream_t s, SliceState* st, const double* part, int np_rz, int np_rr,

@@ -79,9 +79,12 @@ void penta_setup(int batch, int n, cudaStream_t s, const SliceState* st, const f
 
 enum IluMode { ILU_INIT = 0, ILU_STEP = 1, ILU_LAST = 2 };
 // shape: shared-memory ring, 10 * rows per stage + stages (0: chosen from n and batch)
+// fuse_scalars: the CTA finishes the PCG scalars itself from its sums (rho
+// at ILU_INIT; rr, the residual test against pcg_tol, beta and rho at ILU_STEP)
 void ilu_step(int batch, int n, cudaStream_t s, SliceState* st, double* part, int mode,
               float2* x, const float2* d, float2* r, const float2* q, const float2* atb, float2* y,
-              float2* z, const float* ia, const float* wtv, int shape);
+              float2* z, const float* ia, const float* wtv, int shape, int fuse_scalars = 0,
+              float pcg_tol = 0.f);
 int ilu_default_shape(int n, int batch);
 bool ilu_shape_fits(int n, int shape);
 
