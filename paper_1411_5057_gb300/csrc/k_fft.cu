@@ -33,6 +33,12 @@ template <int N> constexpr int col_smem_bytes() {
   return N * 8 + 2 * N * (COLS + 1) * 4 + N * COLS;
 }
 
+FI void cp_async16_fft(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+
 template <int N> FI void load_twiddles(float2* tw, const float2* __restrict__ twg) {
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
 }
@@ -107,12 +113,44 @@ __global__ void __launch_bounds__(256) k_row_ahb(const float2* __restrict__ b, c
 // Load a 16-column tile of t into shared memory (SoA, row stride COLS+1).
 template <int N>
 FI void load_col_tile(const float2* __restrict__ src, float* tre, float* tim, size_t sbase, int c0) {
-  for (int idx = threadIdx.x; idx < N * COLS; idx += blockDim.x) {
-    const int r = idx / COLS, c = idx % COLS;
-    const float2 g = src[sbase + (size_t)r * N + c0 + c];
-    tre[r * (COLS + 1) + c] = g.x;
-    tim[r * (COLS + 1) + c] = g.y;
+  // every thread issues all its 16-byte loads (two columns each) before the
+  // first shared-memory store, so a whole tile is in flight at once
+  constexpr int NT = COLS * FftCfg<N>::T, HC = COLS / 2, K = N * HC / NT;
+  static_assert(N * HC % NT == 0, "column tile split");
+  float4 g[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int idx = threadIdx.x + NT * k, r = idx / HC, cp = idx % HC;
+    g[k] = *reinterpret_cast<const float4*>(src + sbase + (size_t)r * N + c0 + 2 * cp);
   }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int idx = threadIdx.x + NT * k, r = idx / HC, cp = idx % HC;
+    tre[r * (COLS + 1) + 2 * cp] = g[k].x;
+    tim[r * (COLS + 1) + 2 * cp] = g[k].y;
+    tre[r * (COLS + 1) + 2 * cp + 1] = g[k].z;
+    tim[r * (COLS + 1) + 2 * cp + 1] = g[k].w;
+  }
+}
+
+template <int N>
+FI void store_col_tile(float2* __restrict__ dst, const float* tre, const float* tim, size_t sbase, int c0) {
+  constexpr int NT = COLS * FftCfg<N>::T, HC = COLS / 2, K = N * HC / NT;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int idx = threadIdx.x + NT * k, r = idx / HC, cp = idx % HC;
+    const int o = r * (COLS + 1) + 2 * cp;
+    *reinterpret_cast<float4*>(dst + sbase + (size_t)r * N + c0 + 2 * cp) =
+        make_float4(tre[o], tim[o], tre[o + 1], tim[o + 1]);
+  }
+}
+
+// The 16 mask bytes of each row of a column tile, one 16-byte load per row.
+template <int N>
+FI void load_mask_tile(const uint8_t* __restrict__ mask, uint8_t* msk, size_t sbase, int c0) {
+  constexpr int NT = COLS * FftCfg<N>::T;
+  for (int r = threadIdx.x; r < N; r += NT)
+    *reinterpret_cast<uint4*>(msk + r * COLS) = *reinterpret_cast<const uint4*>(mask + sbase + (size_t)r * N + c0);
 }
 
 // In place on t: t = colIFFT(mask * colFFT(t)) for a 16-column tile.
@@ -132,11 +170,8 @@ __global__ void __launch_bounds__(512) k_col_mask(float2* __restrict__ tbuf, con
   const int c0 = blockIdx.x * COLS;
   const size_t sbase = (size_t)s * N * N;
   load_twiddles<N>(tw, twg);
+  load_mask_tile<N>(mask, msk, sbase, c0);
   load_col_tile<N>(tbuf, tre, tim, sbase, c0);
-  for (int idx = threadIdx.x; idx < N * COLS; idx += blockDim.x) {
-    const int r = idx / COLS, c = idx % COLS;
-    msk[idx] = mask[sbase + (size_t)r * N + c0 + c];
-  }
   __syncthreads();
   const int c = threadIdx.x / T, t = threadIdx.x % T;
   float2 v[E];
@@ -161,10 +196,7 @@ __global__ void __launch_bounds__(512) k_col_mask(float2* __restrict__ tbuf, con
     tim[r * (COLS + 1) + c] = v[e].y;
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < N * COLS; idx += blockDim.x) {
-    const int r = idx / COLS, cc = idx % COLS;
-    tbuf[sbase + (size_t)r * N + c0 + cc] = make_float2(tre[r * (COLS + 1) + cc], tim[r * (COLS + 1) + cc]);
-  }
+  store_col_tile<N>(tbuf, tre, tim, sbase, c0);
 }
 
 // atb = (1/n) colIFFT(t)  [real: imaginary part dropped]; x = atb if x != null;
@@ -263,10 +295,7 @@ __global__ void __launch_bounds__(512) k_col_dc(float2* __restrict__ tbuf, const
     tim[r * (COLS + 1) + c] = v[e].y;
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < N * COLS; idx += blockDim.x) {
-    const int r = idx / COLS, cc = idx % COLS;
-    tbuf[sbase + (size_t)r * N + c0 + cc] = make_float2(tre[r * (COLS + 1) + cc], tim[r * (COLS + 1) + cc]);
-  }
+  store_col_tile<N>(tbuf, tre, tim, sbase, c0);
 }
 
 // Data term of F: partial sum over sampled entries of |(1/n) colFFT(t) - b|^2,
@@ -329,20 +358,30 @@ __global__ void __launch_bounds__(256) k_row_inv(const float2* __restrict__ tbuf
   float* lines = reinterpret_cast<float*>(smem + N * 8);
   float2* ds = reinterpret_cast<float2*>(smem + N * 8 + R * 2 * LW * 4);  // rows r0-1 .. r0+R
   float* ws = reinterpret_cast<float*>(ds + (R + 2) * N);                 // rows r0 .. r0+R
-  load_twiddles<N>(tw, twg);
   const int r0 = blockIdx.x * R;
   const size_t sbase = (size_t)s * N * N;
   const bool tv = (wtv != nullptr);
   if (tv) {
-    for (int idx = threadIdx.x; idx < (R + 2) * N; idx += blockDim.x) {
-      const int rr = r0 - 1 + idx / N, cc = idx % N;
-      ds[idx] = (rr >= 0 && rr < N) ? d[sbase + (size_t)rr * N + cc] : make_float2(0.f, 0.f);
+    // halo rows straight to shared memory, all copies in flight at once
+    constexpr int NT = R * T, KD = (R + 2) * N / 2, KW = (R + 1) * N / 4;
+    static_assert((N * 8 + R * 2 * LW * 4) % 16 == 0 && N % 4 == 0, "16-byte staging");
+    for (int idx = threadIdx.x; idx < KD; idx += NT) {
+      const int rr = r0 - 1 + (2 * idx) / N, cc = (2 * idx) % N;
+      if (rr >= 0 && rr < N)
+        cp_async16_fft(ds + 2 * idx, d + sbase + (size_t)rr * N + cc);
+      else
+        *reinterpret_cast<float4*>(ds + 2 * idx) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    for (int idx = threadIdx.x; idx < (R + 1) * N; idx += blockDim.x) {
-      const int rr = r0 + idx / N, cc = idx % N;
-      ws[idx] = (rr < N) ? wtv[sbase + (size_t)rr * N + cc] : 0.f;
+    for (int idx = threadIdx.x; idx < KW; idx += NT) {
+      const int rr = r0 + (4 * idx) / N, cc = (4 * idx) % N;
+      if (rr < N)
+        cp_async16_fft(ws + 4 * idx, wtv + sbase + (size_t)rr * N + cc);
+      else
+        *reinterpret_cast<float4*>(ws + 4 * idx) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
+  load_twiddles<N>(tw, twg);
   const int lr = threadIdx.x / T, t = threadIdx.x % T;
   const int row = r0 + lr;
   const size_t base = sbase + (size_t)row * N;
@@ -353,6 +392,7 @@ __global__ void __launch_bounds__(256) k_row_inv(const float2* __restrict__ tbuf
 #pragma unroll
     for (int e = 0; e < E; ++e) uv[e] = u[base + t + T * e];
   }
+  if (tv) asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
   fft_line<N, +1>(v, lines + lr * 2 * LW, lines + lr * 2 * LW + LW, tw, t);
   const float sc = 1.0f / ((float)N * (float)N);
