@@ -166,8 +166,12 @@ def run_ours(args):
         b = torch.from_numpy(b_h).cuda()
         ctx = F.Context(N, batch=B, stream=stream)
         ctx.set_operator(masks[:B], F.PSI_TV | F.PSI_DB4, LEVELS)
+        # tile shapes (wavelet rows per CTA, on-chip wavelet block, ILU ring)
+        # timed on this context's own buffers before anything is measured
+        tuning = ctx.autotune() if args.autotune else ctx.tuning()
         x = torch.empty_like(b)
     stream.synchronize()
+    print(f"[bench] tuning {tuning}", file=sys.stderr, flush=True)
     mlist, blist, xlist = list(masks), list(b), list(x)
 
     def barrier():
@@ -176,10 +180,10 @@ def run_ours(args):
 
     done_per_step = S - B if args.steady else S
 
-    def step(x0s=None):
+    def step(x0s=None, counters=None):
         with torch.cuda.stream(stream):
             return F.serve(ctx, mlist, blist, lams, lam_tvs, params, xlist, x0s=x0s, max_outer=args.outer,
-                           stop_after=S - B if args.steady else None)
+                           stop_after=S - B if args.steady else None, counters=counters)
 
     # ---- device-resident throughput: continuous batching over S slices ----
     for _ in range(args.warmup):
@@ -190,9 +194,10 @@ def run_ours(args):
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    served = {}
     e0.record(stream)
     for _ in range(args.steps):
-        steps = step()
+        steps = step(counters=served)
     e1.record(stream)
     e1.synchronize()
     torch.cuda.synchronize()
@@ -221,7 +226,6 @@ def run_ours(args):
     print("[bench] per outer step: " + ", ".join(f"{k} {v[0]:.2f} ms/{v[1]}" for k, v in kt.items()),
           file=sys.stderr, flush=True)
     launches_per_outer = sum(v[1] for v in kt.values())
-    chunks = -(-int(steps.sum()) // (8 * B)) + 1
     kern = {k: {"ms_per_outer": round(v[0], 4), "launches": v[1]} for k, v in kt.items()}
     # applications per outer step: the S operator (its three FFT passes and the
     # wavelet term, itself 5 launches) runs inner + 1 times, the ILU inner times
@@ -290,7 +294,8 @@ def run_ours(args):
                           else "every slice of the queue, including the drain",
                           "l2": "working set > L2 (no flush needed)", "parallelism": f"replicas{world}"},
                "roofline": roofline, "kernels_per_outer_step": kern,
-               "gpu_launches": int(launches_per_outer * chunks * 8 * args.steps),
+               # graph replays x kernels per outer step, plus 4 kernels per slot load and 1 per retire
+               "gpu_launches": int(launches_per_outer * served["runs"] * 8 + 4 * served["loads"] + served["retires"]),
                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
                "solve_stats": {"mean_outer_steps": round(float(steps.mean()), 2), "max_outer_steps": int(steps.max()),
                                "capped": int((steps >= args.outer).sum()),
@@ -425,6 +430,7 @@ def main(argv=None):
     ap.add_argument("--outer", type=int, default=OUTER)
     ap.add_argument("--inner", type=int, default=INNER)
     ap.add_argument("--outer-tol", type=float, default=OUTER_TOL)
+    ap.add_argument("--autotune", type=int, default=1, help="autotune tile shapes before timing (1/0)")
     ap.add_argument("--learned", type=int, default=1, help="also time the learned warm start (1/0)")
     ap.add_argument("--learned-train", type=int, default=512)
     ap.add_argument("--learned-epochs", type=int, default=20)

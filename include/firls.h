@@ -251,6 +251,14 @@ firls_status firls_warm_start_guard(firls_ctx* ctx, const void* b, const firls_p
  * either pointer may be NULL. */
 firls_status firls_get_weights(firls_ctx* ctx, float* w_wavelet, float* w_tv);
 
+/* Copy out the TV preconditioner's diagonal pieces of the last outer step
+ * (Eq. ptv with the wavelet term of the combined TV + wavelet case):
+ * wavelet_diag = diag(Phi^T W Phi) (needs a wavelet term) and inv_a = 1/a,
+ * a = abar + lam_tv (D1^T W D1 + D2^T W D2)_ii + lam diag(Phi^T W Phi)_i.
+ * Device float [batch][n][n] each; either may be NULL.  FIRLS_E_STATE
+ * without FIRLS_PSI_TV. */
+firls_status firls_get_precond(firls_ctx* ctx, float* wavelet_diag, float* inv_a);
+
 /* Copy out the inverse group map (device int32: offsets [n*n+1], ids
  * [total members]).  FIRLS_E_STATE if no group map is set. */
 firls_status firls_get_inverse_map(firls_ctx* ctx, int32_t* offsets, int32_t* ids);

@@ -21,7 +21,7 @@ REAL_X = 1
 
 EXPORTED = ["firls_size_supported", "firls_create", "firls_set_operator", "firls_solve", "firls_solve_multi",
             "firls_last_error", "firls_destroy", "firls_apply_AHA", "firls_apply_Phi", "firls_apply_PhiT",
-            "firls_apply_S_P", "firls_get_weights", "firls_get_inverse_map", "firls_get_popcounts",
+            "firls_apply_S_P", "firls_get_weights", "firls_get_precond", "firls_get_inverse_map", "firls_get_popcounts",
             "firls_set_timing", "firls_get_timing", "firls_apply_AHA_noalloc",
             "firls_cnn_create", "firls_cnn_set_params", "firls_cnn_get_params", "firls_cnn_get_grads",
             "firls_cnn_forward", "firls_cnn_train_step", "firls_cnn_destroy", "firls_objective",
@@ -81,6 +81,7 @@ def lib():
     L.firls_apply_PhiT.argtypes = [vp, vp, vp]
     L.firls_apply_S_P.argtypes = [vp, ctypes.POINTER(Params), vp, vp, vp, vp, vp]
     L.firls_get_weights.argtypes = [vp, vp, vp]
+    L.firls_get_precond.argtypes = [vp, vp, vp]
     L.firls_get_inverse_map.argtypes = [vp, vp, vp]
     L.firls_get_popcounts.argtypes = [vp, vp]
     L.firls_apply_AHA_noalloc.argtypes = [i32, i32, vp, vp, vp, vp]
@@ -262,6 +263,9 @@ class Context:
     def get_weights(self, w_wavelet=None, w_tv=None):
         self._check(lib().firls_get_weights(self.h, _ptr(w_wavelet), _ptr(w_tv)), "get_weights")
 
+    def get_precond(self, wavelet_diag=None, inv_a=None):
+        self._check(lib().firls_get_precond(self.h, _ptr(wavelet_diag), _ptr(inv_a)), "get_precond")
+
     def get_inverse_map(self, offsets, ids):
         self._check(lib().firls_get_inverse_map(self.h, _ptr(offsets), _ptr(ids)), "get_inverse_map")
 
@@ -372,7 +376,8 @@ class Cnn:
             pass
 
 
-def serve(ctx, masks, bs, lams, lam_tvs, params, outs, x0s=None, chunk=8, max_outer=400, stop_after=None):
+def serve(ctx, masks, bs, lams, lam_tvs, params, outs, x0s=None, chunk=8, max_outer=400, stop_after=None,
+          counters=None):
     """Continuous batching over a queue of slices with ctx.batch slots.
 
     masks/bs/outs: per-slice device tensors ([n][n]); lams/lam_tvs: floats;
@@ -381,7 +386,12 @@ def serve(ctx, masks, bs, lams, lam_tvs, params, outs, x0s=None, chunk=8, max_ou
     reached max_outer outer steps.  With stop_after, returns once that many
     slices have completed and retires the slices still in flight (their
     entry in the result stays 0).  Returns the outer steps of every slice.
+    counters (a dict, optional) receives "runs" (calls of ctx.run, each
+    `chunk` outer-step graph replays), "loads" and "retires".
     """
+    cnt = counters if counters is not None else {}
+    for k in ("runs", "loads", "retires"):
+        cnt.setdefault(k, 0)
     q = len(bs)
     steps = [0] * q
     slot_of = [-1] * ctx.batch
@@ -389,10 +399,12 @@ def serve(ctx, masks, bs, lams, lam_tvs, params, outs, x0s=None, chunk=8, max_ou
     for s in range(ctx.batch):
         if nxt < q:
             ctx.slot_load(s, masks[nxt], bs[nxt], lams[nxt], lam_tvs[nxt], None if x0s is None else x0s[nxt])
+            cnt["loads"] += 1
             slot_of[s] = nxt
             nxt += 1
         else:
             ctx.slot_retire(s)
+            cnt["retires"] += 1
     run = Params.from_buffer_copy(params)
     run.outer_iters = chunk
     active = sum(1 for v in slot_of if v >= 0)
@@ -402,9 +414,11 @@ def serve(ctx, masks, bs, lams, lam_tvs, params, outs, x0s=None, chunk=8, max_ou
             for s in range(ctx.batch):
                 if slot_of[s] >= 0:
                     ctx.slot_retire(s)
+                    cnt["retires"] += 1
                     slot_of[s] = -1
             break
         ctx.run(run)
+        cnt["runs"] += 1
         done, od, _ = ctx.slot_status()
         for s in range(ctx.batch):
             i = slot_of[s]
@@ -415,10 +429,12 @@ def serve(ctx, masks, bs, lams, lam_tvs, params, outs, x0s=None, chunk=8, max_ou
             completed += 1
             if nxt < q:
                 ctx.slot_load(s, masks[nxt], bs[nxt], lams[nxt], lam_tvs[nxt], None if x0s is None else x0s[nxt])
+                cnt["loads"] += 1
                 slot_of[s] = nxt
                 nxt += 1
             else:
                 ctx.slot_retire(s)
+                cnt["retires"] += 1
                 slot_of[s] = -1
                 active -= 1
     return steps

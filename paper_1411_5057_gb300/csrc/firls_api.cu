@@ -1202,6 +1202,18 @@ extern "C" firls_status firls_get_weights(firls_ctx* c, float* w_wavelet, float*
   return FIRLS_OK;
 }
 
+extern "C" firls_status firls_get_precond(firls_ctx* c, float* wavelet_diag, float* inv_a) {
+  if (!c) return FIRLS_E_INVALID_ARG;
+  if (!has_tv(c)) return fail(c, FIRLS_E_STATE, "the TV preconditioner exists only with FIRLS_PSI_TV");
+  const size_t bytes = sizeof(float) * (size_t)c->batch * c->n * c->n;
+  if (wavelet_diag) {
+    if (!c->kind) return fail(c, FIRLS_E_STATE, "no wavelet term");
+    CU(cudaMemcpyAsync(wavelet_diag, c->wdiag, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  if (inv_a) CU(cudaMemcpyAsync(inv_a, c->ia, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  return FIRLS_OK;
+}
+
 extern "C" firls_status firls_get_inverse_map(firls_ctx* c, int32_t* offsets, int32_t* ids) {
   if (!c || !offsets || !ids) return FIRLS_E_INVALID_ARG;
   if (!c->groups) return fail(c, FIRLS_E_STATE, "no group map set");

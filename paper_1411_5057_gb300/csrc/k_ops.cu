@@ -357,9 +357,11 @@ static void set_wav_attrs() {
 }
 
 void ilu_prepare();
+void wavelet_diag_prepare();
 void wav_prepare() {
   set_wav_attrs();
   ilu_prepare();
+  wavelet_diag_prepare();
 }
 
 // First level handled by the coarse kernel: its input side m <= cmax.
@@ -514,50 +516,97 @@ void tv_weights(int batch, int n, cudaStream_t s, const SliceState* st, const fl
   k_tv_weights<<<dim3(blocks, batch), 256, 0, s>>>(n, st, x, wtv);
 }
 
-// Exact diag(Phi^T diag(w) Phi): each 2-D basis function is an outer product
-// of 1-D level-l functions f_{l,type}(i - 2^l p) whose squares are tabulated
-// (sqtab[(l-1)*2 + type][0..len)), so the diagonal is a separable sum.
+// Exact diag(Phi^T diag(w) Phi).  Each 2-D basis function of level l is an
+// outer product of 1-D level-l functions f_{l,type}(i - 2^l p) (type 0 low,
+// 1 high) whose squares are tabulated (sqtab[(l-1)*2 + type][0 .. sqlen)),
+// so the diagonal is a separable sum over levels and subbands:
+//   diag(r, c) = sum_l sum_br sum_pr F_{l,br}(r - 2^l pr) T_{l,br}(pr, c),
+//   T_{l,br}(pr, c) = sum_{bands (br, bc)} sum_pc F_{l,bc}(c - 2^l pc) w_band(pr, pc),
+// indices periodic.  A CTA owns WD_RB output rows: per level it forms the
+// T rows those outputs need in shared memory (both row types), then adds
+// their row-filtered sums.  Bands at level l (h = n >> l, Mallat layout):
+// (0,1) rows [0,h) cols [h,2h); (1,0) rows [h,2h) cols [0,h); (1,1) rows and
+// cols [h,2h); at the last level also (0,0), rows and cols [0,h).
+constexpr int WD_RB = 16;
+constexpr int WD_PRMAX = WD_RB / 2 + 4;  // coarse rows a level needs (filters of <= 3 * 2^l taps)
+
 __global__ void __launch_bounds__(256) k_wavelet_diag(int n, int levels, const SliceState* __restrict__ st,
                                                       const float* __restrict__ w, float* __restrict__ out,
                                                       const float* __restrict__ sqtab,
                                                       const int* __restrict__ sqlen) {
   const int s = blockIdx.y;
   if (!slice_running(st, s)) return;
-  const int r = blockIdx.x;  // one image row per CTA: the row taps are uniform
+  extern __shared__ __align__(16) float tsm[];  // [2][WD_PRMAX][n]
+  const int r0 = blockIdx.x * WD_RB;
+  const int rows = min(WD_RB, n - r0);
   const size_t base = (size_t)s * n * n;
   const float* ws = w + base;
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    float acc = 0.f;
-    for (int l = 1; l <= levels; ++l) {
-      const int h = n >> l, msk = (1 << l) - 1, step = 1 << l;
-      const int nb = (l == levels) ? 4 : 3;
-      for (int b = 0; b < nb; ++b) {
-        // bands: (0,1) low/high, (1,0) high/low, (1,1) high/high, (0,0) low/low
-        const int br = (b == 1 || b == 2) ? 1 : 0;
-        const int bc = (b == 0 || b == 2) ? 1 : 0;
-        const float* fr = sqtab + (size_t)((l - 1) * 2 + br) * n;
-        const float* fc = sqtab + (size_t)((l - 1) * 2 + bc) * n;
-        const int lr = sqlen[(l - 1) * 2 + br], lc = sqlen[(l - 1) * 2 + bc];
-        for (int sr = r & msk; sr < lr; sr += step) {
-          int pr = r - sr;
-          if (pr < 0) pr += n;
-          const float vr = fr[sr];
-          const float* wrow = ws + (size_t)(br * h + (pr >> l)) * n + bc * h;
-          for (int sc = c & msk; sc < lc; sc += step) {
-            int pc = c - sc;
-            if (pc < 0) pc += n;
-            acc = fmaf(vr * fc[sc], wrow[pc >> l], acc);
-          }
+  constexpr int PER = WD_RB * 512 / 256;  // outputs per thread, n <= 512
+  float acc[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) acc[k] = 0.f;
+  for (int l = 1; l <= levels; ++l) {
+    const int h = n >> l, step = 1 << l, msk = step - 1;
+    const int len[2] = {sqlen[(l - 1) * 2], sqlen[(l - 1) * 2 + 1]};
+    const float* F[2] = {sqtab + (size_t)((l - 1) * 2) * n, sqtab + (size_t)((l - 1) * 2 + 1) * n};
+    const int lmax = len[0] > len[1] ? len[0] : len[1];
+    // coarse rows pr = pr_lo + j (mod h), j < cnt, cover every r - sr with sr < lmax
+    const int pr_lo = (r0 - (lmax - 1) - (step - 1)) >> l;  // floor division (arithmetic shift)
+    int cnt = ((r0 + rows - 1) >> l) - pr_lo + 1;
+    if (cnt > WD_PRMAX) cnt = WD_PRMAX;
+    const int pr0 = ((pr_lo % h) + h) % h;
+    __syncthreads();  // the previous level's T rows are no longer read
+    for (int idx = threadIdx.x; idx < 2 * cnt * n; idx += blockDim.x) {
+      const int br = idx / (cnt * n), j = (idx / n) % cnt, c = idx % n;
+      const int pr = (pr0 + j) % h;
+      float t = 0.f;
+      for (int bc = 0; bc < 2; ++bc) {
+        if (br == 0 && bc == 0 && l != levels) continue;  // LL is a band only at the last level
+        const float* wrow = ws + (size_t)(br * h + pr) * n + bc * h;
+        const float* fc = F[bc];
+        for (int sc = c & msk; sc < len[bc]; sc += step) {
+          int pc = c - sc;
+          if (pc < 0) pc += n;
+          t = fmaf(fc[sc], wrow[pc >> l], t);
         }
       }
+      tsm[(size_t)(br * WD_PRMAX + j) * n + c] = t;
     }
-    out[base + (size_t)r * n + c] = acc;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int idx = threadIdx.x + 256 * k;
+      if (idx < rows * n) {
+        const int r = r0 + idx / n, c = idx % n;
+        float a = acc[k];
+        for (int br = 0; br < 2; ++br) {
+          const float* fr = F[br];
+          for (int sr = r & msk; sr < len[br]; sr += step) {
+            int pr = r - sr;
+            if (pr < 0) pr += n;
+            const int j = (((pr >> l) - pr0) % h + h) % h;
+            a = fmaf(fr[sr], tsm[(size_t)(br * WD_PRMAX + j) * n + c], a);
+          }
+        }
+        acc[k] = a;
+      }
+    }
   }
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int idx = threadIdx.x + 256 * k;
+    if (idx < rows * n) out[base + (size_t)(r0 + idx / n) * n + idx % n] = acc[k];
+  }
+}
+
+void wavelet_diag_prepare() {
+  cudaFuncSetAttribute(k_wavelet_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * WD_PRMAX * 512 * 4);
 }
 
 void wavelet_diag(int batch, int n, int levels, cudaStream_t s, const SliceState* st, const float* w,
                   float* out, const float* sqtab, const int* sqlen) {
-  k_wavelet_diag<<<dim3(n, batch), n < 256 ? n : 256, 0, s>>>(n, levels, st, w, out, sqtab, sqlen);
+  k_wavelet_diag<<<dim3((n + WD_RB - 1) / WD_RB, batch), 256, 2 * WD_PRMAX * n * 4, s>>>(n, levels, st, w, out,
+                                                                                        sqtab, sqlen);
 }
 
 // P = abar I + lam_tv (D1^T W D1 + D2^T W D2) [+ lam diag(Phi^T W Phi)] (Eq. ptv):

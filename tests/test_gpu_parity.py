@@ -370,6 +370,35 @@ def test_tolerances_and_stats(F):
     assert rel(x.real, x_ref) < 1e-3
 
 
+@pytest.mark.parametrize("n,psi,levels", [(64, fs.PSI_TV | fs.PSI_DB4, 4), (96, fs.PSI_TV | fs.PSI_HAAR, 3),
+                                           (256, fs.PSI_TV | fs.PSI_DB4, 4), (512, fs.PSI_TV | fs.PSI_DB4, 5)])
+def test_tv_preconditioner_diagonal(F, n, psi, levels):
+    """diag(Phi^T W Phi) and 1/a of the TV preconditioner (Eq. ptv with the
+    wavelet term) on the GPU's own weights, against their definitions: the
+    oracle's dense-product wavelet diagonal and diag(D1^T W D1 + D2^T W D2)
+    from the sparse difference matrices.  FP32 sums of positive terms: 2e-5."""
+    import scipy.sparse as sp
+    p = fs.make_problem(n, 0.25, 0.01, 5, real=False, psi=psi, levels=levels, lam=5e-4, lam_tv=1e-3)
+    ctx = F.Context(n)
+    ctx.set_operator(dev(p.mask[None]), p.psi, p.levels)
+    ctx.solve(c64(p.b[None]), F.make_params(1, 1, lam=p.lam, lam_tv=p.lam_tv))
+    ww = torch.empty(1, n, n, device="cuda")
+    wt, wd, ia = torch.empty_like(ww), torch.empty_like(ww), torch.empty_like(ww)
+    ctx.get_weights(ww, wt)
+    ctx.get_precond(wd, ia)
+    torch.cuda.synchronize()
+    w = ww[0].cpu().numpy().astype(np.float64)
+    kind = O.PSI_DB4 if psi & fs.PSI_DB4 else O.PSI_HAAR
+    ref = O.wavelet_diag(w, n, kind, levels)
+    got = wd[0].cpu().numpy().astype(np.float64)
+    assert np.allclose(got, ref, rtol=2e-5, atol=1e-7 * np.abs(ref).max())
+    D1, D2 = O.tv_matrices(n)
+    Wd = sp.diags(wt[0].cpu().numpy().astype(np.float64).reshape(-1))
+    tvdiag = (D1.T @ Wd @ D1 + D2.T @ Wd @ D2).diagonal()
+    a = O.a_bar(p.mask) + p.lam_tv * tvdiag + p.lam * ref.reshape(-1)
+    assert np.allclose(ia[0].cpu().numpy().astype(np.float64).reshape(-1), 1.0 / a, rtol=2e-5)
+
+
 @pytest.mark.parametrize("own_stream", [True, False], ids=["graph", "default_stream"])
 def test_kernel_timing_does_not_change_the_result(F, own_stream):
     """Per-kernel-class timing works both in a captured graph (own stream) and
