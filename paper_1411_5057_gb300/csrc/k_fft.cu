@@ -29,9 +29,16 @@ template <int N> constexpr int row_smem_bytes(bool tv) {
   return b;
 }
 
-template <int N> constexpr int col_smem_bytes() {
-  return N * 8 + 2 * N * (COLS + 1) * 4 + N * COLS;
+// Shared memory of a column-pass CTA: twiddles (N float2) | region | mask
+// tile transposed ([COLS][N] bytes).  The region holds the N x COLS complex
+// tile (rows of 16 float2, XOR-swizzled: element (r, c) at r*COLS + (c ^ (r
+// mod COLS)), so that row-major fills and 16-row column reads are both free
+// of bank conflicts) or, while the FFT runs, the per-column exchange lines.
+template <int N> __host__ __device__ constexpr int col_region_bytes() {
+  return N * COLS * 8 > COLS * 2 * fft_line_words<N>() * 4 ? N * COLS * 8 : COLS * 2 * fft_line_words<N>() * 4;
 }
+template <int N> __host__ __device__ constexpr int col_smem_bytes() { return N * 8 + col_region_bytes<N>() + N * COLS; }
+FI int tslot(int r, int c) { return r * COLS + (c ^ (r & (COLS - 1))); }
 
 FI void cp_async16_fft(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
@@ -112,7 +119,7 @@ __global__ void __launch_bounds__(256) k_row_ahb(const float2* __restrict__ b, c
 
 // Load a 16-column tile of t into shared memory (SoA, row stride COLS+1).
 template <int N>
-FI void load_col_tile(const float2* __restrict__ src, float* tre, float* tim, size_t sbase, int c0) {
+FI void load_col_tile(const float2* __restrict__ src, float2* tile, size_t sbase, int c0) {
   // every thread issues all its 16-byte loads (two columns each) before the
   // first shared-memory store, so a whole tile is in flight at once
   constexpr int NT = COLS * FftCfg<N>::T, HC = COLS / 2, K = N * HC / NT;
@@ -126,31 +133,33 @@ FI void load_col_tile(const float2* __restrict__ src, float* tre, float* tim, si
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const int idx = threadIdx.x + NT * k, r = idx / HC, cp = idx % HC;
-    tre[r * (COLS + 1) + 2 * cp] = g[k].x;
-    tim[r * (COLS + 1) + 2 * cp] = g[k].y;
-    tre[r * (COLS + 1) + 2 * cp + 1] = g[k].z;
-    tim[r * (COLS + 1) + 2 * cp + 1] = g[k].w;
+    tile[tslot(r, 2 * cp)] = make_float2(g[k].x, g[k].y);
+    tile[tslot(r, 2 * cp + 1)] = make_float2(g[k].z, g[k].w);
   }
 }
 
 template <int N>
-FI void store_col_tile(float2* __restrict__ dst, const float* tre, const float* tim, size_t sbase, int c0) {
+FI void store_col_tile(float2* __restrict__ dst, const float2* tile, size_t sbase, int c0) {
   constexpr int NT = COLS * FftCfg<N>::T, HC = COLS / 2, K = N * HC / NT;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const int idx = threadIdx.x + NT * k, r = idx / HC, cp = idx % HC;
-    const int o = r * (COLS + 1) + 2 * cp;
-    *reinterpret_cast<float4*>(dst + sbase + (size_t)r * N + c0 + 2 * cp) =
-        make_float4(tre[o], tim[o], tre[o + 1], tim[o + 1]);
+    const float2 a = tile[tslot(r, 2 * cp)], b = tile[tslot(r, 2 * cp + 1)];
+    *reinterpret_cast<float4*>(dst + sbase + (size_t)r * N + c0 + 2 * cp) = make_float4(a.x, a.y, b.x, b.y);
   }
 }
 
-// The 16 mask bytes of each row of a column tile, one 16-byte load per row.
+// The 16 mask bytes of each row of a column tile (one 16-byte load per row),
+// stored transposed: mskt[c * N + r].
 template <int N>
-FI void load_mask_tile(const uint8_t* __restrict__ mask, uint8_t* msk, size_t sbase, int c0) {
+FI void load_mask_tile(const uint8_t* __restrict__ mask, uint8_t* mskt, size_t sbase, int c0) {
   constexpr int NT = COLS * FftCfg<N>::T;
-  for (int r = threadIdx.x; r < N; r += NT)
-    *reinterpret_cast<uint4*>(msk + r * COLS) = *reinterpret_cast<const uint4*>(mask + sbase + (size_t)r * N + c0);
+  for (int r = threadIdx.x; r < N; r += NT) {
+    const uint4 m = *reinterpret_cast<const uint4*>(mask + sbase + (size_t)r * N + c0);
+    const unsigned w[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+    for (int c = 0; c < COLS; ++c) mskt[c * N + r] = (uint8_t)(w[c >> 2] >> (8 * (c & 3)));
+  }
 }
 
 // In place on t: t = colIFFT(mask * colFFT(t)) for a 16-column tile.
@@ -164,39 +173,37 @@ __global__ void __launch_bounds__(512) k_col_mask(float2* __restrict__ tbuf, con
   if (st != nullptr && !slice_running(st, s)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tw = reinterpret_cast<float2*>(smem);
-  float* tre = reinterpret_cast<float*>(smem + N * 8);
-  float* tim = tre + N * (COLS + 1);
-  uint8_t* msk = reinterpret_cast<uint8_t*>(tim + N * (COLS + 1));
+  float2* tile = reinterpret_cast<float2*>(smem + N * 8);
+  uint8_t* mskt = smem + N * 8 + col_region_bytes<N>();
   const int c0 = blockIdx.x * COLS;
   const size_t sbase = (size_t)s * N * N;
   load_twiddles<N>(tw, twg);
-  load_mask_tile<N>(mask, msk, sbase, c0);
-  load_col_tile<N>(tbuf, tre, tim, sbase, c0);
+  load_mask_tile<N>(mask, mskt, sbase, c0);
+  load_col_tile<N>(tbuf, tile, sbase, c0);
   __syncthreads();
   const int c = threadIdx.x / T, t = threadIdx.x % T;
   float2 v[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int r = t + T * e;
-    v[e] = make_float2(tre[r * (COLS + 1) + c], tim[r * (COLS + 1) + c]);
+    v[e] = tile[tslot(r, c)];
   }
   __syncthreads();
-  float* bre = tre + c * LW;
-  float* bim = tim + c * LW;
+  float* bre = reinterpret_cast<float*>(tile) + c * 2 * LW;
+  float* bim = bre + LW;
   fft_line<N, -1>(v, bre, bim, tw, t);
 #pragma unroll
   for (int e = 0; e < E; ++e)
-    if (!msk[(t + T * e) * COLS + c]) v[e] = make_float2(0.f, 0.f);
+    if (!mskt[c * N + t + T * e]) v[e] = make_float2(0.f, 0.f);
   fft_line<N, +1>(v, bre, bim, tw, t);
   __syncthreads();
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int r = t + T * e;
-    tre[r * (COLS + 1) + c] = v[e].x;
-    tim[r * (COLS + 1) + c] = v[e].y;
+    tile[tslot(r, c)] = v[e];
   }
   __syncthreads();
-  store_col_tile<N>(tbuf, tre, tim, sbase, c0);
+  store_col_tile<N>(tbuf, tile, sbase, c0);
 }
 
 // atb = (1/n) colIFFT(t)  [real: imaginary part dropped]; x = atb if x != null;
@@ -211,23 +218,22 @@ __global__ void __launch_bounds__(512) k_col_inv(const float2* __restrict__ tbuf
   const int s = blockIdx.y;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tw = reinterpret_cast<float2*>(smem);
-  float* tre = reinterpret_cast<float*>(smem + N * 8);
-  float* tim = tre + N * (COLS + 1);
+  float2* tile = reinterpret_cast<float2*>(smem + N * 8);
   __shared__ double red[32];
   const int c0 = blockIdx.x * COLS;
   const size_t sbase = (size_t)s * N * N;
   load_twiddles<N>(tw, twg);
-  load_col_tile<N>(tbuf, tre, tim, sbase, c0);
+  load_col_tile<N>(tbuf, tile, sbase, c0);
   __syncthreads();
   const int c = threadIdx.x / T, t = threadIdx.x % T;
   float2 v[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int r = t + T * e;
-    v[e] = make_float2(tre[r * (COLS + 1) + c], tim[r * (COLS + 1) + c]);
+    v[e] = tile[tslot(r, c)];
   }
   __syncthreads();
-  fft_line<N, +1>(v, tre + c * LW, tim + c * LW, tw, t);
+  fft_line<N, +1>(v, reinterpret_cast<float*>(tile) + c * 2 * LW, reinterpret_cast<float*>(tile) + c * 2 * LW + LW, tw, t);
   const float sc = 1.0f / (float)N;
   float acc = 0.f;
 #pragma unroll
@@ -239,13 +245,12 @@ __global__ void __launch_bounds__(512) k_col_inv(const float2* __restrict__ tbuf
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int r = t + T * e;
-    tre[r * (COLS + 1) + c] = v[e].x;
-    tim[r * (COLS + 1) + c] = v[e].y;
+    tile[tslot(r, c)] = v[e];
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < N * COLS; idx += blockDim.x) {
     const int r = idx / COLS, cc = idx % COLS;
-    const float2 o = make_float2(tre[r * (COLS + 1) + cc], tim[r * (COLS + 1) + cc]);
+    const float2 o = tile[tslot(r, cc)];
     const size_t gi = sbase + (size_t)r * N + c0 + cc;
     atb[gi] = o;
     if (x) x[gi] = o;
@@ -265,37 +270,35 @@ __global__ void __launch_bounds__(512) k_col_dc(float2* __restrict__ tbuf, const
   const int s = blockIdx.y;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tw = reinterpret_cast<float2*>(smem);
-  float* tre = reinterpret_cast<float*>(smem + N * 8);
-  float* tim = tre + N * (COLS + 1);
+  float2* tile = reinterpret_cast<float2*>(smem + N * 8);
   const int c0 = blockIdx.x * COLS;
   const size_t sbase = (size_t)s * N * N;
   load_twiddles<N>(tw, twg);
-  load_col_tile<N>(tbuf, tre, tim, sbase, c0);
+  load_col_tile<N>(tbuf, tile, sbase, c0);
   __syncthreads();
   const int c = threadIdx.x / T, t = threadIdx.x % T;
   float2 v[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int r = t + T * e;
-    v[e] = make_float2(tre[r * (COLS + 1) + c], tim[r * (COLS + 1) + c]);
+    v[e] = tile[tslot(r, c)];
   }
   __syncthreads();
-  fft_line<N, -1>(v, tre + c * LW, tim + c * LW, tw, t);
+  fft_line<N, -1>(v, reinterpret_cast<float*>(tile) + c * 2 * LW, reinterpret_cast<float*>(tile) + c * 2 * LW + LW, tw, t);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const size_t gi = sbase + (size_t)(t + T * e) * N + c0 + c;
     if (mask[gi]) v[e] = cscale(b[gi], (float)N);
   }
-  fft_line<N, +1>(v, tre + c * LW, tim + c * LW, tw, t);
+  fft_line<N, +1>(v, reinterpret_cast<float*>(tile) + c * 2 * LW, reinterpret_cast<float*>(tile) + c * 2 * LW + LW, tw, t);
   __syncthreads();
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int r = t + T * e;
-    tre[r * (COLS + 1) + c] = v[e].x;
-    tim[r * (COLS + 1) + c] = v[e].y;
+    tile[tslot(r, c)] = v[e];
   }
   __syncthreads();
-  store_col_tile<N>(tbuf, tre, tim, sbase, c0);
+  store_col_tile<N>(tbuf, tile, sbase, c0);
 }
 
 // Data term of F: partial sum over sampled entries of |(1/n) colFFT(t) - b|^2,
@@ -309,23 +312,22 @@ __global__ void __launch_bounds__(512) k_col_resid(const float2* __restrict__ tb
   const int s = blockIdx.y;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tw = reinterpret_cast<float2*>(smem);
-  float* tre = reinterpret_cast<float*>(smem + N * 8);
-  float* tim = tre + N * (COLS + 1);
+  float2* tile = reinterpret_cast<float2*>(smem + N * 8);
   __shared__ double red[32];
   const int c0 = blockIdx.x * COLS;
   const size_t sbase = (size_t)s * N * N;
   load_twiddles<N>(tw, twg);
-  load_col_tile<N>(tbuf, tre, tim, sbase, c0);
+  load_col_tile<N>(tbuf, tile, sbase, c0);
   __syncthreads();
   const int c = threadIdx.x / T, t = threadIdx.x % T;
   float2 v[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int r = t + T * e;
-    v[e] = make_float2(tre[r * (COLS + 1) + c], tim[r * (COLS + 1) + c]);
+    v[e] = tile[tslot(r, c)];
   }
   __syncthreads();
-  fft_line<N, -1>(v, tre + c * LW, tim + c * LW, tw, t);
+  fft_line<N, -1>(v, reinterpret_cast<float*>(tile) + c * 2 * LW, reinterpret_cast<float*>(tile) + c * 2 * LW + LW, tw, t);
   const float sc = 1.0f / (float)N;
   float acc = 0.f;
 #pragma unroll
