@@ -221,6 +221,13 @@ firls_status firls_autotune(firls_ctx* ctx, const char* cache_path);
 /* The tile shapes in use (0 = built-in default). */
 firls_status firls_get_tuning(const firls_ctx* ctx, int* rows_per_cta, int* coarse_max, int* ilu_depth);
 
+/* Set the tile shapes explicitly (0 = built-in default for that shape):
+ * rows per CTA of the tiled wavelet levels, the largest wavelet block kept
+ * in shared memory, and the ILU ring shape (10 * rows per stage + stages).
+ * FIRLS_E_INVALID_ARG if a shape does not fit this size.  A captured outer
+ * step is re-captured at the next solve. */
+firls_status firls_set_tuning(firls_ctx* ctx, int rows_per_cta, int coarse_max, int ilu_shape);
+
 /* atb = A^H b = F^H R^T b (real unknown: its real part), the zero-filled
  * reconstruction and x^1 of Sec. 3.3.  b, atb device complex64 [batch][n][n]. */
 firls_status firls_adjoint(firls_ctx* ctx, const void* b, void* atb);

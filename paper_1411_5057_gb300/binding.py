@@ -21,7 +21,8 @@ REAL_X = 1
 
 EXPORTED = ["firls_size_supported", "firls_create", "firls_set_operator", "firls_solve", "firls_solve_multi",
             "firls_last_error", "firls_destroy", "firls_apply_AHA", "firls_apply_Phi", "firls_apply_PhiT",
-            "firls_apply_S_P", "firls_get_weights", "firls_get_precond", "firls_get_inverse_map", "firls_get_popcounts",
+            "firls_apply_S_P", "firls_get_weights", "firls_get_precond", "firls_get_inverse_map",
+            "firls_set_tuning", "firls_get_popcounts",
             "firls_set_timing", "firls_get_timing", "firls_apply_AHA_noalloc",
             "firls_cnn_create", "firls_cnn_set_params", "firls_cnn_get_params", "firls_cnn_get_grads",
             "firls_cnn_forward", "firls_cnn_train_step", "firls_cnn_destroy", "firls_objective",
@@ -82,6 +83,7 @@ def lib():
     L.firls_apply_S_P.argtypes = [vp, ctypes.POINTER(Params), vp, vp, vp, vp, vp]
     L.firls_get_weights.argtypes = [vp, vp, vp]
     L.firls_get_precond.argtypes = [vp, vp, vp]
+    L.firls_set_tuning.argtypes = [vp, i32, i32, i32]
     L.firls_get_inverse_map.argtypes = [vp, vp, vp]
     L.firls_get_popcounts.argtypes = [vp, vp]
     L.firls_apply_AHA_noalloc.argtypes = [i32, i32, vp, vp, vp, vp]
@@ -228,6 +230,14 @@ class Context:
         """Time the tile-shape choices on this context and keep the fastest."""
         self._check(lib().firls_autotune(self.h, cache_path.encode() if cache_path else None), "autotune")
         return self.tuning()
+
+    def set_tuning(self, rows_per_cta=None, coarse_max=None, ilu_depth=None):
+        """Set tile shapes (None keeps the current one, 0 the built-in default)."""
+        cur = self.tuning()
+        a = cur["rows_per_cta"] if rows_per_cta is None else rows_per_cta
+        b = cur["coarse_max"] if coarse_max is None else coarse_max
+        c = cur["ilu_depth"] if ilu_depth is None else ilu_depth
+        self._check(lib().firls_set_tuning(self.h, a, b, c), "set_tuning")
 
     def tuning(self):
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

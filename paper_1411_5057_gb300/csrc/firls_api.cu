@@ -1103,6 +1103,25 @@ extern "C" firls_status firls_autotune(firls_ctx* c, const char* cache_path) {
   return FIRLS_OK;
 }
 
+extern "C" firls_status firls_set_tuning(firls_ctx* c, int rows_per_cta, int coarse_max, int ilu_shape) {
+  if (!c) return FIRLS_E_INVALID_ARG;
+  if (rows_per_cta < 0 || coarse_max < 0 || ilu_shape < 0)
+    return fail(c, FIRLS_E_INVALID_ARG, "tile shapes must be >= 0 (0 = default)");
+  if (ilu_shape > 0 && !ilu_shape_fits(c->n, ilu_shape))
+    return fail(c, FIRLS_E_INVALID_ARG, "ILU shape does not fit this size");
+  if (c->tune_rb != rows_per_cta || c->tune_cmax != coarse_max || c->tune_ilu != ilu_shape) {
+    c->tune_rb = rows_per_cta;
+    c->tune_cmax = coarse_max;
+    c->tune_ilu = ilu_shape;
+    multi_forget(c);
+    if (c->exec) {  // the captured outer step changes shape
+      cudaGraphExecDestroy(c->exec);
+      c->exec = nullptr;
+    }
+  }
+  return FIRLS_OK;
+}
+
 extern "C" firls_status firls_get_tuning(const firls_ctx* c, int* rows_per_cta, int* coarse_max, int* ilu_depth) {
   if (!c) return FIRLS_E_INVALID_ARG;
   if (rows_per_cta) *rows_per_cta = c->tune_rb;

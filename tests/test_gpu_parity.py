@@ -436,3 +436,23 @@ def test_errors_are_status_codes(F):
     with pytest.raises(F.FirlsError) as e:
         ctx.set_operator(dev(np.ones((1, 32, 32), np.uint8)), F.PSI_DB4, 6)
     assert e.value.status == 2
+
+
+def test_set_tuning_shapes(F):
+    """Explicit tile shapes: each ILU ring shape that fits gives the same
+    iterate (the shape only changes staging, not arithmetic order); shapes
+    that do not fit are rejected."""
+    p = fs.tv_db4_256(n=64)
+    params = F.make_params(1, 10, lam=p.lam, lam_tv=p.lam_tv)
+    ref = None
+    for shape in (22, 23, 42, 43):
+        ctx = F.Context(64)
+        ctx.set_operator(dev(p.mask[None]), p.psi, p.levels)
+        ctx.set_tuning(rows_per_cta=4, coarse_max=32, ilu_depth=shape)
+        assert ctx.tuning() == {"rows_per_cta": 4, "coarse_max": 32, "ilu_depth": shape}
+        x = host(ctx.solve(c64(p.b[None]), params))
+        if ref is None:
+            ref = x
+        assert np.array_equal(x, ref), shape
+    with pytest.raises(F.FirlsError):
+        ctx.set_tuning(ilu_depth=33)  # 3-row stages do not exist
