@@ -496,6 +496,8 @@ extern "C" firls_status firls_create(firls_ctx** out, int n_rows, int n_cols, in
   // d is read (times 0) nowhere, but keep the workspace finite
   cudaMemset(c->d, 0, sizeof(float2) * BN);
   cudaMemset(c->part, 0, sizeof(double) * batch * NSLOT * MAXPART);
+  // slots that are never loaded read as idle: nothing running, no steps
+  cudaMemset(c->st, 0, sizeof(SliceState) * batch);
   prepare_kernels(n);
   if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) {
     firls_destroy(c);
