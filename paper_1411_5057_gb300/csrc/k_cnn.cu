@@ -1,9 +1,12 @@
 // Learned warm start: a 6-layer 3x3 CNN (3 -> 32 -> 32 -> 32 -> 32 -> 32 -> 2,
 // ReLU between layers) that maps [Re A^H b, Im A^H b, mask] to a correction,
 // x1 = A^H b + CNN(.).  BF16 weights and activations (NHWC), FP32 accumulation
-// on the tensor cores (mma.m16n8k16 BF16), FP32 master weights and Adam.
+// on the tensor cores, FP32 master weights and Adam.
 //
-// Convolution as an implicit GEMM per tile of 8 x 32 output pixels: the input
+// Forward and data-gradient convolutions run on tcgen05 (TMEM accumulators,
+// k_conv3x3_tc) when n is a multiple of 128; otherwise, and for the weight
+// gradient, on mma.m16n8k16.  The mma.sync form is an implicit GEMM per tile
+// of 8 x 32 output pixels: the input
 // tile with a one-pixel halo sits in shared memory; each of the 9 taps is a
 // shifted view of it (the A operand, pixels x input channels) times the tap's
 // weights (input x output channels).  The same kernel runs the backward data
@@ -148,6 +151,175 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3x3(int n, const __nv_bflo
 }
 
 template <int CIN, int COUT> constexpr int conv_smem() { return (HH * HW * (CIN + 8) + 9 * COUT * (CIN + 8)) * 2; }
+
+// ---- the same convolution on the 5th-generation tensor cores (tcgen05) ----
+// A CTA computes TC_R image rows x TC_W pixels.  Per output row r the GEMM
+// D_r[pixel][co] = sum_tap sum_ci X[row r + dy][pixel + dx][ci] W[tap][co][ci]
+// runs as 9 * CIN/16 tcgen05.mma (M = 128 pixels, N = COUT, K = 16) with its
+// FP32 accumulator in TMEM (columns 32 r ..).  Operands sit in shared memory
+// in the canonical K-major layout without swizzle: 8-channel planes of
+// 16-byte pixel (or weight-row) records, so the A operand of tap (dy, dx) is
+// the halo row r + dy starting at pixel dx: core matrices 128 bytes apart
+// along M (SBO), planes one plane apart along K (LBO).  One thread issues the
+// MMAs and commits them to an mbarrier; after the (bounded) wait each warp
+// reads its 32 pixel lanes with tcgen05.ld and runs the epilogue.
+constexpr int TC_W = 128, TC_R = 4, TC_HW = TC_W + 2, TC_HR = TC_R + 2;
+constexpr int TC_THREADS = 128;
+
+FI unsigned cnn_su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// tcgen05 shared-memory matrix descriptor: start, leading (K) and stride (M/N)
+// byte offsets, fixed version bits 46-48 = 1, no swizzle.
+FI uint64_t umma_desc(const void* p, unsigned lbo, unsigned sbo) {
+  uint64_t d = (uint64_t)((cnn_su32(p) & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Operand bytes, but at least 64 KB so that at most 3 CTAs share an SM and
+// their 3 x 128 TMEM columns fit the SM's 512.
+template <int CIN, int COUT> constexpr int tc_smem() {
+  return TC_HR * TC_HW * CIN * 2 + 9 * COUT * CIN * 2 > 64 * 1024 ? TC_HR * TC_HW * CIN * 2 + 9 * COUT * CIN * 2
+                                                                   : 64 * 1024;
+}
+
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_conv3x3_tc(int n, const __nv_bfloat16* __restrict__ in,
+                                                              const __nv_bfloat16* __restrict__ wt,
+                                                              const float* __restrict__ bias,
+                                                              __nv_bfloat16* __restrict__ out,
+                                                              const __nv_bfloat16* __restrict__ gate,
+                                                              const float2* __restrict__ atb, float2* __restrict__ x1,
+                                                              int* __restrict__ err) {
+  constexpr int KP = CIN / 8;                  // 8-channel planes
+  constexpr int XPL = TC_HR * TC_HW * 16;      // bytes per activation plane
+  constexpr int WPL = COUT * 16;               // bytes per weight plane
+  static_assert(COUT % 16 == 0 && COUT <= 32 && CIN % 16 == 0, "tcgen05 conv shape");
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* xs = smem;                    // [KP][TC_HR * TC_HW pixels][16 B]
+  unsigned char* wsm = smem + KP * XPL;        // [9][KP][COUT][16 B]
+  __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) uint64_t bar;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int segs = n / TC_W;
+  const int y0 = (blockIdx.x / segs) * TC_R, x0 = (blockIdx.x % segs) * TC_W;
+  const int img = blockIdx.y;
+  const size_t ibase = (size_t)img * n * n;
+  // halo rows y0-1 .. y0+TC_R, pixels x0-1 .. x0+TC_W, zero outside the image
+  for (int idx = t; idx < TC_HR * TC_HW * KP; idx += TC_THREADS) {
+    const int px = idx / KP, ch = idx % KP;
+    const int y = y0 - 1 + px / TC_HW, x = x0 - 1 + px % TC_HW;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (y >= 0 && y < n && x >= 0 && x < n) v = reinterpret_cast<const uint4*>(in + (ibase + (size_t)y * n + x) * CIN)[ch];
+    *reinterpret_cast<uint4*>(xs + (size_t)ch * XPL + px * 16) = v;
+  }
+  for (int idx = t; idx < 9 * COUT * KP; idx += TC_THREADS) {
+    const int row = idx / KP, ch = idx % KP;  // row = tap * COUT + co
+    const int tap = row / COUT, co = row % COUT;
+    *reinterpret_cast<uint4*>(wsm + ((size_t)(tap * KP + ch) * COUT + co) * 16) =
+        reinterpret_cast<const uint4*>(wt + (size_t)row * CIN)[ch];
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic writes -> tensor core reads
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(cnn_su32(&tmem_base)),
+                 "r"(TC_R * 32)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (t == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(cnn_su32(&bar)) : "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  // D f32, A and B bf16, both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+  constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(COUT >> 3) << 17) | ((uint32_t)(TC_W >> 4) << 24);
+  if (t == 0) {
+    for (int r = 0; r < TC_R; ++r) {
+      const uint32_t d = tmem + (uint32_t)(r * 32);
+      int k = 0;
+      for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap % 3;
+        for (int kk = 0; kk < CIN / 16; ++kk, ++k) {
+          const uint64_t ad = umma_desc(xs + (size_t)(2 * kk) * XPL + ((r + dy) * TC_HW + dx) * 16, XPL, 128);
+          const uint64_t bd = umma_desc(wsm + (size_t)(tap * KP + 2 * kk) * WPL, WPL, 128);
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(k > 0 ? 1u : 0u)
+              : "memory");
+        }
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(cnn_su32(&bar))
+                 : "memory");
+  }
+  bool done = false;
+  for (int it = 0; it < 10000 && !done; ++it) {  // bounded (about a second): the MMAs take microseconds
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0, %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(cnn_su32(&bar)), "r"(100000u)
+                 : "memory");
+    done = ok != 0;
+  }
+  done = __all_sync(0xffffffffu, done);
+  if (!done && lane == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (done) {
+    for (int r = 0; r < TC_R; ++r) {
+      uint32_t v[32];
+      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(r * 32);
+      if (COUT == 32) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+            "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(ta));
+      } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(ta));
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      // this thread's pixel: row y0 + r, column x0 + 32 warp + lane
+      const size_t p = ibase + (size_t)(y0 + r) * n + x0 + warp * 32 + lane;
+      if (MODE == MODE_LAST) {
+        const float2 ab = atb[p];
+        x1[p] = make_float2(ab.x + __uint_as_float(v[0]) + bias[0], ab.y + __uint_as_float(v[1]) + bias[1]);
+      } else {
+        uint32_t pk[COUT / 2];
+#pragma unroll
+        for (int j = 0; j < COUT / 2; ++j) {
+          float a = __uint_as_float(v[2 * j]), b = __uint_as_float(v[2 * j + 1]);
+          if (MODE == MODE_HIDDEN) {
+            a = fmaxf(a + bias[2 * j], 0.f);
+            b = fmaxf(b + bias[2 * j + 1], 0.f);
+          } else {
+            const __nv_bfloat162 gt = *reinterpret_cast<const __nv_bfloat162*>(gate + p * COUT + 2 * j);
+            if (!(__bfloat162float(gt.x) > 0.f)) a = 0.f;
+            if (!(__bfloat162float(gt.y) > 0.f)) b = 0.f;
+          }
+          const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+          pk[j] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        uint4* o = reinterpret_cast<uint4*>(out + p * COUT);
+#pragma unroll
+        for (int q = 0; q < COUT / 8; ++q) o[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_R * 32) : "memory");
+}
 
 // dW[t][ci][co] = sum_p X[p + off(t)][ci] dZ[p][co]; db[co] = sum_p dZ[p][co].
 // Per-CTA partials over a strided set of tiles: pw [cta][9][CIN][COUT], pb [cta][COUT].
@@ -342,6 +514,7 @@ struct firls_cnn {
   __nv_bfloat16 *dza = nullptr, *dzb = nullptr;
   float *pw = nullptr, *pb = nullptr;
   double* lpart = nullptr;
+  int* err = nullptr;  // set by a tcgen05 convolution whose bounded wait ran out
   int adam_t = 0;
   bool params_set = false;
 };
@@ -359,6 +532,18 @@ template <typename T> firls_status cnn_alloc(firls_cnn* c, T** p, size_t count) 
 template <int CIN, int COUT, int MODE> void launch_conv(firls_cnn* c, const __nv_bfloat16* in, const __nv_bfloat16* wt,
                                                        const float* bias, __nv_bfloat16* out,
                                                        const __nv_bfloat16* gate, const float2* atb, float2* x1) {
+  if (c->n % TC_W == 0 && c->n % TC_R == 0) {  // tcgen05 form
+    static bool tattr = false;
+    if (!tattr) {
+      cudaFuncSetAttribute(k_conv3x3_tc<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           tc_smem<CIN, COUT>());
+      tattr = true;
+    }
+    const dim3 grid((c->n / TC_W) * (c->n / TC_R), c->batch);
+    k_conv3x3_tc<CIN, COUT, MODE><<<grid, TC_THREADS, tc_smem<CIN, COUT>(), c->stream>>>(c->n, in, wt, bias, out, gate,
+                                                                                          atb, x1, c->err);
+    return;
+  }
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_conv3x3<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -432,10 +617,12 @@ extern "C" firls_status firls_cnn_create(firls_cnn** out, int n, int batch, void
   A(&c->pw, (size_t)WG_CTAS * 9 * 32 * 32);
   A(&c->pb, (size_t)WG_CTAS * 32);
   A(&c->lpart, 1024);
+  A(&c->err, 1);
   if (s != FIRLS_OK) {
     firls_cnn_destroy(c);
     return s;
   }
+  cudaMemset(c->err, 0, sizeof(int));
   *out = c;
   return FIRLS_OK;
 }
@@ -531,6 +718,9 @@ extern "C" firls_status firls_cnn_train_step(firls_cnn* c, const void* atb, cons
     double s = 0.0;
     for (double v : h) s += v;
     *loss = s;
+    int e = 0;
+    if (cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FIRLS_E_CUDA;
+    if (e) return FIRLS_E_DEVICE_TIMEOUT;
   }
   return cudaGetLastError() == cudaSuccess ? FIRLS_OK : FIRLS_E_CUDA;
 }

@@ -63,8 +63,11 @@ def oracle_inputs(atb, masks, params):
     return inp, qp
 
 
-def test_forward_parity(F):
-    n, B = 64, 3
+@pytest.mark.parametrize("n", [64, 128], ids=["mma_sync", "tcgen05"])
+def test_forward_parity(F, n):
+    """n = 128 runs the convolutions on tcgen05 (TMEM accumulators), n = 64
+    on mma.sync; both against the FP64 oracle."""
+    B = 3
     atb, masks, _ = batch_inputs(n, B, 40)
     params = random_params(1)
     net = F.Cnn(n, B)
@@ -78,8 +81,9 @@ def test_forward_parity(F):
     assert rel(x1 - atb.astype(np.complex64).astype(np.complex128), ref) < TOL_FWD
 
 
-def test_gradients_and_adam_step_parity(F):
-    n, B = 64, 2
+@pytest.mark.parametrize("n", [64, 128], ids=["mma_sync", "tcgen05"])
+def test_gradients_and_adam_step_parity(F, n):
+    B = 2
     atb, masks, tgt = batch_inputs(n, B, 50)
     params = random_params(2)
     net = F.Cnn(n, B)
