@@ -207,20 +207,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3x3_tc(int n, const __nv_
   const int y0 = (blockIdx.x / segs) * TC_R, x0 = (blockIdx.x % segs) * TC_W;
   const int img = blockIdx.y;
   const size_t ibase = (size_t)img * n * n;
-  // halo rows y0-1 .. y0+TC_R, pixels x0-1 .. x0+TC_W, zero outside the image
+  // halo rows y0-1 .. y0+TC_R, pixels x0-1 .. x0+TC_W (zero outside the
+  // image) and the weights: asynchronous 16-byte copies, all in flight at once
   for (int idx = t; idx < TC_HR * TC_HW * KP; idx += TC_THREADS) {
     const int px = idx / KP, ch = idx % KP;
     const int y = y0 - 1 + px / TC_HW, x = x0 - 1 + px % TC_HW;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (y >= 0 && y < n && x >= 0 && x < n) v = reinterpret_cast<const uint4*>(in + (ibase + (size_t)y * n + x) * CIN)[ch];
-    *reinterpret_cast<uint4*>(xs + (size_t)ch * XPL + px * 16) = v;
+    unsigned char* dst = xs + (size_t)ch * XPL + px * 16;
+    if (y >= 0 && y < n && x >= 0 && x < n)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(cnn_su32(dst)),
+                   "l"(reinterpret_cast<const uint4*>(in + (ibase + (size_t)y * n + x) * CIN) + ch)
+                   : "memory");
+    else
+      *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
   }
   for (int idx = t; idx < 9 * COUT * KP; idx += TC_THREADS) {
     const int row = idx / KP, ch = idx % KP;  // row = tap * COUT + co
     const int tap = row / COUT, co = row % COUT;
-    *reinterpret_cast<uint4*>(wsm + ((size_t)(tap * KP + ch) * COUT + co) * 16) =
-        reinterpret_cast<const uint4*>(wt + (size_t)row * CIN)[ch];
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
+                     cnn_su32(wsm + ((size_t)(tap * KP + ch) * COUT + co) * 16)),
+                 "l"(reinterpret_cast<const uint4*>(wt + (size_t)row * CIN) + ch)
+                 : "memory");
   }
+  asm volatile("cp.async.commit_group;\n cp.async.wait_all;\n" ::: "memory");
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic writes -> tensor core reads
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(cnn_su32(&tmem_base)),
