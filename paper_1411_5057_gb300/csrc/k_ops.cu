@@ -293,29 +293,49 @@ k_wav_coarse(const float2* __restrict__ src, size_t src_ss, int src_ld, float2* 
   float2* cs = c + (size_t)s * nn;
   float* ws = w ? w + (size_t)s * nn : nullptr;
   const int cnt = m0 * m0;
-  if (flags & COARSE_FWD) {
-    const float2* sp = src + (size_t)s * src_ss;
+  // the block goes to shared memory with asynchronous 8-byte copies, all in
+  // flight at once (rows keep the odd stride ls that spreads column accesses)
+  {
+    const float2* sp = (flags & COARSE_FWD) ? src + (size_t)s * src_ss : cs;
+    const size_t sld = (flags & COARSE_FWD) ? (size_t)src_ld : (size_t)n;
     for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
       const int rr = idx / m0, cc = idx % m0;
-      S[rr * ls + cc] = sp[(size_t)rr * src_ld + cc];
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(
+                       (unsigned)__cvta_generic_to_shared(S + rr * ls + cc)),
+                   "l"(sp + rr * sld + cc)
+                   : "memory");
     }
-  } else {
-    for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
-      const int rr = idx / m0, cc = idx % m0;
-      S[rr * ls + cc] = cs[(size_t)rr * n + cc];
-    }
+    asm volatile("cp.async.commit_group;\n cp.async.wait_all;\n" ::: "memory");
   }
   __syncthreads();
   if (flags & COARSE_FWD) {
+    // the coefficient weights this thread scales, fetched before the levels run
+    constexpr int WMAX = COARSE_LIMIT * COARSE_LIMIT / COARSE_THREADS;
+    float wv[WMAX];
+    if ((flags & COARSE_INV) && ws) {
+#pragma unroll
+      for (int k = 0; k < WMAX; ++k) {
+        const int idx = threadIdx.x + COARSE_THREADS * k;
+        wv[k] = idx < cnt ? ws[(size_t)(idx / m0) * n + idx % m0] : 0.f;
+      }
+    }
     for (int lev = 0; lev < nlev; ++lev) smem_fwd_level(S, ls, m0 >> lev, kind);
     const float lam = st ? st[s].lam : 0.f, abar = st ? st[s].abar : 0.f, eps = st ? st[s].eps : 1e-10f;
-    for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
+    if (flags & COARSE_INV) {
+#pragma unroll
+      for (int k = 0; k < WMAX; ++k) {
+        const int idx = threadIdx.x + COARSE_THREADS * k;
+        if (idx < cnt) {
+          float2& v = S[(idx / m0) * ls + idx % m0];
+          v = cscale(v, mode == WAV_MUL_W ? wv[k] : 1.0f / (abar + lam * wv[k]));
+        }
+      }
+    }
+    for (int idx = threadIdx.x; idx < cnt && !(flags & COARSE_INV); idx += blockDim.x) {
       const int rr = idx / m0, cc = idx % m0;
       const size_t p = (size_t)rr * n + cc;
       float2& v = S[rr * ls + cc];
-      if (flags & COARSE_INV) {
-        v = cscale(v, mode == WAV_MUL_W ? ws[p] : 1.0f / (abar + lam * ws[p]));
-      } else if (mode == WAV_RAW) {
+      if (mode == WAV_RAW) {
         cs[p] = v;
       } else if (mode == WAV_MUL_W) {
         cs[p] = cscale(v, ws[p]);
