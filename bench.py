@@ -236,6 +236,9 @@ def run_ours(args):
     alg = ALG_BYTES_PER_PX[dom] * N * N * B
     achieved = alg / per_app_s / 1e9
     traffic = MEASURED_TRAFFIC_PER_PX[dom] * N * N * B if dom in MEASURED_TRAFFIC_PER_PX and N == 256 else None
+    for k in ALG_BYTES_PER_PX:  # op-apply bandwidth of every operator class, on algorithmic bytes
+        if kt[k][0] > 0 and k in apps:
+            kern[k]["alg_gbs"] = round(ALG_BYTES_PER_PX[k] * N * N * B / (kt[k][0] / apps[k] / 1e3) / 1e9, 1)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -432,8 +435,8 @@ def main(argv=None):
     ap.add_argument("--outer-tol", type=float, default=OUTER_TOL)
     ap.add_argument("--autotune", type=int, default=1, help="autotune tile shapes before timing (1/0)")
     ap.add_argument("--learned", type=int, default=1, help="also time the learned warm start (1/0)")
-    ap.add_argument("--learned-train", type=int, default=512)
-    ap.add_argument("--learned-epochs", type=int, default=20)
+    ap.add_argument("--learned-train", type=int, default=4000, help="training instances solved by the method")
+    ap.add_argument("--learned-epochs", type=int, default=10)
     ap.add_argument("--ref-outer", type=int, default=1, help="oracle outer steps per sample")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")

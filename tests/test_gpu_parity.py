@@ -304,7 +304,7 @@ def _gpu_solve_from(F, problems, x0s, outer, inner):
 ONE_STEP_TOL = 1e-4
 
 
-@pytest.mark.parametrize("name", ["haar_l1_64", "tree_128", "tv_96", "tv_db4_256"])
+@pytest.mark.parametrize("name", ["haar_l1_64", "tree_128", "tree_512", "tv_96", "tv_db4_256"])
 def test_one_outer_step_parity(F, name):
     """One outer step (weights, P, 20 PCG steps) from the oracle's own iterate.
 
@@ -319,6 +319,8 @@ def test_one_outer_step_parity(F, name):
         p, ks = fs.haar_l1_64(), (0, 10)
     elif name == "tree_128":
         p, ks = fs.tree_db4_512(n=128), (0, 5)
+    elif name == "tree_512":  # the overlapping-group workload at its full size
+        p, ks = fs.tree_db4_512(), (0,)
     elif name == "tv_96":
         p, ks = fs.make_problem(96, 0.25, 0.01, 11, real=False, psi=4, levels=0, lam=0.0, lam_tv=3e-4), (0, 8)
     else:
