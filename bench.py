@@ -228,7 +228,7 @@ def run_ours(args):
     launches_per_outer = sum(v[1] for v in kt.values())
     kern = {k: {"ms_per_outer": round(v[0], 4), "launches": v[1]} for k, v in kt.items()}
     # applications per outer step: the S operator (its three FFT passes and the
-    # wavelet term, itself 5 launches) runs inner + 1 times, the ILU inner times
+    # wavelet term, one cluster launch) runs inner + 1 times, the ILU inner times
     apps = {"row_fft": args.inner + 1, "col_fft_mask": args.inner + 1, "wavelet_S": args.inner + 1,
             "row_ifft_combine": args.inner + 1, "ilu": args.inner, "axpy": 1}
     dom = max((k for k in ALG_BYTES_PER_PX if kt[k][1] > 0), key=lambda k: kt[k][0])

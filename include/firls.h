@@ -209,8 +209,11 @@ firls_status firls_slot_get(firls_ctx* ctx, int s, void* x_out);
 
 /* Autotuner: time the tile-shape choices of this context's size, batch and
  * regulariser on its own buffers (CUDA events on its stream) and keep the
- * fastest: rows per CTA of the tiled wavelet levels (4, 8, 16), the largest
- * wavelet block kept in shared memory (32, 64), the ILU shared-memory ring
+ * fastest: the wavelet form (1, 2: every level of a slice in one launch on a
+ * thread-block cluster, the weights staged in shared memory or read from
+ * HBM, where the slice fits; 4, 8, 16: rows per CTA of the tiled levels), the
+ * largest wavelet block kept in shared memory by the tiled form (32, 64), the
+ * ILU shared-memory ring
  * shape (10 * rows per stage + stages: 42, 43, 44, 22, 23, 24, as far as
  * they fit).  cache_path (may be NULL) is a text file of earlier
  * results keyed by "n batch psi levels": a hit skips the timing, a miss
@@ -222,9 +225,12 @@ firls_status firls_autotune(firls_ctx* ctx, const char* cache_path);
 firls_status firls_get_tuning(const firls_ctx* ctx, int* rows_per_cta, int* coarse_max, int* ilu_depth);
 
 /* Set the tile shapes explicitly (0 = built-in default for that shape):
- * rows per CTA of the tiled wavelet levels, the largest wavelet block kept
- * in shared memory, and the ILU ring shape (10 * rows per stage + stages).
- * FIRLS_E_INVALID_ARG if a shape does not fit this size.  A captured outer
+ * the wavelet form (1 or 2: the one-launch cluster form as above; 4, 8 or
+ * 16: rows per CTA of the tiled levels; the default is the cluster form with
+ * staged weights where a slice fits, else 8 rows), the largest wavelet block
+ * kept in shared memory by the tiled form, and the ILU ring shape (10 * rows
+ * per stage + stages).  FIRLS_E_INVALID_ARG if a shape does not exist or does
+ * not fit this size.  A captured outer
  * step is re-captured at the next solve. */
 firls_status firls_set_tuning(firls_ctx* ctx, int rows_per_cta, int coarse_max, int ilu_shape);
 

@@ -216,7 +216,7 @@ void enqueue_S(firls_ctx* c, int mode, const float2* zin, float2* din, float2* q
   { TMark m(c, FIRLS_K_COL_FFT_MASK, 1); fft_col_mask(c->n, a); }
   if (c->kind) {
     WavArgs w = wav_args(c, c->st);
-    TMark m(c, FIRLS_K_WAVELET_S, wavelet_apply_launches(c->n, c->levels, c->tune_cmax));
+    TMark m(c, FIRLS_K_WAVELET_S, wavelet_apply_launches(c->n, c->levels, c->kind, c->tune_rb, c->tune_cmax));
     wavelet_apply(w, din, c->cw, c->ww, WAV_MUL_W, c->u, nullptr, a.real);
   }
   a.u = c->kind ? c->u : nullptr;
@@ -264,11 +264,11 @@ void enqueue_update_precond(firls_ctx* c, int step_mode, float pcg_tol, bool ini
     }
     WavArgs w = wav_args(c, c->st);
     {
-      TMark m(c, FIRLS_K_WAVELET_P, wavelet_apply_launches(n, c->levels, c->tune_cmax));
+      TMark m(c, FIRLS_K_WAVELET_P, wavelet_apply_launches(n, c->levels, c->kind, c->tune_rb, c->tune_cmax));
       wavelet_apply(w, c->r, c->cw, c->ww, WAV_MUL_PINV, c->z, c->r, real);
     }
     TMark m(c, FIRLS_K_SCALARS, 1);
-    const int np = wavelet_inverse_ctas(n, c->levels, c->tune_rb, c->tune_cmax);
+    const int np = wavelet_apply_ctas(n, c->levels, c->kind, c->tune_rb, c->tune_cmax);
     if (init)
       pcg_rho_init(B, c->stream, c->st, c->part, np, axpy_ctas(n));
     else
@@ -1058,8 +1058,10 @@ extern "C" firls_status firls_autotune(firls_ctx* c, const char* cache_path) {
     if (has_tv(c)) penta_setup(B, n, c->stream, c->st, c->wtv, nullptr, c->ia);
     float best = 1e30f;
     if (c->kind) {
-      for (int r : {4, 8, 16})
+      for (int r : {1, 2, 4, 8, 16})
         for (int m : {32, 64}) {
+          const bool cluster = r < 4;
+          if (cluster && (m != 64 || !wavelet_cluster_ctas(n, c->levels, c->kind, r))) continue;
           WavArgs w = wav_args(c, c->st);
           w.rb = r;
           w.coarse_max = m;
@@ -1111,6 +1113,10 @@ extern "C" firls_status firls_set_tuning(firls_ctx* c, int rows_per_cta, int coa
     return fail(c, FIRLS_E_INVALID_ARG, "tile shapes must be >= 0 (0 = default)");
   if (ilu_shape > 0 && !ilu_shape_fits(c->n, ilu_shape))
     return fail(c, FIRLS_E_INVALID_ARG, "ILU shape does not fit this size");
+  if ((rows_per_cta == 1 || rows_per_cta == 2) && c->kind && !wavelet_cluster_ctas(c->n, c->levels, c->kind, rows_per_cta))
+    return fail(c, FIRLS_E_INVALID_ARG, "the one-launch cluster wavelet form does not fit this size");
+  if (rows_per_cta == 3 || (rows_per_cta > 4 && rows_per_cta != 8 && rows_per_cta != 16))
+    return fail(c, FIRLS_E_INVALID_ARG, "wavelet rows per CTA must be 0, 1, 2, 4, 8 or 16");
   if (c->tune_rb != rows_per_cta || c->tune_cmax != coarse_max || c->tune_ilu != ilu_shape) {
     c->tune_rb = rows_per_cta;
     c->tune_cmax = coarse_max;

@@ -365,6 +365,390 @@ k_wav_coarse(const float2* __restrict__ src, size_t src_ss, int src_ld, float2* 
   }
 }
 
+// ---- every level of one slice on a thread-block cluster ----
+// u = Phi^T (s o Phi x) in one launch: the C CTAs of a cluster own R = n/C
+// consecutive rows of the slice each, so the whole slice lives in their
+// shared memory and only x, the weights and u cross HBM.  All levels run in
+// place.  Level l (side m = n >> (l-1), R_l = R >> (l-1) rows per CTA) keeps
+// its row r at local row r << (l-1); the row step stores each row as
+// [lowpass | highpass], the column step stores output pair k as rows 2k
+// (lowpass) and 2k+1 (highpass), so the next level's block is the even rows'
+// left halves, and every local position ends holding exactly one
+// coefficient.  The column step scales each coefficient by its weight as
+// soon as it is final, so no separate pass touches them.
+// The Daubechies-4 column step of the last pair needs the next CTA's first
+// two rows, the inverse column step of the first pair the previous CTA's last
+// pair.  Each exchange e (forward level l: e = l - 1; inverse level l:
+// e = 2L - l) has its own halo buffer and mbarrier in the receiving CTA: the
+// sender writes the rows there with st.async, which counts the bytes on that
+// mbarrier, and the receiver waits for them (bounded).  No buffer is written
+// twice in a launch, so one cluster barrier at the start (every mbarrier
+// armed before any remote write) is the only cluster-wide synchronisation.
+constexpr int WCL_THREADS = 256;
+constexpr int WCL_NMAX = 256;
+constexpr int WCL_LANE_PAIRS = WCL_NMAX / 64;  // pairs per lane of a row
+constexpr int WCL_LMAX = 5;
+constexpr int WCL_RMAX = 32;  // rows per CTA: two CTAs per SM fit with the weights mirrored
+
+FI unsigned wcl_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+FI unsigned wcl_smem(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+// 16 bytes to the same shared-memory offset in CTA `rank`, counted on that
+// CTA's mbarrier at the offset of `bar`
+FI void wcl_st_async16(const void* dst, const uint64_t* bar, unsigned rank, float4 v) {
+  unsigned ra, rb;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(wcl_smem(dst)), "r"(rank));
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(rb) : "r"(wcl_smem(bar)), "r"(rank));
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                   ra),
+               "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(rb)
+               : "memory");
+}
+// bounded wait (about a second) for the first phase of `bar`, with
+// cluster-scope acquire of the remote writes it counted
+FI bool wcl_wait(const uint64_t* bar) {
+  for (int it = 0; it < 20000; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0, %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(wcl_smem(bar)), "r"(50000u)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+FI void wcl_cp16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(wcl_smem(sdst)), "l"(gsrc) : "memory");
+}
+
+// level of exchange e, and the offset (float2) of its halo buffer
+__host__ __device__ inline int wcl_ex_level(int L, int e) { return e < L ? e + 1 : 2 * L - e; }
+__host__ __device__ inline int wcl_halo_off(int n, int L, int e) {
+  int off = 0;
+  for (int q = 0; q < e; ++q) off += 2 * (n >> (wcl_ex_level(L, q) - 1));
+  return off;
+}
+
+// Mallat row (in the n x n coefficient array) of the coefficient held at
+// local row rho, column j of CTA `rank` after all L analysis levels.
+FI int wcl_coef_row(int rho, int j, int n, int L, int R, int rank) {
+  for (int l = 1;; ++l) {
+    const int m = n >> (l - 1), r = rho >> (l - 1);
+    const int k = rank * ((R >> (l - 1)) / 2) + (r >> 1);  // global pair index at level l
+    if (r & 1) return m / 2 + k;                            // highpass row
+    if (j >= m / 2 || l == L) return k;                     // lowpass row, final
+  }
+}
+
+struct WclScale {  // per-coefficient factor: w (MUL_W) or 1/(abar + lam w)
+  const float* Wm;  // mirrored weights, or null: read from ws
+  const float* ws;
+  int n, L, R, rank, mode;
+  float lam, abar;
+  FI float2 apply(float2 v, int rho, int j) const {
+    const float wv = Wm ? Wm[rho * n + j] : __ldg(ws + (size_t)wcl_coef_row(rho, j, n, L, R, rank) * n + j);
+    return cscale(v, mode == WAV_MUL_W ? wv : 1.0f / (abar + lam * wv));
+  }
+};
+
+// one level-l row step over the R_l rows (a warp per row); the inverse of
+// level 1 (out != null) writes the samples straight to `out` (row stride n)
+// with the optional real projection and partial Re<r, out>
+FI float wcl_rows(float2* D, int n, int sr, int Rl, int m, int kind, bool inverse, float2* out = nullptr,
+                  const float2* rr_ = nullptr, int real = 0) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, half = m / 2;
+  float acc = 0.f;
+  for (int rr = wid; rr < Rl; rr += WCL_THREADS / 32) {
+    float2* L = D + rr * sr * n;
+    float2 o0[WCL_LANE_PAIRS], o1[WCL_LANE_PAIRS];
+#pragma unroll
+    for (int u = 0; u < WCL_LANE_PAIRS; ++u) {
+      const int k = lane + 32 * u;
+      if (k >= half) continue;
+      if (!inverse) {
+        const float4 p0 = reinterpret_cast<const float4*>(L)[k];
+        if (kind == 2) {
+          const float4 p1 = reinterpret_cast<const float4*>(L)[k + 1 < half ? k + 1 : 0];
+          lift::fwd_db4(make_float2(p0.x, p0.y), make_float2(p0.z, p0.w), make_float2(p1.x, p1.y),
+                        make_float2(p1.z, p1.w), o0[u], o1[u]);
+        } else {
+          lift::fwd_haar(make_float2(p0.x, p0.y), make_float2(p0.z, p0.w), o0[u], o1[u]);
+        }
+      } else if (kind == 2) {
+        const int km = k ? k - 1 : half - 1;
+        lift::inv_db4(L[km], L[half + km], L[k], L[half + k], o0[u], o1[u]);
+      } else {
+        lift::inv_haar(L[k], L[half + k], o0[u], o1[u]);
+      }
+    }
+    if (out) {
+#pragma unroll
+      for (int u = 0; u < WCL_LANE_PAIRS; ++u) {
+        const int k = lane + 32 * u;
+        if (k >= half) continue;
+        float4 v = make_float4(o0[u].x, o0[u].y, o1[u].x, o1[u].y);
+        if (real) v.y = v.w = 0.f;
+        reinterpret_cast<float4*>(out + (size_t)rr * n)[k] = v;
+        if (rr_) {
+          const float4 q = reinterpret_cast<const float4*>(rr_ + (size_t)rr * n)[k];
+          acc += q.x * v.x + q.y * v.y + q.z * v.z + q.w * v.w;
+        }
+      }
+      continue;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < WCL_LANE_PAIRS; ++u) {
+      const int k = lane + 32 * u;
+      if (k >= half) continue;
+      if (!inverse) {
+        L[k] = o0[u];
+        L[half + k] = o1[u];
+      } else {
+        reinterpret_cast<float4*>(L)[k] = make_float4(o0[u].x, o0[u].y, o1[u].x, o1[u].y);
+      }
+    }
+    __syncwarp();
+  }
+  return acc;
+}
+
+// one level-l column step, a thread per column streaming down its R_l rows;
+// H holds the halo rows (forward: the next CTA's rows 0, 1; inverse: the
+// previous CTA's last pair).  The forward step scales the coefficients that
+// are final after this level (highpass rows; lowpass rows right of m/2 or
+// at the last level).
+FI void wcl_cols(float2* D, const float2* H, int n, int sr, int Rl, int m, int kind, bool inverse, bool last_level,
+                 const WclScale& sc) {
+  const int rs = sr * n;
+  for (int j = threadIdx.x; j < m; j += WCL_THREADS) {
+    float2* Dc = D + j;
+    const bool lo_final = last_level || j >= m / 2;
+    if (kind != 2) {
+      for (int kk = 0; kk < Rl / 2; ++kk) {
+        float2 o0, o1;
+        if (!inverse) {
+          lift::fwd_haar(Dc[2 * kk * rs], Dc[(2 * kk + 1) * rs], o0, o1);
+          if (lo_final) o0 = sc.apply(o0, 2 * kk * sr, j);
+          o1 = sc.apply(o1, (2 * kk + 1) * sr, j);
+        } else {
+          lift::inv_haar(Dc[2 * kk * rs], Dc[(2 * kk + 1) * rs], o0, o1);
+        }
+        Dc[2 * kk * rs] = o0;
+        Dc[(2 * kk + 1) * rs] = o1;
+      }
+    } else if (!inverse) {
+      // two pairs per step, every load before the first store: pair k reads
+      // rows 2k..2k+3, of which only rows >= 2k+4 are still unwritten later
+      float2 r0 = Dc[0], r1 = Dc[rs];
+      int kk = 0;
+      for (; kk + 1 < Rl / 2; kk += 2) {
+        const bool last = 2 * kk + 4 >= Rl;
+        const float2 r2 = Dc[(2 * kk + 2) * rs], r3 = Dc[(2 * kk + 3) * rs];
+        const float2 r4 = last ? H[j] : Dc[(2 * kk + 4) * rs];
+        const float2 r5 = last ? H[m + j] : Dc[(2 * kk + 5) * rs];
+        float2 a0, d0, a1, d1;
+        lift::fwd_db4(r0, r1, r2, r3, a0, d0);
+        lift::fwd_db4(r2, r3, r4, r5, a1, d1);
+        if (lo_final) {
+          a0 = sc.apply(a0, 2 * kk * sr, j);
+          a1 = sc.apply(a1, (2 * kk + 2) * sr, j);
+        }
+        Dc[2 * kk * rs] = a0;
+        Dc[(2 * kk + 1) * rs] = sc.apply(d0, (2 * kk + 1) * sr, j);
+        Dc[(2 * kk + 2) * rs] = a1;
+        Dc[(2 * kk + 3) * rs] = sc.apply(d1, (2 * kk + 3) * sr, j);
+        r0 = r4;
+        r1 = r5;
+      }
+      if (kk < Rl / 2) {  // the last pair alone (its rows 2k+2, 2k+3 are the halo)
+        float2 a, d;
+        lift::fwd_db4(r0, r1, H[j], H[m + j], a, d);
+        if (lo_final) a = sc.apply(a, 2 * kk * sr, j);
+        Dc[2 * kk * rs] = a;
+        Dc[(2 * kk + 1) * rs] = sc.apply(d, (2 * kk + 1) * sr, j);
+      }
+    } else {
+      // two pairs per step; pair k needs pair k-1 as it was before its update
+      float2 am = H[j], dm = H[m + j];
+      int kk = 0;
+      for (; kk + 1 < Rl / 2; kk += 2) {
+        const float2 al = Dc[2 * kk * rs], dl = Dc[(2 * kk + 1) * rs];
+        const float2 bl = Dc[(2 * kk + 2) * rs], el = Dc[(2 * kk + 3) * rs];
+        float2 x0, x1, y0, y1;
+        lift::inv_db4(am, dm, al, dl, x0, x1);
+        lift::inv_db4(al, dl, bl, el, y0, y1);
+        Dc[2 * kk * rs] = x0;
+        Dc[(2 * kk + 1) * rs] = x1;
+        Dc[(2 * kk + 2) * rs] = y0;
+        Dc[(2 * kk + 3) * rs] = y1;
+        am = bl;
+        dm = el;
+      }
+      if (kk < Rl / 2) {
+        const float2 al = Dc[2 * kk * rs], dl = Dc[(2 * kk + 1) * rs];
+        float2 x0, x1;
+        lift::inv_db4(am, dm, al, dl, x0, x1);
+        Dc[2 * kk * rs] = x0;
+        Dc[(2 * kk + 1) * rs] = x1;
+      }
+    }
+  }
+}
+
+// rows row0, row1 (local) of width m to halo buffer Hb of CTA `to`
+// (buffer rows of width m), counted on its mbarrier `bar`
+FI void wcl_push(const float2* D, const float2* Hb, const uint64_t* bar, int n, int row0, int row1, int m,
+                 unsigned to) {
+  const int q4 = m / 2;  // float4 per row
+  for (int q = threadIdx.x; q < 2 * q4; q += WCL_THREADS) {
+    const int h = q / q4, jj = 2 * (q % q4);
+    const float4 v = *reinterpret_cast<const float4*>(D + (h ? row1 : row0) * n + jj);
+    wcl_st_async16(Hb + h * m + jj, bar, to, v);
+  }
+}
+
+__global__ void __launch_bounds__(WCL_THREADS, 2)
+k_wav_cluster(const float2* x, float2* u, const float* __restrict__ w, int n, int L, int kind, int mode,
+              int mirror, const float2* __restrict__ r, double* __restrict__ part, int real,
+              SliceState* __restrict__ st) {
+  const int s = blockIdx.y;
+  // the same slice for every CTA of the cluster: all of them leave or none
+  if (st != nullptr && !slice_running(st, s)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[32];
+  const unsigned rank = wcl_rank();
+  const unsigned C = gridDim.x;
+  const int R = n / (int)C, tid = threadIdx.x;
+  float2* D = reinterpret_cast<float2*>(smem);        // [R][n]
+  float2* H = D + R * n;                              // halo buffers of the 2L exchanges
+  uint64_t* mb = reinterpret_cast<uint64_t*>(H + wcl_halo_off(n, L, 2 * L));  // their mbarriers
+  float* Wm = reinterpret_cast<float*>(mb + 2 * L);   // [R][n] weights (mirror)
+  const size_t nn = (size_t)n * n;
+  const float* ws = w + (size_t)s * nn;
+  {
+    const float2* xs = x + (size_t)s * nn + (size_t)rank * R * n;
+    for (int q = tid; q < R * n / 2; q += WCL_THREADS) wcl_cp16(D + 2 * q, xs + 2 * q);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    if (mirror) {  // the weight of the coefficient each position will hold
+      for (int q = tid; q < R * n / 4; q += WCL_THREADS) {
+        const int rho = 4 * q / n, j = 4 * q % n;
+        wcl_cp16(Wm + 4 * q, ws + (size_t)wcl_coef_row(rho, j, n, L, R, rank) * n + j);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  if (kind == 2 && tid == 0) {  // arm every exchange: two halo rows of its level
+    for (int e = 0; e < 2 * L; ++e) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(wcl_smem(mb + e)) : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    for (int e = 0; e < 2 * L; ++e) {
+      const unsigned bytes = 2u * (unsigned)(n >> (wcl_ex_level(L, e) - 1)) * 8u;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(wcl_smem(mb + e)), "r"(bytes)
+                   : "memory");
+    }
+  }
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+  __syncthreads();
+  if (kind == 2)  // every CTA's mbarriers armed before any remote write
+    asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+  WclScale sc;
+  sc.Wm = mirror ? Wm : nullptr;
+  sc.ws = ws;
+  sc.n = n;
+  sc.L = L;
+  sc.R = R;
+  sc.rank = (int)rank;
+  sc.mode = mode;
+  sc.lam = st ? st[s].lam : 0.f;
+  sc.abar = st ? st[s].abar : 0.f;
+  bool ok = true;
+  for (int l = 1; l <= L; ++l) {
+    const int m = n >> (l - 1), Rl = R >> (l - 1), sr = 1 << (l - 1), e = l - 1;
+    wcl_rows(D, n, sr, Rl, m, kind, false);
+    __syncthreads();
+    const float2* He = H + wcl_halo_off(n, L, e);
+    if (kind == 2) {
+      wcl_push(D, He, mb + e, n, 0, sr, m, (rank + C - 1) % C);
+      ok = wcl_wait(mb + e) && ok;
+    }
+    if (l == 1) {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      __syncthreads();
+    }
+    wcl_cols(D, He, n, sr, Rl, m, kind, false, l == L, sc);
+    __syncthreads();
+  }
+  float acc = 0.f;
+  for (int l = L; l >= 1; --l) {
+    const int m = n >> (l - 1), Rl = R >> (l - 1), sr = 1 << (l - 1), e = 2 * L - l;
+    const float2* He = H + wcl_halo_off(n, L, e);
+    if (kind == 2) {
+      wcl_push(D, He, mb + e, n, (Rl - 2) * sr, (Rl - 1) * sr, m, (rank + 1) % C);
+      ok = wcl_wait(mb + e) && ok;
+    }
+    wcl_cols(D, He, n, sr, Rl, m, kind, true, false, sc);
+    __syncthreads();
+    if (l > 1) {
+      wcl_rows(D, n, sr, Rl, m, kind, true);
+      __syncthreads();
+    } else {  // the last row step writes u
+      const size_t off = (size_t)s * nn + (size_t)rank * R * n;
+      acc = wcl_rows(D, n, 1, R, n, kind, true, u + off, r ? r + off : nullptr, real);
+    }
+  }
+  if (!ok && st) st[s].fault = 1;  // a halo never arrived: results invalid
+  if (part) {
+    const double tot = block_sum((double)acc, red);
+    if (tid == 0) part[((size_t)s * NSLOT + SLOT_RZ) * MAXPART + rank] = tot;
+  }
+}
+
+static int wcl_smem_bytes(int n, int R, int L, bool mirror) {
+  return R * n * 8 + wcl_halo_off(n, L, 2 * L) * 8 + 2 * L * 8 + (mirror ? R * n * 4 : 0);
+}
+
+// Rows per CTA of the one-launch form (0 when it does not apply): the
+// fewest rows (most CTAs, at most 8 per cluster) for which every level has an
+// even number of rows per CTA.  choice: 0 default, 1 weights mirrored in
+// shared memory, 2 read from HBM; *mirror receives which.
+static int wcl_rows_per_cta(int n, int L, int kind, int choice, bool* mirror) {
+  if (kind != 1 && kind != 2) return 0;
+  if (choice != 0 && choice != 1 && choice != 2) return 0;
+  if (n % 8 || n > WCL_NMAX || L < 1 || L > WCL_LMAX || (n >> L) % 4) return 0;
+  for (int C = 8; C >= 1; --C) {
+    if (n % (C << L) || n / C > WCL_RMAX) continue;
+    if (mirror) *mirror = choice != 2;
+    return n / C;
+  }
+  return 0;
+}
+
+static void wcl_launch(const WavArgs& a, int R, bool mirror, const float2* x, const float* w, int mode, float2* u,
+                       const float2* r, int real) {
+  const int C = a.n / R;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C, a.batch);
+  cfg.blockDim = dim3(WCL_THREADS);
+  cfg.dynamicSmemBytes = wcl_smem_bytes(a.n, R, a.levels, mirror);
+  cfg.stream = a.stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_wav_cluster, x, u, w, a.n, a.levels, a.kind, mode, mirror ? 1 : 0, r,
+                     r ? a.part : nullptr, real, const_cast<SliceState*>(a.st));
+}
+
 static int coarse_smem(int m0) { return m0 * (m0 + 1) * 8; }
 
 static void set_wav_attrs() {
@@ -374,6 +758,8 @@ static void set_wav_attrs() {
   cudaFuncSetAttribute(k_wav_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (2 * 16 + 2) * 512 * 8);
   cudaFuncSetAttribute(k_wav_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 16 * 512 * 8);
   cudaFuncSetAttribute(k_wav_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, coarse_smem(COARSE_LIMIT));
+  cudaFuncSetAttribute(k_wav_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       wcl_smem_bytes(WCL_NMAX, WCL_RMAX, WCL_LMAX, true));
 }
 
 void ilu_prepare();
@@ -479,6 +865,12 @@ void wavelet_apply(const WavArgs& a, const float2* x, float2* c, float* w, int m
                    const float2* r, int real) {
   set_wav_attrs();
   const int n = a.n, L = a.levels;
+  bool mirror = false;
+  const int R = wcl_rows_per_cta(n, L, a.kind, a.rb, &mirror);
+  if (R > 0) {  // every level on chip, c untouched
+    wcl_launch(a, R, mirror, x, w, mode, u, r, real);
+    return;
+  }
   const int l0 = coarse_first_level(n, L, a.coarse_max);
   if (l0 > L) {
     wavelet_forward(a, x, c, w, mode);
@@ -499,14 +891,23 @@ void wavelet_apply(const WavArgs& a, const float2* x, float2* c, float* w, int m
   if (!final_coarse) tiled_inverse(a, dst, dss, dld, c, u, l0 - 1, r, real);
 }
 
-// Partial-sum count of the stage that computes Re<r, Phi^T ...>.
-int wavelet_inverse_ctas(int n, int levels, int rb, int cmax) {
+// CTAs per slice of the one-launch cluster form of wavelet_apply (0: tiled).
+int wavelet_cluster_ctas(int n, int levels, int kind, int rb) {
+  const int R = wcl_rows_per_cta(n, levels, kind, rb, nullptr);
+  return R ? n / R : 0;
+}
+
+// Partial-sum count of the wavelet_apply stage that computes Re<r, Phi^T ...>.
+int wavelet_apply_ctas(int n, int levels, int kind, int rb, int cmax) {
+  const int C = wavelet_cluster_ctas(n, levels, kind, rb);
+  if (C > 0) return C;
   if (coarse_first_level(n, levels, cmax) == 1) return 1;
   return (n / 2 + wav_rb(n, rb) - 1) / wav_rb(n, rb);
 }
 
 // Launches per wavelet_apply call (for the launch count).
-int wavelet_apply_launches(int n, int levels, int cmax) {
+int wavelet_apply_launches(int n, int levels, int kind, int rb, int cmax) {
+  if (wavelet_cluster_ctas(n, levels, kind, rb) > 0) return 1;
   const int l0 = coarse_first_level(n, levels, cmax);
   if (l0 > levels) return 2 * levels;
   return 2 * (l0 - 1) + 1;

@@ -61,13 +61,17 @@ struct WavArgs {
 void wavelet_forward(const WavArgs& a, const float2* x, float2* c, float* w, int mode);
 // x = Phi^T c; if r != null also partial Re<r, x> into SLOT_RZ.
 void wavelet_inverse(const WavArgs& a, const float2* c, float2* x, const float2* r, int real);
-// u = Phi^T (s o Phi x), s = w (MUL_W) or 1/(abar + lam w) (MUL_PINV); levels
-// that fit in shared memory are fused (their coefficients stay on chip); the
-// fine levels' scaled details go through c.  Optional partial Re<r, u>.
+// u = Phi^T (s o Phi x), s = w (MUL_W) or 1/(abar + lam w) (MUL_PINV).
+// Where a slice fits the shared memory of one thread-block cluster (rb 0, 1
+// or 2) every level runs in one launch and c is not touched; otherwise
+// (rb 4, 8, 16, or no fit) the fine levels are tiled, a launch per level,
+// their scaled details going through c, and the levels that fit one CTA's
+// shared memory are fused.  Optional partial Re<r, u>.
 void wavelet_apply(const WavArgs& a, const float2* x, float2* c, float* w, int mode, float2* u,
                    const float2* r, int real);
-int wavelet_inverse_ctas(int n, int levels, int rb, int coarse_max);
-int wavelet_apply_launches(int n, int levels, int coarse_max);
+int wavelet_cluster_ctas(int n, int levels, int kind, int rb);
+int wavelet_apply_ctas(int n, int levels, int kind, int rb, int coarse_max);
+int wavelet_apply_launches(int n, int levels, int kind, int rb, int coarse_max);
 void wav_prepare();
 
 // ---- TV, preconditioner, groups, PCG scalars ----

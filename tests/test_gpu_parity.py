@@ -152,6 +152,22 @@ def _cases():
 @pytest.mark.parametrize("name,n,cfg", _cases(), ids=[c[0] for c in _cases()])
 def test_weights_S_Pinv_parity(F, name, n, cfg):
     """Weights (Eq. gw/Wog/wi), S d (Eq. subprob/sub) and P^-1 r (Eq. pog / LU of Sec. 4.2)."""
+    _check_weights_S_Pinv(F, n, cfg)
+
+
+_WAVELET_CASES = [c for c in _cases() if c[2]["psi"] & 3]
+
+
+@pytest.mark.parametrize("form", [1, 2, 4, 16])
+@pytest.mark.parametrize("name,n,cfg", _WAVELET_CASES, ids=[c[0] for c in _WAVELET_CASES])
+def test_wavelet_forms_S_Pinv_parity(F, name, n, cfg, form):
+    """Every form of Phi^T (s o Phi d) inside S d and P^-1 r: the one-launch
+    cluster form with the weights staged in shared memory (1) or read from
+    HBM (2), and the tiled levels with 4 or 16 rows per CTA."""
+    _check_weights_S_Pinv(F, n, cfg, form)
+
+
+def _check_weights_S_Pinv(F, n, cfg, form=None):
     rng = np.random.default_rng(7)
     mask = fs.vd_mask(n, 0.25, 3)
     groups = fs.tree_groups(n, cfg["levels"]) if cfg["groups"] == "tree" else None
@@ -165,6 +181,8 @@ def test_weights_S_Pinv_parity(F, name, n, cfg):
     sysm.update_weights(x)
     ctx = F.Context(n, real=cfg["real"])
     ctx.set_operator(dev(mask)[None], cfg["psi"], cfg["levels"], dev(groups) if groups is not None else None)
+    if form is not None:  # every case here fits a cluster (n <= 320, 4 | n >> levels)
+        ctx.set_tuning(rows_per_cta=form)
     p = F.make_params(1, 1, lam=cfg["lam"], lam_tv=cfg["lam_tv"])
     q = torch.empty(1, n, n, dtype=torch.complex64, device="cuda")
     z = torch.empty_like(q)
@@ -458,3 +476,10 @@ def test_set_tuning_shapes(F):
         assert np.array_equal(x, ref), shape
     with pytest.raises(F.FirlsError):
         ctx.set_tuning(ilu_depth=33)  # 3-row stages do not exist
+    with pytest.raises(F.FirlsError):
+        ctx.set_tuning(rows_per_cta=3)  # no such wavelet form
+    big = F.Context(512)
+    big.set_operator(dev(np.ones((1, 512, 512), np.uint8)), fs.PSI_DB4, 5)
+    with pytest.raises(F.FirlsError):
+        big.set_tuning(rows_per_cta=1)  # a 512^2 slice does not fit one cluster's shared memory
+    big.set_tuning(rows_per_cta=16)
