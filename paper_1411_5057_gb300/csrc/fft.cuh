@@ -40,9 +40,25 @@ FIRLS_FFT_CFG(384, 12, 5, 3, 4, 4, 4, 2)
 FIRLS_FFT_CFG(512, 16, 3, 8, 8, 8, 1, 1)
 #undef FIRLS_FFT_CFG
 
-// Shared-memory words per line buffer (re or im plane), padded.
-template <int N> __host__ __device__ constexpr int fft_line_words() { return N + (N >> 5) + 1; }
-FI int fpad(int a) { return a + (a >> 5); }
+// Shared-memory words per line buffer (re or im plane): one padding word per
+// 16, so that a radix-16 pass of 16 threads stores word 17 t + q and reads
+// word t + 17 s, both on 16 distinct banks; the plane length is 8 mod 16, so
+// the two lines that share a warp (their buffers 2 planes apart, 16 banks
+// apart) never meet on a bank either.
+template <int N> __host__ __device__ constexpr int fft_line_words() {
+  return N + (N >> 4) + ((8 - (N + (N >> 4)) % 16) + 16) % 16;
+}
+FI int fpad(int a) { return a + (a >> 4); }
+
+// Shared twiddle tables, one per pass after the first: the pass with radix R
+// applied after P points (P > 1) multiplies input q of butterfly k by
+// w_N^(q k N / (P R)); its table holds those factors as [q - 1][k]
+// (q = 1..R-1, k < P), so the threads of a line, whose k are consecutive,
+// read consecutive entries.  The tables of all passes together hold N - R0
+// entries (R0 the first radix); the table of the pass after P points starts
+// at entry P - R0.
+template <int N> __host__ __device__ constexpr int tw_words() { return (N + 1) & ~1; }
+template <int N> __host__ __device__ constexpr int tw_bytes() { return tw_words<N>() * 8; }
 
 // ---- small DFTs in registers (DIR = -1 forward, +1 inverse) ----
 template <int DIR> FI float2 mul_i(float2 a) {  // a * (DIR * i)
@@ -190,8 +206,9 @@ FI void fft_pass(float2 (&v)[FftCfg<N>::E], float* bre, float* bim, const float2
 #pragma unroll
     for (int q = 0; q < R; ++q) a[q] = v[m + q * M];
     if (P > 1) {
+      const float2* twp = tw + (P - C::radix(0)) + k;
 #pragma unroll
-      for (int q = 1; q < R; ++q) a[q] = cmul(a[q], twiddle<DIR>(tw, q * k * (N / (P * R))));
+      for (int q = 1; q < R; ++q) a[q] = cmul(a[q], twiddle<DIR>(twp, (q - 1) * P));
     }
     Dft<R, DIR>::run(a);
     if (LAST) {

@@ -24,12 +24,12 @@ template <int N> __host__ __device__ constexpr int rows_per_cta() {
 
 template <int N> constexpr int row_smem_bytes(bool tv) {
   constexpr int R = rows_per_cta<N>();
-  int b = N * 8 + R * 2 * fft_line_words<N>() * 4;
+  int b = tw_bytes<N>() + R * 2 * fft_line_words<N>() * 4;
   if (tv) b += (R + 2) * N * 8 + (R + 1) * N * 4;
   return b;
 }
 
-// Shared memory of a column-pass CTA: twiddles (N float2) | region | mask
+// Shared memory of a column-pass CTA: twiddles (padded table) | region | mask
 // tile transposed ([COLS][N] bytes).  The region holds the N x COLS complex
 // tile (rows of 16 float2, XOR-swizzled: element (r, c) at r*COLS + (c ^ (r
 // mod COLS)), so that row-major fills and 16-row column reads are both free
@@ -37,7 +37,9 @@ template <int N> constexpr int row_smem_bytes(bool tv) {
 template <int N> __host__ __device__ constexpr int col_region_bytes() {
   return N * COLS * 8 > COLS * 2 * fft_line_words<N>() * 4 ? N * COLS * 8 : COLS * 2 * fft_line_words<N>() * 4;
 }
-template <int N> __host__ __device__ constexpr int col_smem_bytes() { return N * 8 + col_region_bytes<N>() + N * COLS; }
+template <int N> __host__ __device__ constexpr int col_smem_bytes() {
+  return tw_bytes<N>() + col_region_bytes<N>() + N * COLS;
+}
 FI int tslot(int r, int c) { return r * COLS + (c ^ (r & (COLS - 1))); }
 
 FI void cp_async16_fft(void* dst, const void* src) {
@@ -46,8 +48,20 @@ FI void cp_async16_fft(void* dst, const void* src) {
                : "memory");
 }
 
+// The per-pass twiddle tables (see fft.cuh) from the global table
+// twg[j] = exp(-2 pi i j / N).
 template <int N> FI void load_twiddles(float2* tw, const float2* __restrict__ twg) {
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  using C = FftCfg<N>;
+  int P = C::radix(0);
+#pragma unroll
+  for (int p = 1; p < C::NP; ++p) {
+    const int R = C::radix(p), step = N / (P * R), off = P - C::radix(0);
+    for (int i = threadIdx.x; i < (R - 1) * P; i += blockDim.x) {
+      const int q = i / P + 1, k = i % P;
+      tw[off + i] = twg[q * k * step];
+    }
+    P *= R;
+  }
 }
 
 // d = z (mode 0) | d = z + beta d (mode 1) | use d as is (mode 2); t = rowFFT(d)
@@ -62,7 +76,7 @@ __global__ void __launch_bounds__(256) k_row_fwd(const float2* __restrict__ z, f
   if (!slice_running(st, s)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tw = reinterpret_cast<float2*>(smem);
-  float* lines = reinterpret_cast<float*>(smem + N * 8);
+  float* lines = reinterpret_cast<float*>(smem + tw_bytes<N>());
   load_twiddles<N>(tw, twg);
   const int lr = threadIdx.x / T, t = threadIdx.x % T;
   const int row = blockIdx.x * R + lr;
@@ -100,7 +114,7 @@ __global__ void __launch_bounds__(256) k_row_ahb(const float2* __restrict__ b, c
   const int s = blockIdx.y;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tw = reinterpret_cast<float2*>(smem);
-  float* lines = reinterpret_cast<float*>(smem + N * 8);
+  float* lines = reinterpret_cast<float*>(smem + tw_bytes<N>());
   load_twiddles<N>(tw, twg);
   const int lr = threadIdx.x / T, t = threadIdx.x % T;
   const int row = blockIdx.x * R + lr;
@@ -173,8 +187,8 @@ __global__ void __launch_bounds__(512) k_col_mask(float2* __restrict__ tbuf, con
   if (st != nullptr && !slice_running(st, s)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tw = reinterpret_cast<float2*>(smem);
-  float2* tile = reinterpret_cast<float2*>(smem + N * 8);
-  uint8_t* mskt = smem + N * 8 + col_region_bytes<N>();
+  float2* tile = reinterpret_cast<float2*>(smem + tw_bytes<N>());
+  uint8_t* mskt = smem + tw_bytes<N>() + col_region_bytes<N>();
   const int c0 = blockIdx.x * COLS;
   const size_t sbase = (size_t)s * N * N;
   load_twiddles<N>(tw, twg);
@@ -218,7 +232,7 @@ __global__ void __launch_bounds__(512) k_col_inv(const float2* __restrict__ tbuf
   const int s = blockIdx.y;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tw = reinterpret_cast<float2*>(smem);
-  float2* tile = reinterpret_cast<float2*>(smem + N * 8);
+  float2* tile = reinterpret_cast<float2*>(smem + tw_bytes<N>());
   __shared__ double red[32];
   const int c0 = blockIdx.x * COLS;
   const size_t sbase = (size_t)s * N * N;
@@ -270,7 +284,7 @@ __global__ void __launch_bounds__(512) k_col_dc(float2* __restrict__ tbuf, const
   const int s = blockIdx.y;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tw = reinterpret_cast<float2*>(smem);
-  float2* tile = reinterpret_cast<float2*>(smem + N * 8);
+  float2* tile = reinterpret_cast<float2*>(smem + tw_bytes<N>());
   const int c0 = blockIdx.x * COLS;
   const size_t sbase = (size_t)s * N * N;
   load_twiddles<N>(tw, twg);
@@ -312,7 +326,7 @@ __global__ void __launch_bounds__(512) k_col_resid(const float2* __restrict__ tb
   const int s = blockIdx.y;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tw = reinterpret_cast<float2*>(smem);
-  float2* tile = reinterpret_cast<float2*>(smem + N * 8);
+  float2* tile = reinterpret_cast<float2*>(smem + tw_bytes<N>());
   __shared__ double red[32];
   const int c0 = blockIdx.x * COLS;
   const size_t sbase = (size_t)s * N * N;
@@ -357,8 +371,8 @@ __global__ void __launch_bounds__(256) k_row_inv(const float2* __restrict__ tbuf
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
   float2* tw = reinterpret_cast<float2*>(smem);
-  float* lines = reinterpret_cast<float*>(smem + N * 8);
-  float2* ds = reinterpret_cast<float2*>(smem + N * 8 + R * 2 * LW * 4);  // rows r0-1 .. r0+R
+  float* lines = reinterpret_cast<float*>(smem + tw_bytes<N>());
+  float2* ds = reinterpret_cast<float2*>(smem + tw_bytes<N>() + R * 2 * LW * 4);  // rows r0-1 .. r0+R
   float* ws = reinterpret_cast<float*>(ds + (R + 2) * N);                 // rows r0 .. r0+R
   const int r0 = blockIdx.x * R;
   const size_t sbase = (size_t)s * N * N;
@@ -366,7 +380,7 @@ __global__ void __launch_bounds__(256) k_row_inv(const float2* __restrict__ tbuf
   if (tv) {
     // halo rows straight to shared memory, all copies in flight at once
     constexpr int NT = R * T, KD = (R + 2) * N / 2, KW = (R + 1) * N / 4;
-    static_assert((N * 8 + R * 2 * LW * 4) % 16 == 0 && N % 4 == 0, "16-byte staging");
+    static_assert((tw_bytes<N>() + R * 2 * LW * 4) % 16 == 0 && N % 4 == 0, "16-byte staging");
     for (int idx = threadIdx.x; idx < KD; idx += NT) {
       const int rr = r0 - 1 + (2 * idx) / N, cc = (2 * idx) % N;
       if (rr >= 0 && rr < N)
