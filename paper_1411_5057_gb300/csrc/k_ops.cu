@@ -613,18 +613,23 @@ FI void wcl_push(const float2* D, const float2* Hb, const uint64_t* bar, int n, 
   }
 }
 
+// NT, RT, LT, KT: side, rows per CTA, levels and wavelet kind fixed at
+// compile time (0: taken from the arguments and the grid), so that the
+// common shape runs with constant loop bounds, strides and offsets.
+template <int NT, int RT, int LT, int KT>
 __global__ void __launch_bounds__(WCL_THREADS, 2)
-k_wav_cluster(const float2* x, float2* u, const float* __restrict__ w, int n, int L, int kind, int mode,
-              int mirror, const float2* __restrict__ r, double* __restrict__ part, int real,
+k_wav_cluster(const float2* x, float2* u, const float* __restrict__ w, int n_arg, int L_arg, int kind_arg,
+              int mode, int mirror, const float2* __restrict__ r, double* __restrict__ part, int real,
               SliceState* __restrict__ st) {
   const int s = blockIdx.y;
   // the same slice for every CTA of the cluster: all of them leave or none
   if (st != nullptr && !slice_running(st, s)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
+  const int n = NT ? NT : n_arg, L = LT ? LT : L_arg, kind = KT ? KT : kind_arg;
   const unsigned rank = wcl_rank();
-  const unsigned C = gridDim.x;
-  const int R = n / (int)C, tid = threadIdx.x;
+  const unsigned C = RT ? (unsigned)(n / RT) : gridDim.x;
+  const int R = RT ? RT : n / (int)C, tid = threadIdx.x;
   float2* D = reinterpret_cast<float2*>(smem);        // [R][n]
   float2* H = D + R * n;                              // halo buffers of the 2L exchanges
   uint64_t* mb = reinterpret_cast<uint64_t*>(H + wcl_halo_off(n, L, 2 * L));  // their mbarriers
@@ -669,7 +674,9 @@ k_wav_cluster(const float2* x, float2* u, const float* __restrict__ w, int n, in
   sc.lam = st ? st[s].lam : 0.f;
   sc.abar = st ? st[s].abar : 0.f;
   bool ok = true;
-  for (int l = 1; l <= L; ++l) {
+#pragma unroll
+  for (int l = 1; l <= (LT ? LT : WCL_LMAX); ++l) {
+    if (l > L) break;
     const int m = n >> (l - 1), Rl = R >> (l - 1), sr = 1 << (l - 1), e = l - 1;
     wcl_rows(D, n, sr, Rl, m, kind, false);
     __syncthreads();
@@ -686,7 +693,10 @@ k_wav_cluster(const float2* x, float2* u, const float* __restrict__ w, int n, in
     __syncthreads();
   }
   float acc = 0.f;
-  for (int l = L; l >= 1; --l) {
+#pragma unroll
+  for (int lr = 0; lr < (LT ? LT : WCL_LMAX); ++lr) {
+    const int l = L - lr;
+    if (l < 1) break;
     const int m = n >> (l - 1), Rl = R >> (l - 1), sr = 1 << (l - 1), e = 2 * L - l;
     const float2* He = H + wcl_halo_off(n, L, e);
     if (kind == 2) {
@@ -745,8 +755,13 @@ static void wcl_launch(const WavArgs& a, int R, bool mirror, const float2* x, co
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_wav_cluster, x, u, w, a.n, a.levels, a.kind, mode, mirror ? 1 : 0, r,
-                     r ? a.part : nullptr, real, const_cast<SliceState*>(a.st));
+  SliceState* st = const_cast<SliceState*>(a.st);
+  double* pp = r ? a.part : nullptr;
+  const int mi = mirror ? 1 : 0;
+  if (a.n == 256 && R == 32 && a.levels == 4 && a.kind == 2)  // the 256^2 four-level Daubechies-4 shape
+    cudaLaunchKernelEx(&cfg, k_wav_cluster<256, 32, 4, 2>, x, u, w, a.n, a.levels, a.kind, mode, mi, r, pp, real, st);
+  else
+    cudaLaunchKernelEx(&cfg, k_wav_cluster<0, 0, 0, 0>, x, u, w, a.n, a.levels, a.kind, mode, mi, r, pp, real, st);
 }
 
 static int coarse_smem(int m0) { return m0 * (m0 + 1) * 8; }
@@ -758,8 +773,10 @@ static void set_wav_attrs() {
   cudaFuncSetAttribute(k_wav_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (2 * 16 + 2) * 512 * 8);
   cudaFuncSetAttribute(k_wav_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 16 * 512 * 8);
   cudaFuncSetAttribute(k_wav_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, coarse_smem(COARSE_LIMIT));
-  cudaFuncSetAttribute(k_wav_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_wav_cluster<0, 0, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        wcl_smem_bytes(WCL_NMAX, WCL_RMAX, WCL_LMAX, true));
+  cudaFuncSetAttribute(k_wav_cluster<256, 32, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       wcl_smem_bytes(256, 32, 4, true));
 }
 
 void ilu_prepare();
