@@ -384,7 +384,8 @@ k_wav_coarse(const float2* __restrict__ src, size_t src_ss, int src_ld, float2* 
 // mbarrier, and the receiver waits for them (bounded).  No buffer is written
 // twice in a launch, so one cluster barrier at the start (every mbarrier
 // armed before any remote write) is the only cluster-wide synchronisation.
-constexpr int WCL_THREADS = 256;
+constexpr int WCL_THREADS = 256;      // threads per CTA of the generic shape
+constexpr int WCL_THREADS_256 = 512;  // and of the 256^2 four-level shape (two threads per column)
 constexpr int WCL_NMAX = 256;
 constexpr int WCL_LANE_PAIRS = WCL_NMAX / 64;  // pairs per lane of a row
 constexpr int WCL_LMAX = 5;
@@ -459,11 +460,11 @@ struct WclScale {  // per-coefficient factor: w (MUL_W) or 1/(abar + lam w)
 // one level-l row step over the R_l rows (a warp per row); the inverse of
 // level 1 (out != null) writes the samples straight to `out` (row stride n)
 // with the optional real projection and partial Re<r, out>
-FI float wcl_rows(float2* D, int n, int sr, int Rl, int m, int kind, bool inverse, float2* out = nullptr,
+FI float wcl_rows(float2* D, int n, int sr, int Rl, int m, int kind, bool inverse, int nth, float2* out = nullptr,
                   const float2* rr_ = nullptr, int real = 0) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, half = m / 2;
   float acc = 0.f;
-  for (int rr = wid; rr < Rl; rr += WCL_THREADS / 32) {
+  for (int rr = wid; rr < Rl; rr += nth / 32) {
     float2* L = D + rr * sr * n;
     float2 o0[WCL_LANE_PAIRS], o1[WCL_LANE_PAIRS];
 #pragma unroll
@@ -518,95 +519,125 @@ FI float wcl_rows(float2* D, int n, int sr, int Rl, int m, int kind, bool invers
   return acc;
 }
 
-// one level-l column step, a thread per column streaming down its R_l rows;
-// H holds the halo rows (forward: the next CTA's rows 0, 1; inverse: the
-// previous CTA's last pair).  The forward step scales the coefficients that
-// are final after this level (highpass rows; lowpass rows right of m/2 or
-// at the last level).
-FI void wcl_cols(float2* D, const float2* H, int n, int sr, int Rl, int m, int kind, bool inverse, bool last_level,
-                 const WclScale& sc) {
-  const int rs = sr * n;
-  for (int j = threadIdx.x; j < m; j += WCL_THREADS) {
-    float2* Dc = D + j;
-    const bool lo_final = last_level || j >= m / 2;
-    if (kind != 2) {
-      for (int kk = 0; kk < Rl / 2; ++kk) {
-        float2 o0, o1;
-        if (!inverse) {
-          lift::fwd_haar(Dc[2 * kk * rs], Dc[(2 * kk + 1) * rs], o0, o1);
-          if (lo_final) o0 = sc.apply(o0, 2 * kk * sr, j);
-          o1 = sc.apply(o1, (2 * kk + 1) * sr, j);
-        } else {
-          lift::inv_haar(Dc[2 * kk * rs], Dc[(2 * kk + 1) * rs], o0, o1);
-        }
-        Dc[2 * kk * rs] = o0;
-        Dc[(2 * kk + 1) * rs] = o1;
+// Pairs [k0, k1) of one column of a level-l column step, streaming down the
+// column in place, two pairs per step with every load before the first
+// store.  Forward: rows 2 k1 and 2 k1 + 1 (the next part's first rows, or the
+// halo) are (e0, e1); the step scales the coefficients that are final after
+// this level (highpass rows; lowpass rows right of m/2 or at the last
+// level).  Inverse: (e0, e1) is pair k0 - 1 as it was before its update.
+FI void wcl_col_pairs(float2* Dc, int rs, int sr, int j, int k0, int k1, float2 e0, float2 e1, int kind,
+                      bool inverse, bool lo_final, const WclScale& sc) {
+  if (kind != 2) {
+    for (int kk = k0; kk < k1; ++kk) {
+      float2 o0, o1;
+      if (!inverse) {
+        lift::fwd_haar(Dc[2 * kk * rs], Dc[(2 * kk + 1) * rs], o0, o1);
+        if (lo_final) o0 = sc.apply(o0, 2 * kk * sr, j);
+        o1 = sc.apply(o1, (2 * kk + 1) * sr, j);
+      } else {
+        lift::inv_haar(Dc[2 * kk * rs], Dc[(2 * kk + 1) * rs], o0, o1);
       }
-    } else if (!inverse) {
-      // two pairs per step, every load before the first store: pair k reads
-      // rows 2k..2k+3, of which only rows >= 2k+4 are still unwritten later
-      float2 r0 = Dc[0], r1 = Dc[rs];
-      int kk = 0;
-      for (; kk + 1 < Rl / 2; kk += 2) {
-        const bool last = 2 * kk + 4 >= Rl;
-        const float2 r2 = Dc[(2 * kk + 2) * rs], r3 = Dc[(2 * kk + 3) * rs];
-        const float2 r4 = last ? H[j] : Dc[(2 * kk + 4) * rs];
-        const float2 r5 = last ? H[m + j] : Dc[(2 * kk + 5) * rs];
-        float2 a0, d0, a1, d1;
-        lift::fwd_db4(r0, r1, r2, r3, a0, d0);
-        lift::fwd_db4(r2, r3, r4, r5, a1, d1);
-        if (lo_final) {
-          a0 = sc.apply(a0, 2 * kk * sr, j);
-          a1 = sc.apply(a1, (2 * kk + 2) * sr, j);
-        }
-        Dc[2 * kk * rs] = a0;
-        Dc[(2 * kk + 1) * rs] = sc.apply(d0, (2 * kk + 1) * sr, j);
-        Dc[(2 * kk + 2) * rs] = a1;
-        Dc[(2 * kk + 3) * rs] = sc.apply(d1, (2 * kk + 3) * sr, j);
-        r0 = r4;
-        r1 = r5;
+      Dc[2 * kk * rs] = o0;
+      Dc[(2 * kk + 1) * rs] = o1;
+    }
+  } else if (!inverse) {
+    float2 r0 = Dc[2 * k0 * rs], r1 = Dc[(2 * k0 + 1) * rs];
+    int kk = k0;
+    for (; kk + 1 < k1; kk += 2) {
+      const bool last = kk + 2 >= k1;
+      const float2 r2 = Dc[(2 * kk + 2) * rs], r3 = Dc[(2 * kk + 3) * rs];
+      const float2 r4 = last ? e0 : Dc[(2 * kk + 4) * rs];
+      const float2 r5 = last ? e1 : Dc[(2 * kk + 5) * rs];
+      float2 a0, d0, a1, d1;
+      lift::fwd_db4(r0, r1, r2, r3, a0, d0);
+      lift::fwd_db4(r2, r3, r4, r5, a1, d1);
+      if (lo_final) {
+        a0 = sc.apply(a0, 2 * kk * sr, j);
+        a1 = sc.apply(a1, (2 * kk + 2) * sr, j);
       }
-      if (kk < Rl / 2) {  // the last pair alone (its rows 2k+2, 2k+3 are the halo)
-        float2 a, d;
-        lift::fwd_db4(r0, r1, H[j], H[m + j], a, d);
-        if (lo_final) a = sc.apply(a, 2 * kk * sr, j);
-        Dc[2 * kk * rs] = a;
-        Dc[(2 * kk + 1) * rs] = sc.apply(d, (2 * kk + 1) * sr, j);
-      }
-    } else {
-      // two pairs per step; pair k needs pair k-1 as it was before its update
-      float2 am = H[j], dm = H[m + j];
-      int kk = 0;
-      for (; kk + 1 < Rl / 2; kk += 2) {
-        const float2 al = Dc[2 * kk * rs], dl = Dc[(2 * kk + 1) * rs];
-        const float2 bl = Dc[(2 * kk + 2) * rs], el = Dc[(2 * kk + 3) * rs];
-        float2 x0, x1, y0, y1;
-        lift::inv_db4(am, dm, al, dl, x0, x1);
-        lift::inv_db4(al, dl, bl, el, y0, y1);
-        Dc[2 * kk * rs] = x0;
-        Dc[(2 * kk + 1) * rs] = x1;
-        Dc[(2 * kk + 2) * rs] = y0;
-        Dc[(2 * kk + 3) * rs] = y1;
-        am = bl;
-        dm = el;
-      }
-      if (kk < Rl / 2) {
-        const float2 al = Dc[2 * kk * rs], dl = Dc[(2 * kk + 1) * rs];
-        float2 x0, x1;
-        lift::inv_db4(am, dm, al, dl, x0, x1);
-        Dc[2 * kk * rs] = x0;
-        Dc[(2 * kk + 1) * rs] = x1;
-      }
+      Dc[2 * kk * rs] = a0;
+      Dc[(2 * kk + 1) * rs] = sc.apply(d0, (2 * kk + 1) * sr, j);
+      Dc[(2 * kk + 2) * rs] = a1;
+      Dc[(2 * kk + 3) * rs] = sc.apply(d1, (2 * kk + 3) * sr, j);
+      r0 = r4;
+      r1 = r5;
+    }
+    if (kk < k1) {  // the last pair alone: its rows 2k+2, 2k+3 are (e0, e1)
+      float2 a, d;
+      lift::fwd_db4(r0, r1, e0, e1, a, d);
+      if (lo_final) a = sc.apply(a, 2 * kk * sr, j);
+      Dc[2 * kk * rs] = a;
+      Dc[(2 * kk + 1) * rs] = sc.apply(d, (2 * kk + 1) * sr, j);
+    }
+  } else {
+    float2 am = e0, dm = e1;
+    int kk = k0;
+    for (; kk + 1 < k1; kk += 2) {
+      const float2 al = Dc[2 * kk * rs], dl = Dc[(2 * kk + 1) * rs];
+      const float2 bl = Dc[(2 * kk + 2) * rs], el = Dc[(2 * kk + 3) * rs];
+      float2 x0, x1, y0, y1;
+      lift::inv_db4(am, dm, al, dl, x0, x1);
+      lift::inv_db4(al, dl, bl, el, y0, y1);
+      Dc[2 * kk * rs] = x0;
+      Dc[(2 * kk + 1) * rs] = x1;
+      Dc[(2 * kk + 2) * rs] = y0;
+      Dc[(2 * kk + 3) * rs] = y1;
+      am = bl;
+      dm = el;
+    }
+    if (kk < k1) {
+      const float2 al = Dc[2 * kk * rs], dl = Dc[(2 * kk + 1) * rs];
+      float2 x0, x1;
+      lift::inv_db4(am, dm, al, dl, x0, x1);
+      Dc[2 * kk * rs] = x0;
+      Dc[(2 * kk + 1) * rs] = x1;
     }
   }
+}
+
+// One level-l column step over the m columns and R_l rows; H holds the halo
+// rows (forward: the next CTA's rows 0, 1; inverse: the previous CTA's last
+// pair).  With at least 2m threads the pairs of a column are split into
+// `parts` ranges, one thread each: every part first reads the rows its
+// neighbour will overwrite (forward: the next part's first two rows;
+// inverse: the previous part's last pair), the CTA synchronises, then all
+// parts stream in place.
+FI void wcl_cols(float2* D, const float2* H, int n, int sr, int Rl, int m, int kind, bool inverse, bool last_level,
+                 const WclScale& sc, int nth) {
+  const int rs = sr * n, npair = Rl / 2;
+  int parts = 1;
+  while (parts * 2 * m <= nth && npair % (parts * 2) == 0) parts *= 2;  // equal ranges only
+  if (parts == 1) {
+    for (int j = threadIdx.x; j < m; j += nth) {
+      const bool lo_final = last_level || j >= m / 2;
+      wcl_col_pairs(D + j, rs, sr, j, 0, npair, H[j], H[m + j], kind, inverse, lo_final, sc);
+    }
+    return;
+  }
+  const int per = npair / parts, tid = threadIdx.x, j = tid % m, p = tid / m, k0 = p * per;
+  const bool act = tid < m * parts;
+  float2* Dc = D + j;
+  float2 e0 = make_float2(0.f, 0.f), e1 = e0;
+  if (act) {
+    if (!inverse) {
+      const bool edge = p + 1 == parts;
+      e0 = edge ? H[j] : Dc[2 * (k0 + per) * rs];
+      e1 = edge ? H[m + j] : Dc[(2 * (k0 + per) + 1) * rs];
+    } else {
+      e0 = p == 0 ? H[j] : Dc[(2 * k0 - 2) * rs];
+      e1 = p == 0 ? H[m + j] : Dc[(2 * k0 - 1) * rs];
+    }
+  }
+  __syncthreads();
+  if (act) wcl_col_pairs(Dc, rs, sr, j, k0, k0 + per, e0, e1, kind, inverse, last_level || j >= m / 2, sc);
 }
 
 // rows row0, row1 (local) of width m to halo buffer Hb of CTA `to`
 // (buffer rows of width m), counted on its mbarrier `bar`
 FI void wcl_push(const float2* D, const float2* Hb, const uint64_t* bar, int n, int row0, int row1, int m,
-                 unsigned to) {
+                 unsigned to, int nth) {
   const int q4 = m / 2;  // float4 per row
-  for (int q = threadIdx.x; q < 2 * q4; q += WCL_THREADS) {
+  for (int q = threadIdx.x; q < 2 * q4; q += nth) {
     const int h = q / q4, jj = 2 * (q % q4);
     const float4 v = *reinterpret_cast<const float4*>(D + (h ? row1 : row0) * n + jj);
     wcl_st_async16(Hb + h * m + jj, bar, to, v);
@@ -616,8 +647,8 @@ FI void wcl_push(const float2* D, const float2* Hb, const uint64_t* bar, int n, 
 // NT, RT, LT, KT: side, rows per CTA, levels and wavelet kind fixed at
 // compile time (0: taken from the arguments and the grid), so that the
 // common shape runs with constant loop bounds, strides and offsets.
-template <int NT, int RT, int LT, int KT>
-__global__ void __launch_bounds__(WCL_THREADS, 2)
+template <int NT, int RT, int LT, int KT, int TH>
+__global__ void __launch_bounds__(TH, 2)
 k_wav_cluster(const float2* x, float2* u, const float* __restrict__ w, int n_arg, int L_arg, int kind_arg,
               int mode, int mirror, const float2* __restrict__ r, double* __restrict__ part, int real,
               SliceState* __restrict__ st) {
@@ -638,10 +669,10 @@ k_wav_cluster(const float2* x, float2* u, const float* __restrict__ w, int n_arg
   const float* ws = w + (size_t)s * nn;
   {
     const float2* xs = x + (size_t)s * nn + (size_t)rank * R * n;
-    for (int q = tid; q < R * n / 2; q += WCL_THREADS) wcl_cp16(D + 2 * q, xs + 2 * q);
+    for (int q = tid; q < R * n / 2; q += TH) wcl_cp16(D + 2 * q, xs + 2 * q);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     if (mirror) {  // the weight of the coefficient each position will hold
-      for (int q = tid; q < R * n / 4; q += WCL_THREADS) {
+      for (int q = tid; q < R * n / 4; q += TH) {
         const int rho = 4 * q / n, j = 4 * q % n;
         wcl_cp16(Wm + 4 * q, ws + (size_t)wcl_coef_row(rho, j, n, L, R, rank) * n + j);
       }
@@ -678,18 +709,18 @@ k_wav_cluster(const float2* x, float2* u, const float* __restrict__ w, int n_arg
   for (int l = 1; l <= (LT ? LT : WCL_LMAX); ++l) {
     if (l > L) break;
     const int m = n >> (l - 1), Rl = R >> (l - 1), sr = 1 << (l - 1), e = l - 1;
-    wcl_rows(D, n, sr, Rl, m, kind, false);
+    wcl_rows(D, n, sr, Rl, m, kind, false, TH);
     __syncthreads();
     const float2* He = H + wcl_halo_off(n, L, e);
     if (kind == 2) {
-      wcl_push(D, He, mb + e, n, 0, sr, m, (rank + C - 1) % C);
+      wcl_push(D, He, mb + e, n, 0, sr, m, (rank + C - 1) % C, TH);
       ok = wcl_wait(mb + e) && ok;
     }
     if (l == 1) {
       asm volatile("cp.async.wait_group 0;\n" ::: "memory");
       __syncthreads();
     }
-    wcl_cols(D, He, n, sr, Rl, m, kind, false, l == L, sc);
+    wcl_cols(D, He, n, sr, Rl, m, kind, false, l == L, sc, TH);
     __syncthreads();
   }
   float acc = 0.f;
@@ -700,17 +731,17 @@ k_wav_cluster(const float2* x, float2* u, const float* __restrict__ w, int n_arg
     const int m = n >> (l - 1), Rl = R >> (l - 1), sr = 1 << (l - 1), e = 2 * L - l;
     const float2* He = H + wcl_halo_off(n, L, e);
     if (kind == 2) {
-      wcl_push(D, He, mb + e, n, (Rl - 2) * sr, (Rl - 1) * sr, m, (rank + 1) % C);
+      wcl_push(D, He, mb + e, n, (Rl - 2) * sr, (Rl - 1) * sr, m, (rank + 1) % C, TH);
       ok = wcl_wait(mb + e) && ok;
     }
-    wcl_cols(D, He, n, sr, Rl, m, kind, true, false, sc);
+    wcl_cols(D, He, n, sr, Rl, m, kind, true, false, sc, TH);
     __syncthreads();
     if (l > 1) {
-      wcl_rows(D, n, sr, Rl, m, kind, true);
+      wcl_rows(D, n, sr, Rl, m, kind, true, TH);
       __syncthreads();
     } else {  // the last row step writes u
       const size_t off = (size_t)s * nn + (size_t)rank * R * n;
-      acc = wcl_rows(D, n, 1, R, n, kind, true, u + off, r ? r + off : nullptr, real);
+      acc = wcl_rows(D, n, 1, R, n, kind, true, TH, u + off, r ? r + off : nullptr, real);
     }
   }
   if (!ok && st) st[s].fault = 1;  // a halo never arrived: results invalid
@@ -758,10 +789,14 @@ static void wcl_launch(const WavArgs& a, int R, bool mirror, const float2* x, co
   SliceState* st = const_cast<SliceState*>(a.st);
   double* pp = r ? a.part : nullptr;
   const int mi = mirror ? 1 : 0;
-  if (a.n == 256 && R == 32 && a.levels == 4 && a.kind == 2)  // the 256^2 four-level Daubechies-4 shape
-    cudaLaunchKernelEx(&cfg, k_wav_cluster<256, 32, 4, 2>, x, u, w, a.n, a.levels, a.kind, mode, mi, r, pp, real, st);
-  else
-    cudaLaunchKernelEx(&cfg, k_wav_cluster<0, 0, 0, 0>, x, u, w, a.n, a.levels, a.kind, mode, mi, r, pp, real, st);
+  if (a.n == 256 && R == 32 && a.levels == 4 && a.kind == 2) {  // the 256^2 four-level Daubechies-4 shape
+    cfg.blockDim = dim3(WCL_THREADS_256);
+    cudaLaunchKernelEx(&cfg, k_wav_cluster<256, 32, 4, 2, WCL_THREADS_256>, x, u, w, a.n, a.levels, a.kind, mode, mi, r,
+                       pp, real, st);
+  } else {
+    cudaLaunchKernelEx(&cfg, k_wav_cluster<0, 0, 0, 0, WCL_THREADS>, x, u, w, a.n, a.levels, a.kind, mode, mi, r, pp,
+                       real, st);
+  }
 }
 
 static int coarse_smem(int m0) { return m0 * (m0 + 1) * 8; }
@@ -773,9 +808,9 @@ static void set_wav_attrs() {
   cudaFuncSetAttribute(k_wav_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (2 * 16 + 2) * 512 * 8);
   cudaFuncSetAttribute(k_wav_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 16 * 512 * 8);
   cudaFuncSetAttribute(k_wav_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, coarse_smem(COARSE_LIMIT));
-  cudaFuncSetAttribute(k_wav_cluster<0, 0, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_wav_cluster<0, 0, 0, 0, WCL_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        wcl_smem_bytes(WCL_NMAX, WCL_RMAX, WCL_LMAX, true));
-  cudaFuncSetAttribute(k_wav_cluster<256, 32, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_wav_cluster<256, 32, 4, 2, WCL_THREADS_256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        wcl_smem_bytes(256, 32, 4, true));
 }
 
