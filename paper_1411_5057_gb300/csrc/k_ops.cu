@@ -595,41 +595,73 @@ FI void wcl_col_pairs(float2* Dc, int rs, int sr, int j, int k0, int k1, float2 
   }
 }
 
+// Pairs [k0, k1) of one column when the range touches the halo (forward:
+// its last pair reads the next CTA's rows 0, 1; inverse: its first pair reads
+// the previous CTA's last pair).  Every other pair is done first; the halo is
+// waited for only before the pair that reads it, so the exchange overlaps the
+// column work.  The inverse order is in-place safe: pairs k0+1.. need pair
+// k0 as it was, and pair k0 is updated last.
+FI void wcl_col_edge(float2* Dc, const float2* H, const uint64_t* bar, bool& ok, int rs, int sr, int j, int m,
+                     int k0, int k1, int kind, bool inverse, bool lo_final, const WclScale& sc) {
+  if (!inverse) {
+    if (k1 - k0 >= 2)
+      wcl_col_pairs(Dc, rs, sr, j, k0, k1 - 1, Dc[2 * (k1 - 1) * rs], Dc[(2 * (k1 - 1) + 1) * rs], kind, false,
+                    lo_final, sc);
+    ok = wcl_wait(bar) && ok;
+    wcl_col_pairs(Dc, rs, sr, j, k1 - 1, k1, H[j], H[m + j], kind, false, lo_final, sc);
+  } else {
+    if (k1 - k0 >= 2)
+      wcl_col_pairs(Dc, rs, sr, j, k0 + 1, k1, Dc[2 * k0 * rs], Dc[(2 * k0 + 1) * rs], kind, true, lo_final, sc);
+    ok = wcl_wait(bar) && ok;
+    wcl_col_pairs(Dc, rs, sr, j, k0, k0 + 1, H[j], H[m + j], kind, true, lo_final, sc);
+  }
+}
+
 // One level-l column step over the m columns and R_l rows; H holds the halo
 // rows (forward: the next CTA's rows 0, 1; inverse: the previous CTA's last
-// pair).  With at least 2m threads the pairs of a column are split into
-// `parts` ranges, one thread each: every part first reads the rows its
-// neighbour will overwrite (forward: the next part's first two rows;
-// inverse: the previous part's last pair), the CTA synchronises, then all
-// parts stream in place.
-FI void wcl_cols(float2* D, const float2* H, int n, int sr, int Rl, int m, int kind, bool inverse, bool last_level,
-                 const WclScale& sc, int nth) {
+// pair), counted on `bar` (Daubechies-4 only; null for Haar).  With at least
+// 2m threads the pairs of a column are split into `parts` ranges, one thread
+// each: every part first reads the rows its neighbouring part will overwrite
+// (forward: the next part's first two rows; inverse: the previous part's
+// last pair), the CTA synchronises, then all parts stream in place.
+FI void wcl_cols(float2* D, const float2* H, const uint64_t* bar, bool& ok, int n, int sr, int Rl, int m, int kind,
+                 bool inverse, bool last_level, const WclScale& sc, int nth) {
   const int rs = sr * n, npair = Rl / 2;
+  const bool halo = kind == 2;
   int parts = 1;
   while (parts * 2 * m <= nth && npair % (parts * 2) == 0) parts *= 2;  // equal ranges only
   if (parts == 1) {
     for (int j = threadIdx.x; j < m; j += nth) {
       const bool lo_final = last_level || j >= m / 2;
-      wcl_col_pairs(D + j, rs, sr, j, 0, npair, H[j], H[m + j], kind, inverse, lo_final, sc);
+      if (halo)
+        wcl_col_edge(D + j, H, bar, ok, rs, sr, j, m, 0, npair, kind, inverse, lo_final, sc);
+      else
+        wcl_col_pairs(D + j, rs, sr, j, 0, npair, H[j], H[m + j], kind, inverse, lo_final, sc);
     }
     return;
   }
   const int per = npair / parts, tid = threadIdx.x, j = tid % m, p = tid / m, k0 = p * per;
   const bool act = tid < m * parts;
+  const bool edge = halo && (inverse ? p == 0 : p + 1 == parts);
   float2* Dc = D + j;
   float2 e0 = make_float2(0.f, 0.f), e1 = e0;
-  if (act) {
+  if (act && !edge) {
     if (!inverse) {
-      const bool edge = p + 1 == parts;
-      e0 = edge ? H[j] : Dc[2 * (k0 + per) * rs];
-      e1 = edge ? H[m + j] : Dc[(2 * (k0 + per) + 1) * rs];
-    } else {
-      e0 = p == 0 ? H[j] : Dc[(2 * k0 - 2) * rs];
-      e1 = p == 0 ? H[m + j] : Dc[(2 * k0 - 1) * rs];
+      const bool last = p + 1 == parts;  // Haar: no row beyond the range is read
+      e0 = last ? e0 : Dc[2 * (k0 + per) * rs];
+      e1 = last ? e1 : Dc[(2 * (k0 + per) + 1) * rs];
+    } else if (p > 0) {
+      e0 = Dc[(2 * k0 - 2) * rs];
+      e1 = Dc[(2 * k0 - 1) * rs];
     }
   }
   __syncthreads();
-  if (act) wcl_col_pairs(Dc, rs, sr, j, k0, k0 + per, e0, e1, kind, inverse, last_level || j >= m / 2, sc);
+  if (!act) return;
+  const bool lo_final = last_level || j >= m / 2;
+  if (edge)
+    wcl_col_edge(Dc, H, bar, ok, rs, sr, j, m, k0, k0 + per, kind, inverse, lo_final, sc);
+  else
+    wcl_col_pairs(Dc, rs, sr, j, k0, k0 + per, e0, e1, kind, inverse, lo_final, sc);
 }
 
 // rows row0, row1 (local) of width m to halo buffer Hb of CTA `to`
@@ -714,13 +746,12 @@ k_wav_cluster(const float2* x, float2* u, const float* __restrict__ w, int n_arg
     const float2* He = H + wcl_halo_off(n, L, e);
     if (kind == 2) {
       wcl_push(D, He, mb + e, n, 0, sr, m, (rank + C - 1) % C, TH);
-      ok = wcl_wait(mb + e) && ok;
     }
     if (l == 1) {
       asm volatile("cp.async.wait_group 0;\n" ::: "memory");
       __syncthreads();
     }
-    wcl_cols(D, He, n, sr, Rl, m, kind, false, l == L, sc, TH);
+    wcl_cols(D, He, mb + e, ok, n, sr, Rl, m, kind, false, l == L, sc, TH);
     __syncthreads();
   }
   float acc = 0.f;
@@ -732,9 +763,8 @@ k_wav_cluster(const float2* x, float2* u, const float* __restrict__ w, int n_arg
     const float2* He = H + wcl_halo_off(n, L, e);
     if (kind == 2) {
       wcl_push(D, He, mb + e, n, (Rl - 2) * sr, (Rl - 1) * sr, m, (rank + 1) % C, TH);
-      ok = wcl_wait(mb + e) && ok;
     }
-    wcl_cols(D, He, n, sr, Rl, m, kind, true, false, sc, TH);
+    wcl_cols(D, He, mb + e, ok, n, sr, Rl, m, kind, true, false, sc, TH);
     __syncthreads();
     if (l > 1) {
       wcl_rows(D, n, sr, Rl, m, kind, true, TH);
