@@ -1033,12 +1033,16 @@ void tv_weights(int batch, int n, cudaStream_t s, const SliceState* st, const fl
 constexpr int WD_RB = 16;
 constexpr int WD_PRMAX = WD_RB / 2 + 4;  // coarse rows a level needs (filters of <= 3 * 2^l taps)
 
-__global__ void __launch_bounds__(256) k_wavelet_diag(int n, int levels, const SliceState* __restrict__ st,
+// NT, LT: side and levels fixed at compile time (0: from the arguments), so
+// that the common shape's row and column index arithmetic is shifts and masks.
+template <int NT, int LT>
+__global__ void __launch_bounds__(256) k_wavelet_diag(int n_arg, int levels_arg, const SliceState* __restrict__ st,
                                                       const float* __restrict__ w, float* __restrict__ out,
                                                       const float* __restrict__ sqtab,
                                                       const int* __restrict__ sqlen) {
   const int s = blockIdx.y;
   if (!slice_running(st, s)) return;
+  const int n = NT ? NT : n_arg, levels = LT ? LT : levels_arg;
   extern __shared__ __align__(16) float tsm[];  // [2][WD_PRMAX][n]
   const int r0 = blockIdx.x * WD_RB;
   const int rows = min(WD_RB, n - r0);
@@ -1048,7 +1052,8 @@ __global__ void __launch_bounds__(256) k_wavelet_diag(int n, int levels, const S
   float acc[PER];
 #pragma unroll
   for (int k = 0; k < PER; ++k) acc[k] = 0.f;
-  for (int l = 1; l <= levels; ++l) {
+#pragma unroll
+  for (int l = 1; l <= levels; ++l) {  // a constant trip count (unrolled) for LT > 0
     const int h = n >> l, step = 1 << l, msk = step - 1;
     const int len[2] = {sqlen[(l - 1) * 2], sqlen[(l - 1) * 2 + 1]};
     const float* F[2] = {sqtab + (size_t)((l - 1) * 2) * n, sqtab + (size_t)((l - 1) * 2 + 1) * n};
@@ -1103,13 +1108,17 @@ __global__ void __launch_bounds__(256) k_wavelet_diag(int n, int levels, const S
 }
 
 void wavelet_diag_prepare() {
-  cudaFuncSetAttribute(k_wavelet_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * WD_PRMAX * 512 * 4);
+  cudaFuncSetAttribute(k_wavelet_diag<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * WD_PRMAX * 512 * 4);
+  cudaFuncSetAttribute(k_wavelet_diag<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * WD_PRMAX * 256 * 4);
 }
 
 void wavelet_diag(int batch, int n, int levels, cudaStream_t s, const SliceState* st, const float* w,
                   float* out, const float* sqtab, const int* sqlen) {
-  k_wavelet_diag<<<dim3((n + WD_RB - 1) / WD_RB, batch), 256, 2 * WD_PRMAX * n * 4, s>>>(n, levels, st, w, out,
-                                                                                        sqtab, sqlen);
+  const dim3 grid((n + WD_RB - 1) / WD_RB, batch);
+  if (n == 256 && levels == 4)
+    k_wavelet_diag<256, 4><<<grid, 256, 2 * WD_PRMAX * n * 4, s>>>(n, levels, st, w, out, sqtab, sqlen);
+  else
+    k_wavelet_diag<0, 0><<<grid, 256, 2 * WD_PRMAX * n * 4, s>>>(n, levels, st, w, out, sqtab, sqlen);
 }
 
 // P = abar I + lam_tv (D1^T W D1 + D2^T W D2) [+ lam diag(Phi^T W Phi)] (Eq. ptv):
