@@ -438,12 +438,13 @@ __host__ __device__ inline int wcl_halo_off(int n, int L, int e) {
 // Mallat row (in the n x n coefficient array) of the coefficient held at
 // local row rho, column j of CTA `rank` after all L analysis levels.
 FI int wcl_coef_row(int rho, int j, int n, int L, int R, int rank) {
-  for (int l = 1;; ++l) {
+  for (int l = 1; l <= L; ++l) {
     const int m = n >> (l - 1), r = rho >> (l - 1);
     const int k = rank * ((R >> (l - 1)) / 2) + (r >> 1);  // global pair index at level l
     if (r & 1) return m / 2 + k;                            // highpass row
     if (j >= m / 2 || l == L) return k;                     // lowpass row, final
   }
+  return 0;  // not reached for L >= 1
 }
 
 struct WclScale {  // per-coefficient factor: w (MUL_W) or 1/(abar + lam w)
