@@ -287,15 +287,7 @@ def run_ours(args):
         out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f32 (FP64 PCG scalars)", "data": "synthetic",
-               "config": {"workload": f"firls_tv_db4_{N}", "n": N, "slices_per_step_per_gpu": S, "slots": B,
-                          "outer_max": args.outer, "inner": args.inner, "outer_tol": args.outer_tol,
-                          "mask_ratio": RATIO, "sigma": SIGMA, "lambda_tv": LAM_TV, "lambda_w": LAM_W,
-                          "wavelet": "db4", "levels": LEVELS, "batching": "continuous (slots refilled on convergence)",
-                          "completions_per_step": done_per_step,
-                          "counted": ("steady state: slices completed while the queue refills every slot; "
-                                      "slices still in flight at the end are retired uncounted") if args.steady
-                          else "every slice of the queue, including the drain",
-                          "l2": "working set > L2 (no flush needed)", "parallelism": f"replicas{world}"},
+               "config": workload_config(args, world, done_per_step),
                "roofline": roofline, "kernels_per_outer_step": kern,
                # graph replays x kernels per outer step, plus 4 kernels per slot load and 1 per retire
                "gpu_launches": int(launches_per_outer * served["runs"] * 8 + 4 * served["loads"] + served["retires"]),
@@ -368,6 +360,19 @@ def run_learned(args, F, torch, stream, b, masks, B, S, plain_value, plain_steps
             "train_instances": args.learned_train, "train_epochs": args.learned_epochs, "setup_s": round(train_s, 1)}
 
 
+def workload_config(args, world, done_per_step=None):
+    """The workload both arms report: the served 256^2 TV + D4 queue."""
+    return {"workload": f"firls_tv_db4_{N}", "n": N, "slices_per_step_per_gpu": args.queue, "slots": args.batch,
+            "outer_max": args.outer, "inner": args.inner, "outer_tol": args.outer_tol,
+            "mask_ratio": RATIO, "sigma": SIGMA, "lambda_tv": LAM_TV, "lambda_w": LAM_W,
+            "wavelet": "db4", "levels": LEVELS, "batching": "continuous (slots refilled on convergence)",
+            "completions_per_step": args.queue if done_per_step is None else done_per_step,
+            "counted": ("steady state: slices completed while the queue refills every slot; "
+                        "slices still in flight at the end are retired uncounted") if args.steady
+            else "every slice of the queue, including the drain",
+            "l2": "working set > L2 (no flush needed)", "parallelism": f"replicas{world}"}
+
+
 def oracle_sample(outer_steps, seed=2):
     """Time ``outer_steps`` FIRLS outer steps of the FP64 oracle on one slice."""
     from oracle import firls_oracle as O
@@ -408,12 +413,11 @@ def run_reference(args):
     value = (args.ref_outer / REF_OUTER_PER_RECON) / sec
     cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
            "sample": f"FP64 oracle, one {N}^2 slice, {args.ref_outer} of {REF_OUTER_PER_RECON} outer steps x "
-                     f"{args.inner} PCG per bench step"}
+                     f"{args.inner} PCG per bench step (the oracle's own outer steps to 1e-4 of x* on seed 2)"}
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"firls_tv_db4_{N}", "n": N, "batch_per_gpu": 1,
-                      "outer_per_recon": REF_OUTER_PER_RECON, "inner": args.inner, "parallelism": "cpu"},
+           "config": workload_config(args, world),
            "cpu_baseline": cpu, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

@@ -1,0 +1,30 @@
+"""The reference arm of bench.py (the FP64 oracle on one host core) prints
+one JSON line on the same workload config, metric and unit as the GPU arm,
+with its cpu_baseline and an end-to-end entry that moves no bytes."""
+import io
+import json
+import contextlib
+
+import bench
+
+
+def test_reference_arm_line():
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        out = bench.main(["--impl", "reference", "--steps", "1", "--warmup", "0", "--ref-outer", "1",
+                          "--inner", "5"])
+    line = json.loads(buf.getvalue().strip().splitlines()[-1])
+    assert line == json.loads(json.dumps(out))
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["higher_is_better"] is True and line["value"] > 0
+    # the GPU arm's config at the parser defaults (608 slices through 304 slots)
+    ours = bench.workload_config(type("A", (), {"queue": 608, "batch": 304, "outer": bench.OUTER, "inner": 5,
+                                                "outer_tol": bench.OUTER_TOL, "steady": 0})(), 1)
+    assert line["config"] == ours
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
