@@ -383,9 +383,11 @@ k_wav_coarse(const float2* __restrict__ src, size_t src_ss, int src_ld, float2* 
 // sender writes the rows there with st.async, which counts the bytes on that
 // mbarrier, and the receiver waits for them (bounded).  No buffer is written
 // twice in a launch, so one cluster barrier at the start (every mbarrier
-// armed before any remote write) is the only cluster-wide synchronisation.
+// armed before any remote write) is the only cluster-wide synchronisation;
+// only the thread range whose pair reads a halo waits for it, just before
+// that pair, so the exchange overlaps the rest of the column step.
 constexpr int WCL_THREADS = 256;      // threads per CTA of the generic shape
-constexpr int WCL_THREADS_256 = 512;  // and of the 256^2 four-level shape (two threads per column)
+constexpr int WCL_THREADS_256 = 512;  // and of the 256^2 four-level shape (a column's pairs split over 2-4 threads)
 constexpr int WCL_NMAX = 256;
 constexpr int WCL_LANE_PAIRS = WCL_NMAX / 64;  // pairs per lane of a row
 constexpr int WCL_LMAX = 5;
