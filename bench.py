@@ -399,21 +399,42 @@ def cpu_baseline(args, outer_per_recon=None):
                       f"same stopping rule takes on this workload)"}
 
 
+def _oracle_worker(a):
+    """One oracle sample in a worker process: (outer steps, PCG steps, seed)."""
+    outer, inner, seed = a
+    ARGS_INNER[0] = inner
+    return oracle_sample(outer, seed)
+
+
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
         return None
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[k] = "1"
+        os.environ[k] = "1"  # one thread per oracle instance (inherited by the workers)
     ARGS_INNER[0] = args.inner
-    for _ in range(args.warmup):
-        oracle_sample(1)
-    t = [oracle_sample(args.ref_outer) for _ in range(args.steps)]
+    procs = args.ref_procs if args.ref_procs > 0 else (os.cpu_count() or 1)
+    if procs == 1:
+        for _ in range(args.warmup):
+            oracle_sample(1)
+        t = [oracle_sample(args.ref_outer) for _ in range(args.steps)]
+    else:
+        # one independent slice per host core (seeds 2, 3, ...), all at once
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(procs) as pool:
+            for _ in range(args.warmup):
+                pool.map(_oracle_worker, [(1, args.inner, 2 + i) for i in range(procs)])
+            t = []
+            for _ in range(args.steps):
+                t0 = time.perf_counter()
+                pool.map(_oracle_worker, [(args.ref_outer, args.inner, 2 + i) for i in range(procs)])
+                t.append(time.perf_counter() - t0)
     sec = float(np.mean(t))
-    value = (args.ref_outer / REF_OUTER_PER_RECON) / sec
-    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"FP64 oracle, one {N}^2 slice, {args.ref_outer} of {REF_OUTER_PER_RECON} outer steps x "
-                     f"{args.inner} PCG per bench step (the oracle's own outer steps to 1e-4 of x* on seed 2)"}
+    value = procs * (args.ref_outer / REF_OUTER_PER_RECON) / sec
+    cpu = {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+           "sample": f"FP64 oracle, {procs} independent {N}^2 slice(s) at once, one per host core, each "
+                     f"{args.ref_outer} of {REF_OUTER_PER_RECON} outer steps x {args.inner} PCG per bench step "
+                     f"(the oracle's own outer steps to 1e-4 of x* on seed 2)"}
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -442,6 +463,8 @@ def main(argv=None):
     ap.add_argument("--learned-train", type=int, default=4000, help="training instances solved by the method")
     ap.add_argument("--learned-epochs", type=int, default=10)
     ap.add_argument("--ref-outer", type=int, default=1, help="oracle outer steps per sample")
+    ap.add_argument("--ref-procs", type=int, default=0,
+                    help="reference arm: oracle instances run at once, one per host core (0: all cores)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

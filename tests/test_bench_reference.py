@@ -8,11 +8,15 @@ import contextlib
 import bench
 
 
-def test_reference_arm_line():
+import pytest
+
+
+@pytest.mark.parametrize("procs", [1, 2])
+def test_reference_arm_line(procs):
     buf = io.StringIO()
     with contextlib.redirect_stdout(buf):
         out = bench.main(["--impl", "reference", "--steps", "1", "--warmup", "0", "--ref-outer", "1",
-                          "--inner", "5"])
+                          "--inner", "5", "--ref-procs", str(procs)])
     line = json.loads(buf.getvalue().strip().splitlines()[-1])
     assert line == json.loads(json.dumps(out))
     for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
@@ -24,7 +28,7 @@ def test_reference_arm_line():
     ours = bench.workload_config(type("A", (), {"queue": 608, "batch": 304, "outer": bench.OUTER, "inner": 5,
                                                 "outer_tol": bench.OUTER_TOL, "steady": 0})(), 1)
     assert line["config"] == ours
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == procs
     assert line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
