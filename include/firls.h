@@ -95,8 +95,10 @@ firls_status firls_create(firls_ctx** out, int n_rows, int n_cols, int batch,
  * map (CSR, ascending group ids per coefficient) used to sum the
  * duplicated weights of Eq. Wog into diag(G^T W G) without atomics.
  * Synchronises the stream (reads back the popcounts and the map check).
- * Returns FIRLS_E_GROUPMAP if an index is outside [0, n^2) or the offsets
- * are not non-decreasing. */
+ * Returns FIRLS_E_INVALID_ARG if a slice's mask is empty (popcount 0: A = 0,
+ * nothing to reconstruct) and FIRLS_E_GROUPMAP if an index is outside
+ * [0, n^2) or the offsets are not non-decreasing; after either error the
+ * operator counts as not set. */
 firls_status firls_set_operator(firls_ctx* ctx, const uint8_t* mask,
                                 unsigned psi_kind, int wavelet_levels,
                                 const int32_t* group_idx, const int32_t* group_off,
@@ -139,7 +141,10 @@ typedef struct {
  * Operators run in FP32; the PCG inner products, alpha, beta, rho, the
  * residual norms and the relative change are accumulated in FP64.
  * Returns FIRLS_E_BREAKDOWN if any slice broke down (its x_out holds its
- * last iterate; the other slices are unaffected). */
+ * last iterate; the other slices are unaffected).  A slice whose A^H b is
+ * not finite (a NaN or infinity in b on the mask) is not iterated and counts
+ * as a breakdown; its x_out holds its start (x0, or A^H b).  b = 0 is not a
+ * breakdown: x = 0 is then exact and PCG stops at rho = 0. */
 firls_status firls_solve(firls_ctx* ctx, const void* b, const firls_params* params,
                          const void* x0, void* x_out, firls_stats* stats);
 
@@ -194,6 +199,8 @@ firls_status firls_apply_S_P(firls_ctx* ctx, const firls_params* params,
  *   [n][n]) and k-space b (device complex64 [n][n]), compute its A^H b and
  *   popcount, start from x0 (device, one slice) or A^H b, reset its state
  *   with its own lambdas (eps <= 0 selects 1e-10).  Other slots untouched.
+ *   Reads back the popcount (synchronises the stream): an empty mask returns
+ *   FIRLS_E_INVALID_ARG and leaves the slot retired.
  * firls_run: enqueue params->outer_iters outer steps of every slot that is
  *   not done (one captured graph per step; no host synchronisation).
  * firls_slot_status: per-slot done flag, outer steps and last relative
@@ -220,6 +227,16 @@ firls_status firls_slot_get(firls_ctx* ctx, int s, void* x_out);
  * appends the new result.  Overwrites the context's workspace; call after
  * firls_set_operator and before solving.  Synchronises the stream. */
 firls_status firls_autotune(firls_ctx* ctx, const char* cache_path);
+
+/* Failure-detection test hook (no counterpart in the paper).  With enable = 1
+ * the TV preconditioner kernel (the ILU sweeps of Sec. 4.2) of every later
+ * outer step runs in a test form: its producer issues no copy and every
+ * bounded wait between its warps gives up after the first poll.  The waits
+ * run out with nothing in flight, the slices are marked faulted and
+ * firls_solve returns FIRLS_E_DEVICE_TIMEOUT; the context stays usable.
+ * enable = 0 restores the normal kernel.  Only contexts with FIRLS_PSI_TV
+ * launch that kernel. */
+firls_status firls_set_wait_test(firls_ctx* ctx, int enable);
 
 /* The tile shapes in use (0 = built-in default). */
 firls_status firls_get_tuning(const firls_ctx* ctx, int* rows_per_cta, int* coarse_max, int* ilu_depth);
@@ -354,7 +371,7 @@ void firls_cnn_destroy(firls_cnn* net);
  *
  * Scratch: instead of allocating, the library keeps fixed-size __device__
  * arrays (FFT intermediate of FIRLS_NOALLOC_MAX_ELEMS complex values, a
- * twiddle table, per-slice state and partial sums: about 8.4 MB) that every
+ * twiddle table, per-slice state and partial sums: 8.4 MiB) that every
  * GPU loading the library holds until the process exits.  Limits:
  * batch * n * n <= FIRLS_NOALLOC_MAX_ELEMS and batch <= FIRLS_NOALLOC_MAX_BATCH;
  * larger requests return FIRLS_E_SHAPE, as do unsupported n.  Null pointers
@@ -367,6 +384,10 @@ void firls_cnn_destroy(firls_cnn* net);
  * arrays, which keep the last call's contents; each call rewrites what it
  * reads before reading it.  Calls that overlap on the GPU (different
  * streams, or different host threads) race on the arrays: serialise them.
+ * The host-side set-up is guarded by a lock, so first calls from several
+ * host threads are safe.  A CUDA error makes the next call redo the set-up;
+ * a cudaDeviceReset in the process is not supported (the cached addresses
+ * and the twiddle table are not refreshed after it).
  * No cudaMalloc, cudaFree or allocating library routine is called. */
 #define FIRLS_NOALLOC_MAX_ELEMS (1 << 20)
 #define FIRLS_NOALLOC_MAX_BATCH 64

@@ -15,14 +15,15 @@ LIB_PATH = os.path.join(HERE, "libfirls.so")
 
 FIRLS_OK = 0
 STATUS = {0: "FIRLS_OK", 1: "FIRLS_E_INVALID_ARG", 2: "FIRLS_E_SHAPE", 3: "FIRLS_E_GROUPMAP",
-          4: "FIRLS_E_CUDA", 5: "FIRLS_E_NOMEM", 6: "FIRLS_E_BREAKDOWN", 7: "FIRLS_E_STATE"}
+          4: "FIRLS_E_CUDA", 5: "FIRLS_E_NOMEM", 6: "FIRLS_E_BREAKDOWN", 7: "FIRLS_E_STATE",
+          8: "FIRLS_E_DEVICE_TIMEOUT"}
 PSI_HAAR, PSI_DB4, PSI_TV = 1, 2, 4
 REAL_X = 1
 
 EXPORTED = ["firls_size_supported", "firls_create", "firls_set_operator", "firls_solve", "firls_solve_multi",
             "firls_last_error", "firls_destroy", "firls_apply_AHA", "firls_apply_Phi", "firls_apply_PhiT",
             "firls_apply_S_P", "firls_get_weights", "firls_get_precond", "firls_get_inverse_map",
-            "firls_set_tuning", "firls_get_popcounts",
+            "firls_set_tuning", "firls_get_popcounts", "firls_set_wait_test",
             "firls_set_timing", "firls_get_timing", "firls_apply_AHA_noalloc",
             "firls_cnn_create", "firls_cnn_set_params", "firls_cnn_get_params", "firls_cnn_get_grads",
             "firls_cnn_forward", "firls_cnn_train_step", "firls_cnn_destroy", "firls_objective",
@@ -86,6 +87,7 @@ def lib():
     L.firls_set_tuning.argtypes = [vp, i32, i32, i32]
     L.firls_get_inverse_map.argtypes = [vp, vp, vp]
     L.firls_get_popcounts.argtypes = [vp, vp]
+    L.firls_set_wait_test.argtypes = [vp, i32]
     L.firls_apply_AHA_noalloc.argtypes = [i32, i32, vp, vp, vp, vp]
     L.firls_objective.argtypes = [vp, vp, ctypes.POINTER(Params), vp, ctypes.POINTER(ctypes.c_double)]
     L.firls_adjoint.argtypes = [vp, vp, vp]
@@ -238,6 +240,10 @@ class Context:
         b = cur["coarse_max"] if coarse_max is None else coarse_max
         c = cur["ilu_depth"] if ilu_depth is None else ilu_depth
         self._check(lib().firls_set_tuning(self.h, a, b, c), "set_tuning")
+
+    def set_wait_test(self, enable=True):
+        """Failure-detection test hook: the ILU kernel's bounded waits run out."""
+        self._check(lib().firls_set_wait_test(self.h, 1 if enable else 0), "set_wait_test")
 
     def tuning(self):
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

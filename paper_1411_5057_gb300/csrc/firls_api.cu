@@ -40,6 +40,7 @@ struct firls_ctx {
   int* sqlen = nullptr;
   // tile shapes (autotuned or defaults)
   int tune_rb = 0, tune_cmax = 0, tune_ilu = 0;  // 0: ILU ring shape chosen from n and batch
+  int wait_test = 0;  // failure-detection test: the ILU's bounded waits run out (firls_set_wait_test)
   SliceState* st = nullptr;
   double* part = nullptr;
   float *lam_d = nullptr, *lamtv_d = nullptr;
@@ -255,7 +256,7 @@ void enqueue_update_precond(firls_ctx* c, int step_mode, float pcg_tol, bool ini
       TMark m(c, FIRLS_K_ILU, 1);
       // the ILU CTA finishes rho (and beta) from its own sums
       ilu_step(B, n, c->stream, c->st, c->part, init ? ILU_INIT : ILU_STEP, c->x, c->d, c->r, c->q, c->atb,
-               c->u, c->z, c->ia, c->wtv, c->tune_ilu, 1, pcg_tol);
+               c->u, c->z, c->ia, c->wtv, c->tune_ilu, 1, pcg_tol, c->wait_test);
     }
   } else {
     {
@@ -526,9 +527,17 @@ extern "C" firls_status firls_set_operator(firls_ctx* c, const uint8_t* mask, un
     return fail(c, FIRLS_E_INVALID_ARG, "bad group counts");
   const int B = c->batch;
   const size_t N = (size_t)n * n;
+  c->op_set = false;  // until every check below has passed
   CU(cudaMemcpyAsync(c->mask, mask, N * B, cudaMemcpyDeviceToDevice, c->stream));
   CU(cudaMemsetAsync(c->counts, 0, sizeof(int) * B, c->stream));
   mask_popcount(B, n, c->stream, c->mask, c->counts);
+  {  // an empty mask (abar = 0, A = 0) leaves nothing to reconstruct: rejected
+    std::vector<int> hc(B);
+    CU(cudaMemcpyAsync(hc.data(), c->counts, sizeof(int) * B, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    for (int s = 0; s < B; ++s)
+      if (hc[s] <= 0) return fail(c, FIRLS_E_INVALID_ARG, "empty mask in slice " + std::to_string(s));
+  }
   c->groups = false;
   if (group_idx) {
     int total = 0;
@@ -913,6 +922,9 @@ firls_status objective_read(firls_ctx* c, const firls_params* p, double* out) {
 
 // ---- continuous batching: per-slot load, run, status, read-out ----
 
+// Retire a slot: it stops taking part in the outer steps until reloaded.
+__global__ void k_slot_retire(SliceState* st) { st->done = 1; st->active = 0; }
+
 extern "C" firls_status firls_slot_load(firls_ctx* c, int s, const uint8_t* mask, const void* b, const void* x0,
                                         float lambda, float lambda_tv, float eps) {
   if (!c || !mask || !b) return FIRLS_E_INVALID_ARG;
@@ -925,6 +937,16 @@ extern "C" firls_status firls_slot_load(firls_ctx* c, int s, const uint8_t* mask
   CU(cudaMemcpyAsync(c->mask + off, mask, N, cudaMemcpyDeviceToDevice, c->stream));
   CU(cudaMemsetAsync(c->counts + s, 0, sizeof(int), c->stream));
   mask_popcount(1, n, c->stream, c->mask + off, c->counts + s);
+  {  // an empty mask is rejected; the slot is left retired
+    int hc = 0;
+    CU(cudaMemcpyAsync(&hc, c->counts + s, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (hc <= 0) {
+      k_slot_retire<<<1, 1, 0, c->stream>>>(c->st + s);
+      CU(cudaGetLastError());
+      return fail(c, FIRLS_E_INVALID_ARG, "empty mask");
+    }
+  }
   const float lam[2] = {c->kind ? lambda : 0.f, has_tv(c) ? lambda_tv : 0.f};
   CU(cudaMemcpyAsync(c->lam_d + s, &lam[0], sizeof(float), cudaMemcpyHostToDevice, c->stream));
   CU(cudaMemcpyAsync(c->lamtv_d + s, &lam[1], sizeof(float), cudaMemcpyHostToDevice, c->stream));
@@ -981,8 +1003,6 @@ extern "C" firls_status firls_slot_status(firls_ctx* c, int* done, int* outer_do
   return FIRLS_OK;
 }
 
-// Retire a slot: it stops taking part in the outer steps until reloaded.
-__global__ void k_slot_retire(SliceState* st) { st->done = 1; st->active = 0; }
 
 extern "C" firls_status firls_slot_retire(firls_ctx* c, int s) {
   if (!c || s < 0 || s >= c->batch) return FIRLS_E_INVALID_ARG;
@@ -1123,6 +1143,20 @@ extern "C" firls_status firls_set_tuning(firls_ctx* c, int rows_per_cta, int coa
     c->tune_ilu = ilu_shape;
     multi_forget(c);
     if (c->exec) {  // the captured outer step changes shape
+      cudaGraphExecDestroy(c->exec);
+      c->exec = nullptr;
+    }
+  }
+  return FIRLS_OK;
+}
+
+extern "C" firls_status firls_set_wait_test(firls_ctx* c, int enable) {
+  if (!c) return FIRLS_E_INVALID_ARG;
+  const int v = enable ? 1 : 0;
+  if (v != c->wait_test) {
+    c->wait_test = v;
+    multi_forget(c);
+    if (c->exec) {  // the captured outer step changes
       cudaGraphExecDestroy(c->exec);
       c->exec = nullptr;
     }

@@ -56,8 +56,9 @@ FI void pcg_alpha_from(SliceState* v, double dq) {
     v->active = 0;
     return;
   }
-  if (!(dq > 0.0) || !isfinite(dq) || !isfinite(rho)) {
+  if (!(dq > 0.0) || !isfinite(dq) || !isfinite(rho)) {  // breakdown: the slice stops, x keeps its last value
     v->active = 0;
+    v->done = 1;
     v->breakdown = 1;
     return;
   }

@@ -9,6 +9,7 @@
 // per-slice state and the partial sums live in file-scope __device__ arrays
 // of fixed size that every GPU loading this library holds until exit.
 #include <cmath>
+#include <mutex>
 
 #include "firls.h"
 #include "launch.h"
@@ -20,7 +21,7 @@ namespace {
 constexpr int kMaxDevices = 64;
 constexpr int kMaxTw = 512;
 
-// Fixed scratch (about 8.7 MB per device).
+// Fixed scratch: 8,792,064 bytes (8.4 MiB) per device.
 __device__ __align__(256) float2 g_na_t[FIRLS_NOALLOC_MAX_ELEMS];
 __device__ __align__(256) float2 g_na_tw[kMaxTw];
 __device__ __align__(256) SliceState g_na_st[FIRLS_NOALLOC_MAX_BATCH];
@@ -35,6 +36,9 @@ struct NaPtrs {
 };
 NaPtrs g_ptrs[kMaxDevices];
 bool g_ready[kMaxDevices];
+// Guards g_ptrs / g_ready and the twiddle-table bookkeeping against host
+// threads that make their first call (or change n) at the same time.
+std::mutex g_mu;
 
 __global__ void k_na_state(int B, SliceState* st) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -55,6 +59,7 @@ firls_status setup(int dev, NaPtrs** out) {
     if (cudaGetSymbolAddress((void**)&p.tw, g_na_tw) != cudaSuccess) return FIRLS_E_CUDA;
     if (cudaGetSymbolAddress((void**)&p.st, g_na_st) != cudaSuccess) return FIRLS_E_CUDA;
     if (cudaGetSymbolAddress((void**)&p.part, g_na_part) != cudaSuccess) return FIRLS_E_CUDA;
+    p.tw_n = 0;
     g_ptrs[dev] = p;
     g_ready[dev] = true;
   }
@@ -72,37 +77,51 @@ extern "C" firls_status firls_apply_AHA_noalloc(int n, int batch, const uint8_t*
     return FIRLS_E_SHAPE;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return FIRLS_E_CUDA;
-  NaPtrs* p = nullptr;
-  const firls_status s0 = setup(dev, &p);
-  if (s0 != FIRLS_OK) return s0;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
-  fft_prepare(n);
-  if (p->tw_n != n) {  // twiddles exp(-2 pi i j / n), written into the fixed table
-    float2 tw[kMaxTw];
-    for (int j = 0; j < n; ++j) {
-      const double ang = -2.0 * 3.14159265358979323846 * (double)j / (double)n;
-      tw[j] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  NaPtrs p;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    NaPtrs* pp = nullptr;
+    const firls_status s0 = setup(dev, &pp);
+    if (s0 != FIRLS_OK) return s0;
+    if (pp->tw_n != n) {  // twiddles exp(-2 pi i j / n), written into the fixed table
+      float2 tw[kMaxTw];
+      for (int j = 0; j < n; ++j) {
+        const double ang = -2.0 * 3.14159265358979323846 * (double)j / (double)n;
+        tw[j] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+      }
+      pp->tw_n = 0;
+      if (cudaMemcpyAsync(pp->tw, tw, sizeof(float2) * n, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+          cudaStreamSynchronize(stream) != cudaSuccess) {  // tw is a stack buffer
+        g_ready[dev] = false;
+        return FIRLS_E_CUDA;
+      }
+      pp->tw_n = n;
     }
-    if (cudaMemcpyAsync(p->tw, tw, sizeof(float2) * n, cudaMemcpyHostToDevice, stream) != cudaSuccess)
-      return FIRLS_E_CUDA;
-    if (cudaStreamSynchronize(stream) != cudaSuccess) return FIRLS_E_CUDA;  // tw is a stack buffer
-    p->tw_n = n;
+    p = *pp;
   }
+  fft_prepare(n);
   // the state of every slice is rewritten: lambdas 0, running
-  k_na_state<<<(batch + 127) / 128, 128, 0, stream>>>(batch, p->st);
+  k_na_state<<<(batch + 127) / 128, 128, 0, stream>>>(batch, p.st);
   FftArgs a;
   a.batch = batch;
   a.stream = stream;
-  a.tw = p->tw;
-  a.st = p->st;
-  a.part = p->part;
+  a.tw = p.tw;
+  a.st = p.st;
+  a.part = p.part;
   a.d = const_cast<float2*>(static_cast<const float2*>(d));
-  a.t = p->t;
+  a.t = p.t;
   a.mode = 2;
   fft_row_fwd(n, a);
   a.mask = mask;
   fft_col_mask(n, a);
   a.q = static_cast<float2*>(q);
   fft_row_inv(n, a);
-  return cudaGetLastError() == cudaSuccess ? FIRLS_OK : FIRLS_E_CUDA;
+  if (cudaGetLastError() != cudaSuccess) {
+    // set up again at the next call (the table may not hold n's twiddles)
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_ready[dev] = false;
+    return FIRLS_E_CUDA;
+  }
+  return FIRLS_OK;
 }

@@ -23,6 +23,7 @@
 
 #include "firls.h"
 #include "firls_common.cuh"
+#include "per_device.h"
 
 using namespace firls;
 
@@ -541,34 +542,32 @@ template <int CIN, int COUT, int MODE> void launch_conv(firls_cnn* c, const __nv
                                                        const float* bias, __nv_bfloat16* out,
                                                        const __nv_bfloat16* gate, const float2* atb, float2* x1) {
   if (c->n % TC_W == 0 && c->n % TC_R == 0) {  // tcgen05 form
-    static bool tattr = false;
-    if (!tattr) {
-      cudaFuncSetAttribute(k_conv3x3_tc<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           tc_smem<CIN, COUT>());
-      tattr = true;
-    }
+    static PerDeviceOnce tattr;
+    tattr.run([] {
+      return cudaFuncSetAttribute(k_conv3x3_tc<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tc_smem<CIN, COUT>()) == cudaSuccess;
+    });
     const dim3 grid((c->n / TC_W) * (c->n / TC_R), c->batch);
     k_conv3x3_tc<CIN, COUT, MODE><<<grid, TC_THREADS, tc_smem<CIN, COUT>(), c->stream>>>(c->n, in, wt, bias, out, gate,
                                                                                           atb, x1, c->err);
     return;
   }
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_conv3x3<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         conv_smem<CIN, COUT>());
-    attr = true;
-  }
+  static PerDeviceOnce attr;
+  attr.run([] {
+    return cudaFuncSetAttribute(k_conv3x3<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                conv_smem<CIN, COUT>()) == cudaSuccess;
+  });
   const dim3 grid((c->n / TW) * (c->n / TH), c->batch);
   k_conv3x3<CIN, COUT, MODE><<<grid, CONV_THREADS, conv_smem<CIN, COUT>(), c->stream>>>(c->n, in, wt, bias, out, gate,
                                                                                          atb, x1);
 }
 
 template <int CIN, int COUT> void launch_wgrad(firls_cnn* c, const __nv_bfloat16* x, const __nv_bfloat16* dz, int l) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_wgrad<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, wgrad_smem<CIN, COUT>());
-    attr = true;
-  }
+  static PerDeviceOnce attr;
+  attr.run([] {
+    return cudaFuncSetAttribute(k_wgrad<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                wgrad_smem<CIN, COUT>()) == cudaSuccess;
+  });
   k_wgrad<CIN, COUT><<<WG_CTAS, CONV_THREADS, wgrad_smem<CIN, COUT>(), c->stream>>>(c->n, c->batch, x, dz, c->pw,
                                                                                    c->pb);
   k_wgrad_reduce<<<64, 256, 0, c->stream>>>(WG_CTAS, CIN, COUT, CH[l], CH[l + 1], c->pw, c->pb, c->gw[l], c->gb[l]);

@@ -10,6 +10,7 @@
 // with 128-byte row segments.
 #include "fft.cuh"
 #include "launch.h"
+#include "per_device.h"
 
 namespace firls {
 
@@ -443,17 +444,20 @@ __global__ void __launch_bounds__(256) k_row_inv(const float2* __restrict__ tbuf
 
 // ------------------------------------------------------------------ launch --
 
+// Dynamic shared-memory limits of one size's kernels, set once per device.
 template <int N> static void set_smem_attrs() {
-  static bool done = false;
-  if (done) return;
-  done = true;
-  cudaFuncSetAttribute(k_row_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem_bytes<N>(false));
-  cudaFuncSetAttribute(k_row_ahb<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem_bytes<N>(false));
-  cudaFuncSetAttribute(k_row_inv<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, row_smem_bytes<N>(true));
-  cudaFuncSetAttribute(k_col_mask<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem_bytes<N>());
-  cudaFuncSetAttribute(k_col_inv<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem_bytes<N>());
-  cudaFuncSetAttribute(k_col_resid<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem_bytes<N>());
-  cudaFuncSetAttribute(k_col_dc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem_bytes<N>());
+  static PerDeviceOnce once;
+  once.run([] {
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    bool ok = cudaFuncSetAttribute(k_row_fwd<N>, A, row_smem_bytes<N>(false)) == cudaSuccess;
+    ok = cudaFuncSetAttribute(k_row_ahb<N>, A, row_smem_bytes<N>(false)) == cudaSuccess && ok;
+    ok = cudaFuncSetAttribute(k_row_inv<N>, A, row_smem_bytes<N>(true)) == cudaSuccess && ok;
+    ok = cudaFuncSetAttribute(k_col_mask<N>, A, col_smem_bytes<N>()) == cudaSuccess && ok;
+    ok = cudaFuncSetAttribute(k_col_inv<N>, A, col_smem_bytes<N>()) == cudaSuccess && ok;
+    ok = cudaFuncSetAttribute(k_col_resid<N>, A, col_smem_bytes<N>()) == cudaSuccess && ok;
+    ok = cudaFuncSetAttribute(k_col_dc<N>, A, col_smem_bytes<N>()) == cudaSuccess && ok;
+    return ok;
+  });
 }
 
 template <int N> struct FftLaunch {

@@ -3,6 +3,7 @@
 // (Eq. pog, Eq. ptv with the L U factors of Sec. 4.2), PCG vector updates
 // and the FP64 PCG scalars.
 #include "launch.h"
+#include "per_device.h"
 
 namespace firls {
 
@@ -766,6 +767,9 @@ k_wav_cluster(const float2* x, float2* u, const float* __restrict__ w, int n_arg
     const float2* He = H + wcl_halo_off(n, L, e);
     if (kind == 2) {
       wcl_push(D, He, mb + e, n, (Rl - 2) * sr, (Rl - 1) * sr, m, (rank + 1) % C, TH);
+      // the last remote write of this CTA is issued: arrive on the cluster
+      // barrier that every CTA waits on before it exits
+      if (l == 1) asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
     }
     wcl_cols(D, He, mb + e, ok, n, sr, Rl, m, kind, true, false, sc, TH);
     __syncthreads();
@@ -782,6 +786,10 @@ k_wav_cluster(const float2* x, float2* u, const float* __restrict__ w, int n_arg
     const double tot = block_sum((double)acc, red);
     if (tid == 0) part[((size_t)s * NSLOT + SLOT_RZ) * MAXPART + rank] = tot;
   }
+  // no CTA leaves (releasing its shared memory) while a peer of the cluster
+  // may still issue a write into it, even after a halo wait ran out; every
+  // CTA reaches this point, so the wait ends
+  if (kind == 2) asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
 static int wcl_smem_bytes(int n, int R, int L, bool mirror) {
@@ -834,26 +842,29 @@ static void wcl_launch(const WavArgs& a, int R, bool mirror, const float2* x, co
 
 static int coarse_smem(int m0) { return m0 * (m0 + 1) * 8; }
 
+bool ilu_prepare();
+bool wavelet_diag_prepare();
+
+// Dynamic shared-memory limits of the wavelet, ILU and pseudo-diagonal
+// kernels, set once per device.
 static void set_wav_attrs() {
-  static bool done = false;
-  if (done) return;
-  done = true;
-  cudaFuncSetAttribute(k_wav_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (2 * 16 + 2) * 512 * 8);
-  cudaFuncSetAttribute(k_wav_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 16 * 512 * 8);
-  cudaFuncSetAttribute(k_wav_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, coarse_smem(COARSE_LIMIT));
-  cudaFuncSetAttribute(k_wav_cluster<0, 0, 0, 0, WCL_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       wcl_smem_bytes(WCL_NMAX, WCL_RMAX, WCL_LMAX, true));
-  cudaFuncSetAttribute(k_wav_cluster<256, 32, 4, 2, WCL_THREADS_256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       wcl_smem_bytes(256, 32, 4, true));
+  static PerDeviceOnce once;
+  once.run([] {
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    bool ok = cudaFuncSetAttribute(k_wav_fwd, A, (2 * 16 + 2) * 512 * 8) == cudaSuccess;
+    ok = cudaFuncSetAttribute(k_wav_inv, A, 2 * 16 * 512 * 8) == cudaSuccess && ok;
+    ok = cudaFuncSetAttribute(k_wav_coarse, A, coarse_smem(COARSE_LIMIT)) == cudaSuccess && ok;
+    ok = cudaFuncSetAttribute(k_wav_cluster<0, 0, 0, 0, WCL_THREADS>, A,
+                              wcl_smem_bytes(WCL_NMAX, WCL_RMAX, WCL_LMAX, true)) == cudaSuccess && ok;
+    ok = cudaFuncSetAttribute(k_wav_cluster<256, 32, 4, 2, WCL_THREADS_256>, A, wcl_smem_bytes(256, 32, 4, true)) ==
+             cudaSuccess && ok;
+    ok = ilu_prepare() && ok;
+    ok = wavelet_diag_prepare() && ok;
+    return ok;
+  });
 }
 
-void ilu_prepare();
-void wavelet_diag_prepare();
-void wav_prepare() {
-  set_wav_attrs();
-  ilu_prepare();
-  wavelet_diag_prepare();
-}
+void wav_prepare() { set_wav_attrs(); }
 
 // First level handled by the coarse kernel: its input side m <= cmax.
 static int coarse_first_level(int n, int levels, int cmax = 0) {
@@ -1110,9 +1121,10 @@ __global__ void __launch_bounds__(256) k_wavelet_diag(int n_arg, int levels_arg,
   }
 }
 
-void wavelet_diag_prepare() {
-  cudaFuncSetAttribute(k_wavelet_diag<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * WD_PRMAX * 512 * 4);
-  cudaFuncSetAttribute(k_wavelet_diag<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * WD_PRMAX * 256 * 4);
+bool wavelet_diag_prepare() {
+  const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  bool ok = cudaFuncSetAttribute(k_wavelet_diag<0, 0>, A, 2 * WD_PRMAX * 512 * 4) == cudaSuccess;
+  return cudaFuncSetAttribute(k_wavelet_diag<256, 4>, A, 2 * WD_PRMAX * 256 * 4) == cudaSuccess && ok;
 }
 
 void wavelet_diag(int batch, int n, int levels, cudaStream_t s, const SliceState* st, const float* w,
@@ -1212,9 +1224,11 @@ FI bool mbar_try(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-FI bool mbar_wait(uint64_t* bar, unsigned parity) {
+// Bounded wait: `tries` suspended polls of about 100 us each after a first
+// test (10000 tries: about a second).
+FI bool mbar_wait(uint64_t* bar, unsigned parity, int tries = 10000) {
   if (mbar_test(bar, parity)) return true;
-  for (int it = 0; it < 10000; ++it)
+  for (int it = 0; it < tries; ++it)
     if (mbar_try(bar, parity)) return true;
   return false;
 }
@@ -1238,8 +1252,8 @@ FI void st_release(int* p, int v) {
 }
 // Bounded poll until *p >= want (about a second at most); returns the value
 // seen, or -1 when the wait ran out.
-FI int poll_at_least(const int* p, int want) {
-  for (int it = 0; it < (1 << 24); ++it) {
+FI int poll_at_least(const int* p, int want, int tries = 1 << 24) {
+  for (int it = 0; it < tries; ++it) {
     const int v = ld_acquire(p);
     if (v >= want) return v;
     if (it >= 256) __nanosleep(32);
@@ -1333,9 +1347,13 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
           float2* __restrict__ x, const float2* __restrict__ d, float2* __restrict__ r,
           const float2* __restrict__ q, const float2* __restrict__ atb, float2* __restrict__ y,
           float2* __restrict__ z, const float* __restrict__ ia, const float* __restrict__ wtv, int fuse,
-          float pcg_tol) {
+          float pcg_tol, int wait_test) {
   const int s = blockIdx.x;
   if (!slice_running(st, s)) return;
+  // wait_test (failure-detection test only): the producer issues no copy and
+  // every wait gives up after its first poll, so the waits run out with
+  // nothing in flight and the slice is reported faulted
+  const int tries = wait_test ? 0 : 10000;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_full[IW_MAXSTAGES], bar_empty[IW_MAXSTAGES];
   __shared__ __align__(8) uint64_t bar_ready[IW_MAXSTAGES], bar_used[IW_MAXSTAGES];
@@ -1400,7 +1418,7 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
 #pragma unroll
       for (int e = 0; e < E; ++e) vab[e] = make_float2(0.f, 0.f);
       for (int gg = 0; gg < NG; ++gg) {
-        if (!__all_sync(0xffffffffu, mbar_wait(&bar_ready[pos.s], pos.ph))) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&bar_ready[pos.s], pos.ph, tries))) {
           ok = false;
           break;
         }
@@ -1469,12 +1487,16 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
       bool ok = true;
       for (int g = 0; g < 2 * NG && ok; ++g) {
         if (abort_flag) break;
-        // the stage's previous group (g - S) has been left by every helper
-        if (g >= S && !mbar_wait(&bar_empty[pos.s], pos.ph ^ 1u)) {
+        if (wait_test) {  // no copy is issued: the consumers' waits run out
           ok = false;
           break;
         }
-        if (g == NG && poll_at_least(&y_stored, 1) < 1) {  // backward copies read y
+        // the stage's previous group (g - S) has been left by every helper
+        if (g >= S && !mbar_wait(&bar_empty[pos.s], pos.ph ^ 1u, tries)) {
+          ok = false;
+          break;
+        }
+        if (g == NG && poll_at_least(&y_stored, 1, tries ? 1 << 24 : 0) < 1) {  // backward copies read y
           ok = false;
           break;
         }
@@ -1518,8 +1540,8 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
         for (int c = 0; c < IW_MAXCH; ++c) prev[c] = make_float2(0.f, 0.f);
       }
       unsigned char* sp = smem + (size_t)pos.s * lay.bytes;
-      bool got = mbar_wait(&bar_full[pos.s], pos.ph);
-      if (g >= S) got = got && mbar_wait(&bar_used[pos.s], pos.ph ^ 1u);  // scan warp left group g - S
+      bool got = mbar_wait(&bar_full[pos.s], pos.ph, tries);
+      if (g >= S) got = got && mbar_wait(&bar_used[pos.s], pos.ph ^ 1u, tries);  // scan warp left group g - S
       if (!__all_sync(0xffffffffu, got)) {
         ok = false;
         break;
@@ -1618,7 +1640,7 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
 }
 
 typedef void (*IluKernel)(int, int, int, IwLayout, SliceState*, double*, float2*, const float2*, float2*,
-                          const float2*, const float2*, float2*, float2*, const float*, const float*, int, float);
+                          const float2*, const float2*, float2*, float2*, const float*, const float*, int, float, int);
 template <int G>
 static IluKernel ilu_kernel_g(int E) {
   switch (E) {
@@ -1642,10 +1664,13 @@ static IluKernel ilu_kernel(int n, int G) {
 
 static constexpr int ILU_SMEM_MAX = 200 * 1024;
 
-void ilu_prepare() {
+bool ilu_prepare() {
+  bool ok = true;
   for (int e : {1, 2, 3, 4, 5, 6, 8, 10, 12, 16})
     for (int G : {2, 4})
-      cudaFuncSetAttribute(ilu_kernel(32 * e, G), cudaFuncAttributeMaxDynamicSharedMemorySize, ILU_SMEM_MAX);
+      ok = cudaFuncSetAttribute(ilu_kernel(32 * e, G), cudaFuncAttributeMaxDynamicSharedMemorySize, ILU_SMEM_MAX) ==
+               cudaSuccess && ok;
+  return ok;
 }
 
 // Ring shape, encoded 10 * G + S: G rows per stage and S stages.  With one
@@ -1673,12 +1698,12 @@ bool ilu_shape_fits(int n, int shape) {
 
 void ilu_step(int batch, int n, cudaStream_t s, SliceState* st, double* part, int mode, float2* x,
               const float2* d, float2* r, const float2* q, const float2* atb, float2* y, float2* z,
-              const float* ia, const float* wtv, int shape, int fuse_scalars, float pcg_tol) {
+              const float* ia, const float* wtv, int shape, int fuse_scalars, float pcg_tol, int wait_test) {
   if (shape <= 0 || !ilu_shape_fits(n, shape)) shape = ilu_default_shape(n, batch);
   const int G = shape / 10, S = shape % 10;
   const IwLayout lay = iw_layout(n, G);
   ilu_kernel(n, G)<<<batch, IW_THREADS, (size_t)S * lay.bytes, s>>>(n, mode, S, lay, st, part, x, d, r, q, atb, y,
-                                                                     z, ia, wtv, fuse_scalars, pcg_tol);
+                                                                     z, ia, wtv, fuse_scalars, pcg_tol, wait_test);
 }
 
 // =========================================================== PCG vectors ==
@@ -1987,9 +2012,12 @@ __global__ void k_state_init(int B, SliceState* st, const double* part, int np, 
   v.rr = v.rhs2;
   v.relchg = 0.0;
   v.relchg_prev = 0.0;
-  v.active = 1;
-  v.done = 0;
-  v.breakdown = 0;
+  // non-finite k-space on the mask makes A^H b non-finite: the slice is not
+  // iterated and counts as a breakdown (its x keeps the start)
+  const bool bad = !isfinite(v.rhs2);
+  v.active = bad ? 0 : 1;
+  v.done = bad ? 1 : 0;
+  v.breakdown = bad ? 1 : 0;
   v.pcg_steps = 0;
   v.outer_done = 0;
   v.fault = 0;

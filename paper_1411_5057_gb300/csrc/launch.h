@@ -88,7 +88,7 @@ enum IluMode { ILU_INIT = 0, ILU_STEP = 1, ILU_LAST = 2 };
 void ilu_step(int batch, int n, cudaStream_t s, SliceState* st, double* part, int mode,
               float2* x, const float2* d, float2* r, const float2* q, const float2* atb, float2* y,
               float2* z, const float* ia, const float* wtv, int shape, int fuse_scalars = 0,
-              float pcg_tol = 0.f);
+              float pcg_tol = 0.f, int wait_test = 0);
 int ilu_default_shape(int n, int batch);
 bool ilu_shape_fits(int n, int shape);
 

@@ -134,6 +134,92 @@ def test_db4_level1_bruteforce():
             assert abs(c[half + k, half + l] - acc["HH"]) < 1e-13
 
 
+def test_haar_multilevel_closed_form():
+    """Two and three Haar levels in closed form (Mallat pyramid on the LL band).
+
+    With h = (1, 1)/sqrt2 and g = (1, -1)/sqrt2 every level-l coefficient is
+    a signed sum over a 2^l x 2^l block divided by 2^l: LL the plain sum,
+    the horizontal detail left half minus right half, the vertical detail
+    top half minus bottom half, the diagonal detail the checkerboard of the
+    four quadrants.  A recursion on another quadrant than LL, or a band
+    stored in the other off-diagonal quadrant, fails here.
+    """
+    x = rng(5).standard_normal((16, 16))
+    for levels in (1, 2, 3):
+        c = O.wavedec2(x, O.PSI_HAAR, levels)
+        n = 16
+        for l in range(1, levels + 1):
+            b = 1 << l           # block side at level l
+            h = n >> l           # side of each level-l band
+            hb = b // 2
+            for p in range(h):
+                for q in range(h):
+                    blk = x[p * b:(p + 1) * b, q * b:(q + 1) * b]
+                    tl, tr = blk[:hb, :hb].sum(), blk[:hb, hb:].sum()
+                    bl, br = blk[hb:, :hb].sum(), blk[hb:, hb:].sum()
+                    assert abs(c[p, h + q] - (tl + bl - tr - br) / b) < 1e-12      # horizontal detail
+                    assert abs(c[h + p, q] - (tl + tr - bl - br) / b) < 1e-12      # vertical detail
+                    assert abs(c[h + p, h + q] - (tl - tr - bl + br) / b) < 1e-12  # diagonal detail
+                    if l == levels:
+                        assert abs(c[p, q] - blk.sum() / b) < 1e-12                # LL of the last level
+
+
+def _db4_taps_from_golden():
+    vals = [float(l) for l in open(os.path.join(GOLDEN, "db4_taps.txt")) if l.strip() and not l.startswith("#")]
+    h = np.array(vals)
+    g = np.array([(-1) ** t * h[3 - t] for t in range(4)])
+    return h, g
+
+
+def _analysis_rows_bruteforce(n, levels, h, g):
+    """1-D level-l scaling (type 0) and wavelet (type 1) functionals by loops.
+
+    Level 1: row k of the lowpass is e_i -> sum_t h_t [i == (2k + t) mod n].
+    Level l: row k is sum_t f_t * (level l-1 scaling row (2k + t) mod m),
+    m = n / 2^(l-1), with f = h (scaling) or g (wavelet).
+    Returns rows[l][type] as arrays [n / 2^l][n].
+    """
+    rows = {}
+    prev = np.eye(n)   # level-0 scaling rows: the unit vectors
+    for l in range(1, levels + 1):
+        m = n >> (l - 1)
+        lo = np.zeros((m // 2, n))
+        hi = np.zeros((m // 2, n))
+        for k in range(m // 2):
+            for t in range(len(h)):
+                lo[k] += h[t] * prev[(2 * k + t) % m]
+                hi[k] += g[t] * prev[(2 * k + t) % m]
+        rows[l] = (lo, hi)
+        prev = lo
+    return rows
+
+
+@pytest.mark.parametrize("n,levels", [(16, 2), (16, 3), (32, 4)])
+def test_db4_multilevel_bruteforce(n, levels):
+    """Every coefficient of the multi-level D4 pyramid against a brute-force
+    separable sum of level-l functionals built from the published taps.
+
+    The level-l band (vertical type br, horizontal type bc) at rows
+    [br h, br h + h) and columns [bc h, bc h + h), h = n / 2^l, holds
+    c[p, q] = sum_{i,j} R_{l,br}[p, i] R_{l,bc}[q, j] x[i, j]; the LL band
+    of the last level sits at the top-left.  Checks the recursion quadrant,
+    the band placement and the row/column roles at every level.
+    """
+    h, g = _db4_taps_from_golden()
+    rows = _analysis_rows_bruteforce(n, levels, h, g)
+    x = rng(6).standard_normal((n, n)) + 1j * rng(7).standard_normal((n, n))
+    c = O.wavedec2(x, O.PSI_DB4, levels)
+    expect = np.full((n, n), np.nan, dtype=complex)
+    for l in range(1, levels + 1):
+        hh = n >> l
+        for br, bc in ((0, 1), (1, 0), (1, 1)):
+            expect[br * hh:(br + 1) * hh, bc * hh:(bc + 1) * hh] = rows[l][br] @ x @ rows[l][bc].T
+    hh = n >> levels
+    expect[:hh, :hh] = rows[levels][0] @ x @ rows[levels][0].T
+    assert not np.isnan(expect).any()
+    assert np.max(np.abs(c - expect)) < 1e-12 * np.max(np.abs(expect))
+
+
 @pytest.mark.parametrize("kind,levels", [(O.PSI_HAAR, 2), (O.PSI_HAAR, 3), (O.PSI_DB4, 2), (O.PSI_DB4, 3)])
 def test_wavelet_diag_bruteforce(kind, levels):
     """diag(Phi^T W Phi) against the dense product at n = 16."""

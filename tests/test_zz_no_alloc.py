@@ -4,16 +4,20 @@ firls_apply_AHA_noalloc exists for callers that must not allocate device
 memory (a host framework's memory pool, a real-time loop, a plug-in handed
 only its buffers); it keeps its scratch in fixed device arrays instead.
 Called here through the C ABI, twice in a row with different inputs and then
-at another size, it must reproduce firls_apply_AHA (same kernels) within the
-operator tolerance used by the other parity tests.  The file name makes pytest
-collect it last.
+at another size, it must reproduce firls_apply_AHA (same kernels) and the FP64
+oracle's A^H A = F^H R^T R F (Sec. 5.4) within the operator tolerance used by
+the other parity tests.  A last test makes first calls from several host
+threads at once (the set-up is guarded by a lock) and checks each result.
+The file name makes pytest collect it last.
 """
 import ctypes
+import threading
 
 import numpy as np
 import pytest
 
 import firls_synth as fs
+from oracle import firls_oracle as O
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -60,6 +64,11 @@ def test_noalloc_matches_context_entry_point(F):
         assert _noalloc(F, n, B, mask, d, q, stream) == 0
         torch.cuda.synchronize()
         assert _rel(q, q_ref) < TOL_OP, (n, seed)
+        mh, dh = mask.cpu().numpy().astype(np.float64), d.cpu().numpy().astype(np.complex128)
+        qh = q.cpu().numpy().astype(np.complex128)
+        for s in range(B):
+            ref = O.op_AH(O.op_A(dh[s], mh[s]), mh[s], False)
+            assert np.linalg.norm(qh[s] - ref) / np.linalg.norm(ref) < TOL_OP, (n, seed, s)
         ctx.close()
 
 
@@ -74,3 +83,35 @@ def test_noalloc_rejects_oversize_and_bad_args(F):
     assert _noalloc(F, 64, 65, mask, d, q, stream) == 2
     assert lib.firls_apply_AHA_noalloc(64, 1, None, ctypes.c_void_p(d.data_ptr()), ctypes.c_void_p(q.data_ptr()),
                                        ctypes.c_void_p(stream.cuda_stream)) == 1
+
+
+def test_noalloc_concurrent_first_calls(F):
+    """First calls of a new size from four host threads at once.  They share
+    one stream, so the GPU runs them one after another (the scratch arrays are
+    shared); the host-side set-up and twiddle rewrite race and must not mix."""
+    n, B = 128, 2
+    inputs = [_inputs(n, B, 20 + i) for i in range(4)]
+    outs = [torch.full_like(d, float("nan")) for _, d in inputs]
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    codes = [None] * 4
+    start = threading.Barrier(4)
+
+    def work(i):
+        mask, d = inputs[i]
+        start.wait()
+        codes[i] = _noalloc(F, n, B, mask, d, outs[i], stream)
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    stream.synchronize()
+    assert codes == [0, 0, 0, 0]
+    for (mask, d), q in zip(inputs, outs):
+        mh, dh = mask.cpu().numpy().astype(np.float64), d.cpu().numpy().astype(np.complex128)
+        qh = q.cpu().numpy().astype(np.complex128)
+        for s in range(B):
+            ref = O.op_AH(O.op_A(dh[s], mh[s]), mh[s], False)
+            assert np.linalg.norm(qh[s] - ref) / np.linalg.norm(ref) < TOL_OP
