@@ -43,14 +43,16 @@ RATIO, SIGMA, LAM_TV, LAM_W, LEVELS = 0.20, 0.01, 1e-3, 5e-4, 4
 # oracle's converged minimiser x*: 60 PCG steps per outer step (an oracle
 # study of 40..120 found 60 needs the fewest PCG steps to 1e-4, 2580 for
 # seed 2) and a per-slice stop once the estimated distance to the limit,
-# relchg * mu / (1 - mu) with the measured contraction mu, falls below 6e-5
-# (on seed 2's oracle trajectory the estimate runs 10-30% below the true
-# distance), at most 400 outer steps.  A fixed relative-change threshold
-# would under-solve slowly contracting slices and over-solve fast ones.
+# relchg * mu / (1 - mu) with mu the mean contraction over the last 24 outer
+# steps, falls below 3e-5, or once the relative change has stayed at the FP32
+# floor of the outer iteration (<= 6e-7, four steps in a row); at most 800
+# outer steps.  Per-step GPU trajectories of the stored-x* seeds (the slowest
+# slices of the queue among them, 400-560 outer steps) picked these values.
 # Slices are served by continuous batching: a converged slice leaves its
 # slot, the next enters.  Checked against stored oracle x* by
-# tests/test_gpu_parity.py::test_bench_workload_reaches_converged_oracle.
-OUTER, INNER, OUTER_TOL = 400, 60, 6e-5
+# tests/test_gpu_parity.py::test_bench_workload_reaches_converged_oracle and
+# reported per result in the bench line ("accuracy").
+OUTER, INNER, OUTER_TOL, STALL_TOL = 800, 60, 3e-5, 6e-7
 REF_OUTER_PER_RECON = 43   # FP64 oracle outer steps (x 60 PCG) to 1e-4 of x* on seed 2
 
 # Algorithmic bytes per pixel per launch of each kernel class: every distinct
@@ -159,7 +161,7 @@ def run_ours(args):
     masks_h, b_h = make_batch(S, 2 + rank * S)
     stream = torch.cuda.Stream()
     params = F.make_params(args.outer, args.inner, lam=LAM_W, lam_tv=LAM_TV, outer_tol=args.outer_tol,
-                           stop_on_distance=True)
+                           stop_on_distance=True, stall_tol=args.stall_tol)
     lams, lam_tvs = [LAM_W] * S, [LAM_TV] * S
     with torch.cuda.stream(stream):
         masks = torch.from_numpy(masks_h).cuda()
@@ -209,6 +211,10 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world * done_per_step / (ms / 1e3)
+    acc = accuracy(xlist, 2 + rank * S, steps)
+    if acc is not None:
+        print(f"[bench] accuracy vs stored oracle x*: {acc['n_checked']} slices, max rel err {acc['max_rel_err']:.2e} "
+              f"(seed {acc['worst_seed']}), median {acc['median_rel_err']:.2e}", file=sys.stderr, flush=True)
     steps = np.asarray(steps)
     steps = steps[steps > 0]
     print(f"[bench] {S} slices through {B} slots, <= {args.outer}x{args.inner}, stop {args.outer_tol}: "
@@ -276,10 +282,16 @@ def run_ours(args):
                "h2d_bytes_per_step": int(bh.numel() * 8 + mh.numel()),
                "d2h_bytes_per_step": int(xh.numel() * 8)}
 
+    # ---- preconditioner comparison (PCG iteration counts, untimed) ----
+    pcg_iters = precond_comparison(F, torch, stream) if args.precond_cmp else None
+    if pcg_iters is not None:
+        print("[bench] PCG steps to 1e-6: " + json.dumps({k: v for k, v in pcg_iters.items()
+                                                           if isinstance(v, dict)}), file=sys.stderr, flush=True)
+
     # ---- learned warm start (CNN trained on solver-generated pairs) ----
     learned = None
     if args.learned:
-        learned = run_learned(args, F, torch, stream, b, masks, B, S, value, steps, step, rank, done_per_step)
+        learned = run_learned(args, F, torch, stream, b, masks, B, S, value, steps, step, rank, done_per_step, xlist)
 
     out = None
     if rank == 0:
@@ -295,7 +307,7 @@ def run_ours(args):
                "solve_stats": {"mean_outer_steps": round(float(steps.mean()), 2), "max_outer_steps": int(steps.max()),
                                "capped": int((steps >= args.outer).sum()),
                                "mean_pcg_steps": round(float(steps.mean()) * args.inner, 1)},
-               "learned": learned}
+               "accuracy": acc, "learned": learned, "pcg_iterations": pcg_iters}
         print(json.dumps(out), flush=True)
     ctx.close()
     if dist is not None:
@@ -303,7 +315,7 @@ def run_ours(args):
     return out
 
 
-def run_learned(args, F, torch, stream, b, masks, B, S, plain_value, plain_steps, step, rank, done_per_step):
+def run_learned(args, F, torch, stream, b, masks, B, S, plain_value, plain_steps, step, rank, done_per_step, xs):
     """Train the CNN (untimed) on pairs the solver generates, then time the
     guarded learned start (CNN, data consistency, F_eps guard) plus the same
     continuous-batching solve over the same slices."""
@@ -351,19 +363,88 @@ def run_learned(args, F, torch, stream, b, masks, B, S, plain_value, plain_steps
     ms = e0.elapsed_time(e1) / args.steps
     inf.close()
     prep.close()
+    lacc = accuracy(xs, 2 + rank * S, lsteps)
     lsteps = np.asarray(lsteps)
     lsteps = lsteps[lsteps > 0]
     value = done_per_step / (ms / 1e3)
     return {"value": round(value, 3), "unit": UNIT, "ms_per_step": round(ms, 3),
             "mean_outer_steps": round(float(lsteps.mean()), 2), "plain_mean_outer_steps": round(float(plain_steps.mean()), 2),
             "max_outer_steps": int(lsteps.max()), "kept_cnn_start": kept[0], "vs_plain": round(value / plain_value, 4),
-            "train_instances": args.learned_train, "train_epochs": args.learned_epochs, "setup_s": round(train_s, 1)}
+            "train_instances": args.learned_train, "train_epochs": args.learned_epochs, "setup_s": round(train_s, 1),
+            "accuracy": lacc}
+
+
+XSTAR_DIR = os.path.join(ROOT, "tests", "golden", "xstar_tv_db4_256")
+
+
+def stored_xstar():
+    """{seed: (x*, estimated distance of x* to the limit)} written by
+    tests/golden/make_xstar.py (FP64 oracle run to its limit)."""
+    out = {}
+    if os.path.isdir(XSTAR_DIR):
+        for f in sorted(os.listdir(XSTAR_DIR)):
+            if f.startswith("seed") and f.endswith(".npz"):
+                z = np.load(os.path.join(XSTAR_DIR, f))
+                out[int(f[4:-4])] = (z["x"].astype(np.complex128), float(z["dist_est"]))
+    return out
+
+
+def accuracy(xs, first_seed, steps=None):
+    """Relative l2 error of each served result that has a stored oracle x*
+    (untimed, after the timed steps)."""
+    ref = stored_xstar()
+    errs, seeds = [], []
+    for seed, (xstar, _) in ref.items():
+        i = seed - first_seed
+        if 0 <= i < len(xs):
+            x = xs[i].cpu().numpy().astype(np.complex128)
+            errs.append(float(np.linalg.norm(x - xstar) / np.linalg.norm(xstar)))
+            seeds.append(seed)
+    if not errs:
+        return None
+    worst = int(np.argmax(errs))
+    out = {"n_checked": len(errs), "max_rel_err": max(errs), "median_rel_err": float(np.median(errs)),
+           "worst_seed": seeds[worst], "seeds": seeds, "rel_err": [round(e, 8) for e in errs],
+           "reference": "FP64 oracle x* (tests/golden/xstar_tv_db4_256), estimated distance to its limit <= "
+                        f"{max(ref[s][1] for s in seeds):.1e}"}
+    if steps is not None:
+        out["outer_steps"] = [int(steps[s - first_seed]) for s in seeds]
+    return out
+
+
+def precond_comparison(F, torch, stream, outer_steps=(1, 5, 20), tol=1e-6, cap=5000):
+    """PCG steps to ||r|| <= tol ||A^H b|| with the proposed P, Jacobi and no
+    preconditioner (Sec. 5.2, Fig. 2 and the TV figure), from the iterates of
+    the proposed PCG's own FIRLS trajectory (20 PCG steps per outer step) at
+    the given outer steps; workload 1 (64^2 Haar l1, real) and one 256^2
+    TV + D4 slice (seed 2).  Untimed."""
+    import firls_synth as fs
+    out = {"tol_rel_residual": tol, "cap": cap, "trajectory_inner": 20}
+    for name, p in (("haar_l1_64", fs.haar_l1_64()), ("tv_db4_256", problem(2))):
+        with torch.cuda.stream(stream):
+            ctx = F.Context(p.n, batch=1, real=p.real, stream=stream)
+            ctx.set_operator(torch.from_numpy(p.mask).cuda()[None], p.psi, p.levels)
+            b = torch.from_numpy(p.b.astype(np.complex64)).cuda()[None]
+            rows = {}
+            for k in outer_steps:
+                x0 = None
+                if k > 1:
+                    x0 = ctx.solve(b, F.make_params(k - 1, 20, lam=p.lam, lam_tv=p.lam_tv)).clone()
+                row = {}
+                for pre in ("paper", "jacobi", "none"):
+                    _, st = ctx.solve(b, F.make_params(1, cap, lam=p.lam, lam_tv=p.lam_tv, pcg_tol=tol,
+                                                       precond=pre), x0=x0, stats=True)
+                    row[pre] = int(st["pcg_steps"])
+                rows[f"outer_step_{k}"] = row
+            ctx.close()
+        out[name] = rows
+    return out
 
 
 def workload_config(args, world, done_per_step=None):
     """The workload both arms report: the served 256^2 TV + D4 queue."""
     return {"workload": f"firls_tv_db4_{N}", "n": N, "slices_per_step_per_gpu": args.queue, "slots": args.batch,
-            "outer_max": args.outer, "inner": args.inner, "outer_tol": args.outer_tol,
+            "outer_max": args.outer, "inner": args.inner, "outer_tol": args.outer_tol, "stall_tol": args.stall_tol,
             "mask_ratio": RATIO, "sigma": SIGMA, "lambda_tv": LAM_TV, "lambda_w": LAM_W,
             "wavelet": "db4", "levels": LEVELS, "batching": "continuous (slots refilled on convergence)",
             "completions_per_step": args.queue if done_per_step is None else done_per_step,
@@ -406,6 +487,30 @@ def _oracle_worker(a):
     return oracle_sample(outer, seed)
 
 
+def oracle_outer_per_recon(seeds):
+    """Mean of the FP64 oracle's own outer steps (60 PCG each) to 1e-4 of x*
+    on the given seeds, as stored by tests/golden/make_xstar.py (--steps-to),
+    and the seeds it covers; REF_OUTER_PER_RECON where none is stored."""
+    got = []
+    for s in seeds:
+        f = os.path.join(XSTAR_DIR, f"seed{s}.npz")
+        if os.path.exists(f):
+            z = np.load(f)
+            if "outer_to_1e4" in z.files:
+                got.append((s, int(z["outer_to_1e4"])))
+    if not got:
+        return float(REF_OUTER_PER_RECON), []
+    return float(np.mean([v for _, v in got])), [s for s, _ in got]
+
+
+def host_cores():
+    """Cores this process may run on (affinity / cgroup), not the host's count."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
@@ -413,28 +518,31 @@ def run_reference(args):
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[k] = "1"  # one thread per oracle instance (inherited by the workers)
     ARGS_INNER[0] = args.inner
-    procs = args.ref_procs if args.ref_procs > 0 else (os.cpu_count() or 1)
+    procs = args.ref_procs if args.ref_procs > 0 else host_cores()
+    seeds = [2 + i for i in range(procs)]
     if procs == 1:
+        oracle_sample(1)  # warm-up: imports and first-touch costs
         for _ in range(args.warmup):
             oracle_sample(1)
         t = [oracle_sample(args.ref_outer) for _ in range(args.steps)]
     else:
-        # one independent slice per host core (seeds 2, 3, ...), all at once
+        # one independent slice per host core (seeds 2, 3, ...), all at once;
+        # a step takes as long as its slowest worker
         import multiprocessing as mp
         with mp.get_context("spawn").Pool(procs) as pool:
-            for _ in range(args.warmup):
-                pool.map(_oracle_worker, [(1, args.inner, 2 + i) for i in range(procs)])
-            t = []
-            for _ in range(args.steps):
-                t0 = time.perf_counter()
-                pool.map(_oracle_worker, [(args.ref_outer, args.inner, 2 + i) for i in range(procs)])
-                t.append(time.perf_counter() - t0)
+            for _ in range(max(1, args.warmup)):
+                pool.map(_oracle_worker, [(1, args.inner, s) for s in seeds])
+            t = [max(pool.map(_oracle_worker, [(args.ref_outer, args.inner, s) for s in seeds]))
+                 for _ in range(args.steps)]
     sec = float(np.mean(t))
-    value = procs * (args.ref_outer / REF_OUTER_PER_RECON) / sec
+    outer, covered = oracle_outer_per_recon(seeds)
+    value = procs * (args.ref_outer / outer) / sec
+    how = (f"the mean of the oracle's own outer steps to 1e-4 of its x* on seeds {covered}" if covered else
+           f"{REF_OUTER_PER_RECON} outer steps (the oracle's own outer steps to 1e-4 of x* on seed 2)")
     cpu = {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
            "sample": f"FP64 oracle, {procs} independent {N}^2 slice(s) at once, one per host core, each "
-                     f"{args.ref_outer} of {REF_OUTER_PER_RECON} outer steps x {args.inner} PCG per bench step "
-                     f"(the oracle's own outer steps to 1e-4 of x* on seed 2)"}
+                     f"{args.ref_outer} outer step(s) x {args.inner} PCG per bench step, scaled to {outer:.1f} "
+                     f"outer steps per reconstruction ({how})"}
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -458,6 +566,7 @@ def main(argv=None):
     ap.add_argument("--outer", type=int, default=OUTER)
     ap.add_argument("--inner", type=int, default=INNER)
     ap.add_argument("--outer-tol", type=float, default=OUTER_TOL)
+    ap.add_argument("--stall-tol", type=float, default=STALL_TOL)
     ap.add_argument("--autotune", type=int, default=1, help="autotune tile shapes before timing (1/0)")
     ap.add_argument("--learned", type=int, default=1, help="also time the learned warm start (1/0)")
     ap.add_argument("--learned-train", type=int, default=4000, help="training instances solved by the method")
@@ -466,6 +575,8 @@ def main(argv=None):
     ap.add_argument("--ref-procs", type=int, default=0,
                     help="reference arm: oracle instances run at once, one per host core (0: all cores)")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--precond-cmp", type=int, default=1,
+                    help="report PCG steps to 1e-6 for the proposed, Jacobi and no preconditioner (1/0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
     if args.impl == "reference":

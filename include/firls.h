@@ -117,10 +117,27 @@ typedef struct {
   int outer_tol_kind;  /* 0: stop when the relative change <= outer_tol;
                           1: stop when the estimated distance to the limit,
                           relchg * mu / (1 - mu) with the contraction
-                          mu = sqrt(relchg_k / relchg_{k-2}) (linear
-                          convergence), and the relative change are both
-                          <= outer_tol (after >= 4 outer steps)               */
+                          mu = (relchg_k / relchg_{k-24})^(1/24), at most
+                          0.999 (linear convergence), and the relative change
+                          are both <= outer_tol (after > 24 outer steps)      */
+  int precond;         /* FIRLS_PRECOND_*: the PCG preconditioner (0 = the
+                          paper's)                                            */
+  float outer_stall_tol; /* stop a slice once its relative change has stayed
+                          at or below this for 4 consecutive outer steps: the
+                          FP32 rounding floor of the outer iteration, where
+                          it cannot move closer (0 = never)                   */
+  int pcg_tol_kind;    /* 0: pcg_tol is relative to ||A^H b||; 1: relative to
+                          the first residual r_0 of each outer step (the
+                          forcing term of an inexact inner solve: PCG runs
+                          until ||r|| <= pcg_tol ||r_0|| or pcg_iters steps)  */
 } firls_params;
+
+/* Preconditioners of the PCG steps, for the comparison of Sec. 5.2 (Fig. 2
+ * and the TV figure).  PAPER: the proposed P (Eq. pog: Phi^T (abar I +
+ * lambda G^T W G)^{-1} Phi without TV; Eq. ptv with the printed L U factors of
+ * Sec. 4.2 with TV).  JACOBI: P = diag(S) = abar + lambda diag(Phi^T G^T W G
+ * Phi) + lambda_tv diag(D1^T W D1 + D2^T W D2).  NONE: P = I (standard CG). */
+enum { FIRLS_PRECOND_PAPER = 0, FIRLS_PRECOND_JACOBI = 1, FIRLS_PRECOND_NONE = 2 };
 
 typedef struct {
   int outer_done;            /* outer steps run (max over slices)             */
@@ -203,14 +220,14 @@ firls_status firls_apply_S_P(firls_ctx* ctx, const firls_params* params,
  *   FIRLS_E_INVALID_ARG and leaves the slot retired.
  * firls_run: enqueue params->outer_iters outer steps of every slot that is
  *   not done (one captured graph per step; no host synchronisation).
- * firls_slot_status: per-slot done flag, outer steps and last relative
- *   change (host arrays [batch], each may be NULL); synchronises.
+ * firls_slot_status: per-slot done flag, outer steps, last relative change
+ *   and PCG steps (host arrays [batch], each may be NULL); synchronises.
  * firls_slot_retire: slot s stops taking part until reloaded.
  * firls_slot_get: copy slot s's current x (device complex64 [n][n]). */
 firls_status firls_slot_load(firls_ctx* ctx, int s, const uint8_t* mask, const void* b, const void* x0,
                              float lambda, float lambda_tv, float eps);
 firls_status firls_run(firls_ctx* ctx, const firls_params* params);
-firls_status firls_slot_status(firls_ctx* ctx, int* done, int* outer_done, double* rel_change);
+firls_status firls_slot_status(firls_ctx* ctx, int* done, int* outer_done, double* rel_change, int* pcg_steps);
 firls_status firls_slot_retire(firls_ctx* ctx, int s);
 firls_status firls_slot_get(firls_ctx* ctx, int s, void* x_out);
 

@@ -298,11 +298,23 @@ def wavelet_diag(w, n, kind, levels):
 # The system S and the preconditioners
 # ---------------------------------------------------------------------------
 
+PRECONDS = ("paper", "jacobi", "none")
+
+
 class System:
     """S = A^H A + lam_W Phi^T G^T W G Phi + lam_TV (D1^T W D1 + D2^T W D2)
-    (Eq. subprob, Eq. sub) and its preconditioner P (Eq. pog, Eq. ptv)."""
+    (Eq. subprob, Eq. sub) and its preconditioner P.
 
-    def __init__(self, mask, real, psi, levels, lam, lam_tv, groups=None, eps=EPS):
+    ``precond`` selects P for the comparison of Sec. 5.2 (Fig. 2 and the TV
+    figure): "paper" is the proposed P (Eq. pog, Eq. ptv with the printed L
+    U factors), "jacobi" is P = diag(S) (conventional Jacobi PCG), "none" is
+    P = I (standard CG).
+    """
+
+    def __init__(self, mask, real, psi, levels, lam, lam_tv, groups=None, eps=EPS, precond="paper"):
+        if precond not in PRECONDS:
+            raise ValueError("unknown preconditioner")
+        self.precond = precond
         self.eps = float(eps)
         self.mask = np.asarray(mask).astype(np.float64)
         self.n = self.mask.shape[0]
@@ -333,7 +345,23 @@ class System:
             self.Wtv = tv_weights(xf, self.D1, self.D2, self.eps)
         self._build_preconditioner()
 
+    def diag_S(self):
+        """diag(S): abar (every diagonal entry of A^H A, Sec. 5.4) plus
+        lam_W diag(Phi^T W Phi) plus lam_TV diag(D1^T W D1 + D2^T W D2)."""
+        d = np.full(self.N, self.abar)
+        if self.kind:
+            d = d + self.lam * wavelet_diag(self.w, self.n, self.kind, self.levels).reshape(-1)
+        if self.psi & PSI_TV:
+            Wd = sp.diags(self.Wtv)
+            d = d + self.lam_tv * (self.D1.T @ Wd @ self.D1 + self.D2.T @ Wd @ self.D2).diagonal()
+        return d
+
     def _build_preconditioner(self):
+        if self.precond == "jacobi":
+            self.jacobi = 1.0 / self.diag_S()
+            return
+        if self.precond == "none":
+            return
         if self.psi & PSI_TV:
             # P = abar I + lam (D1^T W D1 + D2^T W D2)  (Eq. ptv), penta-diagonal
             Wd = sp.diags(self.Wtv)
@@ -370,6 +398,10 @@ class System:
         return out
 
     def apply_Pinv(self, r):
+        if self.precond == "jacobi":
+            return (self.jacobi * np.asarray(r).reshape(-1)).reshape(self.n, self.n)
+        if self.precond == "none":
+            return np.array(r, copy=True)
         if self.psi & PSI_TV:
             rf = r.reshape(-1)
             y = spl.spsolve_triangular(self.L, rf, lower=True)
@@ -433,7 +465,7 @@ def objective(x, b, mask, real, psi, levels, lam, lam_tv, groups=None, eps=0.0):
 
 
 def firls(b, mask, *, real, psi, levels, lam, lam_tv=0.0, groups=None, outer=50, inner=20,
-          pcg_tol=0.0, outer_tol=0.0, x_init=None, record=False, eps=EPS):
+          pcg_tol=0.0, outer_tol=0.0, x_init=None, record=False, eps=EPS, precond="paper"):
     """FIRLS outer loop (Alg. 2 FIRLS_OG / Alg. 3 FIRLS_TV).
 
     x^1 = A^H b unless ``x_init`` is given (Sec. 3.3: x^0 = A^T b).  Each outer
@@ -441,7 +473,7 @@ def firls(b, mask, *, real, psi, levels, lam, lam_tv=0.0, groups=None, outer=50,
     warm-started at x^k.  Returns (x, info) with per-step history.
     """
     mask = np.asarray(mask)
-    system = System(mask, real, psi, levels, lam, lam_tv, groups, eps)
+    system = System(mask, real, psi, levels, lam, lam_tv, groups, eps, precond)
     rhs = op_AH(mask * b, mask.astype(np.float64), real)
     rhs_norm = math.sqrt(rdot(rhs, rhs))
     x = rhs.copy() if x_init is None else np.array(x_init, copy=True)
@@ -465,11 +497,11 @@ def firls(b, mask, *, real, psi, levels, lam, lam_tv=0.0, groups=None, outer=50,
     return x, info
 
 
-def firls_problem(p, outer=50, inner=20, pcg_tol=0.0, outer_tol=0.0, x_init=None, record=False):
+def firls_problem(p, outer=50, inner=20, pcg_tol=0.0, outer_tol=0.0, x_init=None, record=False, precond="paper"):
     """Convenience wrapper over a ``firls_synth.Problem``."""
     return firls(p.b, p.mask, real=p.real, psi=p.psi, levels=p.levels, lam=p.lam,
                  lam_tv=p.lam_tv, groups=p.groups, outer=outer, inner=inner,
-                 pcg_tol=pcg_tol, outer_tol=outer_tol, x_init=x_init, record=record)
+                 pcg_tol=pcg_tol, outer_tol=outer_tol, x_init=x_init, record=record, precond=precond)
 
 
 def inverse_group_map(groups, N):

@@ -18,6 +18,7 @@ STATUS = {0: "FIRLS_OK", 1: "FIRLS_E_INVALID_ARG", 2: "FIRLS_E_SHAPE", 3: "FIRLS
           4: "FIRLS_E_CUDA", 5: "FIRLS_E_NOMEM", 6: "FIRLS_E_BREAKDOWN", 7: "FIRLS_E_STATE",
           8: "FIRLS_E_DEVICE_TIMEOUT"}
 PSI_HAAR, PSI_DB4, PSI_TV = 1, 2, 4
+PRECONDS = {"paper": 0, "jacobi": 1, "none": 2}
 REAL_X = 1
 
 EXPORTED = ["firls_size_supported", "firls_create", "firls_set_operator", "firls_solve", "firls_solve_multi",
@@ -44,7 +45,8 @@ class Params(ctypes.Structure):
     _fields_ = [("outer_iters", ctypes.c_int), ("pcg_iters", ctypes.c_int), ("pcg_tol", ctypes.c_float),
                 ("outer_tol", ctypes.c_float), ("lambda_", ctypes.c_float), ("lambda_tv", ctypes.c_float),
                 ("eps", ctypes.c_float), ("lambda_per_slice", ctypes.POINTER(ctypes.c_float)),
-                ("lambda_tv_per_slice", ctypes.POINTER(ctypes.c_float)), ("outer_tol_kind", ctypes.c_int)]
+                ("lambda_tv_per_slice", ctypes.POINTER(ctypes.c_float)), ("outer_tol_kind", ctypes.c_int),
+                ("precond", ctypes.c_int), ("outer_stall_tol", ctypes.c_float), ("pcg_tol_kind", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -94,7 +96,8 @@ def lib():
     L.firls_autotune.argtypes = [vp, ctypes.c_char_p]
     L.firls_slot_load.argtypes = [vp, i32, vp, vp, vp, ctypes.c_float, ctypes.c_float, ctypes.c_float]
     L.firls_run.argtypes = [vp, ctypes.POINTER(Params)]
-    L.firls_slot_status.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]
+    L.firls_slot_status.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(i32)]
     L.firls_slot_retire.argtypes = [vp, i32]
     L.firls_slot_get.argtypes = [vp, i32, vp]
     L.firls_get_tuning.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
@@ -124,9 +127,15 @@ def size_supported(n: int) -> bool:
 
 
 def make_params(outer, pcg, lam=0.0, lam_tv=0.0, pcg_tol=0.0, outer_tol=0.0, eps=0.0,
-                lam_per_slice=None, lam_tv_per_slice=None, stop_on_distance=False):
+                lam_per_slice=None, lam_tv_per_slice=None, stop_on_distance=False, precond="paper",
+                stall_tol=0.0, pcg_tol_rel=False):
+    """firls_params; precond is "paper", "jacobi" or "none" (FIRLS_PRECOND_*);
+    pcg_tol_rel: pcg_tol is relative to each outer step's first residual."""
     p = Params()
+    p.outer_stall_tol = float(stall_tol)
+    p.pcg_tol_kind = 1 if pcg_tol_rel else 0
     p.outer_tol_kind = 1 if stop_on_distance else 0
+    p.precond = PRECONDS[precond]
     p.outer_iters, p.pcg_iters = int(outer), int(pcg)
     p.pcg_tol, p.outer_tol = float(pcg_tol), float(outer_tol)
     p.lambda_, p.lambda_tv, p.eps = float(lam), float(lam_tv), float(eps)
@@ -216,10 +225,13 @@ class Context:
     def run(self, params):
         self._check(lib().firls_run(self.h, ctypes.byref(params)), "run")
 
-    def slot_status(self):
+    def slot_status(self, with_pcg=False):
+        """(done, outer steps, last relative change[, PCG steps]) per slot."""
         k = self.batch
-        done, od, rc = (ctypes.c_int * k)(), (ctypes.c_int * k)(), (ctypes.c_double * k)()
-        self._check(lib().firls_slot_status(self.h, done, od, rc), "slot_status")
+        done, od, rc, pc = (ctypes.c_int * k)(), (ctypes.c_int * k)(), (ctypes.c_double * k)(), (ctypes.c_int * k)()
+        self._check(lib().firls_slot_status(self.h, done, od, rc, pc), "slot_status")
+        if with_pcg:
+            return list(done), list(od), list(rc), list(pc)
         return list(done), list(od), list(rc)
 
     def slot_retire(self, s):
@@ -393,7 +405,7 @@ class Cnn:
 
 
 def serve(ctx, masks, bs, lams, lam_tvs, params, outs, x0s=None, chunk=8, max_outer=400, stop_after=None,
-          counters=None):
+          counters=None, pcg_steps=None):
     """Continuous batching over a queue of slices with ctx.batch slots.
 
     masks/bs/outs: per-slice device tensors ([n][n]); lams/lam_tvs: floats;
@@ -403,7 +415,8 @@ def serve(ctx, masks, bs, lams, lam_tvs, params, outs, x0s=None, chunk=8, max_ou
     slices have completed and retires the slices still in flight (their
     entry in the result stays 0).  Returns the outer steps of every slice.
     counters (a dict, optional) receives "runs" (calls of ctx.run, each
-    `chunk` outer-step graph replays), "loads" and "retires".
+    `chunk` outer-step graph replays), "loads" and "retires"; pcg_steps (a
+    list of len(bs), optional) receives the PCG steps of every slice.
     """
     cnt = counters if counters is not None else {}
     for k in ("runs", "loads", "retires"):
@@ -435,13 +448,15 @@ def serve(ctx, masks, bs, lams, lam_tvs, params, outs, x0s=None, chunk=8, max_ou
             break
         ctx.run(run)
         cnt["runs"] += 1
-        done, od, _ = ctx.slot_status()
+        done, od, _, pc = ctx.slot_status(with_pcg=True)
         for s in range(ctx.batch):
             i = slot_of[s]
             if i < 0 or not (done[s] or od[s] >= max_outer):
                 continue
             ctx.slot_get(s, outs[i])
             steps[i] = od[s]
+            if pcg_steps is not None:
+                pcg_steps[i] = pc[s]
             completed += 1
             if nxt < q:
                 ctx.slot_load(s, masks[nxt], bs[nxt], lams[nxt], lam_tvs[nxt], None if x0s is None else x0s[nxt])

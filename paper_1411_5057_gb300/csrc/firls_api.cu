@@ -31,7 +31,9 @@ struct firls_ctx {
   int* counts = nullptr;
   float2* tw = nullptr;
   float2 *atb = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *d = nullptr, *q = nullptr;
-  float2 *t = nullptr, *u = nullptr, *cw = nullptr, *xprev = nullptr, *tmpA = nullptr, *tmpB = nullptr;
+  float2 *t = nullptr, *u = nullptr, *cw = nullptr, *dx = nullptr, *tmpA = nullptr, *tmpB = nullptr;
+  // dx: the update of the current outer step, sum_j alpha_j d_j, accumulated
+  // from zero by the PCG steps and added to x once at the end of the step
   float *ww = nullptr, *wtv = nullptr, *ia = nullptr, *wdiag = nullptr;
   float* wg = nullptr;
   int *gidx = nullptr, *goff = nullptr, *inv_off = nullptr, *inv_ids = nullptr;
@@ -58,8 +60,7 @@ struct firls_ctx {
   bool marks_valid = false;
   // cached outer-step graph
   cudaGraphExec_t exec = nullptr;
-  int g_pcg = -1, g_kind = -1;
-  float g_ptol = -1.f, g_otol = -1.f;
+  firls_params g_sched{};  // schedule the cached graph was captured for
   bool use_graph = true;
 };
 
@@ -227,7 +228,7 @@ void enqueue_S(firls_ctx* c, int mode, const float2* zin, float2* din, float2* q
 }
 
 // Update W^k and P from x (Alg. 2/3, first two lines of the loop body).
-void enqueue_weights(firls_ctx* c, const float2* x) {
+void enqueue_weights(firls_ctx* c, const float2* x, int precond) {
   const int B = c->batch, n = c->n;
   TMark mk(c, FIRLS_K_WEIGHTS, 0);
   if (c->kind) {
@@ -241,27 +242,44 @@ void enqueue_weights(firls_ctx* c, const float2* x) {
     }
   }
   if (has_tv(c)) {
+    // with TV, 1/a of the penta-diagonal P is also 1/diag(S) (the Jacobi scale)
     tv_weights(B, n, c->stream, c->st, x, c->wtv);
     if (c->kind) wavelet_diag(B, n, c->levels, c->stream, c->st, c->ww, c->wdiag, c->sqtab, c->sqlen);
     penta_setup(B, n, c->stream, c->st, c->wtv, c->kind ? c->wdiag : nullptr, c->ia);
+  } else if (precond == FIRLS_PRECOND_JACOBI) {
+    wavelet_diag(B, n, c->levels, c->stream, c->st, c->ww, c->wdiag, c->sqtab, c->sqlen);
+    jacobi_wavelet_setup(B, n, c->stream, c->st, c->wdiag, c->ia);
   }
 }
 
 // z = P^{-1} r after the residual update of `mode` (ILU_INIT / ILU_STEP).
-void enqueue_update_precond(firls_ctx* c, int step_mode, float pcg_tol, bool init) {
+void enqueue_update_precond(firls_ctx* c, int step_mode, float pcg_tol, bool init, int precond) {
   const int B = c->batch, n = c->n;
   const int real = (c->flags & FIRLS_REAL_X) ? 1 : 0;
+  if (precond != FIRLS_PRECOND_PAPER) {  // Jacobi or none: one fused pass, then the FP64 scalars
+    {
+      TMark m(c, FIRLS_K_AXPY, 1);
+      axpy_diag_step(B, n, c->stream, c->st, c->part, init ? AXPY_INIT : AXPY_STEP, c->dx, c->d, c->r, c->q, c->atb,
+                     precond == FIRLS_PRECOND_JACOBI ? c->ia : nullptr, c->z);
+    }
+    TMark m(c, FIRLS_K_SCALARS, 1);
+    if (init)
+      pcg_rho_init(B, c->stream, c->st, c->part, axpy_ctas(n), axpy_ctas(n));
+    else
+      pcg_beta(B, c->stream, c->st, c->part, axpy_ctas(n), axpy_ctas(n), pcg_tol);
+    return;
+  }
   if (has_tv(c)) {
     {
       TMark m(c, FIRLS_K_ILU, 1);
       // the ILU CTA finishes rho (and beta) from its own sums
-      ilu_step(B, n, c->stream, c->st, c->part, init ? ILU_INIT : ILU_STEP, c->x, c->d, c->r, c->q, c->atb,
+      ilu_step(B, n, c->stream, c->st, c->part, init ? ILU_INIT : ILU_STEP, c->dx, c->d, c->r, c->q, c->atb,
                c->u, c->z, c->ia, c->wtv, c->tune_ilu, 1, pcg_tol, c->wait_test);
     }
   } else {
     {
       TMark m(c, FIRLS_K_AXPY, 1);
-      axpy_step(B, n, c->stream, c->st, c->part, init ? AXPY_INIT : AXPY_STEP, c->x, c->d, c->r, c->q, c->atb);
+      axpy_step(B, n, c->stream, c->st, c->part, init ? AXPY_INIT : AXPY_STEP, c->dx, c->d, c->r, c->q, c->atb);
     }
     WavArgs w = wav_args(c, c->st);
     {
@@ -279,18 +297,20 @@ void enqueue_update_precond(firls_ctx* c, int step_mode, float pcg_tol, bool ini
 }
 
 // One outer step of FIRLS: weights, P, PCG warm-started at x^k, relative change.
-void enqueue_outer(firls_ctx* c, int J, float pcg_tol, float outer_tol, int tol_kind) {
+void enqueue_outer(firls_ctx* c, const firls_params& sc) {
   const int B = c->batch, n = c->n;
+  const int J = sc.pcg_iters, precond = sc.precond;
+  const float pcg_tol = sc.pcg_tol;
   marks_reset(c);
   {
     TMark m(c, FIRLS_K_OTHER, 1);
-    outer_begin(B, c->stream, c->st);
-    cudaMemcpyAsync(c->xprev, c->x, sizeof(float2) * (size_t)B * n * n, cudaMemcpyDeviceToDevice, c->stream);
+    outer_begin(B, c->stream, c->st, sc.pcg_tol_kind);
+    cudaMemsetAsync(c->dx, 0, sizeof(float2) * (size_t)B * n * n, c->stream);
   }
-  enqueue_weights(c, c->x);
+  enqueue_weights(c, c->x, precond);
   // r = A^H b - S x^k, z = P^{-1} r, rho = Re<r, z>
   enqueue_S(c, 2, nullptr, c->x, c->q);
-  enqueue_update_precond(c, 0, pcg_tol, true);
+  enqueue_update_precond(c, 0, pcg_tol, true, precond);
   for (int j = 1; j <= J; ++j) {
     enqueue_S(c, j == 1 ? 0 : 1, c->z, c->d, c->q);
     {
@@ -298,15 +318,23 @@ void enqueue_outer(firls_ctx* c, int J, float pcg_tol, float outer_tol, int tol_
       pcg_alpha(B, c->stream, c->st, c->part, fft_row_ctas(n));
     }
     if (j < J) {
-      enqueue_update_precond(c, 1, pcg_tol, false);
+      enqueue_update_precond(c, 1, pcg_tol, false, precond);
     } else {
       TMark m(c, FIRLS_K_AXPY, 1);
-      axpy_step(B, n, c->stream, c->st, c->part, AXPY_LAST, c->x, c->d, c->r, c->q, c->atb);
+      axpy_step(B, n, c->stream, c->st, c->part, AXPY_LAST, c->dx, c->d, c->r, c->q, c->atb);
     }
   }
   TMark m(c, FIRLS_K_OTHER, 2);
-  relchange_parts(B, n, c->stream, c->st, c->x, c->xprev, c->part);
-  outer_end(B, c->stream, c->st, c->part, axpy_ctas(n), outer_tol, tol_kind);
+  outer_apply(B, n, c->stream, c->st, c->x, c->dx, c->part);
+  outer_end(B, c->stream, c->st, c->part, axpy_ctas(n), sc.outer_tol, sc.outer_tol_kind, sc.outer_stall_tol);
+}
+
+// Two parameter sets capture the same outer-step graph (everything but the
+// outer count and the lambdas, which live in device memory).
+bool same_schedule(const firls_params& a, const firls_params& b) {
+  return a.pcg_iters == b.pcg_iters && a.pcg_tol == b.pcg_tol && a.outer_tol == b.outer_tol &&
+         a.outer_tol_kind == b.outer_tol_kind && a.precond == b.precond && a.outer_stall_tol == b.outer_stall_tol &&
+         a.pcg_tol_kind == b.pcg_tol_kind;
 }
 
 firls_status check_params(firls_ctx* c, const firls_params* p) {
@@ -314,6 +342,10 @@ firls_status check_params(firls_ctx* c, const firls_params* p) {
   if (p->outer_iters < 1 || p->pcg_iters < 1) return fail(c, FIRLS_E_INVALID_ARG, "iteration counts must be >= 1");
   if (!(p->pcg_tol >= 0.f) || !(p->outer_tol >= 0.f)) return fail(c, FIRLS_E_INVALID_ARG, "tolerances must be >= 0");
   if (p->outer_tol_kind != 0 && p->outer_tol_kind != 1) return fail(c, FIRLS_E_INVALID_ARG, "bad outer_tol_kind");
+  if (p->precond < FIRLS_PRECOND_PAPER || p->precond > FIRLS_PRECOND_NONE)
+    return fail(c, FIRLS_E_INVALID_ARG, "bad precond");
+  if (!(p->outer_stall_tol >= 0.f)) return fail(c, FIRLS_E_INVALID_ARG, "outer_stall_tol must be >= 0");
+  if (p->pcg_tol_kind != 0 && p->pcg_tol_kind != 1) return fail(c, FIRLS_E_INVALID_ARG, "bad pcg_tol_kind");
   const int B = c->batch;
   for (int s = 0; s < B; ++s) {
     const float l = p->lambda_per_slice ? p->lambda_per_slice[s] : p->lambda;
@@ -363,19 +395,18 @@ firls_status enqueue_setup(firls_ctx* c, const void* b, const firls_params* p, c
 firls_status run_outer_steps(firls_ctx* c, const firls_params* p) {
   const bool graph = c->use_graph && c->stream != nullptr;
   if (!graph) {
-    for (int k = 0; k < p->outer_iters; ++k) enqueue_outer(c, p->pcg_iters, p->pcg_tol, p->outer_tol, p->outer_tol_kind);
+    for (int k = 0; k < p->outer_iters; ++k) enqueue_outer(c, *p);
     c->marks_valid = c->timing;
     return cuda_check(c, cudaGetLastError(), "outer step launch");
   }
-  if (!c->exec || c->g_pcg != p->pcg_iters || c->g_ptol != p->pcg_tol || c->g_otol != p->outer_tol ||
-      c->g_kind != p->outer_tol_kind) {
+  if (!c->exec || !same_schedule(c->g_sched, *p)) {
     if (c->exec) {
       cudaGraphExecDestroy(c->exec);
       c->exec = nullptr;
     }
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_outer(c, p->pcg_iters, p->pcg_tol, p->outer_tol, p->outer_tol_kind);
+    enqueue_outer(c, *p);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (e != cudaSuccess) return cuda_check(c, e, "graph capture");
     e = cudaGraphInstantiate(&c->exec, g, 0);
@@ -384,10 +415,7 @@ firls_status run_outer_steps(firls_ctx* c, const firls_params* p) {
       c->exec = nullptr;
       return cuda_check(c, e, "graph instantiate");
     }
-    c->g_pcg = p->pcg_iters;
-    c->g_ptol = p->pcg_tol;
-    c->g_otol = p->outer_tol;
-    c->g_kind = p->outer_tol_kind;
+    c->g_sched = *p;
   }
   // With an outer tolerance, poll the per-slice done flags every
   // kPoll replays and stop launching once every slice has stopped.
@@ -438,8 +466,7 @@ void prepare_kernels(int n);
 
 struct MultiGraph {
   std::vector<firls_ctx*> ctxs;
-  int J = -1, kind = -1;
-  float ptol = -1.f, otol = -1.f;
+  firls_params sched{};
   cudaGraphExec_t exec = nullptr;
 };
 static MultiGraph g_multi;  // last multi-context graph (per process)
@@ -476,7 +503,7 @@ extern "C" firls_status firls_create(firls_ctx** out, int n_rows, int n_cols, in
   A(&c->mask, BN);
   A(&c->counts, (size_t)batch);
   A(&c->tw, (size_t)n);
-  for (float2** p : {&c->atb, &c->x, &c->r, &c->z, &c->d, &c->q, &c->t, &c->u, &c->cw, &c->xprev}) A(p, BN);
+  for (float2** p : {&c->atb, &c->x, &c->r, &c->z, &c->d, &c->q, &c->t, &c->u, &c->cw, &c->dx}) A(p, BN);
   A(&c->tmpA, BH);
   A(&c->tmpB, BH);
   for (float** p : {&c->ww, &c->wtv, &c->ia, &c->wdiag}) A(p, BN);
@@ -589,7 +616,7 @@ extern "C" firls_status firls_set_operator(firls_ctx* c, const uint8_t* mask, un
     c->gsize = group_size;
     c->gtotal = total;
   }
-  if (kind && (psi_kind & FIRLS_PSI_TV)) {
+  if (kind) {  // squared basis tables of diag(Phi^T W Phi) (TV preconditioner, Jacobi)
     std::vector<float> tab;
     std::vector<int> len;
     basis_tables(n, wavelet_levels, kind == 1 ? FIRLS_PSI_HAAR : FIRLS_PSI_DB4, tab, len);
@@ -652,8 +679,7 @@ extern "C" firls_status firls_solve_multi(firls_ctx* const* ctxs, int n_ctx, con
     firls_ctx* c = ctxs[i];
     if (!c || !c->op_set) return FIRLS_E_STATE;
     TRY(check_params(c, &pa[i]));
-    if (pa[i].outer_iters != p->outer_iters || pa[i].pcg_iters != p->pcg_iters || pa[i].pcg_tol != p->pcg_tol ||
-        pa[i].outer_tol != p->outer_tol || pa[i].outer_tol_kind != p->outer_tol_kind)
+    if (pa[i].outer_iters != p->outer_iters || !same_schedule(pa[i], *p))
       return fail(c, FIRLS_E_INVALID_ARG, "solve_multi: contexts must share the schedule and tolerances");
     if (!c->stream || !c->use_graph) graphable = false;
     for (int j = 0; j < i; ++j)
@@ -681,11 +707,9 @@ extern "C" firls_status firls_solve_multi(firls_ctx* const* ctxs, int n_ctx, con
   }
   if (!graphable) {
     for (int k = 0; k < p->outer_iters; ++k)
-      for (int i = 0; i < n_ctx; ++i) enqueue_outer(ctxs[i], p->pcg_iters, p->pcg_tol, p->outer_tol, p->outer_tol_kind);
+      for (int i = 0; i < n_ctx; ++i) enqueue_outer(ctxs[i], *p);
   } else {
-    const bool same = g_multi.exec && g_multi.J == p->pcg_iters && g_multi.ptol == p->pcg_tol &&
-                      g_multi.otol == p->outer_tol && g_multi.kind == p->outer_tol_kind &&
-                      (int)g_multi.ctxs.size() == n_ctx &&
+    const bool same = g_multi.exec && same_schedule(g_multi.sched, *p) && (int)g_multi.ctxs.size() == n_ctx &&
                       std::equal(g_multi.ctxs.begin(), g_multi.ctxs.end(), ctxs);
     // every context's set-up must precede the replays on c0's stream
     for (int i = 1; i < n_ctx; ++i) {
@@ -703,7 +727,7 @@ extern "C" firls_status firls_solve_multi(firls_ctx* const* ctxs, int n_ctx, con
       }
       cudaEventRecord(fork, c0->stream);
       for (int i = 1; i < n_ctx; ++i) cudaStreamWaitEvent(ctxs[i]->stream, fork, 0);
-      for (int i = 0; i < n_ctx; ++i) enqueue_outer(ctxs[i], p->pcg_iters, p->pcg_tol, p->outer_tol, p->outer_tol_kind);
+      for (int i = 0; i < n_ctx; ++i) enqueue_outer(ctxs[i], *p);
       for (int i = 1; i < n_ctx; ++i) {
         cudaEventRecord(join[i], ctxs[i]->stream);
         cudaStreamWaitEvent(c0->stream, join[i], 0);
@@ -721,10 +745,7 @@ extern "C" firls_status firls_solve_multi(firls_ctx* const* ctxs, int n_ctx, con
         return cuda_check(c0, e, "multi instantiate");
       }
       g_multi.ctxs.assign(ctxs, ctxs + n_ctx);
-      g_multi.J = p->pcg_iters;
-      g_multi.ptol = p->pcg_tol;
-      g_multi.otol = p->outer_tol;
-      g_multi.kind = p->outer_tol_kind;
+      g_multi.sched = *p;
     }
     for (int k = 0; k < p->outer_iters; ++k) {
       cudaError_t e = cudaGraphLaunch(g_multi.exec, c0->stream);
@@ -858,14 +879,14 @@ extern "C" firls_status firls_apply_S_P(firls_ctx* c, const firls_params* p, con
   const size_t bytes = sizeof(float2) * (size_t)B * n * n;
   state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, eps_of(p));
   CU(cudaMemcpyAsync(c->x, x, bytes, cudaMemcpyDeviceToDevice, c->stream));
-  enqueue_weights(c, c->x);
+  enqueue_weights(c, c->x, p->precond);
   // q = S d
   CU(cudaMemcpyAsync(c->d, d, bytes, cudaMemcpyDeviceToDevice, c->stream));
   enqueue_S(c, 2, nullptr, c->d, static_cast<float2*>(q));
   // z = P^{-1} r: feed r as "A^H b" with q = 0 through the INIT path
   CU(cudaMemcpyAsync(c->atb, r, bytes, cudaMemcpyDeviceToDevice, c->stream));
   CU(cudaMemsetAsync(c->q, 0, bytes, c->stream));
-  enqueue_update_precond(c, 0, 0.f, true);
+  enqueue_update_precond(c, 0, 0.f, true, p->precond);
   CU(cudaMemcpyAsync(z, c->z, bytes, cudaMemcpyDeviceToDevice, c->stream));
   return cuda_check(c, cudaGetLastError(), "apply_S_P");
 }
@@ -974,12 +995,15 @@ extern "C" firls_status firls_run(firls_ctx* c, const firls_params* p) {
   firls_params q = *p;
   q.outer_tol = p->outer_tol;  // no polling inside: the caller polls with firls_slot_status
   const bool graph = c->use_graph && c->stream != nullptr;
+  if (q.precond < FIRLS_PRECOND_PAPER || q.precond > FIRLS_PRECOND_NONE)
+    return fail(c, FIRLS_E_INVALID_ARG, "bad precond");
+  if (!(q.outer_stall_tol >= 0.f)) return fail(c, FIRLS_E_INVALID_ARG, "outer_stall_tol must be >= 0");
+  if (q.pcg_tol_kind != 0 && q.pcg_tol_kind != 1) return fail(c, FIRLS_E_INVALID_ARG, "bad pcg_tol_kind");
   if (!graph) {
-    for (int k = 0; k < q.outer_iters; ++k) enqueue_outer(c, q.pcg_iters, q.pcg_tol, q.outer_tol, q.outer_tol_kind);
+    for (int k = 0; k < q.outer_iters; ++k) enqueue_outer(c, q);
     return cuda_check(c, cudaGetLastError(), "run");
   }
-  if (!c->exec || c->g_pcg != q.pcg_iters || c->g_ptol != q.pcg_tol || c->g_otol != q.outer_tol ||
-      c->g_kind != q.outer_tol_kind) {
+  if (!c->exec || !same_schedule(c->g_sched, q)) {
     firls_params one = q;
     one.outer_iters = 1;
     TRY(run_outer_steps(c, &one));  // captures (and runs) one step
@@ -990,7 +1014,8 @@ extern "C" firls_status firls_run(firls_ctx* c, const firls_params* p) {
   return FIRLS_OK;
 }
 
-extern "C" firls_status firls_slot_status(firls_ctx* c, int* done, int* outer_done, double* rel_change) {
+extern "C" firls_status firls_slot_status(firls_ctx* c, int* done, int* outer_done, double* rel_change,
+                                          int* pcg_steps) {
   if (!c) return FIRLS_E_INVALID_ARG;
   std::vector<SliceState> hs(c->batch);
   CU(cudaMemcpyAsync(hs.data(), c->st, sizeof(SliceState) * c->batch, cudaMemcpyDeviceToHost, c->stream));
@@ -999,6 +1024,7 @@ extern "C" firls_status firls_slot_status(firls_ctx* c, int* done, int* outer_do
     if (done) done[s] = hs[s].done;
     if (outer_done) outer_done[s] = hs[s].outer_done;
     if (rel_change) rel_change[s] = hs[s].relchg;
+    if (pcg_steps) pcg_steps[s] = hs[s].pcg_steps;
   }
   return FIRLS_OK;
 }

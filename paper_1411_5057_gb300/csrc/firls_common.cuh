@@ -8,6 +8,12 @@
 
 namespace firls {
 
+// Outer steps over which the contraction of the outer iteration is measured
+// by the distance-to-the-limit stop (outer_tol_kind 1).
+constexpr int MU_WINDOW = 24;
+// Consecutive outer steps at or below the stall tolerance that stop a slice.
+constexpr int STALL_STEPS = 4;
+
 // Per-slice PCG / outer-loop state, FP64 scalars (the only FP64 steps:
 // inner products, alpha, beta, rho, residual norms, relative change).
 struct SliceState {
@@ -16,8 +22,8 @@ struct SliceState {
   double beta;       // rho_new / rho
   double rhs2;       // ||A^H b||^2
   double rr;         // ||r||^2 after the last update
+  double rr0;        // ||r_0||^2, the first residual of the current outer step
   double relchg;     // ||x^{k+1} - x^k|| / ||x^k|| of the last outer step
-  double relchg_prev;  // the same one outer step earlier
   int active;        // PCG running in this outer step
   int done;          // outer loop stopped (outer_tol reached)
   int breakdown;     // PCG broke down at least once
@@ -28,6 +34,9 @@ struct SliceState {
   float lam_tv;      // TV lambda
   float abar;        // mean(diag(A^H A)) = popcount / N
   float eps;         // smoothing eps
+  int stall;         // consecutive outer steps with relchg <= the stall tolerance
+  int pcg_rel;       // PCG tolerance relative to ||r_0|| (1) or to ||A^H b|| (0)
+  float hist[MU_WINDOW];  // relchg of the last MU_WINDOW outer steps (ring, by outer_done)
 };
 
 // Partial-sum slots (double part[B][NSLOT][MAXPART]).
@@ -69,13 +78,15 @@ FI void pcg_alpha_from(SliceState* v, double dq) {
 FI void pcg_rho_init_from(SliceState* v, double rz, double rr) {
   v->rho = rz;
   v->rr = rr;
+  v->rr0 = rr;
   v->beta = 0.0;
 }
-// After the residual update: stop on ||r|| <= tol ||A^H b||, else
-// beta = rho_new / rho.
+// After the residual update: stop on ||r|| <= tol ||A^H b|| (or, with
+// pcg_rel, ||r|| <= tol ||r_0||: the forcing term of an inexact inner solve),
+// else beta = rho_new / rho.
 FI void pcg_beta_from(SliceState* v, double rz, double rr, float tol) {
   v->rr = rr;
-  if (tol > 0.f && sqrt(rr) <= (double)tol * sqrt(v->rhs2)) {
+  if (tol > 0.f && sqrt(rr) <= (double)tol * sqrt(v->pcg_rel ? v->rr0 : v->rhs2)) {
     v->active = 0;
     return;
   }

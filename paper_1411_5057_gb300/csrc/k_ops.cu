@@ -1751,9 +1751,73 @@ void axpy_step(int batch, int n, cudaStream_t s, const SliceState* st, double* p
   k_axpy<<<dim3(axpy_ctas(n), batch), 256, 0, s>>>(n * n, mode, st, part, x, d, r, q, atb);
 }
 
-// partial ||x - xprev||^2 (SLOT_DX) and ||xprev||^2 (SLOT_XX)
-__global__ void k_relchange(int N, const SliceState* __restrict__ st, const float2* __restrict__ x,
-                            const float2* __restrict__ xp, double* __restrict__ part) {
+// Residual update with a diagonal preconditioner (Jacobi PCG, sdiag = 1 /
+// diag(S)) or none (standard CG, sdiag null), for the comparison of Sec. 5.2.
+__global__ void k_axpy_diag(int N, int mode, const SliceState* __restrict__ st, double* __restrict__ part,
+                            float2* __restrict__ x, const float2* __restrict__ d, float2* __restrict__ r,
+                            const float2* __restrict__ q, const float2* __restrict__ atb,
+                            const float* __restrict__ sdiag, float2* __restrict__ z) {
+  const int s = blockIdx.y;
+  if (!slice_running(st, s)) return;
+  __shared__ double red[32];
+  const float alpha = (float)st[s].alpha;
+  const size_t base = (size_t)s * N;
+  const int chunk = (N + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * chunk, hi = min(N, lo + chunk);
+  float rz = 0.f, rr = 0.f;
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const size_t g = base + i;
+    float2 rv;
+    if (mode == AXPY_INIT) {
+      rv = csub(atb[g], q[g]);
+    } else {
+      x[g] = cfma(alpha, d[g], x[g]);
+      rv = cfma(-alpha, q[g], r[g]);
+    }
+    r[g] = rv;
+    const float sc = sdiag ? sdiag[g] : 1.f;
+    z[g] = cscale(rv, sc);
+    const float r2 = cabs2(rv);
+    rr += r2;
+    rz = fmaf(sc, r2, rz);
+  }
+  const double trz = block_sum((double)rz, red);
+  __syncthreads();
+  const double trr = block_sum((double)rr, red);
+  if (threadIdx.x == 0) {
+    part[((size_t)s * NSLOT + SLOT_RZ) * MAXPART + blockIdx.x] = trz;
+    part[((size_t)s * NSLOT + SLOT_RR) * MAXPART + blockIdx.x] = trr;
+  }
+}
+
+void axpy_diag_step(int batch, int n, cudaStream_t s, const SliceState* st, double* part, int mode, float2* x,
+                    const float2* d, float2* r, const float2* q, const float2* atb, const float* sdiag, float2* z) {
+  k_axpy_diag<<<dim3(axpy_ctas(n), batch), 256, 0, s>>>(n * n, mode, st, part, x, d, r, q, atb, sdiag, z);
+}
+
+__global__ void k_jacobi_wavelet(int N, const SliceState* __restrict__ st, const float* __restrict__ wdiag,
+                                 float* __restrict__ ia) {
+  const int s = blockIdx.y;
+  if (!slice_running(st, s)) return;
+  const float abar = st[s].abar, lw = st[s].lam;
+  const size_t base = (size_t)s * N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+    ia[base + i] = 1.0f / fmaf(lw, wdiag[base + i], abar);
+}
+
+void jacobi_wavelet_setup(int batch, int n, cudaStream_t s, const SliceState* st, const float* wdiag, float* ia) {
+  const int N = n * n;
+  const int blocks = (N + 255) / 256 < 64 ? (N + 255) / 256 : 64;
+  k_jacobi_wavelet<<<dim3(blocks, batch), 256, 0, s>>>(N, st, wdiag, ia);
+}
+
+// End of an outer step: x^{k+1} = x^k + dx, where dx = sum_j alpha_j d_j was
+// accumulated from zero by the PCG steps (so its rounding is relative to the
+// step, not to x); partial ||dx||^2 (SLOT_DX) and ||x^k||^2 (SLOT_XX) for the
+// relative change.  Slices that are done (converged earlier, or broken down
+// in this step) keep x^k.
+__global__ void k_outer_apply(int N, const SliceState* __restrict__ st, float2* __restrict__ x,
+                              const float2* __restrict__ dx, double* __restrict__ part) {
   const int s = blockIdx.y;
   if (st[s].done) return;
   __shared__ double red[32];
@@ -1762,9 +1826,10 @@ __global__ void k_relchange(int N, const SliceState* __restrict__ st, const floa
   const int lo = blockIdx.x * chunk, hi = min(N, lo + chunk);
   float a = 0.f, b = 0.f;
   for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const float2 xv = x[base + i], pv = xp[base + i];
-    a += cabs2(csub(xv, pv));
-    b += cabs2(pv);
+    const float2 xv = x[base + i], dv = dx[base + i];
+    a += cabs2(dv);
+    b += cabs2(xv);
+    x[base + i] = cadd(xv, dv);
   }
   const double ta = block_sum((double)a, red);
   __syncthreads();
@@ -1775,9 +1840,9 @@ __global__ void k_relchange(int N, const SliceState* __restrict__ st, const floa
   }
 }
 
-void relchange_parts(int batch, int n, cudaStream_t s, const SliceState* st, const float2* x,
-                     const float2* xprev, double* part) {
-  k_relchange<<<dim3(axpy_ctas(n), batch), 256, 0, s>>>(n * n, st, x, xprev, part);
+void outer_apply(int batch, int n, cudaStream_t s, const SliceState* st, float2* x, const float2* dx,
+                 double* part) {
+  k_outer_apply<<<dim3(axpy_ctas(n), batch), 256, 0, s>>>(n * n, st, x, dx, part);
 }
 
 // ================================================================ groups ===
@@ -2010,8 +2075,11 @@ __global__ void k_state_init(int B, SliceState* st, const double* part, int np, 
   v.beta = 0.0;
   v.rhs2 = sum_parts(part, s, SLOT_RHS, np);
   v.rr = v.rhs2;
+  v.rr0 = v.rhs2;
+  v.pcg_rel = 0;
   v.relchg = 0.0;
-  v.relchg_prev = 0.0;
+  v.stall = 0;
+  for (int i = 0; i < MU_WINDOW; ++i) v.hist[i] = 0.f;
   // non-finite k-space on the mask makes A^H b non-finite: the slice is not
   // iterated and counts as a breakdown (its x keeps the start)
   const bool bad = !isfinite(v.rhs2);
@@ -2033,14 +2101,15 @@ void state_init(int batch, cudaStream_t s, SliceState* st, const double* part, i
   k_state_init<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np, counts, n * n, lam, lam_tv, eps);
 }
 
-__global__ void k_outer_begin(int B, SliceState* st) {
+__global__ void k_outer_begin(int B, SliceState* st, int pcg_rel) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B) return;
   st[s].active = st[s].done ? 0 : 1;
+  st[s].pcg_rel = pcg_rel;
 }
 
-void outer_begin(int batch, cudaStream_t s, SliceState* st) {
-  k_outer_begin<<<(batch + 127) / 128, 128, 0, s>>>(batch, st);
+void outer_begin(int batch, cudaStream_t s, SliceState* st, int pcg_rel) {
+  k_outer_begin<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, pcg_rel);
 }
 
 __global__ void k_alpha(int B, SliceState* st, const double* part, int np) {
@@ -2077,29 +2146,42 @@ void pcg_beta(int batch, cudaStream_t s, SliceState* st, const double* part, int
 // Outer-loop stop.  kind 0: relative change <= tol.  kind 1: estimated
 // distance to the limit <= tol.  Under linear convergence x^k -> x* with
 // contraction mu, ||x^k - x*|| ~ relchg_k mu / (1 - mu) (the sum of the
-// remaining steps) relative to ||x^k||; mu is the two-step geometric mean
-// sqrt(relchg_k / relchg_{k-2}), capped at 0.999.
-__global__ void k_outer_end(int B, SliceState* st, const double* part, int np, float tol, int kind) {
+// remaining steps) relative to ||x^k||; mu is the geometric mean contraction
+// over the last MU_WINDOW steps, (relchg_k / relchg_{k-W})^(1/W), capped at
+// 0.999 (a long window: the rate drifts early on and FP32 rounding jitters
+// single steps).  Either kind also stops a slice whose relative change has
+// stayed at or below stall_tol for STALL_STEPS consecutive steps: the FP32
+// rounding floor of the outer iteration, below which it cannot move.
+__global__ void k_outer_end(int B, SliceState* st, const double* part, int np, float tol, int kind,
+                            float stall_tol) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B || st[s].done) return;
+  SliceState* v = st + s;
   const double dx = sum_parts(part, s, SLOT_DX, np);
   const double xx = sum_parts(part, s, SLOT_XX, np);
   const double rel = xx > 0.0 ? sqrt(dx / xx) : INFINITY;
-  const double prev2 = st[s].relchg_prev;
-  st[s].relchg_prev = st[s].relchg;
-  st[s].relchg = rel;
-  st[s].outer_done += 1;
+  const int k = v->outer_done;  // this step's index
+  const float old = v->hist[k % MU_WINDOW];  // relchg of step k - MU_WINDOW
+  v->hist[k % MU_WINDOW] = (float)rel;
+  v->relchg = rel;
+  v->outer_done = k + 1;
+  v->stall = (stall_tol > 0.f && rel <= (double)stall_tol) ? v->stall + 1 : 0;
+  if (v->stall >= STALL_STEPS) {
+    v->done = 1;
+    return;
+  }
   if (!(tol > 0.f)) return;
   if (kind == 0) {
-    if (rel <= (double)tol) st[s].done = 1;
-  } else if (st[s].outer_done >= 4 && prev2 > 0.0) {
-    const double mu = fmin(sqrt(rel / prev2), 0.999);
-    if (rel * mu / (1.0 - mu) <= (double)tol && rel <= (double)tol) st[s].done = 1;
+    if (rel <= (double)tol) v->done = 1;
+  } else if (k >= MU_WINDOW && old > 0.f) {
+    const double mu = fmin(pow(rel / (double)old, 1.0 / MU_WINDOW), 0.999);
+    if (rel * mu / (1.0 - mu) <= (double)tol && rel <= (double)tol) v->done = 1;
   }
 }
 
-void outer_end(int batch, cudaStream_t s, SliceState* st, const double* part, int np, float tol, int kind) {
-  k_outer_end<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np, tol, kind);
+void outer_end(int batch, cudaStream_t s, SliceState* st, const double* part, int np, float tol, int kind,
+               float stall_tol) {
+  k_outer_end<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np, tol, kind, stall_tol);
 }
 
 }  // namespace firls

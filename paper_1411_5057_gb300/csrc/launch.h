@@ -81,6 +81,9 @@ void wavelet_diag(int batch, int n, int levels, cudaStream_t s, const SliceState
 void penta_setup(int batch, int n, cudaStream_t s, const SliceState* st, const float* wtv,
                  const float* wdiag, float* ia);
 
+// In the PCG-step kernels below, `x` is the vector that receives alpha d: the
+// solver passes the outer step's update accumulator dx (added to the iterate
+// once per outer step by outer_apply).
 enum IluMode { ILU_INIT = 0, ILU_STEP = 1, ILU_LAST = 2 };
 // shape: shared-memory ring, 10 * rows per stage + stages (0: chosen from n and batch)
 // fuse_scalars: the CTA finishes the PCG scalars itself from its sums (rho
@@ -93,6 +96,13 @@ int ilu_default_shape(int n, int batch);
 bool ilu_shape_fits(int n, int shape);
 
 enum AxpyMode { AXPY_INIT = 0, AXPY_STEP = 1, AXPY_LAST = 2 };
+// Residual update (INIT: r = A^H b - q; STEP: r -= alpha q, x += alpha d) with
+// a diagonal preconditioner z = sdiag o r (sdiag null: z = r), partial
+// Re<r, z> into SLOT_RZ and ||r||^2 into SLOT_RR (axpy_ctas parts).
+void axpy_diag_step(int batch, int n, cudaStream_t s, const SliceState* st, double* part, int mode, float2* x,
+                    const float2* d, float2* r, const float2* q, const float2* atb, const float* sdiag, float2* z);
+// Jacobi scale of a wavelet-only system: ia = 1 / (abar + lam diag(Phi^T W Phi)).
+void jacobi_wavelet_setup(int batch, int n, cudaStream_t s, const SliceState* st, const float* wdiag, float* ia);
 void axpy_step(int batch, int n, cudaStream_t s, const SliceState* st, double* part, int mode,
                float2* x, const float2* d, float2* r, const float2* q, const float2* atb);
 int axpy_ctas(int n);
@@ -120,11 +130,13 @@ void pcg_rho_init(int batch, cudaStream_t s, SliceState* st, const double* part,
                   int nparts_rr);
 void pcg_beta(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts_rz,
               int nparts_rr, float pcg_tol);
-void outer_begin(int batch, cudaStream_t s, SliceState* st);
-void relchange_parts(int batch, int n, cudaStream_t s, const SliceState* st, const float2* x,
-                     const float2* xprev, double* part);
+void outer_begin(int batch, cudaStream_t s, SliceState* st, int pcg_rel);
+// x += dx (the outer step's accumulated update) with partial ||dx||^2 and
+// ||x||^2 (before the update) for the relative change.
+void outer_apply(int batch, int n, cudaStream_t s, const SliceState* st, float2* x, const float2* dx,
+                 double* part);
 void outer_end(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts,
-               float outer_tol, int tol_kind);
+               float outer_tol, int tol_kind, float stall_tol);
 void state_init(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts_rhs,
                 const int* counts, int n, const float* lam, const float* lam_tv, float eps);
 

@@ -26,7 +26,8 @@ def test_reference_arm_line(procs):
     assert line["higher_is_better"] is True and line["value"] > 0
     # the GPU arm's config at the parser defaults (608 slices through 304 slots)
     ours = bench.workload_config(type("A", (), {"queue": 608, "batch": 304, "outer": bench.OUTER, "inner": 5,
-                                                "outer_tol": bench.OUTER_TOL, "steady": 0})(), 1)
+                                                "outer_tol": bench.OUTER_TOL, "stall_tol": bench.STALL_TOL,
+                                                "steady": 0})(), 1)
     assert line["config"] == ours
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == procs
     assert line["cpu_baseline"]["value"] == line["value"]

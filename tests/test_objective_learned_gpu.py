@@ -118,8 +118,9 @@ def test_learned_warm_start_saves_pcg_steps(F):
     bd = torch.from_numpy(b_h).cuda()
     xstar = ctx.solve(bd, F.make_params(150, inner, lam=meta["lam"], lam_tv=meta["lam_tv"]))
     atb_h = ctx.adjoint(bd)
-    gold = np.load(os.path.join(os.path.dirname(__file__), "golden", "xstar_tv_db4_256_seed2_stride4.npy"))
-    xs0 = xstar[0].cpu().numpy().astype(np.complex128)[::4, ::4]
+    gold = np.load(os.path.join(os.path.dirname(__file__), "golden", "xstar_tv_db4_256", "seed2.npz"))["x"]
+    gold = gold.astype(np.complex128)
+    xs0 = xstar[0].cpu().numpy().astype(np.complex128)
     assert np.linalg.norm(xs0 - gold) / np.linalg.norm(gold) < 2e-5
     net = F.Cnn(n, 16)
     net.set_params(fs.cnn_init_weights(0))

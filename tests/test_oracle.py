@@ -388,25 +388,49 @@ def test_tree_weights_dense():
 
 # ------------------------------------------------------------------ PCG ---
 
-def _system(n, psi, real=False, groups=None, levels=2, ratio=0.3, seed=0):
+def _system(n, psi, real=False, groups=None, levels=2, ratio=0.3, seed=0, precond="paper"):
     mask = fs.vd_mask(n, ratio, seed)
-    s = O.System(mask, real, psi, levels, 0.05, 0.02, groups)
+    s = O.System(mask, real, psi, levels, 0.05, 0.02, groups, precond=precond)
     r = rng(seed + 10)
     x = r.standard_normal((n, n)) if real else crandn(r, n, n)
     s.update_weights(x)
     return s, mask
 
 
+@pytest.mark.parametrize("precond", O.PRECONDS)
 @pytest.mark.parametrize("psi", [O.PSI_HAAR, O.PSI_DB4, O.PSI_TV, O.PSI_TV | O.PSI_DB4])
-def test_pcg_matches_dense_direct_solve(psi):
+def test_pcg_matches_dense_direct_solve(psi, precond):
+    """PCG with the proposed P, with Jacobi and without a preconditioner (plain
+    CG) reaches the dense direct solve of S x = rhs (S Hermitian positive
+    definite, so PCG with any SPD P converges in at most 2N real dimensions)."""
     n = 8
-    s, mask = _system(n, psi)
+    s, mask = _system(n, psi, precond=precond)
     Sd = dense_op(s.apply_S, n)
     assert np.allclose(Sd, Sd.conj().T, atol=1e-12)        # Hermitian
     rhs = crandn(rng(11), n, n)
     x_direct = np.linalg.solve(Sd, rhs.reshape(-1)).reshape(n, n)
     x, steps = O.pcg(s, rhs, np.zeros((n, n), complex), 4 * n * n, 1e-14, np.linalg.norm(rhs))
     assert np.linalg.norm(x - x_direct) <= 1e-9 * np.linalg.norm(x_direct)
+
+
+@pytest.mark.parametrize("psi,groups", [(O.PSI_HAAR, None), (O.PSI_DB4, "tree"), (O.PSI_TV, None),
+                                         (O.PSI_TV | O.PSI_DB4, None)])
+def test_jacobi_preconditioner_is_the_dense_diagonal(psi, groups):
+    """Jacobi PCG (Sec. 5.2) divides by diag(S); diag(S) equals the diagonal of
+    the dense S built column by column from apply_S, for a real unknown too."""
+    n = 8
+    gr = fs.tree_groups(n, 2) if groups == "tree" else None
+    for real in (False, True):
+        if real and psi & O.PSI_TV:
+            continue
+        s, _ = _system(n, psi, real=real, groups=gr, precond="jacobi")
+        Sd = dense_op(s.apply_S, n, dtype=float if real else complex)
+        assert np.allclose(s.diag_S(), np.real(np.diag(Sd)), rtol=1e-12, atol=1e-12)
+        r = crandn(rng(12), n, n)
+        assert np.allclose(s.apply_Pinv(r), r / np.real(np.diag(Sd)).reshape(n, n), rtol=1e-12)
+    s, _ = _system(n, psi, groups=gr, precond="none")
+    r = crandn(rng(13), n, n)
+    assert np.array_equal(s.apply_Pinv(r), r)
 
 
 def test_S_is_gradient_of_quadratic_model():

@@ -6,8 +6,9 @@ only its buffers); it keeps its scratch in fixed device arrays instead.
 Called here through the C ABI, twice in a row with different inputs and then
 at another size, it must reproduce firls_apply_AHA (same kernels) and the FP64
 oracle's A^H A = F^H R^T R F (Sec. 5.4) within the operator tolerance used by
-the other parity tests.  A last test makes first calls from several host
-threads at once (the set-up is guarded by a lock) and checks each result.
+the other parity tests.  A last test calls it from several host threads
+(whole calls serialised by the callers, as the header requires) and checks
+each result.
 The file name makes pytest collect it last.
 """
 import ctypes
@@ -85,29 +86,32 @@ def test_noalloc_rejects_oversize_and_bad_args(F):
                                        ctypes.c_void_p(stream.cuda_stream)) == 1
 
 
-def test_noalloc_concurrent_first_calls(F):
-    """First calls of a new size from four host threads at once.  They share
-    one stream, so the GPU runs them one after another (the scratch arrays are
-    shared); the host-side set-up and twiddle rewrite race and must not mix."""
+def test_noalloc_calls_from_several_host_threads(F):
+    """Four host threads, each on its own stream, start together on a size not
+    used before.  The scratch arrays are shared, so, as the header requires,
+    the callers serialise whole calls (a lock around call and stream
+    synchronisation); whichever thread comes first makes the size's set-up."""
     n, B = 128, 2
     inputs = [_inputs(n, B, 20 + i) for i in range(4)]
     outs = [torch.full_like(d, float("nan")) for _, d in inputs]
-    stream = torch.cuda.Stream()
+    streams = [torch.cuda.Stream() for _ in inputs]
     torch.cuda.synchronize()
+    lock = threading.Lock()
     codes = [None] * 4
     start = threading.Barrier(4)
 
     def work(i):
         mask, d = inputs[i]
         start.wait()
-        codes[i] = _noalloc(F, n, B, mask, d, outs[i], stream)
+        with lock:
+            codes[i] = _noalloc(F, n, B, mask, d, outs[i], streams[i])
+            streams[i].synchronize()
 
     threads = [threading.Thread(target=work, args=(i,)) for i in range(4)]
     for t in threads:
         t.start()
     for t in threads:
         t.join()
-    stream.synchronize()
     assert codes == [0, 0, 0, 0]
     for (mask, d), q in zip(inputs, outs):
         mh, dh = mask.cpu().numpy().astype(np.float64), d.cpu().numpy().astype(np.complex128)
