@@ -40,19 +40,26 @@ UNIT = "recons/s"
 N = 256
 RATIO, SIGMA, LAM_TV, LAM_W, LEVELS = 0.20, 0.01, 1e-3, 5e-4, 4
 # Schedule that brings every TV + D4 256^2 slice within 1e-4 of the FP64
-# oracle's converged minimiser x*: 60 PCG steps per outer step (an oracle
-# study of 40..120 found 60 needs the fewest PCG steps to 1e-4, 2580 for
-# seed 2) and a per-slice stop once the estimated distance to the limit,
+# oracle's converged minimiser x*.  Inner solves: 60 PCG steps per outer step
+# (an oracle study of 40..120 found 60 needs the fewest PCG steps to 1e-4 on
+# a typical slice), and 240 from a slice's 60th outer step on: the slices
+# still running then have ill-conditioned subproblems whose outer rate is set
+# by the inexact inner solve (with 60 steps they crawl to 1e-4 in 400-560
+# outer steps; with 240 from the 60th step the slowest stored slice needs
+# 18k PCG steps instead of 34k, and slices done by then are unaffected).
+# Every slice advances on its own, so slices in either phase never wait for
+# each other.  Outer stop per slice: the estimated distance to the limit,
 # relchg * mu / (1 - mu) with mu the mean contraction over the last 24 outer
-# steps, falls below 3e-5, or once the relative change has stayed at the FP32
-# floor of the outer iteration (<= 6e-7, four steps in a row); at most 800
-# outer steps.  Per-step GPU trajectories of the stored-x* seeds (the slowest
-# slices of the queue among them, 400-560 outer steps) picked these values.
-# Slices are served by continuous batching: a converged slice leaves its
-# slot, the next enters.  Checked against stored oracle x* by
+# steps, below OUTER_TOL, or the relative change at the FP32 floor of the
+# outer iteration (<= STALL_TOL four steps in a row); at most OUTER outer
+# steps.  Per-step GPU trajectories of the 20 stored-x* seeds (the slowest
+# slices of the queue among them) picked these values (worst 5.6e-5 at the
+# stop).  Slices are served by continuous batching: a converged slice leaves
+# its slot, the next enters.  Checked against stored oracle x* by
 # tests/test_gpu_parity.py::test_bench_workload_reaches_converged_oracle and
 # reported per result in the bench line ("accuracy").
-OUTER, INNER, OUTER_TOL, STALL_TOL = 800, 60, 3e-5, 6e-7
+OUTER, INNER, INNER_LATE, OUTER_LATE, OUTER_TOL, STALL_TOL = 800, 60, 240, 60, 3e-5, 6e-7
+SERVE_CHUNK = 64   # macro steps between polls of the slots
 REF_OUTER_PER_RECON = 43   # FP64 oracle outer steps (x 60 PCG) to 1e-4 of x* on seed 2
 
 # Algorithmic bytes per pixel per launch of each kernel class: every distinct
@@ -161,7 +168,8 @@ def run_ours(args):
     masks_h, b_h = make_batch(S, 2 + rank * S)
     stream = torch.cuda.Stream()
     params = F.make_params(args.outer, args.inner, lam=LAM_W, lam_tv=LAM_TV, outer_tol=args.outer_tol,
-                           stop_on_distance=True, stall_tol=args.stall_tol)
+                           stop_on_distance=True, stall_tol=args.stall_tol, pcg_late=args.inner_late,
+                           outer_late=args.outer_late)
     lams, lam_tvs = [LAM_W] * S, [LAM_TV] * S
     with torch.cuda.stream(stream):
         masks = torch.from_numpy(masks_h).cuda()
@@ -181,10 +189,12 @@ def run_ours(args):
             dist.barrier()
 
     done_per_step = S - B if args.steady else S
+    pcg_counts = [0] * S
 
     def step(x0s=None, counters=None):
         with torch.cuda.stream(stream):
             return F.serve(ctx, mlist, blist, lams, lam_tvs, params, xlist, x0s=x0s, max_outer=args.outer,
+                           chunk=SERVE_CHUNK, pcg_steps=pcg_counts,
                            stop_after=S - B if args.steady else None, counters=counters)
 
     # ---- device-resident throughput: continuous batching over S slices ----
@@ -219,7 +229,8 @@ def run_ours(args):
     steps = steps[steps > 0]
     print(f"[bench] {S} slices through {B} slots, <= {args.outer}x{args.inner}, stop {args.outer_tol}: "
           f"{ms:.1f} ms/step for {done_per_step} completions; outer steps mean {steps.mean():.1f} "
-          f"max {steps.max()} capped {(steps >= args.outer).sum()}", file=sys.stderr, flush=True)
+          f"max {steps.max()} capped {(steps >= args.outer).sum()}; PCG steps mean {np.mean(pcg_counts):.0f} "
+          f"max {np.max(pcg_counts)}", file=sys.stderr, flush=True)
 
     # ---- per-kernel timing of one outer step over all B slots ----
     ctx.set_timing(True)
@@ -232,11 +243,11 @@ def run_ours(args):
     print("[bench] per outer step: " + ", ".join(f"{k} {v[0]:.2f} ms/{v[1]}" for k, v in kt.items()),
           file=sys.stderr, flush=True)
     launches_per_outer = sum(v[1] for v in kt.values())
-    kern = {k: {"ms_per_outer": round(v[0], 4), "launches": v[1]} for k, v in kt.items()}
-    # applications per outer step: the S operator (its three FFT passes and the
-    # wavelet term, one cluster launch) runs inner + 1 times, the ILU inner times
-    apps = {"row_fft": args.inner + 1, "col_fft_mask": args.inner + 1, "wavelet_S": args.inner + 1,
-            "row_ifft_combine": args.inner + 1, "ilu": args.inner, "axpy": 1}
+    kern = {k: {"ms_per_outer": round(v[0], 4), "launches": v[1], "applications": v[2]} for k, v in kt.items()}
+    # operator applications per outer step (inner + 1 macro steps): the S
+    # operator (three FFT passes and the wavelet term, one cluster launch) and
+    # the ILU (first residual, then inner PCG steps) inner + 1 times each
+    apps = {k: v[2] for k, v in kt.items()}
     dom = max((k for k in ALG_BYTES_PER_PX if kt[k][1] > 0), key=lambda k: kt[k][0])
     per_app_s = kt[dom][0] / apps[dom] / 1e3
     alg = ALG_BYTES_PER_PX[dom] * N * N * B
@@ -295,18 +306,20 @@ def run_ours(args):
 
     out = None
     if rank == 0:
-        cpu = cpu_baseline(args, float(steps.mean())) if (world == 1 and not args.no_cpu_baseline) else None
+        cpu = cpu_baseline(args) if (world == 1 and not args.no_cpu_baseline) else None
         out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f32 (FP64 PCG scalars)", "data": "synthetic",
                "config": workload_config(args, world, done_per_step),
                "roofline": roofline, "kernels_per_outer_step": kern,
-               # graph replays x kernels per outer step, plus 4 kernels per slot load and 1 per retire
-               "gpu_launches": int(launches_per_outer * served["runs"] * 8 + 4 * served["loads"] + served["retires"]),
+               # kernels per macro step x macro steps run, plus 4 kernels per slot load and 1 per retire
+               "gpu_launches": int(launches_per_outer / (args.inner + 1) * served["runs"] * SERVE_CHUNK
+                                   + 4 * served["loads"] + served["retires"]),
                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
                "solve_stats": {"mean_outer_steps": round(float(steps.mean()), 2), "max_outer_steps": int(steps.max()),
                                "capped": int((steps >= args.outer).sum()),
-                               "mean_pcg_steps": round(float(steps.mean()) * args.inner, 1)},
+                               "mean_pcg_steps": round(float(np.mean(pcg_counts)), 1),
+                               "max_pcg_steps": int(np.max(pcg_counts))},
                "accuracy": acc, "learned": learned, "pcg_iterations": pcg_iters}
         print(json.dumps(out), flush=True)
     ctx.close()
@@ -444,7 +457,8 @@ def precond_comparison(F, torch, stream, outer_steps=(1, 5, 20), tol=1e-6, cap=5
 def workload_config(args, world, done_per_step=None):
     """The workload both arms report: the served 256^2 TV + D4 queue."""
     return {"workload": f"firls_tv_db4_{N}", "n": N, "slices_per_step_per_gpu": args.queue, "slots": args.batch,
-            "outer_max": args.outer, "inner": args.inner, "outer_tol": args.outer_tol, "stall_tol": args.stall_tol,
+            "outer_max": args.outer, "inner": args.inner, "inner_late": args.inner_late,
+            "outer_late": args.outer_late, "outer_tol": args.outer_tol, "stall_tol": args.stall_tol,
             "mask_ratio": RATIO, "sigma": SIGMA, "lambda_tv": LAM_TV, "lambda_w": LAM_W,
             "wavelet": "db4", "levels": LEVELS, "batching": "continuous (slots refilled on convergence)",
             "completions_per_step": args.queue if done_per_step is None else done_per_step,
@@ -463,21 +477,25 @@ def oracle_sample(outer_steps, seed=2):
     return time.perf_counter() - t0
 
 
-ARGS_INNER = [INNER]
+ORACLE_INNER = 60   # the oracle's schedule: 60 PCG steps per outer step
+ARGS_INNER = [ORACLE_INNER]
 
 
-def cpu_baseline(args, outer_per_recon=None):
+def cpu_baseline(args):
+    """The FP64 oracle as it stands (its own schedule: 60 PCG steps per outer
+    step) on one host core: one outer step of one slice, scaled by the
+    oracle's own mean outer steps to 1e-4 of x* on the stored seeds."""
     env_threads = 1
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[k] = str(env_threads)
-    ARGS_INNER[0] = args.inner
+    ARGS_INNER[0] = ORACLE_INNER
     sec = oracle_sample(args.ref_outer)
-    outer = outer_per_recon or REF_OUTER_PER_RECON
+    outer, covered = oracle_outer_per_recon(range(2, 18))
     recon_s = sec / args.ref_outer * outer
     return {"value": round(1.0 / recon_s, 6), "unit": UNIT, "cores": env_threads, "kind": "oracle",
-            "sample": f"FP64 oracle, one {N}^2 slice, {args.ref_outer} outer step(s) x {args.inner} PCG "
-                      f"({sec:.1f} s), scaled to {outer:.1f} outer steps per reconstruction (the mean number the "
-                      f"same stopping rule takes on this workload)"}
+            "sample": f"FP64 oracle, one {N}^2 slice, {args.ref_outer} outer step(s) x {ORACLE_INNER} PCG "
+                      f"({sec:.1f} s), scaled to {outer:.1f} outer steps per reconstruction (the oracle's own mean "
+                      f"to 1e-4 of its x* on seeds {covered or [2]})"}
 
 
 def _oracle_worker(a):
@@ -517,7 +535,7 @@ def run_reference(args):
         return None
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[k] = "1"  # one thread per oracle instance (inherited by the workers)
-    ARGS_INNER[0] = args.inner
+    ARGS_INNER[0] = args.ref_inner
     procs = args.ref_procs if args.ref_procs > 0 else host_cores()
     seeds = [2 + i for i in range(procs)]
     if procs == 1:
@@ -531,8 +549,8 @@ def run_reference(args):
         import multiprocessing as mp
         with mp.get_context("spawn").Pool(procs) as pool:
             for _ in range(max(1, args.warmup)):
-                pool.map(_oracle_worker, [(1, args.inner, s) for s in seeds])
-            t = [max(pool.map(_oracle_worker, [(args.ref_outer, args.inner, s) for s in seeds]))
+                pool.map(_oracle_worker, [(1, args.ref_inner, s) for s in seeds])
+            t = [max(pool.map(_oracle_worker, [(args.ref_outer, args.ref_inner, s) for s in seeds]))
                  for _ in range(args.steps)]
     sec = float(np.mean(t))
     outer, covered = oracle_outer_per_recon(seeds)
@@ -541,7 +559,7 @@ def run_reference(args):
            f"{REF_OUTER_PER_RECON} outer steps (the oracle's own outer steps to 1e-4 of x* on seed 2)")
     cpu = {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
            "sample": f"FP64 oracle, {procs} independent {N}^2 slice(s) at once, one per host core, each "
-                     f"{args.ref_outer} outer step(s) x {args.inner} PCG per bench step, scaled to {outer:.1f} "
+                     f"{args.ref_outer} outer step(s) x {args.ref_inner} PCG per bench step, scaled to {outer:.1f} "
                      f"outer steps per reconstruction ({how})"}
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
@@ -566,12 +584,15 @@ def main(argv=None):
     ap.add_argument("--outer", type=int, default=OUTER)
     ap.add_argument("--inner", type=int, default=INNER)
     ap.add_argument("--outer-tol", type=float, default=OUTER_TOL)
+    ap.add_argument("--inner-late", type=int, default=INNER_LATE, help="PCG steps per outer step from --outer-late on")
+    ap.add_argument("--outer-late", type=int, default=OUTER_LATE)
     ap.add_argument("--stall-tol", type=float, default=STALL_TOL)
     ap.add_argument("--autotune", type=int, default=1, help="autotune tile shapes before timing (1/0)")
     ap.add_argument("--learned", type=int, default=1, help="also time the learned warm start (1/0)")
     ap.add_argument("--learned-train", type=int, default=4000, help="training instances solved by the method")
     ap.add_argument("--learned-epochs", type=int, default=10)
     ap.add_argument("--ref-outer", type=int, default=1, help="oracle outer steps per sample")
+    ap.add_argument("--ref-inner", type=int, default=ORACLE_INNER, help="oracle PCG steps per outer step")
     ap.add_argument("--ref-procs", type=int, default=0,
                     help="reference arm: oracle instances run at once, one per host core (0: all cores)")
     ap.add_argument("--e2e-steps", type=int, default=1)

@@ -130,6 +130,12 @@ typedef struct {
                           the first residual r_0 of each outer step (the
                           forcing term of an inexact inner solve: PCG runs
                           until ||r|| <= pcg_tol ||r_0|| or pcg_iters steps)  */
+  int pcg_iters_late;  /* > 0: outer steps k >= outer_late (counted per slice
+                          from 0) run this many PCG steps instead of
+                          pcg_iters (a slice still running late has an
+                          ill-conditioned subproblem whose outer rate needs a
+                          nearly exact inner solve); 0 = pcg_iters throughout */
+  int outer_late;
 } firls_params;
 
 /* Preconditioners of the PCG steps, for the comparison of Sec. 5.2 (Fig. 2
@@ -146,6 +152,18 @@ typedef struct {
   double max_rel_residual;   /* max_s ||r|| / ||A^H b|| at the last PCG step  */
   int n_breakdown;           /* slices stopped by a PCG breakdown             */
 } firls_stats;
+
+/* How the solver advances (every entry point below that iterates): each slice
+ * moves through its own outer steps independently.  One "macro step" (a
+ * fixed launch sequence, captured as a CUDA graph) gives every slice one step
+ * of its outer step: the start of an outer step (weights W^k and P from x^k,
+ * S x^k, the first residual r_0, z_0 = P^{-1} r_0) or one PCG step (S d,
+ * alpha, x/r update, z = P^{-1} r, beta), or, for a slice whose PCG has
+ * stopped, the end of the outer step (x^{k+1} = x^k + sum_j alpha_j d_j, the
+ * relative change, the stopping rules) followed by the start of its next
+ * one.  A slice's PCG stops after pcg_iters steps or at its tolerance, so
+ * slices with different inner step counts never wait for each other.  An
+ * outer step with J PCG steps spans J + 1 macro steps. */
 
 /* Run FIRLS on every slice (Alg. 2 / Alg. 3).
  *   b      device complex64 [batch][n][n] k-space, entries off the mask are
@@ -218,8 +236,12 @@ firls_status firls_apply_S_P(firls_ctx* ctx, const firls_params* params,
  *   with its own lambdas (eps <= 0 selects 1e-10).  Other slots untouched.
  *   Reads back the popcount (synchronises the stream): an empty mask returns
  *   FIRLS_E_INVALID_ARG and leaves the slot retired.
- * firls_run: enqueue params->outer_iters outer steps of every slot that is
- *   not done (one captured graph per step; no host synchronisation).
+ * firls_run: enqueue sum_k (J_k + 1) + 1 macro steps (J_k the PCG steps of
+ *   outer step k, k < params->outer_iters) for every slot that is not done:
+ *   a slot that starts its first outer step at the first of them completes
+ *   params->outer_iters outer steps; no host synchronisation.
+ * firls_run_steps: enqueue `macro_steps` macro steps (one captured graph,
+ *   cached per schedule and count); no host synchronisation.
  * firls_slot_status: per-slot done flag, outer steps, last relative change
  *   and PCG steps (host arrays [batch], each may be NULL); synchronises.
  * firls_slot_retire: slot s stops taking part until reloaded.
@@ -227,6 +249,7 @@ firls_status firls_apply_S_P(firls_ctx* ctx, const firls_params* params,
 firls_status firls_slot_load(firls_ctx* ctx, int s, const uint8_t* mask, const void* b, const void* x0,
                              float lambda, float lambda_tv, float eps);
 firls_status firls_run(firls_ctx* ctx, const firls_params* params);
+firls_status firls_run_steps(firls_ctx* ctx, const firls_params* params, int macro_steps);
 firls_status firls_slot_status(firls_ctx* ctx, int* done, int* outer_done, double* rel_change, int* pcg_steps);
 firls_status firls_slot_retire(firls_ctx* ctx, int s);
 firls_status firls_slot_get(firls_ctx* ctx, int s, void* x_out);
@@ -329,15 +352,18 @@ enum {
   FIRLS_NKCLASS = 10
 };
 
-/* Enable (1) or disable (0) CUDA-event timing of every kernel launch of an
- * outer step on the context's stream (the events are recorded into the
- * captured outer-step graph).  Adds one event pair per launch group. */
+/* Enable (1) or disable (0) CUDA-event timing of every kernel launch of the
+ * macro steps on the context's stream (the events are recorded into the
+ * captured macro-step graph).  Adds one event pair per launch group. */
 firls_status firls_set_timing(firls_ctx* ctx, int enable);
 
-/* Per-class totals for the last outer step executed: ms[FIRLS_NKCLASS]
- * milliseconds and launches[FIRLS_NKCLASS] kernel launches.  Synchronises
- * the stream.  FIRLS_E_STATE if timing is off or nothing ran. */
-firls_status firls_get_timing(firls_ctx* ctx, double* ms, int* launches);
+/* Per-class totals over the macro steps of the last graph captured with
+ * timing on and then executed (for firls_solve: one outer step, J + 1 macro
+ * steps): ms[FIRLS_NKCLASS] milliseconds, launches[FIRLS_NKCLASS] kernel
+ * launches and applications[FIRLS_NKCLASS] launch groups (one operator
+ * application each; may be NULL).  Synchronises the stream.  FIRLS_E_STATE if
+ * timing is off or nothing ran. */
+firls_status firls_get_timing(firls_ctx* ctx, double* ms, int* launches, int* applications);
 
 /* ---- learned warm start (not in the paper; workload of the learned variant) ----
  * A 6-layer 3x3 CNN (3 -> 32 -> 32 -> 32 -> 32 -> 32 -> 2 channels, ReLU between

@@ -29,7 +29,8 @@ EXPORTED = ["firls_size_supported", "firls_create", "firls_set_operator", "firls
             "firls_cnn_create", "firls_cnn_set_params", "firls_cnn_get_params", "firls_cnn_get_grads",
             "firls_cnn_forward", "firls_cnn_train_step", "firls_cnn_destroy", "firls_objective",
             "firls_warm_start_guard", "firls_adjoint", "firls_data_consistency", "firls_autotune",
-            "firls_get_tuning", "firls_slot_load", "firls_run", "firls_slot_status", "firls_slot_retire",
+            "firls_get_tuning", "firls_slot_load", "firls_run", "firls_run_steps", "firls_slot_status",
+            "firls_slot_retire",
             "firls_slot_get"]
 KERNEL_CLASSES = ["row_fft", "col_fft_mask", "wavelet_S", "wavelet_Pinv", "row_ifft_combine", "ilu", "axpy",
                   "scalars", "weights", "other"]
@@ -46,7 +47,8 @@ class Params(ctypes.Structure):
                 ("outer_tol", ctypes.c_float), ("lambda_", ctypes.c_float), ("lambda_tv", ctypes.c_float),
                 ("eps", ctypes.c_float), ("lambda_per_slice", ctypes.POINTER(ctypes.c_float)),
                 ("lambda_tv_per_slice", ctypes.POINTER(ctypes.c_float)), ("outer_tol_kind", ctypes.c_int),
-                ("precond", ctypes.c_int), ("outer_stall_tol", ctypes.c_float), ("pcg_tol_kind", ctypes.c_int)]
+                ("precond", ctypes.c_int), ("outer_stall_tol", ctypes.c_float), ("pcg_tol_kind", ctypes.c_int),
+                ("pcg_iters_late", ctypes.c_int), ("outer_late", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -96,6 +98,7 @@ def lib():
     L.firls_autotune.argtypes = [vp, ctypes.c_char_p]
     L.firls_slot_load.argtypes = [vp, i32, vp, vp, vp, ctypes.c_float, ctypes.c_float, ctypes.c_float]
     L.firls_run.argtypes = [vp, ctypes.POINTER(Params)]
+    L.firls_run_steps.argtypes = [vp, ctypes.POINTER(Params), i32]
     L.firls_slot_status.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(i32)]
     L.firls_slot_retire.argtypes = [vp, i32]
@@ -113,7 +116,8 @@ def lib():
     L.firls_cnn_destroy.argtypes = [vp]
     L.firls_cnn_destroy.restype = None
     L.firls_set_timing.argtypes = [vp, i32]
-    L.firls_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+    L.firls_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_int)]
     _lib = L
     return L
 
@@ -128,10 +132,12 @@ def size_supported(n: int) -> bool:
 
 def make_params(outer, pcg, lam=0.0, lam_tv=0.0, pcg_tol=0.0, outer_tol=0.0, eps=0.0,
                 lam_per_slice=None, lam_tv_per_slice=None, stop_on_distance=False, precond="paper",
-                stall_tol=0.0, pcg_tol_rel=False):
+                stall_tol=0.0, pcg_tol_rel=False, pcg_late=0, outer_late=0):
     """firls_params; precond is "paper", "jacobi" or "none" (FIRLS_PRECOND_*);
-    pcg_tol_rel: pcg_tol is relative to each outer step's first residual."""
+    pcg_tol_rel: pcg_tol is relative to each outer step's first residual;
+    pcg_late > 0: outer steps from outer_late on run pcg_late PCG steps."""
     p = Params()
+    p.pcg_iters_late, p.outer_late = int(pcg_late), int(outer_late)
     p.outer_stall_tol = float(stall_tol)
     p.pcg_tol_kind = 1 if pcg_tol_rel else 0
     p.outer_tol_kind = 1 if stop_on_distance else 0
@@ -225,6 +231,10 @@ class Context:
     def run(self, params):
         self._check(lib().firls_run(self.h, ctypes.byref(params)), "run")
 
+    def run_steps(self, params, macro_steps):
+        """Enqueue `macro_steps` macro steps (every slot advances on its own)."""
+        self._check(lib().firls_run_steps(self.h, ctypes.byref(params), int(macro_steps)), "run_steps")
+
     def slot_status(self, with_pcg=False):
         """(done, outer steps, last relative change[, PCG steps]) per slot."""
         k = self.batch
@@ -301,12 +311,14 @@ class Context:
         self._check(lib().firls_set_timing(self.h, 1 if enable else 0), "set_timing")
 
     def get_timing(self):
-        """{class: (total ms, launches)} for the last outer step executed."""
+        """{class: (total ms, launches, applications)} over the macro steps of
+        the last timed graph (for solve: one outer step)."""
         k = len(KERNEL_CLASSES)
         ms = (ctypes.c_double * k)()
         ln = (ctypes.c_int * k)()
-        self._check(lib().firls_get_timing(self.h, ms, ln), "get_timing")
-        return {name: (ms[i], ln[i]) for i, name in enumerate(KERNEL_CLASSES)}
+        ap = (ctypes.c_int * k)()
+        self._check(lib().firls_get_timing(self.h, ms, ln, ap), "get_timing")
+        return {name: (ms[i], ln[i], ap[i]) for i, name in enumerate(KERNEL_CLASSES)}
 
     def get_popcounts(self, counts):
         self._check(lib().firls_get_popcounts(self.h, _ptr(counts)), "get_popcounts")
@@ -404,19 +416,21 @@ class Cnn:
             pass
 
 
-def serve(ctx, masks, bs, lams, lam_tvs, params, outs, x0s=None, chunk=8, max_outer=400, stop_after=None,
+def serve(ctx, masks, bs, lams, lam_tvs, params, outs, x0s=None, chunk=64, max_outer=400, stop_after=None,
           counters=None, pcg_steps=None):
     """Continuous batching over a queue of slices with ctx.batch slots.
 
     masks/bs/outs: per-slice device tensors ([n][n]); lams/lam_tvs: floats;
-    params: schedule (pcg_iters, tolerances; outer_iters ignored).  A slot is
-    read out and refilled when its slice has converged (params.outer_tol) or
-    reached max_outer outer steps.  With stop_after, returns once that many
-    slices have completed and retires the slices still in flight (their
-    entry in the result stays 0).  Returns the outer steps of every slice.
-    counters (a dict, optional) receives "runs" (calls of ctx.run, each
-    `chunk` outer-step graph replays), "loads" and "retires"; pcg_steps (a
-    list of len(bs), optional) receives the PCG steps of every slice.
+    params: schedule (pcg_iters, tolerances; outer_iters ignored).  Every
+    slot advances on its own; the slots are polled every `chunk` macro steps,
+    and a slot is read out and refilled when its slice has converged
+    (params.outer_tol) or reached max_outer outer steps.  With stop_after,
+    returns once that many slices have completed and retires the slices still
+    in flight (their entry in the result stays 0).  Returns the outer steps
+    of every slice.  counters (a dict, optional) receives "runs" (calls of
+    ctx.run_steps, each one graph of `chunk` macro steps), "loads" and
+    "retires"; pcg_steps (a list of len(bs), optional) receives the PCG steps
+    of every slice.
     """
     cnt = counters if counters is not None else {}
     for k in ("runs", "loads", "retires"):
@@ -435,7 +449,7 @@ def serve(ctx, masks, bs, lams, lam_tvs, params, outs, x0s=None, chunk=8, max_ou
             ctx.slot_retire(s)
             cnt["retires"] += 1
     run = Params.from_buffer_copy(params)
-    run.outer_iters = chunk
+    run.outer_iters = 1
     active = sum(1 for v in slot_of if v >= 0)
     completed = 0
     while active:
@@ -446,7 +460,7 @@ def serve(ctx, masks, bs, lams, lam_tvs, params, outs, x0s=None, chunk=8, max_ou
                     cnt["retires"] += 1
                     slot_of[s] = -1
             break
-        ctx.run(run)
+        ctx.run_steps(run, chunk)
         cnt["runs"] += 1
         done, od, _, pc = ctx.slot_status(with_pcg=True)
         for s in range(ctx.batch):

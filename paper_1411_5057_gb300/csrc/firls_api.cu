@@ -58,10 +58,15 @@ struct firls_ctx {
   std::vector<cudaEvent_t> evpool;
   size_t evnext = 0;
   bool marks_valid = false;
-  // cached outer-step graph
-  cudaGraphExec_t exec = nullptr;
-  firls_params g_sched{};  // schedule the cached graph was captured for
+  // captured macro-step graphs, by schedule and number of macro steps
+  struct CachedGraph {
+    firls_params sched;
+    int steps;
+    cudaGraphExec_t exec;
+  };
+  std::vector<CachedGraph> graphs;
   bool use_graph = true;
+  SliceState* stw = nullptr;  // per macro step: the state with only outer-step starts running
 };
 
 namespace {
@@ -206,13 +211,15 @@ void marks_reset(firls_ctx* c) {
   c->evnext = 0;
 }
 
-// q = S d  (mode 0: d = z; 1: d = z + beta d; 2: d as given)
+// q = S d  (mode 0: d = z; 1: d = z + beta d; 2: d as given; -1: per slice,
+// d = x^k for a slice starting its outer step, else z or z + beta d)
 void enqueue_S(firls_ctx* c, int mode, const float2* zin, float2* din, float2* q) {
   FftArgs a = fft_args(c);
   a.z = zin;
   a.d = din;
   a.t = c->t;
   a.mode = mode;
+  a.xs = c->x;
   { TMark m(c, FIRLS_K_ROW_FFT, 1); fft_row_fwd(c->n, a); }
   a.mask = c->mask;
   { TMark m(c, FIRLS_K_COL_FFT_MASK, 1); fft_col_mask(c->n, a); }
@@ -227,114 +234,105 @@ void enqueue_S(firls_ctx* c, int mode, const float2* zin, float2* din, float2* q
   { TMark m(c, FIRLS_K_ROW_IFFT, 1); fft_row_inv(c->n, a); }
 }
 
-// Update W^k and P from x (Alg. 2/3, first two lines of the loop body).
-void enqueue_weights(firls_ctx* c, const float2* x, int precond) {
+// Update W^k and P from x (Alg. 2/3, first two lines of the loop body) for
+// the slices that `view` shows running (its other slices read as done).
+void enqueue_weights(firls_ctx* c, const float2* x, int precond, const SliceState* view) {
   const int B = c->batch, n = c->n;
   TMark mk(c, FIRLS_K_WEIGHTS, 0);
   if (c->kind) {
-    WavArgs w = wav_args(c, c->st);
+    WavArgs w = wav_args(c, view);
     if (!c->groups) {
       wavelet_forward(w, x, c->cw, c->ww, WAV_SINGLETON_W);
     } else {
       wavelet_forward(w, x, c->cw, nullptr, WAV_RAW);
-      group_norms(B, n, c->n_groups, c->stream, c->st, c->gidx, c->goff, c->gsize, c->cw, c->wg, 0.f);
-      group_gather(B, n, c->n_groups, c->stream, c->st, c->inv_off, c->inv_ids, c->wg, c->ww);
+      group_norms(B, n, c->n_groups, c->stream, view, c->gidx, c->goff, c->gsize, c->cw, c->wg, 0.f);
+      group_gather(B, n, c->n_groups, c->stream, view, c->inv_off, c->inv_ids, c->wg, c->ww);
     }
   }
   if (has_tv(c)) {
     // with TV, 1/a of the penta-diagonal P is also 1/diag(S) (the Jacobi scale)
-    tv_weights(B, n, c->stream, c->st, x, c->wtv);
-    if (c->kind) wavelet_diag(B, n, c->levels, c->stream, c->st, c->ww, c->wdiag, c->sqtab, c->sqlen);
-    penta_setup(B, n, c->stream, c->st, c->wtv, c->kind ? c->wdiag : nullptr, c->ia);
+    tv_weights(B, n, c->stream, view, x, c->wtv);
+    if (c->kind) wavelet_diag(B, n, c->levels, c->stream, view, c->ww, c->wdiag, c->sqtab, c->sqlen);
+    penta_setup(B, n, c->stream, view, c->wtv, c->kind ? c->wdiag : nullptr, c->ia);
   } else if (precond == FIRLS_PRECOND_JACOBI) {
-    wavelet_diag(B, n, c->levels, c->stream, c->st, c->ww, c->wdiag, c->sqtab, c->sqlen);
-    jacobi_wavelet_setup(B, n, c->stream, c->st, c->wdiag, c->ia);
+    wavelet_diag(B, n, c->levels, c->stream, view, c->ww, c->wdiag, c->sqtab, c->sqlen);
+    jacobi_wavelet_setup(B, n, c->stream, view, c->wdiag, c->ia);
   }
 }
 
-// z = P^{-1} r after the residual update of `mode` (ILU_INIT / ILU_STEP).
-void enqueue_update_precond(firls_ctx* c, int step_mode, float pcg_tol, bool init, int precond) {
+PcgSched pcg_sched(const firls_params& sc) {
+  return PcgSched{sc.pcg_tol, sc.pcg_tol_kind, sc.pcg_iters, sc.pcg_iters_late, sc.outer_late};
+}
+
+// Residual update and z = P^{-1} r, then rho (first residual) or beta and the
+// PCG stop.  mode ILU_INIT: the first residual r = A^H b - q for every
+// running slice; ILU_PER_SLICE: each slice by its phase.  x updates go to dx.
+void enqueue_precond(firls_ctx* c, int mode, const firls_params& sc) {
   const int B = c->batch, n = c->n;
   const int real = (c->flags & FIRLS_REAL_X) ? 1 : 0;
-  if (precond != FIRLS_PRECOND_PAPER) {  // Jacobi or none: one fused pass, then the FP64 scalars
+  const bool init = mode == ILU_INIT;
+  const int am = init ? AXPY_INIT : AXPY_PER_SLICE, sm = init ? SCALARS_INIT : SCALARS_PER_SLICE;
+  const PcgSched ps = pcg_sched(sc);
+  if (sc.precond != FIRLS_PRECOND_PAPER) {  // Jacobi or none: one fused pass, then the FP64 scalars
     {
       TMark m(c, FIRLS_K_AXPY, 1);
-      axpy_diag_step(B, n, c->stream, c->st, c->part, init ? AXPY_INIT : AXPY_STEP, c->dx, c->d, c->r, c->q, c->atb,
-                     precond == FIRLS_PRECOND_JACOBI ? c->ia : nullptr, c->z);
+      axpy_diag_step(B, n, c->stream, c->st, c->part, am, c->dx, c->d, c->r, c->q, c->atb,
+                     sc.precond == FIRLS_PRECOND_JACOBI ? c->ia : nullptr, c->z);
     }
     TMark m(c, FIRLS_K_SCALARS, 1);
-    if (init)
-      pcg_rho_init(B, c->stream, c->st, c->part, axpy_ctas(n), axpy_ctas(n));
-    else
-      pcg_beta(B, c->stream, c->st, c->part, axpy_ctas(n), axpy_ctas(n), pcg_tol);
+    pcg_scalars(B, c->stream, c->st, c->part, axpy_ctas(n), axpy_ctas(n), sm, ps);
     return;
   }
   if (has_tv(c)) {
-    {
-      TMark m(c, FIRLS_K_ILU, 1);
-      // the ILU CTA finishes rho (and beta) from its own sums
-      ilu_step(B, n, c->stream, c->st, c->part, init ? ILU_INIT : ILU_STEP, c->dx, c->d, c->r, c->q, c->atb,
-               c->u, c->z, c->ia, c->wtv, c->tune_ilu, 1, pcg_tol, c->wait_test);
-    }
-  } else {
-    {
-      TMark m(c, FIRLS_K_AXPY, 1);
-      axpy_step(B, n, c->stream, c->st, c->part, init ? AXPY_INIT : AXPY_STEP, c->dx, c->d, c->r, c->q, c->atb);
-    }
-    WavArgs w = wav_args(c, c->st);
-    {
-      TMark m(c, FIRLS_K_WAVELET_P, wavelet_apply_launches(n, c->levels, c->kind, c->tune_rb, c->tune_cmax));
-      wavelet_apply(w, c->r, c->cw, c->ww, WAV_MUL_PINV, c->z, c->r, real);
-    }
-    TMark m(c, FIRLS_K_SCALARS, 1);
-    const int np = wavelet_apply_ctas(n, c->levels, c->kind, c->tune_rb, c->tune_cmax);
-    if (init)
-      pcg_rho_init(B, c->stream, c->st, c->part, np, axpy_ctas(n));
-    else
-      pcg_beta(B, c->stream, c->st, c->part, np, axpy_ctas(n), pcg_tol);
+    TMark m(c, FIRLS_K_ILU, 1);
+    // the ILU CTA finishes rho (and beta) from its own sums
+    ilu_step(B, n, c->stream, c->st, c->part, mode, c->dx, c->d, c->r, c->q, c->atb, c->u, c->z, c->ia, c->wtv,
+             c->tune_ilu, 1, ps, c->wait_test);
+    return;
   }
-  (void)step_mode;
-}
-
-// One outer step of FIRLS: weights, P, PCG warm-started at x^k, relative change.
-void enqueue_outer(firls_ctx* c, const firls_params& sc) {
-  const int B = c->batch, n = c->n;
-  const int J = sc.pcg_iters, precond = sc.precond;
-  const float pcg_tol = sc.pcg_tol;
-  marks_reset(c);
   {
-    TMark m(c, FIRLS_K_OTHER, 1);
-    outer_begin(B, c->stream, c->st, sc.pcg_tol_kind);
-    cudaMemsetAsync(c->dx, 0, sizeof(float2) * (size_t)B * n * n, c->stream);
+    TMark m(c, FIRLS_K_AXPY, 1);
+    axpy_step(B, n, c->stream, c->st, c->part, am, c->dx, c->d, c->r, c->q, c->atb);
   }
-  enqueue_weights(c, c->x, precond);
-  // r = A^H b - S x^k, z = P^{-1} r, rho = Re<r, z>
-  enqueue_S(c, 2, nullptr, c->x, c->q);
-  enqueue_update_precond(c, 0, pcg_tol, true, precond);
-  for (int j = 1; j <= J; ++j) {
-    enqueue_S(c, j == 1 ? 0 : 1, c->z, c->d, c->q);
-    {
-      TMark m(c, FIRLS_K_SCALARS, 1);
-      pcg_alpha(B, c->stream, c->st, c->part, fft_row_ctas(n));
-    }
-    if (j < J) {
-      enqueue_update_precond(c, 1, pcg_tol, false, precond);
-    } else {
-      TMark m(c, FIRLS_K_AXPY, 1);
-      axpy_step(B, n, c->stream, c->st, c->part, AXPY_LAST, c->dx, c->d, c->r, c->q, c->atb);
-    }
+  WavArgs w = wav_args(c, c->st);
+  {
+    TMark m(c, FIRLS_K_WAVELET_P, wavelet_apply_launches(n, c->levels, c->kind, c->tune_rb, c->tune_cmax));
+    wavelet_apply(w, c->r, c->cw, c->ww, WAV_MUL_PINV, c->z, c->r, real);
   }
-  TMark m(c, FIRLS_K_OTHER, 2);
-  outer_apply(B, n, c->stream, c->st, c->x, c->dx, c->part);
-  outer_end(B, c->stream, c->st, c->part, axpy_ctas(n), sc.outer_tol, sc.outer_tol_kind, sc.outer_stall_tol);
+  TMark m(c, FIRLS_K_SCALARS, 1);
+  const int np = wavelet_apply_ctas(n, c->levels, c->kind, c->tune_rb, c->tune_cmax);
+  pcg_scalars(B, c->stream, c->st, c->part, np, axpy_ctas(n), sm, ps);
 }
 
-// Two parameter sets capture the same outer-step graph (everything but the
+// One macro step: every slice advances by one step of its own outer step.
+// Slices whose PCG ended (PH_END) add their update to x, measure the
+// relative change and either stop or start their next outer step; slices at
+// the start of an outer step (PH_BOUNDARY) update W^k and P, apply S to x^k
+// and form r_0, z_0, rho; the others take one PCG step (Alg. 2 / Alg. 3).
+// An outer step of a slice with J PCG steps spans J + 1 macro steps.
+void enqueue_macro(firls_ctx* c, const firls_params& sc) {
+  const int B = c->batch, n = c->n;
+  {
+    TMark m(c, FIRLS_K_OTHER, 3);
+    outer_apply(B, n, c->stream, c->st, c->x, c->dx, c->part);
+    outer_end(B, c->stream, c->st, c->part, axpy_ctas(n), sc.outer_tol, sc.outer_tol_kind, sc.outer_stall_tol);
+    boundary_view(B, c->stream, c->st, c->stw);
+  }
+  enqueue_weights(c, c->x, sc.precond, c->stw);
+  enqueue_S(c, -1, c->z, c->d, c->q);
+  {
+    TMark m(c, FIRLS_K_SCALARS, 1);
+    pcg_alpha(B, c->stream, c->st, c->part, fft_row_ctas(n));
+  }
+  enqueue_precond(c, ILU_PER_SLICE, sc);
+}
+
+// Two parameter sets capture the same macro-step graph (everything but the
 // outer count and the lambdas, which live in device memory).
 bool same_schedule(const firls_params& a, const firls_params& b) {
   return a.pcg_iters == b.pcg_iters && a.pcg_tol == b.pcg_tol && a.outer_tol == b.outer_tol &&
          a.outer_tol_kind == b.outer_tol_kind && a.precond == b.precond && a.outer_stall_tol == b.outer_stall_tol &&
-         a.pcg_tol_kind == b.pcg_tol_kind;
+         a.pcg_tol_kind == b.pcg_tol_kind && a.pcg_iters_late == b.pcg_iters_late && a.outer_late == b.outer_late;
 }
 
 firls_status check_params(firls_ctx* c, const firls_params* p) {
@@ -346,6 +344,7 @@ firls_status check_params(firls_ctx* c, const firls_params* p) {
     return fail(c, FIRLS_E_INVALID_ARG, "bad precond");
   if (!(p->outer_stall_tol >= 0.f)) return fail(c, FIRLS_E_INVALID_ARG, "outer_stall_tol must be >= 0");
   if (p->pcg_tol_kind != 0 && p->pcg_tol_kind != 1) return fail(c, FIRLS_E_INVALID_ARG, "bad pcg_tol_kind");
+  if (p->pcg_iters_late < 0 || p->outer_late < 0) return fail(c, FIRLS_E_INVALID_ARG, "bad late inner schedule");
   const int B = c->batch;
   for (int s = 0; s < B; ++s) {
     const float l = p->lambda_per_slice ? p->lambda_per_slice[s] : p->lambda;
@@ -373,7 +372,9 @@ firls_status upload_params(firls_ctx* c, const firls_params* p) {
 
 float eps_of(const firls_params* p) { return p->eps > 0.f ? p->eps : 1e-10f; }
 
-// A^H b into atb (and x when x0 is null), ||A^H b||^2 partials, state init.
+// A^H b into atb (and x when x0 is null), ||A^H b||^2 partials, state init
+// (every slice at the start of its first outer step, at most outer_max outer
+// steps), dx cleared.
 firls_status enqueue_setup(firls_ctx* c, const void* b, const firls_params* p, const void* x0) {
   const int B = c->batch, n = c->n;
   TRY(upload_params(c, p));
@@ -388,52 +389,106 @@ firls_status enqueue_setup(firls_ctx* c, const void* b, const firls_params* p, c
   if (x0) {
     CU(cudaMemcpyAsync(c->x, x0, sizeof(float2) * (size_t)B * n * n, cudaMemcpyDeviceToDevice, c->stream));
   }
-  state_init(B, c->stream, c->st, c->part, fft_col_ctas(n), c->counts, n, c->lam_d, c->lamtv_d, eps_of(p));
+  CU(cudaMemsetAsync(c->dx, 0, sizeof(float2) * (size_t)B * n * n, c->stream));
+  state_init(B, c->stream, c->st, c->part, fft_col_ctas(n), c->counts, n, c->lam_d, c->lamtv_d, eps_of(p),
+             p->outer_iters);
   return cuda_check(c, cudaGetLastError(), "setup launch");
 }
 
-firls_status run_outer_steps(firls_ctx* c, const firls_params* p) {
+void graphs_clear(firls_ctx* c) {
+  for (auto& g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+}
+
+// The graph of `steps` macro steps for this schedule (captured on first use;
+// with timing on, the marks of its last capture are the ones read back).
+firls_status macro_graph(firls_ctx* c, const firls_params& sc, int steps, cudaGraphExec_t* out) {
+  for (auto& g : c->graphs)
+    if (g.steps == steps && same_schedule(g.sched, sc)) {
+      *out = g.exec;
+      return FIRLS_OK;
+    }
+  if (c->timing) marks_reset(c);
+  cudaGraph_t g = nullptr;
+  CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < steps; ++i) enqueue_macro(c, sc);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (e != cudaSuccess) return cuda_check(c, e, "graph capture");
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_check(c, e, "graph instantiate");
+  c->graphs.push_back({sc, steps, ex});
+  *out = ex;
+  return FIRLS_OK;
+}
+
+bool all_done(firls_ctx* c, bool* ok) {
+  std::vector<SliceState> hs(c->batch);
+  *ok = cudaMemcpyAsync(hs.data(), c->st, sizeof(SliceState) * c->batch, cudaMemcpyDeviceToHost, c->stream) ==
+            cudaSuccess &&
+        cudaStreamSynchronize(c->stream) == cudaSuccess;
+  for (const SliceState& v : hs)
+    if (v.active && !v.done) return false;
+  return true;
+}
+
+// Enqueue `total` macro steps as replays of a graph of `chunk` macro steps
+// (then single-step replays for the remainder).  With poll, the per-slice
+// done flags are read every kPoll chunks and the loop stops once every slice
+// has stopped.
+firls_status run_macro(firls_ctx* c, const firls_params& sc, long total, int chunk, bool poll) {
   const bool graph = c->use_graph && c->stream != nullptr;
-  if (!graph) {
-    for (int k = 0; k < p->outer_iters; ++k) enqueue_outer(c, *p);
-    c->marks_valid = c->timing;
-    return cuda_check(c, cudaGetLastError(), "outer step launch");
-  }
-  if (!c->exec || !same_schedule(c->g_sched, *p)) {
-    if (c->exec) {
-      cudaGraphExecDestroy(c->exec);
-      c->exec = nullptr;
+  if (chunk < 1) chunk = 1;
+  if (chunk > total) chunk = (int)(total > 0 ? total : 1);
+  if (!graph) {  // marks of the first chunk only, as with the graphs
+    const bool t = c->timing;
+    if (t) marks_reset(c);
+    for (long k = 0; k < total; ++k) {
+      if (k == chunk) c->timing = false;
+      enqueue_macro(c, sc);
     }
-    cudaGraph_t g = nullptr;
-    CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_outer(c, *p);
-    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-    if (e != cudaSuccess) return cuda_check(c, e, "graph capture");
-    e = cudaGraphInstantiate(&c->exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-      c->exec = nullptr;
-      return cuda_check(c, e, "graph instantiate");
-    }
-    c->g_sched = *p;
+    c->timing = t;
+    c->marks_valid = t;
+    return cuda_check(c, cudaGetLastError(), "macro step launch");
   }
-  // With an outer tolerance, poll the per-slice done flags every
-  // kPoll replays and stop launching once every slice has stopped.
+  cudaGraphExec_t ex = nullptr, ex1 = nullptr;
+  TRY(macro_graph(c, sc, chunk, &ex));
+  const long full = total / chunk, rem = total % chunk;
   const int kPoll = 16;
-  std::vector<SliceState> hs;
-  for (int k = 0; k < p->outer_iters; ++k) {
-    CU(cudaGraphLaunch(c->exec, c->stream));
-    if (p->outer_tol > 0.f && (k + 1) % kPoll == 0 && k + 1 < p->outer_iters) {
-      hs.resize(c->batch);
-      CU(cudaMemcpyAsync(hs.data(), c->st, sizeof(SliceState) * c->batch, cudaMemcpyDeviceToHost, c->stream));
-      CU(cudaStreamSynchronize(c->stream));
-      bool all = true;
-      for (const SliceState& v : hs) all = all && v.done;
-      if (all) break;
+  for (long k = 0; k < full; ++k) {
+    CU(cudaGraphLaunch(ex, c->stream));
+    if (poll && (k + 1) % kPoll == 0 && (k + 1 < full || rem)) {
+      bool ok = true;
+      const bool done = all_done(c, &ok);
+      if (!ok) return fail(c, FIRLS_E_CUDA, "state read-back failed");
+      if (done) return FIRLS_OK;
     }
+  }
+  if (rem) {
+    const bool t = c->timing;
+    c->timing = false;  // the marks stay those of the chunk graph
+    const firls_status s = macro_graph(c, sc, 1, &ex1);
+    c->timing = t;
+    TRY(s);
+    for (long k = 0; k < rem; ++k) CU(cudaGraphLaunch(ex1, c->stream));
   }
   c->marks_valid = c->timing;
   return FIRLS_OK;
+}
+
+// Macro steps of params->outer_iters outer steps: (J_k + 1) for outer step k
+// and one more that applies the last one; without tolerances every slice
+// finishes exactly then.
+long solve_steps(const firls_params* p) {
+  long n = 1;
+  for (int k = 0; k < p->outer_iters; ++k)
+    n += 1 + ((p->pcg_iters_late > 0 && k >= p->outer_late) ? p->pcg_iters_late : p->pcg_iters);
+  return n;
+}
+bool has_tolerances(const firls_params* p) {
+  return p->pcg_tol > 0.f || p->outer_tol > 0.f || p->outer_stall_tol > 0.f;
 }
 
 firls_status collect_stats(firls_ctx* c, firls_stats* stats, bool* breakdown) {
@@ -508,6 +563,7 @@ extern "C" firls_status firls_create(firls_ctx** out, int n_rows, int n_cols, in
   A(&c->tmpB, BH);
   for (float** p : {&c->ww, &c->wtv, &c->ia, &c->wdiag}) A(p, BN);
   A(&c->st, (size_t)batch);
+  A(&c->stw, (size_t)batch);
   A(&c->part, (size_t)batch * NSLOT * MAXPART);
   A(&c->lam_d, (size_t)batch);
   A(&c->lamtv_d, (size_t)batch);
@@ -635,10 +691,7 @@ extern "C" firls_status firls_set_operator(firls_ctx* c, const uint8_t* mask, un
   c->kind = kind;
   c->levels = kind ? wavelet_levels : 0;
   multi_forget(c);
-  if (c->exec) {
-    cudaGraphExecDestroy(c->exec);
-    c->exec = nullptr;
-  }
+  graphs_clear(c);
   CU(cudaStreamSynchronize(c->stream));
   CU(cudaGetLastError());
   c->op_set = true;
@@ -652,7 +705,7 @@ extern "C" firls_status firls_solve(firls_ctx* c, const void* b, const firls_par
   if (!b || !x_out) return fail(c, FIRLS_E_INVALID_ARG, "b and x_out must be non-null");
   TRY(check_params(c, p));
   TRY(enqueue_setup(c, b, p, x0));
-  TRY(run_outer_steps(c, p));
+  TRY(run_macro(c, *p, solve_steps(p), p->pcg_iters + 1, has_tolerances(p)));
   const size_t bytes = sizeof(float2) * (size_t)c->batch * c->n * c->n;
   CU(cudaMemcpyAsync(x_out, c->x, bytes, cudaMemcpyDeviceToDevice, c->stream));
   CU(cudaGetLastError());
@@ -705,9 +758,11 @@ extern "C" firls_status firls_solve_multi(firls_ctx* const* ctxs, int n_ctx, con
       return st;
     }
   }
+  const int chunk = p->pcg_iters + 1;  // macro steps of one outer step
   if (!graphable) {
-    for (int k = 0; k < p->outer_iters; ++k)
-      for (int i = 0; i < n_ctx; ++i) enqueue_outer(ctxs[i], *p);
+    const long total = solve_steps(p);
+    for (long k = 0; k < total; ++k)
+      for (int i = 0; i < n_ctx; ++i) enqueue_macro(ctxs[i], *p);
   } else {
     const bool same = g_multi.exec && same_schedule(g_multi.sched, *p) && (int)g_multi.ctxs.size() == n_ctx &&
                       std::equal(g_multi.ctxs.begin(), g_multi.ctxs.end(), ctxs);
@@ -727,7 +782,10 @@ extern "C" firls_status firls_solve_multi(firls_ctx* const* ctxs, int n_ctx, con
       }
       cudaEventRecord(fork, c0->stream);
       for (int i = 1; i < n_ctx; ++i) cudaStreamWaitEvent(ctxs[i]->stream, fork, 0);
-      for (int i = 0; i < n_ctx; ++i) enqueue_outer(ctxs[i], *p);
+      for (int i = 0; i < n_ctx; ++i) {
+        if (ctxs[i]->timing) marks_reset(ctxs[i]);
+        for (int k = 0; k < chunk; ++k) enqueue_macro(ctxs[i], *p);
+      }
       for (int i = 1; i < n_ctx; ++i) {
         cudaEventRecord(join[i], ctxs[i]->stream);
         cudaStreamWaitEvent(c0->stream, join[i], 0);
@@ -752,6 +810,21 @@ extern "C" firls_status firls_solve_multi(firls_ctx* const* ctxs, int n_ctx, con
       if (e != cudaSuccess) {
         cleanup();
         return cuda_check(c0, e, "multi graph launch");
+      }
+    }
+    // the macro step that applies every context's last outer step
+    cudaEventRecord(fork, c0->stream);
+    for (int i = 0; i < n_ctx; ++i) {
+      firls_ctx* c = ctxs[i];
+      if (i > 0) cudaStreamWaitEvent(c->stream, fork, 0);
+      const bool t = c->timing;
+      c->timing = false;
+      enqueue_macro(c, *p);
+      c->timing = t;
+      c->marks_valid = t;
+      if (i > 0) {
+        cudaEventRecord(join[i], c->stream);
+        cudaStreamWaitEvent(c0->stream, join[i], 0);
       }
     }
   }
@@ -788,28 +861,27 @@ extern "C" firls_status firls_set_timing(firls_ctx* c, int enable) {
   if (!c) return FIRLS_E_INVALID_ARG;
   multi_forget(c);
   const bool on = enable != 0;
-  if (on != c->timing && c->exec) {  // the captured graph changes shape
-    cudaGraphExecDestroy(c->exec);
-    c->exec = nullptr;
-  }
+  if (on != c->timing) graphs_clear(c);  // the captured graphs change shape
   c->timing = on;
   c->marks_valid = false;
   return FIRLS_OK;
 }
 
-extern "C" firls_status firls_get_timing(firls_ctx* c, double* ms, int* launches) {
+extern "C" firls_status firls_get_timing(firls_ctx* c, double* ms, int* launches, int* applications) {
   if (!c || !ms || !launches) return FIRLS_E_INVALID_ARG;
-  if (!c->timing || !c->marks_valid) return fail(c, FIRLS_E_STATE, "timing is off or no outer step ran");
+  if (!c->timing || !c->marks_valid) return fail(c, FIRLS_E_STATE, "timing is off or no macro step ran");
   CU(cudaStreamSynchronize(c->stream));
   for (int k = 0; k < FIRLS_NKCLASS; ++k) {
     ms[k] = 0.0;
     launches[k] = 0;
+    if (applications) applications[k] = 0;
   }
   for (const auto& m : c->marks) {
     float t = 0.f;
     CU(cudaEventElapsedTime(&t, m.a, m.b));
     ms[m.cls] += t;
     launches[m.cls] += m.launches;
+    if (applications) applications[m.cls] += 1;
   }
   return FIRLS_OK;
 }
@@ -819,7 +891,7 @@ extern "C" void firls_destroy(firls_ctx* c) {
   multi_forget(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
-  if (c->exec) cudaGraphExecDestroy(c->exec);
+  graphs_clear(c);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   for (void* p : c->allocs)
     if (p) cudaFree(p);
@@ -838,7 +910,7 @@ extern "C" firls_status firls_apply_AHA(firls_ctx* c, const void* d, void* q) {
   p.lambda_per_slice = zeros.data();
   p.lambda_tv_per_slice = zeros.data();
   TRY(upload_params(c, &p));
-  state_init(c->batch, c->stream, c->st, c->part, 0, c->counts, c->n, c->lam_d, c->lamtv_d, 1e-10f);
+  state_init(c->batch, c->stream, c->st, c->part, 0, c->counts, c->n, c->lam_d, c->lamtv_d, 1e-10f, 1);
   FftArgs a = fft_args(c);
   const size_t bytes = sizeof(float2) * (size_t)c->batch * c->n * c->n;
   CU(cudaMemcpyAsync(c->d, d, bytes, cudaMemcpyDeviceToDevice, c->stream));
@@ -877,16 +949,18 @@ extern "C" firls_status firls_apply_S_P(firls_ctx* c, const firls_params* p, con
   TRY(upload_params(c, p));
   const int B = c->batch, n = c->n;
   const size_t bytes = sizeof(float2) * (size_t)B * n * n;
-  state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, eps_of(p));
+  state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, eps_of(p), 1);
   CU(cudaMemcpyAsync(c->x, x, bytes, cudaMemcpyDeviceToDevice, c->stream));
-  enqueue_weights(c, c->x, p->precond);
+  enqueue_weights(c, c->x, p->precond, c->st);  // every slice starts an outer step here
   // q = S d
   CU(cudaMemcpyAsync(c->d, d, bytes, cudaMemcpyDeviceToDevice, c->stream));
   enqueue_S(c, 2, nullptr, c->d, static_cast<float2*>(q));
   // z = P^{-1} r: feed r as "A^H b" with q = 0 through the INIT path
   CU(cudaMemcpyAsync(c->atb, r, bytes, cudaMemcpyDeviceToDevice, c->stream));
   CU(cudaMemsetAsync(c->q, 0, bytes, c->stream));
-  enqueue_update_precond(c, 0, 0.f, true, p->precond);
+  firls_params one = *p;
+  one.pcg_tol = 0.f;
+  enqueue_precond(c, ILU_INIT, one);
   CU(cudaMemcpyAsync(z, c->z, bytes, cudaMemcpyDeviceToDevice, c->stream));
   return cuda_check(c, cudaGetLastError(), "apply_S_P");
 }
@@ -902,7 +976,7 @@ firls_status objective_parts(firls_ctx* c, const void* b, const firls_params* p,
   a.mode = 2;
   // row FFT of x into t (state checks off: the kernel runs every slice)
   TRY(cuda_check(c, cudaMemsetAsync(c->st, 0, sizeof(SliceState) * B, c->stream), "memset"));
-  state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, eps);
+  state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, eps, 1);
   a.st = c->st;
   fft_row_fwd(n, a);
   a.b = static_cast<const float2*>(b);
@@ -983,35 +1057,32 @@ extern "C" firls_status firls_slot_load(firls_ctx* c, int s, const uint8_t* mask
   a.x = x0 ? nullptr : c->x + off;
   fft_col_inv(n, a);
   if (x0) CU(cudaMemcpyAsync(c->x + off, x0, N * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaMemsetAsync(c->dx + off, 0, N * sizeof(float2), c->stream));
+  // no outer-step limit: the caller reads the slot out when it wants
   state_init(1, c->stream, c->st + s, part, fft_col_ctas(n), c->counts + s, n, c->lam_d + s, c->lamtv_d + s,
-             eps > 0.f ? eps : 1e-10f);
+             eps > 0.f ? eps : 1e-10f, 1 << 30);
   return cuda_check(c, cudaGetLastError(), "slot_load");
+}
+
+extern "C" firls_status firls_run_steps(firls_ctx* c, const firls_params* p, int macro_steps) {
+  if (!c || !p) return FIRLS_E_INVALID_ARG;
+  if (!c->op_set) return fail(c, FIRLS_E_STATE, "operator not set");
+  if (macro_steps < 1) return fail(c, FIRLS_E_INVALID_ARG, "macro_steps must be >= 1");
+  firls_params q = *p;
+  q.outer_iters = 1;  // the per-slot limits come from firls_slot_load
+  TRY(check_params(c, &q));
+  // one graph of all the steps: the caller polls with firls_slot_status
+  return run_macro(c, q, macro_steps, macro_steps, false);
 }
 
 extern "C" firls_status firls_run(firls_ctx* c, const firls_params* p) {
   if (!c || !p) return FIRLS_E_INVALID_ARG;
-  if (!c->op_set) return fail(c, FIRLS_E_STATE, "operator not set");
   if (p->outer_iters < 1 || p->pcg_iters < 1) return fail(c, FIRLS_E_INVALID_ARG, "iteration counts must be >= 1");
+  if (!c->op_set) return fail(c, FIRLS_E_STATE, "operator not set");
   firls_params q = *p;
-  q.outer_tol = p->outer_tol;  // no polling inside: the caller polls with firls_slot_status
-  const bool graph = c->use_graph && c->stream != nullptr;
-  if (q.precond < FIRLS_PRECOND_PAPER || q.precond > FIRLS_PRECOND_NONE)
-    return fail(c, FIRLS_E_INVALID_ARG, "bad precond");
-  if (!(q.outer_stall_tol >= 0.f)) return fail(c, FIRLS_E_INVALID_ARG, "outer_stall_tol must be >= 0");
-  if (q.pcg_tol_kind != 0 && q.pcg_tol_kind != 1) return fail(c, FIRLS_E_INVALID_ARG, "bad pcg_tol_kind");
-  if (!graph) {
-    for (int k = 0; k < q.outer_iters; ++k) enqueue_outer(c, q);
-    return cuda_check(c, cudaGetLastError(), "run");
-  }
-  if (!c->exec || !same_schedule(c->g_sched, q)) {
-    firls_params one = q;
-    one.outer_iters = 1;
-    TRY(run_outer_steps(c, &one));  // captures (and runs) one step
-    q.outer_iters -= 1;
-  }
-  for (int k = 0; k < q.outer_iters; ++k) CU(cudaGraphLaunch(c->exec, c->stream));
-  c->marks_valid = c->timing;
-  return FIRLS_OK;
+  q.outer_iters = 1;
+  TRY(check_params(c, &q));
+  return run_macro(c, q, solve_steps(p), p->pcg_iters + 1, false);
 }
 
 extern "C" firls_status firls_slot_status(firls_ctx* c, int* done, int* outer_done, double* rel_change,
@@ -1100,7 +1171,7 @@ extern "C" firls_status firls_autotune(firls_ctx* c, const char* cache_path) {
     p.lambda = 1e-3f;
     p.lambda_tv = 1e-3f;
     TRY(upload_params(c, &p));
-    state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, 1e-10f);
+    state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, 1e-10f, 1);
     if (has_tv(c)) penta_setup(B, n, c->stream, c->st, c->wtv, nullptr, c->ia);
     float best = 1e30f;
     if (c->kind) {
@@ -1146,10 +1217,7 @@ extern "C" firls_status firls_autotune(firls_ctx* c, const char* cache_path) {
   c->tune_cmax = cm;
   c->tune_ilu = il;
   multi_forget(c);
-  if (c->exec) {
-    cudaGraphExecDestroy(c->exec);
-    c->exec = nullptr;
-  }
+  graphs_clear(c);
   return FIRLS_OK;
 }
 
@@ -1168,10 +1236,7 @@ extern "C" firls_status firls_set_tuning(firls_ctx* c, int rows_per_cta, int coa
     c->tune_cmax = coarse_max;
     c->tune_ilu = ilu_shape;
     multi_forget(c);
-    if (c->exec) {  // the captured outer step changes shape
-      cudaGraphExecDestroy(c->exec);
-      c->exec = nullptr;
-    }
+    graphs_clear(c);  // the captured macro steps change shape
   }
   return FIRLS_OK;
 }
@@ -1182,10 +1247,7 @@ extern "C" firls_status firls_set_wait_test(firls_ctx* c, int enable) {
   if (v != c->wait_test) {
     c->wait_test = v;
     multi_forget(c);
-    if (c->exec) {  // the captured outer step changes
-      cudaGraphExecDestroy(c->exec);
-      c->exec = nullptr;
-    }
+    graphs_clear(c);  // the captured macro steps change
   }
   return FIRLS_OK;
 }
@@ -1223,7 +1285,7 @@ extern "C" firls_status firls_data_consistency(firls_ctx* c, const void* b, cons
   p.lambda_per_slice = zeros.data();
   p.lambda_tv_per_slice = zeros.data();
   TRY(upload_params(c, &p));
-  state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, 1e-10f);
+  state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, 1e-10f, 1);
   FftArgs a = fft_args(c);
   a.d = const_cast<float2*>(static_cast<const float2*>(x));
   a.t = c->t;

@@ -14,6 +14,18 @@ constexpr int MU_WINDOW = 24;
 // Consecutive outer steps at or below the stall tolerance that stop a slice.
 constexpr int STALL_STEPS = 4;
 
+// Where a slice is in its own outer step.  Every slice advances on its own:
+// one launch sequence (a macro step) does a PCG step for the slices in
+// PH_PCG and the outer-step transition for the others.
+//   PH_BOUNDARY: start of an outer step: weights and P from x^k, S x^k, the
+//                first residual r_0 = A^H b - S x^k, z_0 and rho.
+//   PH_PCG:      PCG step pcg_j + 1 of the outer step.
+//   PH_END:      the outer step's PCG has stopped; the next macro step adds
+//                its update to x, measures the relative change, applies the
+//                stopping rules and, if the slice goes on, starts the next
+//                outer step.
+enum { PH_BOUNDARY = 0, PH_PCG = 1, PH_END = 2 };
+
 // Per-slice PCG / outer-loop state, FP64 scalars (the only FP64 steps:
 // inner products, alpha, beta, rho, residual norms, relative change).
 struct SliceState {
@@ -35,7 +47,9 @@ struct SliceState {
   float abar;        // mean(diag(A^H A)) = popcount / N
   float eps;         // smoothing eps
   int stall;         // consecutive outer steps with relchg <= the stall tolerance
-  int pcg_rel;       // PCG tolerance relative to ||r_0|| (1) or to ||A^H b|| (0)
+  int phase;         // PH_*: where the slice is in its current outer step
+  int pcg_j;         // PCG steps taken in the current outer step
+  int outer_max;     // outer steps after which the slice stops
   float hist[MU_WINDOW];  // relchg of the last MU_WINDOW outer steps (ring, by outer_done)
 };
 
@@ -54,15 +68,16 @@ FI float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
 FI float rdot2(float2 a, float2 b) { return fmaf(a.x, b.x, a.y * b.y); }
 
 FI bool slice_running(const SliceState* st, int s) { return st[s].active && !st[s].done; }
+FI bool slice_in_pcg(const SliceState* st, int s) { return slice_running(st, s) && st[s].phase == PH_PCG; }
 
 // PCG scalar updates of one slice (FP64), shared by the scalar kernels and
 // the kernels that finish them in place.
 // alpha = rho / <d, S d>; a non-positive or non-finite <d, S d> is a breakdown.
 FI void pcg_alpha_from(SliceState* v, double dq) {
   const double rho = v->rho;
-  if (rho == 0.0) {  // exact solution reached: nothing left to do
+  if (rho == 0.0) {  // exact solution reached: nothing left to do in this outer step
     v->alpha = 0.0;
-    v->active = 0;
+    v->phase = PH_END;
     return;
   }
   if (!(dq > 0.0) || !isfinite(dq) || !isfinite(rho)) {  // breakdown: the slice stops, x keeps its last value
@@ -74,20 +89,33 @@ FI void pcg_alpha_from(SliceState* v, double dq) {
   v->alpha = rho / dq;
   v->pcg_steps += 1;
 }
-// First residual: rho = Re<r, z>, rr = ||r||^2, no previous direction.
+// First residual: rho = Re<r, z>, rr = ||r||^2, no previous direction; the
+// slice's PCG steps begin.
 FI void pcg_rho_init_from(SliceState* v, double rz, double rr) {
   v->rho = rz;
   v->rr = rr;
   v->rr0 = rr;
   v->beta = 0.0;
+  v->phase = PH_PCG;
+  v->pcg_j = 0;
 }
-// After the residual update: stop on ||r|| <= tol ||A^H b|| (or, with
-// pcg_rel, ||r|| <= tol ||r_0||: the forcing term of an inexact inner solve),
-// else beta = rho_new / rho.
-FI void pcg_beta_from(SliceState* v, double rz, double rr, float tol) {
+// Inner-solve schedule of the PCG steps: stop at ||r|| <= tol ||A^H b|| (rel
+// = 0) or tol ||r_0|| (rel = 1), or after J steps per outer step, J_late
+// from outer step k_late on (J_late <= 0: always J).
+struct PcgSched {
+  float tol;
+  int rel, J, J_late, k_late;
+  FI int cap(const SliceState* v) const { return (J_late > 0 && v->outer_done >= k_late) ? J_late : J; }
+};
+// After the residual update of PCG step pcg_j + 1: the outer step's PCG ends
+// on ||r|| <= tol ||A^H b|| (or, with rel, ||r|| <= tol ||r_0||: the forcing
+// term of an inexact inner solve) or after the schedule's steps for this outer
+// step; otherwise beta = rho_new / rho.
+FI void pcg_beta_from(SliceState* v, double rz, double rr, const PcgSched& ps) {
   v->rr = rr;
-  if (tol > 0.f && sqrt(rr) <= (double)tol * sqrt(v->pcg_rel ? v->rr0 : v->rhs2)) {
-    v->active = 0;
+  v->pcg_j += 1;
+  if ((ps.tol > 0.f && sqrt(rr) <= (double)ps.tol * sqrt(ps.rel ? v->rr0 : v->rhs2)) || v->pcg_j >= ps.cap(v)) {
+    v->phase = PH_END;
     return;
   }
   v->beta = rz / v->rho;

@@ -65,16 +65,25 @@ template <int N> FI void load_twiddles(float2* tw, const float2* __restrict__ tw
   }
 }
 
-// d = z (mode 0) | d = z + beta d (mode 1) | use d as is (mode 2); t = rowFFT(d)
+// d = z (mode 0) | d = z + beta d (mode 1) | use d as is (mode 2) | per slice
+// (mode < 0): d = x at the start of its outer step (S x^k), else d = z on the
+// first PCG step and z + beta d after it; t = rowFFT(d)
 template <int N>
 __global__ void __launch_bounds__(256) k_row_fwd(const float2* __restrict__ z, float2* __restrict__ d,
                                                  float2* __restrict__ t_out,
                                                  const SliceState* __restrict__ st,
-                                                 const float2* __restrict__ twg, int mode) {
+                                                 const float2* __restrict__ twg, int mode_arg,
+                                                 const float2* __restrict__ x) {
   using C = FftCfg<N>;
   constexpr int R = rows_per_cta<N>(), E = C::E, T = C::T, LW = fft_line_words<N>();
   const int s = blockIdx.y;
   if (!slice_running(st, s)) return;
+  int mode = mode_arg;
+  if (mode_arg < 0) {
+    const int ph = st[s].phase;
+    if (ph == PH_END) return;
+    mode = ph == PH_BOUNDARY ? 3 : (st[s].pcg_j == 0 ? 0 : 1);
+  }
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tw = reinterpret_cast<float2*>(smem);
   float* lines = reinterpret_cast<float*>(smem + tw_bytes<N>());
@@ -93,6 +102,9 @@ __global__ void __launch_bounds__(256) k_row_fwd(const float2* __restrict__ z, f
       d[i] = dv;
     } else if (mode == 1) {
       dv = cfma((float)beta, d[i], z[i]);
+      d[i] = dv;
+    } else if (mode == 3) {
+      dv = x[i];
       d[i] = dv;
     } else {
       dv = d[i];
@@ -465,7 +477,7 @@ template <int N> struct FftLaunch {
   static void row_fwd(const FftArgs& a) {
     set_smem_attrs<N>();
     k_row_fwd<N><<<dim3(N / R, a.batch), R * FftCfg<N>::T, row_smem_bytes<N>(false), a.stream>>>(
-        a.z, a.d, a.t, a.st, a.tw, a.mode);
+        a.z, a.d, a.t, a.st, a.tw, a.mode, a.xs);
   }
   static void row_ahb(const FftArgs& a) {
     set_smem_attrs<N>();

@@ -1343,13 +1343,18 @@ struct RingPos {
 // row slot u % G.
 template <int E, int G>
 __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
-    k_ilu(int n, int mode, int S, IwLayout lay, SliceState* __restrict__ st, double* __restrict__ part,
+    k_ilu(int n, int mode_arg, int S, IwLayout lay, SliceState* __restrict__ st, double* __restrict__ part,
           float2* __restrict__ x, const float2* __restrict__ d, float2* __restrict__ r,
           const float2* __restrict__ q, const float2* __restrict__ atb, float2* __restrict__ y,
           float2* __restrict__ z, const float* __restrict__ ia, const float* __restrict__ wtv, int fuse,
-          float pcg_tol, int wait_test) {
+          PcgSched ps, int wait_test) {
   const int s = blockIdx.x;
   if (!slice_running(st, s)) return;
+  // ILU_PER_SLICE: the first residual for a slice at the start of its outer
+  // step, a PCG step otherwise
+  const int ph = st[s].phase;
+  if (mode_arg == ILU_PER_SLICE && ph == PH_END) return;
+  const int mode = mode_arg != ILU_PER_SLICE ? mode_arg : (ph == PH_BOUNDARY ? ILU_INIT : ILU_STEP);
   // wait_test (failure-detection test only): the producer issues no copy and
   // every wait gives up after its first poll, so the waits run out with
   // nothing in flight and the slice is reported faulted
@@ -1634,13 +1639,14 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
       if (mode == ILU_INIT)
         pcg_rho_init_from(st + s, 0.0 + trz, 0.0 + trr);
       else
-        pcg_beta_from(st + s, 0.0 + trz, 0.0 + trr, pcg_tol);
+        pcg_beta_from(st + s, 0.0 + trz, 0.0 + trr, ps);
     }
   }
 }
 
 typedef void (*IluKernel)(int, int, int, IwLayout, SliceState*, double*, float2*, const float2*, float2*,
-                          const float2*, const float2*, float2*, float2*, const float*, const float*, int, float, int);
+                          const float2*, const float2*, float2*, float2*, const float*, const float*, int, PcgSched,
+                          int);
 template <int G>
 static IluKernel ilu_kernel_g(int E) {
   switch (E) {
@@ -1698,12 +1704,12 @@ bool ilu_shape_fits(int n, int shape) {
 
 void ilu_step(int batch, int n, cudaStream_t s, SliceState* st, double* part, int mode, float2* x,
               const float2* d, float2* r, const float2* q, const float2* atb, float2* y, float2* z,
-              const float* ia, const float* wtv, int shape, int fuse_scalars, float pcg_tol, int wait_test) {
+              const float* ia, const float* wtv, int shape, int fuse_scalars, PcgSched ps, int wait_test) {
   if (shape <= 0 || !ilu_shape_fits(n, shape)) shape = ilu_default_shape(n, batch);
   const int G = shape / 10, S = shape % 10;
   const IwLayout lay = iw_layout(n, G);
   ilu_kernel(n, G)<<<batch, IW_THREADS, (size_t)S * lay.bytes, s>>>(n, mode, S, lay, st, part, x, d, r, q, atb, y,
-                                                                     z, ia, wtv, fuse_scalars, pcg_tol, wait_test);
+                                                                     z, ia, wtv, fuse_scalars, ps, wait_test);
 }
 
 // =========================================================== PCG vectors ==
@@ -1716,11 +1722,14 @@ int axpy_ctas(int n) {
   return c;
 }
 
-__global__ void k_axpy(int N, int mode, const SliceState* __restrict__ st, double* __restrict__ part,
+__global__ void k_axpy(int N, int mode_arg, const SliceState* __restrict__ st, double* __restrict__ part,
                        float2* __restrict__ x, const float2* __restrict__ d, float2* __restrict__ r,
                        const float2* __restrict__ q, const float2* __restrict__ atb) {
   const int s = blockIdx.y;
   if (!slice_running(st, s)) return;
+  const int ph = st[s].phase;
+  if (mode_arg == AXPY_PER_SLICE && ph == PH_END) return;
+  const int mode = mode_arg != AXPY_PER_SLICE ? mode_arg : (ph == PH_BOUNDARY ? AXPY_INIT : AXPY_STEP);
   __shared__ double red[32];
   const float alpha = (float)st[s].alpha;
   const size_t base = (size_t)s * N;
@@ -1753,12 +1762,15 @@ void axpy_step(int batch, int n, cudaStream_t s, const SliceState* st, double* p
 
 // Residual update with a diagonal preconditioner (Jacobi PCG, sdiag = 1 /
 // diag(S)) or none (standard CG, sdiag null), for the comparison of Sec. 5.2.
-__global__ void k_axpy_diag(int N, int mode, const SliceState* __restrict__ st, double* __restrict__ part,
+__global__ void k_axpy_diag(int N, int mode_arg, const SliceState* __restrict__ st, double* __restrict__ part,
                             float2* __restrict__ x, const float2* __restrict__ d, float2* __restrict__ r,
                             const float2* __restrict__ q, const float2* __restrict__ atb,
                             const float* __restrict__ sdiag, float2* __restrict__ z) {
   const int s = blockIdx.y;
   if (!slice_running(st, s)) return;
+  const int ph = st[s].phase;
+  if (mode_arg == AXPY_PER_SLICE && ph == PH_END) return;
+  const int mode = mode_arg != AXPY_PER_SLICE ? mode_arg : (ph == PH_BOUNDARY ? AXPY_INIT : AXPY_STEP);
   __shared__ double red[32];
   const float alpha = (float)st[s].alpha;
   const size_t base = (size_t)s * N;
@@ -1811,15 +1823,15 @@ void jacobi_wavelet_setup(int batch, int n, cudaStream_t s, const SliceState* st
   k_jacobi_wavelet<<<dim3(blocks, batch), 256, 0, s>>>(N, st, wdiag, ia);
 }
 
-// End of an outer step: x^{k+1} = x^k + dx, where dx = sum_j alpha_j d_j was
-// accumulated from zero by the PCG steps (so its rounding is relative to the
-// step, not to x); partial ||dx||^2 (SLOT_DX) and ||x^k||^2 (SLOT_XX) for the
-// relative change.  Slices that are done (converged earlier, or broken down
-// in this step) keep x^k.
+// End of a slice's outer step (PH_END): x^{k+1} = x^k + dx, where
+// dx = sum_j alpha_j d_j was accumulated from zero by the PCG steps (so its
+// rounding is relative to the step, not to x), and dx is cleared for the next
+// outer step; partial ||dx||^2 (SLOT_DX) and ||x^k||^2 (SLOT_XX) for the
+// relative change.  Slices stopped by a breakdown are done and keep x^k.
 __global__ void k_outer_apply(int N, const SliceState* __restrict__ st, float2* __restrict__ x,
-                              const float2* __restrict__ dx, double* __restrict__ part) {
+                              float2* __restrict__ dx, double* __restrict__ part) {
   const int s = blockIdx.y;
-  if (st[s].done) return;
+  if (!slice_running(st, s) || st[s].phase != PH_END) return;
   __shared__ double red[32];
   const size_t base = (size_t)s * N;
   const int chunk = (N + gridDim.x - 1) / gridDim.x;
@@ -1830,6 +1842,7 @@ __global__ void k_outer_apply(int N, const SliceState* __restrict__ st, float2* 
     a += cabs2(dv);
     b += cabs2(xv);
     x[base + i] = cadd(xv, dv);
+    dx[base + i] = make_float2(0.f, 0.f);
   }
   const double ta = block_sum((double)a, red);
   __syncthreads();
@@ -1840,7 +1853,7 @@ __global__ void k_outer_apply(int N, const SliceState* __restrict__ st, float2* 
   }
 }
 
-void outer_apply(int batch, int n, cudaStream_t s, const SliceState* st, float2* x, const float2* dx,
+void outer_apply(int batch, int n, cudaStream_t s, const SliceState* st, float2* x, float2* dx,
                  double* part) {
   k_outer_apply<<<dim3(axpy_ctas(n), batch), 256, 0, s>>>(n * n, st, x, dx, part);
 }
@@ -2066,7 +2079,7 @@ FI double sum_parts(const double* part, int s, int slot, int np) {
 }
 
 __global__ void k_state_init(int B, SliceState* st, const double* part, int np, const int* counts, int N,
-                             const float* lam, const float* lam_tv, float eps) {
+                             const float* lam, const float* lam_tv, float eps, int outer_max) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B) return;
   SliceState v;
@@ -2076,9 +2089,11 @@ __global__ void k_state_init(int B, SliceState* st, const double* part, int np, 
   v.rhs2 = sum_parts(part, s, SLOT_RHS, np);
   v.rr = v.rhs2;
   v.rr0 = v.rhs2;
-  v.pcg_rel = 0;
   v.relchg = 0.0;
   v.stall = 0;
+  v.phase = PH_BOUNDARY;
+  v.pcg_j = 0;
+  v.outer_max = outer_max;
   for (int i = 0; i < MU_WINDOW; ++i) v.hist[i] = 0.f;
   // non-finite k-space on the mask makes A^H b non-finite: the slice is not
   // iterated and counts as a breakdown (its x keeps the start)
@@ -2097,24 +2112,30 @@ __global__ void k_state_init(int B, SliceState* st, const double* part, int np, 
 }
 
 void state_init(int batch, cudaStream_t s, SliceState* st, const double* part, int np, const int* counts,
-                int n, const float* lam, const float* lam_tv, float eps) {
-  k_state_init<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np, counts, n * n, lam, lam_tv, eps);
+                int n, const float* lam, const float* lam_tv, float eps, int outer_max) {
+  k_state_init<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np, counts, n * n, lam, lam_tv, eps,
+                                                   outer_max);
 }
 
-__global__ void k_outer_begin(int B, SliceState* st, int pcg_rel) {
+// The slices at the start of an outer step, as a copy of the state in which
+// every other slice reads as done: the weight and preconditioner set-up
+// kernels, which skip done slices and never write the state, then work on
+// exactly those slices.
+__global__ void k_boundary_view(int B, const SliceState* __restrict__ st, SliceState* __restrict__ view) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B) return;
-  st[s].active = st[s].done ? 0 : 1;
-  st[s].pcg_rel = pcg_rel;
+  SliceState v = st[s];
+  if (v.phase != PH_BOUNDARY) v.done = 1;
+  view[s] = v;
 }
 
-void outer_begin(int batch, cudaStream_t s, SliceState* st, int pcg_rel) {
-  k_outer_begin<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, pcg_rel);
+void boundary_view(int batch, cudaStream_t s, const SliceState* st, SliceState* view) {
+  k_boundary_view<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, view);
 }
 
 __global__ void k_alpha(int B, SliceState* st, const double* part, int np) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= B || !slice_running(st, s)) return;
+  if (s >= B || !slice_in_pcg(st, s)) return;
   pcg_alpha_from(st + s, sum_parts(part, s, SLOT_DQ, np));
 }
 
@@ -2122,25 +2143,26 @@ void pcg_alpha(int batch, cudaStream_t s, SliceState* st, const double* part, in
   k_alpha<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np);
 }
 
-__global__ void k_rho_init(int B, SliceState* st, const double* part, int np_rz, int np_rr) {
+// After z = P^{-1} r: rho (first residual, slices at the start of an outer
+// step) or beta and the PCG stop (slices in PCG); mode INIT / STEP forces one
+// of them for every running slice.
+__global__ void k_pcg_scalars(int B, SliceState* st, const double* part, int np_rz, int np_rr, int mode,
+                              PcgSched ps) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B || !slice_running(st, s)) return;
-  pcg_rho_init_from(st + s, sum_parts(part, s, SLOT_RZ, np_rz), sum_parts(part, s, SLOT_RR, np_rr));
+  const int ph = st[s].phase;
+  const bool init = mode == SCALARS_INIT || (mode == SCALARS_PER_SLICE && ph == PH_BOUNDARY);
+  const bool step = mode == SCALARS_STEP || (mode == SCALARS_PER_SLICE && ph == PH_PCG);
+  const double rz = sum_parts(part, s, SLOT_RZ, np_rz), rr = sum_parts(part, s, SLOT_RR, np_rr);
+  if (init)
+    pcg_rho_init_from(st + s, rz, rr);
+  else if (step)
+    pcg_beta_from(st + s, rz, rr, ps);
 }
 
-void pcg_rho_init(int batch, cudaStream_t s, SliceState* st, const double* part, int np_rz, int np_rr) {
-  k_rho_init<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np_rz, np_rr);
-}
-
-__global__ void k_beta(int B, SliceState* st, const double* part, int np_rz, int np_rr, float tol) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= B || !slice_running(st, s)) return;
-  pcg_beta_from(st + s, sum_parts(part, s, SLOT_RZ, np_rz), sum_parts(part, s, SLOT_RR, np_rr), tol);
-}
-
-void pcg_beta(int batch, cudaStream_t s, SliceState* st, const double* part, int np_rz, int np_rr,
-              float tol) {
-  k_beta<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np_rz, np_rr, tol);
+void pcg_scalars(int batch, cudaStream_t s, SliceState* st, const double* part, int np_rz, int np_rr, int mode,
+                 const PcgSched& ps) {
+  k_pcg_scalars<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np_rz, np_rr, mode, ps);
 }
 
 // Outer-loop stop.  kind 0: relative change <= tol.  kind 1: estimated
@@ -2155,7 +2177,7 @@ void pcg_beta(int batch, cudaStream_t s, SliceState* st, const double* part, int
 __global__ void k_outer_end(int B, SliceState* st, const double* part, int np, float tol, int kind,
                             float stall_tol) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= B || st[s].done) return;
+  if (s >= B || !slice_running(st, s) || st[s].phase != PH_END) return;
   SliceState* v = st + s;
   const double dx = sum_parts(part, s, SLOT_DX, np);
   const double xx = sum_parts(part, s, SLOT_XX, np);
@@ -2170,13 +2192,16 @@ __global__ void k_outer_end(int B, SliceState* st, const double* part, int np, f
     v->done = 1;
     return;
   }
-  if (!(tol > 0.f)) return;
-  if (kind == 0) {
-    if (rel <= (double)tol) v->done = 1;
-  } else if (k >= MU_WINDOW && old > 0.f) {
-    const double mu = fmin(pow(rel / (double)old, 1.0 / MU_WINDOW), 0.999);
-    if (rel * mu / (1.0 - mu) <= (double)tol && rel <= (double)tol) v->done = 1;
+  if (tol > 0.f) {
+    if (kind == 0) {
+      if (rel <= (double)tol) v->done = 1;
+    } else if (k >= MU_WINDOW && old > 0.f) {
+      const double mu = fmin(pow(rel / (double)old, 1.0 / MU_WINDOW), 0.999);
+      if (rel * mu / (1.0 - mu) <= (double)tol && rel <= (double)tol) v->done = 1;
+    }
   }
+  if (v->outer_done >= v->outer_max) v->done = 1;
+  if (!v->done) v->phase = PH_BOUNDARY;  // the next outer step starts
 }
 
 void outer_end(int batch, cudaStream_t s, SliceState* st, const double* part, int np, float tol, int kind,

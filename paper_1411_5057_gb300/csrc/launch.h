@@ -24,6 +24,7 @@ struct FftArgs {
   const float2* u = nullptr;
   const float* wtv = nullptr;
   float2* q = nullptr;
+  const float2* xs = nullptr;   // row FFT, per-slice mode: x^k of slices starting an outer step
   int mode = 0;
   int real = 0;
 };
@@ -84,18 +85,21 @@ void penta_setup(int batch, int n, cudaStream_t s, const SliceState* st, const f
 // In the PCG-step kernels below, `x` is the vector that receives alpha d: the
 // solver passes the outer step's update accumulator dx (added to the iterate
 // once per outer step by outer_apply).
-enum IluMode { ILU_INIT = 0, ILU_STEP = 1, ILU_LAST = 2 };
+enum IluMode { ILU_INIT = 0, ILU_STEP = 1, ILU_LAST = 2, ILU_PER_SLICE = -1 };
 // shape: shared-memory ring, 10 * rows per stage + stages (0: chosen from n and batch)
 // fuse_scalars: the CTA finishes the PCG scalars itself from its sums (rho
 // at ILU_INIT; rr, the residual test against pcg_tol, beta and rho at ILU_STEP)
 void ilu_step(int batch, int n, cudaStream_t s, SliceState* st, double* part, int mode,
               float2* x, const float2* d, float2* r, const float2* q, const float2* atb, float2* y,
               float2* z, const float* ia, const float* wtv, int shape, int fuse_scalars = 0,
-              float pcg_tol = 0.f, int wait_test = 0);
+              PcgSched ps = PcgSched{0.f, 0, 1 << 30, 0, 0}, int wait_test = 0);
 int ilu_default_shape(int n, int batch);
 bool ilu_shape_fits(int n, int shape);
 
-enum AxpyMode { AXPY_INIT = 0, AXPY_STEP = 1, AXPY_LAST = 2 };
+// AXPY_PER_SLICE (and ILU_PER_SLICE, SCALARS_PER_SLICE, mode < 0 of the row
+// FFT): each slice's own phase picks the first residual (PH_BOUNDARY) or a
+// PCG step (PH_PCG).
+enum AxpyMode { AXPY_INIT = 0, AXPY_STEP = 1, AXPY_LAST = 2, AXPY_PER_SLICE = -1 };
 // Residual update (INIT: r = A^H b - q; STEP: r -= alpha q, x += alpha d) with
 // a diagonal preconditioner z = sdiag o r (sdiag null: z = r), partial
 // Re<r, z> into SLOT_RZ and ||r||^2 into SLOT_RR (axpy_ctas parts).
@@ -126,18 +130,18 @@ void tv_sum(int batch, int n, cudaStream_t s, const float2* x, float eps, double
 
 // PCG scalar updates (one thread per slice)
 void pcg_alpha(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts);
-void pcg_rho_init(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts_rz,
-                  int nparts_rr);
-void pcg_beta(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts_rz,
-              int nparts_rr, float pcg_tol);
-void outer_begin(int batch, cudaStream_t s, SliceState* st, int pcg_rel);
+enum ScalarsMode { SCALARS_INIT = 0, SCALARS_STEP = 1, SCALARS_PER_SLICE = -1 };
+void pcg_scalars(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts_rz, int nparts_rr,
+                 int mode, const PcgSched& ps);
+// view = st with every slice not at the start of its outer step marked done
+void boundary_view(int batch, cudaStream_t s, const SliceState* st, SliceState* view);
 // x += dx (the outer step's accumulated update) with partial ||dx||^2 and
 // ||x||^2 (before the update) for the relative change.
-void outer_apply(int batch, int n, cudaStream_t s, const SliceState* st, float2* x, const float2* dx,
+void outer_apply(int batch, int n, cudaStream_t s, const SliceState* st, float2* x, float2* dx,
                  double* part);
 void outer_end(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts,
                float outer_tol, int tol_kind, float stall_tol);
 void state_init(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts_rhs,
-                const int* counts, int n, const float* lam, const float* lam_tv, float eps);
+                const int* counts, int n, const float* lam, const float* lam_tv, float eps, int outer_max);
 
 }  // namespace firls

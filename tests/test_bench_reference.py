@@ -16,7 +16,7 @@ def test_reference_arm_line(procs):
     buf = io.StringIO()
     with contextlib.redirect_stdout(buf):
         out = bench.main(["--impl", "reference", "--steps", "1", "--warmup", "0", "--ref-outer", "1",
-                          "--inner", "5", "--ref-procs", str(procs)])
+                          "--ref-inner", "5", "--ref-procs", str(procs)])
     line = json.loads(buf.getvalue().strip().splitlines()[-1])
     assert line == json.loads(json.dumps(out))
     for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
@@ -25,7 +25,9 @@ def test_reference_arm_line(procs):
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
     assert line["higher_is_better"] is True and line["value"] > 0
     # the GPU arm's config at the parser defaults (608 slices through 304 slots)
-    ours = bench.workload_config(type("A", (), {"queue": 608, "batch": 304, "outer": bench.OUTER, "inner": 5,
+    ours = bench.workload_config(type("A", (), {"queue": 608, "batch": 304, "outer": bench.OUTER,
+                                                "inner": bench.INNER, "inner_late": bench.INNER_LATE,
+                                                "outer_late": bench.OUTER_LATE,
                                                 "outer_tol": bench.OUTER_TOL, "stall_tol": bench.STALL_TOL,
                                                 "steady": 0})(), 1)
     assert line["config"] == ours

@@ -220,7 +220,7 @@ def _check_weights_S_Pinv(F, n, cfg, form=None, precond="paper"):
 # -------------------------------------------------------- reconstructions ---
 
 def _gpu_solve(F, problems, outer, inner, pcg_tol=0.0, outer_tol=0.0, stats=False, lam_per_slice=None,
-               stop_on_distance=False, stall_tol=0.0):
+               stop_on_distance=False, stall_tol=0.0, pcg_late=0, outer_late=0):
     p0 = problems[0]
     n, B = p0.n, len(problems)
     ctx = F.Context(n, batch=B, real=p0.real)
@@ -228,7 +228,8 @@ def _gpu_solve(F, problems, outer, inner, pcg_tol=0.0, outer_tol=0.0, stats=Fals
     ctx.set_operator(dev(np.stack([p.mask for p in problems])), p0.psi, p0.levels, groups)
     params = F.make_params(outer, inner, lam=p0.lam, lam_tv=p0.lam_tv, pcg_tol=pcg_tol, outer_tol=outer_tol,
                            lam_per_slice=[p.lam for p in problems], lam_tv_per_slice=[p.lam_tv for p in problems],
-                           stop_on_distance=stop_on_distance, stall_tol=stall_tol)
+                           stop_on_distance=stop_on_distance, stall_tol=stall_tol, pcg_late=pcg_late,
+                           outer_late=outer_late)
     res = ctx.solve(c64(np.stack([p.b for p in problems])), params, stats=stats)
     if stats:
         return host(res[0]), res[1]
@@ -293,7 +294,7 @@ def test_bench_workload_reaches_converged_oracle(F):
     assert 2 in seeds and len(seeds) >= 4
     probs = [bench.problem(s) for s in seeds]
     x = _gpu_solve(F, probs, bench.OUTER, bench.INNER, outer_tol=bench.OUTER_TOL, stop_on_distance=True,
-                   stall_tol=bench.STALL_TOL)
+                   stall_tol=bench.STALL_TOL, pcg_late=bench.INNER_LATE, outer_late=bench.OUTER_LATE)
     errs = {s: rel(x[i], ref[s][0]) for i, s in enumerate(seeds)}
     assert max(errs.values()) < TOL_SOLVE, errs
 
@@ -450,7 +451,9 @@ def test_kernel_timing_does_not_change_the_result(F, own_stream):
         ctx.set_timing(False)
     torch.cuda.synchronize()
     assert torch.equal(x0, x1)
-    assert kt["ilu"][1] == J and kt["row_fft"][1] == J + 1
+    # one outer step: J + 1 macro steps, each one S apply and one ILU (the
+    # first residual's, then J PCG steps')
+    assert kt["ilu"][1] == J + 1 and kt["row_fft"][1] == J + 1
     assert all(v[0] >= 0.0 for v in kt.values()) and kt["ilu"][0] > 0.0
 
 

@@ -1,0 +1,72 @@
+"""Inner-solve schedules on the macro-step solver: every slice advances on its
+own, so its result does not depend on the other slices of the batch, and a
+schedule with more PCG steps in later outer steps equals the same outer steps
+taken one by one (the outer loop of Alg. 2 / Alg. 3 is memoryless: W^k and P
+come from x^k, PCG restarts at x^k)."""
+import numpy as np
+import pytest
+
+import firls_synth as fs
+from oracle import firls_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_SOLVE = 1e-4
+
+
+@pytest.fixture(scope="module")
+def F():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1411_5057_gb300 as F
+    return F
+
+
+def _ctx(F, probs):
+    p0 = probs[0]
+    ctx = F.Context(p0.n, batch=len(probs), real=p0.real)
+    ctx.set_operator(torch.from_numpy(np.stack([p.mask for p in probs])).cuda(), p0.psi, p0.levels)
+    b = torch.from_numpy(np.stack([p.b for p in probs]).astype(np.complex64)).cuda()
+    return ctx, b
+
+
+def test_late_inner_schedule_equals_steps_one_by_one(F):
+    p = fs.haar_l1_64()
+    K, J, J_late, k_late = 10, 20, 45, 4
+    ctx, b = _ctx(F, [p])
+    x_sched = ctx.solve(b, F.make_params(K, J, lam=p.lam, pcg_late=J_late, outer_late=k_late)).clone()
+    x = None
+    x_ref = None
+    for k in range(K):
+        jk = J_late if k >= k_late else J
+        x = ctx.solve(b, F.make_params(1, jk, lam=p.lam), x0=x).clone()
+        x_ref, _ = O.firls_problem(p, outer=1, inner=jk, x_init=x_ref)
+    assert torch.equal(x_sched, x)
+    got = x_sched[0].cpu().numpy().astype(np.complex128).real
+    assert np.linalg.norm(got - x_ref) / np.linalg.norm(x_ref) < TOL_SOLVE
+    ctx.close()
+
+
+def test_slices_with_different_inner_counts_are_independent(F):
+    """PCG stopped per slice by a tolerance (relative to each outer step's
+    first residual): slices take different PCG counts per outer step, and each
+    result equals the slice solved alone, bit for bit."""
+    probs = [fs.make_problem(64, 0.15 + 0.05 * i, 0.01, 90 + i, real=False, psi=fs.PSI_TV | fs.PSI_DB4, levels=3,
+                             lam=3e-4 * (1 + i), lam_tv=8e-4) for i in range(3)]
+    params = F.make_params(6, 80, lam_per_slice=[p.lam for p in probs], lam_tv_per_slice=[p.lam_tv for p in probs],
+                           pcg_tol=0.05, pcg_tol_rel=True)
+    ctx, b = _ctx(F, probs)
+    xb, st = ctx.solve(b, params, stats=True)
+    _, od, _, pc = ctx.slot_status(with_pcg=True)
+    assert od == [6, 6, 6]
+    assert len(set(pc)) > 1, pc                       # the slices took different PCG counts
+    for i, p in enumerate(probs):
+        one, b1 = _ctx(F, [p])
+        pp = F.make_params(6, 80, lam_per_slice=[p.lam], lam_tv_per_slice=[p.lam_tv], pcg_tol=0.05, pcg_tol_rel=True)
+        x1 = one.solve(b1, pp)
+        _, _, _, pc1 = one.slot_status(with_pcg=True)
+        assert pc1[0] == pc[i]
+        assert torch.equal(x1[0], xb[i]), i
+        one.close()
+    ctx.close()
