@@ -60,6 +60,7 @@ RATIO, SIGMA, LAM_TV, LAM_W, LEVELS = 0.20, 0.01, 1e-3, 5e-4, 4
 # reported per result in the bench line ("accuracy").
 OUTER, INNER, INNER_LATE, OUTER_LATE, OUTER_TOL, STALL_TOL = 800, 60, 240, 60, 3e-5, 6e-7
 SERVE_CHUNK = 64   # macro steps between polls of the slots
+BOUNDARY_PERIOD = 4  # outer-step transitions (and their weight updates) every 4th macro step
 REF_OUTER_PER_RECON = 43   # FP64 oracle outer steps (x 60 PCG) to 1e-4 of x* on seed 2
 
 # Algorithmic bytes per pixel per launch of each kernel class: every distinct
@@ -169,7 +170,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     params = F.make_params(args.outer, args.inner, lam=LAM_W, lam_tv=LAM_TV, outer_tol=args.outer_tol,
                            stop_on_distance=True, stall_tol=args.stall_tol, pcg_late=args.inner_late,
-                           outer_late=args.outer_late)
+                           outer_late=args.outer_late, boundary_period=args.boundary_period)
     lams, lam_tvs = [LAM_W] * S, [LAM_TV] * S
     with torch.cuda.stream(stream):
         masks = torch.from_numpy(masks_h).cuda()
@@ -459,6 +460,7 @@ def workload_config(args, world, done_per_step=None):
     return {"workload": f"firls_tv_db4_{N}", "n": N, "slices_per_step_per_gpu": args.queue, "slots": args.batch,
             "outer_max": args.outer, "inner": args.inner, "inner_late": args.inner_late,
             "outer_late": args.outer_late, "outer_tol": args.outer_tol, "stall_tol": args.stall_tol,
+            "boundary_period": args.boundary_period,
             "mask_ratio": RATIO, "sigma": SIGMA, "lambda_tv": LAM_TV, "lambda_w": LAM_W,
             "wavelet": "db4", "levels": LEVELS, "batching": "continuous (slots refilled on convergence)",
             "completions_per_step": args.queue if done_per_step is None else done_per_step,
@@ -586,6 +588,8 @@ def main(argv=None):
     ap.add_argument("--outer-tol", type=float, default=OUTER_TOL)
     ap.add_argument("--inner-late", type=int, default=INNER_LATE, help="PCG steps per outer step from --outer-late on")
     ap.add_argument("--outer-late", type=int, default=OUTER_LATE)
+    ap.add_argument("--boundary-period", type=int, default=BOUNDARY_PERIOD,
+                    help="macro steps between outer-step transitions of the served slots")
     ap.add_argument("--stall-tol", type=float, default=STALL_TOL)
     ap.add_argument("--autotune", type=int, default=1, help="autotune tile shapes before timing (1/0)")
     ap.add_argument("--learned", type=int, default=1, help="also time the learned warm start (1/0)")

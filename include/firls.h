@@ -136,6 +136,11 @@ typedef struct {
                           ill-conditioned subproblem whose outer rate needs a
                           nearly exact inner solve); 0 = pcg_iters throughout */
   int outer_late;
+  int boundary_period; /* outer-step transitions and weight updates run in
+                          every this-many-th macro step (0 or 1: every one);
+                          a slice waits at most boundary_period - 1 macro
+                          steps per outer step, and the mostly idle set-up
+                          launches run that much less often                  */
 } firls_params;
 
 /* Preconditioners of the PCG steps, for the comparison of Sec. 5.2 (Fig. 2
@@ -188,7 +193,7 @@ firls_status firls_solve(firls_ctx* ctx, const void* b, const firls_params* para
  * (forked from ctxs[0]'s stream onto each context's own stream and joined
  * back) and replayed outer_iters times on ctxs[0]'s stream.  Arrays have
  * n_ctx entries, params included (per-context lambdas); the schedule and
- * tolerances must be equal in all of them.  Contexts must have distinct,
+ * tolerances must be equal in all of them (boundary_period 0 or 1).  Contexts must have distinct,
  * non-default streams for the graph; otherwise the steps are enqueued
  * directly.  Same buffer rules as firls_solve; results are ordered on
  * ctxs[0]'s stream.  stats (host, may be NULL) has n_ctx entries. */

@@ -48,7 +48,7 @@ class Params(ctypes.Structure):
                 ("eps", ctypes.c_float), ("lambda_per_slice", ctypes.POINTER(ctypes.c_float)),
                 ("lambda_tv_per_slice", ctypes.POINTER(ctypes.c_float)), ("outer_tol_kind", ctypes.c_int),
                 ("precond", ctypes.c_int), ("outer_stall_tol", ctypes.c_float), ("pcg_tol_kind", ctypes.c_int),
-                ("pcg_iters_late", ctypes.c_int), ("outer_late", ctypes.c_int)]
+                ("pcg_iters_late", ctypes.c_int), ("outer_late", ctypes.c_int), ("boundary_period", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -132,12 +132,13 @@ def size_supported(n: int) -> bool:
 
 def make_params(outer, pcg, lam=0.0, lam_tv=0.0, pcg_tol=0.0, outer_tol=0.0, eps=0.0,
                 lam_per_slice=None, lam_tv_per_slice=None, stop_on_distance=False, precond="paper",
-                stall_tol=0.0, pcg_tol_rel=False, pcg_late=0, outer_late=0):
+                stall_tol=0.0, pcg_tol_rel=False, pcg_late=0, outer_late=0, boundary_period=1):
     """firls_params; precond is "paper", "jacobi" or "none" (FIRLS_PRECOND_*);
     pcg_tol_rel: pcg_tol is relative to each outer step's first residual;
     pcg_late > 0: outer steps from outer_late on run pcg_late PCG steps."""
     p = Params()
     p.pcg_iters_late, p.outer_late = int(pcg_late), int(outer_late)
+    p.boundary_period = int(boundary_period)
     p.outer_stall_tol = float(stall_tol)
     p.pcg_tol_kind = 1 if pcg_tol_rel else 0
     p.outer_tol_kind = 1 if stop_on_distance else 0

@@ -305,20 +305,25 @@ void enqueue_precond(firls_ctx* c, int mode, const firls_params& sc) {
 }
 
 // One macro step: every slice advances by one step of its own outer step.
-// Slices whose PCG ended (PH_END) add their update to x, measure the
-// relative change and either stop or start their next outer step; slices at
-// the start of an outer step (PH_BOUNDARY) update W^k and P, apply S to x^k
-// and form r_0, z_0, rho; the others take one PCG step (Alg. 2 / Alg. 3).
-// An outer step of a slice with J PCG steps spans J + 1 macro steps.
-void enqueue_macro(firls_ctx* c, const firls_params& sc) {
+// In a boundary stage, slices whose PCG ended (PH_END) add their update to
+// x, measure the relative change and either stop or make their next outer
+// step due, and slices whose outer step is due (PH_BOUNDARY) update W^k and
+// P.  Then slices with W^k and P ready (PH_START) apply S to x^k and form
+// r_0, z_0, rho, and the others take one PCG step (Alg. 2 / Alg. 3).  With a
+// boundary stage in every macro step, an outer step with J PCG steps spans
+// J + 1 macro steps; with one every P macro steps a slice waits at most
+// P - 1 macro steps per outer step.
+void enqueue_macro(firls_ctx* c, const firls_params& sc, bool boundary_stage = true) {
   const int B = c->batch, n = c->n;
-  {
-    TMark m(c, FIRLS_K_OTHER, 3);
-    outer_apply(B, n, c->stream, c->st, c->x, c->dx, c->part);
-    outer_end(B, c->stream, c->st, c->part, axpy_ctas(n), sc.outer_tol, sc.outer_tol_kind, sc.outer_stall_tol);
-    boundary_view(B, c->stream, c->st, c->stw);
+  if (boundary_stage) {
+    {
+      TMark m(c, FIRLS_K_OTHER, 3);
+      outer_apply(B, n, c->stream, c->st, c->x, c->dx, c->part);
+      outer_end(B, c->stream, c->st, c->part, axpy_ctas(n), sc.outer_tol, sc.outer_tol_kind, sc.outer_stall_tol);
+      boundary_view(B, c->stream, c->st, c->stw);
+    }
+    enqueue_weights(c, c->x, sc.precond, c->stw);
   }
-  enqueue_weights(c, c->x, sc.precond, c->stw);
   enqueue_S(c, -1, c->z, c->d, c->q);
   {
     TMark m(c, FIRLS_K_SCALARS, 1);
@@ -327,12 +332,15 @@ void enqueue_macro(firls_ctx* c, const firls_params& sc) {
   enqueue_precond(c, ILU_PER_SLICE, sc);
 }
 
+int period_of(const firls_params& sc) { return sc.boundary_period > 1 ? sc.boundary_period : 1; }
+
 // Two parameter sets capture the same macro-step graph (everything but the
 // outer count and the lambdas, which live in device memory).
 bool same_schedule(const firls_params& a, const firls_params& b) {
   return a.pcg_iters == b.pcg_iters && a.pcg_tol == b.pcg_tol && a.outer_tol == b.outer_tol &&
          a.outer_tol_kind == b.outer_tol_kind && a.precond == b.precond && a.outer_stall_tol == b.outer_stall_tol &&
-         a.pcg_tol_kind == b.pcg_tol_kind && a.pcg_iters_late == b.pcg_iters_late && a.outer_late == b.outer_late;
+         a.pcg_tol_kind == b.pcg_tol_kind && a.pcg_iters_late == b.pcg_iters_late && a.outer_late == b.outer_late &&
+         period_of(a) == period_of(b);
 }
 
 firls_status check_params(firls_ctx* c, const firls_params* p) {
@@ -345,6 +353,7 @@ firls_status check_params(firls_ctx* c, const firls_params* p) {
   if (!(p->outer_stall_tol >= 0.f)) return fail(c, FIRLS_E_INVALID_ARG, "outer_stall_tol must be >= 0");
   if (p->pcg_tol_kind != 0 && p->pcg_tol_kind != 1) return fail(c, FIRLS_E_INVALID_ARG, "bad pcg_tol_kind");
   if (p->pcg_iters_late < 0 || p->outer_late < 0) return fail(c, FIRLS_E_INVALID_ARG, "bad late inner schedule");
+  if (p->boundary_period < 0 || p->boundary_period > 64) return fail(c, FIRLS_E_INVALID_ARG, "bad boundary_period");
   const int B = c->batch;
   for (int s = 0; s < B; ++s) {
     const float l = p->lambda_per_slice ? p->lambda_per_slice[s] : p->lambda;
@@ -391,7 +400,7 @@ firls_status enqueue_setup(firls_ctx* c, const void* b, const firls_params* p, c
   }
   CU(cudaMemsetAsync(c->dx, 0, sizeof(float2) * (size_t)B * n * n, c->stream));
   state_init(B, c->stream, c->st, c->part, fft_col_ctas(n), c->counts, n, c->lam_d, c->lamtv_d, eps_of(p),
-             p->outer_iters);
+             p->outer_iters, PH_BOUNDARY);
   return cuda_check(c, cudaGetLastError(), "setup launch");
 }
 
@@ -412,7 +421,7 @@ firls_status macro_graph(firls_ctx* c, const firls_params& sc, int steps, cudaGr
   if (c->timing) marks_reset(c);
   cudaGraph_t g = nullptr;
   CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-  for (int i = 0; i < steps; ++i) enqueue_macro(c, sc);
+  for (int i = 0; i < steps; ++i) enqueue_macro(c, sc, i % period_of(sc) == 0);
   cudaError_t e = cudaStreamEndCapture(c->stream, &g);
   if (e != cudaSuccess) return cuda_check(c, e, "graph capture");
   cudaGraphExec_t ex = nullptr;
@@ -447,7 +456,7 @@ firls_status run_macro(firls_ctx* c, const firls_params& sc, long total, int chu
     if (t) marks_reset(c);
     for (long k = 0; k < total; ++k) {
       if (k == chunk) c->timing = false;
-      enqueue_macro(c, sc);
+      enqueue_macro(c, sc, k % period_of(sc) == 0);
     }
     c->timing = t;
     c->marks_valid = t;
@@ -469,7 +478,9 @@ firls_status run_macro(firls_ctx* c, const firls_params& sc, long total, int chu
   if (rem) {
     const bool t = c->timing;
     c->timing = false;  // the marks stay those of the chunk graph
-    const firls_status s = macro_graph(c, sc, 1, &ex1);
+    firls_params one = sc;
+    one.boundary_period = 1;  // single steps: each with its boundary stage
+    const firls_status s = macro_graph(c, one, 1, &ex1);
     c->timing = t;
     TRY(s);
     for (long k = 0; k < rem; ++k) CU(cudaGraphLaunch(ex1, c->stream));
@@ -482,13 +493,14 @@ firls_status run_macro(firls_ctx* c, const firls_params& sc, long total, int chu
 // and one more that applies the last one; without tolerances every slice
 // finishes exactly then.
 long solve_steps(const firls_params* p) {
-  long n = 1;
+  const int P = period_of(*p);
+  long n = P;  // the boundary stage that applies the last outer step comes within P steps
   for (int k = 0; k < p->outer_iters; ++k)
-    n += 1 + ((p->pcg_iters_late > 0 && k >= p->outer_late) ? p->pcg_iters_late : p->pcg_iters);
+    n += P + ((p->pcg_iters_late > 0 && k >= p->outer_late) ? p->pcg_iters_late : p->pcg_iters);
   return n;
 }
 bool has_tolerances(const firls_params* p) {
-  return p->pcg_tol > 0.f || p->outer_tol > 0.f || p->outer_stall_tol > 0.f;
+  return p->pcg_tol > 0.f || p->outer_tol > 0.f || p->outer_stall_tol > 0.f || period_of(*p) > 1;
 }
 
 firls_status collect_stats(firls_ctx* c, firls_stats* stats, bool* breakdown) {
@@ -734,6 +746,7 @@ extern "C" firls_status firls_solve_multi(firls_ctx* const* ctxs, int n_ctx, con
     TRY(check_params(c, &pa[i]));
     if (pa[i].outer_iters != p->outer_iters || !same_schedule(pa[i], *p))
       return fail(c, FIRLS_E_INVALID_ARG, "solve_multi: contexts must share the schedule and tolerances");
+    if (period_of(pa[i]) != 1) return fail(c, FIRLS_E_INVALID_ARG, "solve_multi: boundary_period must be 0 or 1");
     if (!c->stream || !c->use_graph) graphable = false;
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == c || (ctxs[j]->stream == c->stream && c->stream)) graphable = false;
@@ -910,7 +923,7 @@ extern "C" firls_status firls_apply_AHA(firls_ctx* c, const void* d, void* q) {
   p.lambda_per_slice = zeros.data();
   p.lambda_tv_per_slice = zeros.data();
   TRY(upload_params(c, &p));
-  state_init(c->batch, c->stream, c->st, c->part, 0, c->counts, c->n, c->lam_d, c->lamtv_d, 1e-10f, 1);
+  state_init(c->batch, c->stream, c->st, c->part, 0, c->counts, c->n, c->lam_d, c->lamtv_d, 1e-10f, 1, PH_START);
   FftArgs a = fft_args(c);
   const size_t bytes = sizeof(float2) * (size_t)c->batch * c->n * c->n;
   CU(cudaMemcpyAsync(c->d, d, bytes, cudaMemcpyDeviceToDevice, c->stream));
@@ -949,7 +962,7 @@ extern "C" firls_status firls_apply_S_P(firls_ctx* c, const firls_params* p, con
   TRY(upload_params(c, p));
   const int B = c->batch, n = c->n;
   const size_t bytes = sizeof(float2) * (size_t)B * n * n;
-  state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, eps_of(p), 1);
+  state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, eps_of(p), 1, PH_START);
   CU(cudaMemcpyAsync(c->x, x, bytes, cudaMemcpyDeviceToDevice, c->stream));
   enqueue_weights(c, c->x, p->precond, c->st);  // every slice starts an outer step here
   // q = S d
@@ -976,7 +989,7 @@ firls_status objective_parts(firls_ctx* c, const void* b, const firls_params* p,
   a.mode = 2;
   // row FFT of x into t (state checks off: the kernel runs every slice)
   TRY(cuda_check(c, cudaMemsetAsync(c->st, 0, sizeof(SliceState) * B, c->stream), "memset"));
-  state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, eps, 1);
+  state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, eps, 1, PH_START);
   a.st = c->st;
   fft_row_fwd(n, a);
   a.b = static_cast<const float2*>(b);
@@ -1060,7 +1073,7 @@ extern "C" firls_status firls_slot_load(firls_ctx* c, int s, const uint8_t* mask
   CU(cudaMemsetAsync(c->dx + off, 0, N * sizeof(float2), c->stream));
   // no outer-step limit: the caller reads the slot out when it wants
   state_init(1, c->stream, c->st + s, part, fft_col_ctas(n), c->counts + s, n, c->lam_d + s, c->lamtv_d + s,
-             eps > 0.f ? eps : 1e-10f, 1 << 30);
+             eps > 0.f ? eps : 1e-10f, 1 << 30, PH_BOUNDARY);
   return cuda_check(c, cudaGetLastError(), "slot_load");
 }
 
@@ -1171,7 +1184,7 @@ extern "C" firls_status firls_autotune(firls_ctx* c, const char* cache_path) {
     p.lambda = 1e-3f;
     p.lambda_tv = 1e-3f;
     TRY(upload_params(c, &p));
-    state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, 1e-10f, 1);
+    state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, 1e-10f, 1, PH_START);
     if (has_tv(c)) penta_setup(B, n, c->stream, c->st, c->wtv, nullptr, c->ia);
     float best = 1e30f;
     if (c->kind) {
@@ -1285,7 +1298,7 @@ extern "C" firls_status firls_data_consistency(firls_ctx* c, const void* b, cons
   p.lambda_per_slice = zeros.data();
   p.lambda_tv_per_slice = zeros.data();
   TRY(upload_params(c, &p));
-  state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, 1e-10f, 1);
+  state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, 1e-10f, 1, PH_START);
   FftArgs a = fft_args(c);
   a.d = const_cast<float2*>(static_cast<const float2*>(x));
   a.t = c->t;

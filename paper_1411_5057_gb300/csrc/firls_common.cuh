@@ -17,14 +17,18 @@ constexpr int STALL_STEPS = 4;
 // Where a slice is in its own outer step.  Every slice advances on its own:
 // one launch sequence (a macro step) does a PCG step for the slices in
 // PH_PCG and the outer-step transition for the others.
-//   PH_BOUNDARY: start of an outer step: weights and P from x^k, S x^k, the
-//                first residual r_0 = A^H b - S x^k, z_0 and rho.
+//   PH_BOUNDARY: an outer step is due: the next macro step with a boundary
+//                stage updates the weights and P from x^k.
+//   PH_START:    weights and P are ready: S x^k, the first residual
+//                r_0 = A^H b - S x^k, z_0 and rho.
 //   PH_PCG:      PCG step pcg_j + 1 of the outer step.
-//   PH_END:      the outer step's PCG has stopped; the next macro step adds
-//                its update to x, measures the relative change, applies the
-//                stopping rules and, if the slice goes on, starts the next
-//                outer step.
-enum { PH_BOUNDARY = 0, PH_PCG = 1, PH_END = 2 };
+//   PH_END:      the outer step's PCG has stopped; the next boundary stage
+//                adds its update to x, measures the relative change, applies
+//                the stopping rules and, if the slice goes on, sets
+//                PH_BOUNDARY for its next outer step.
+// Boundary stages (weights, transitions) may run only every few macro
+// steps; slices in PH_BOUNDARY or PH_END wait for the next one.
+enum { PH_BOUNDARY = 0, PH_PCG = 1, PH_END = 2, PH_START = 3 };
 
 // Per-slice PCG / outer-loop state, FP64 scalars (the only FP64 steps:
 // inner products, alpha, beta, rho, residual norms, relative change).
@@ -69,6 +73,8 @@ FI float rdot2(float2 a, float2 b) { return fmaf(a.x, b.x, a.y * b.y); }
 
 FI bool slice_running(const SliceState* st, int s) { return st[s].active && !st[s].done; }
 FI bool slice_in_pcg(const SliceState* st, int s) { return slice_running(st, s) && st[s].phase == PH_PCG; }
+// A slice that takes part in this macro step's S apply and PCG update.
+FI bool slice_working(int phase) { return phase == PH_START || phase == PH_PCG; }
 
 // PCG scalar updates of one slice (FP64), shared by the scalar kernels and
 // the kernels that finish them in place.

@@ -81,8 +81,8 @@ __global__ void __launch_bounds__(256) k_row_fwd(const float2* __restrict__ z, f
   int mode = mode_arg;
   if (mode_arg < 0) {
     const int ph = st[s].phase;
-    if (ph == PH_END) return;
-    mode = ph == PH_BOUNDARY ? 3 : (st[s].pcg_j == 0 ? 0 : 1);
+    if (ph != PH_START && ph != PH_PCG) return;  // waiting for its outer-step transition
+    mode = ph == PH_START ? 3 : (st[s].pcg_j == 0 ? 0 : 1);
   }
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tw = reinterpret_cast<float2*>(smem);
@@ -91,25 +91,27 @@ __global__ void __launch_bounds__(256) k_row_fwd(const float2* __restrict__ z, f
   const int lr = threadIdx.x / T, t = threadIdx.x % T;
   const int row = blockIdx.x * R + lr;
   const size_t base = (size_t)s * N * N + (size_t)row * N;
-  const double beta = st[s].beta;
+  const float beta = (float)st[s].beta;
   float2 v[E];
+  // one loop per mode, so that each touches only its own arrays
+  if (mode == 1) {
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const size_t i = base + t + T * e;
-    float2 dv;
-    if (mode == 0) {
-      dv = z[i];
-      d[i] = dv;
-    } else if (mode == 1) {
-      dv = cfma((float)beta, d[i], z[i]);
-      d[i] = dv;
-    } else if (mode == 3) {
-      dv = x[i];
-      d[i] = dv;
-    } else {
-      dv = d[i];
+    for (int e = 0; e < E; ++e) {
+      const size_t i = base + t + T * e;
+      v[e] = cfma(beta, d[i], z[i]);
+      d[i] = v[e];
     }
-    v[e] = dv;
+  } else if (mode == 0 || mode == 3) {
+    const float2* __restrict__ src = mode == 0 ? z : x;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const size_t i = base + t + T * e;
+      v[e] = src[i];
+      d[i] = v[e];
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = d[base + t + T * e];
   }
   __syncthreads();
   fft_line<N, -1>(v, lines + lr * 2 * LW, lines + lr * 2 * LW + LW, tw, t);

@@ -1353,8 +1353,8 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
   // ILU_PER_SLICE: the first residual for a slice at the start of its outer
   // step, a PCG step otherwise
   const int ph = st[s].phase;
-  if (mode_arg == ILU_PER_SLICE && ph == PH_END) return;
-  const int mode = mode_arg != ILU_PER_SLICE ? mode_arg : (ph == PH_BOUNDARY ? ILU_INIT : ILU_STEP);
+  if (mode_arg == ILU_PER_SLICE && !slice_working(ph)) return;
+  const int mode = mode_arg != ILU_PER_SLICE ? mode_arg : (ph == PH_START ? ILU_INIT : ILU_STEP);
   // wait_test (failure-detection test only): the producer issues no copy and
   // every wait gives up after its first poll, so the waits run out with
   // nothing in flight and the slice is reported faulted
@@ -1728,8 +1728,8 @@ __global__ void k_axpy(int N, int mode_arg, const SliceState* __restrict__ st, d
   const int s = blockIdx.y;
   if (!slice_running(st, s)) return;
   const int ph = st[s].phase;
-  if (mode_arg == AXPY_PER_SLICE && ph == PH_END) return;
-  const int mode = mode_arg != AXPY_PER_SLICE ? mode_arg : (ph == PH_BOUNDARY ? AXPY_INIT : AXPY_STEP);
+  if (mode_arg == AXPY_PER_SLICE && !slice_working(ph)) return;
+  const int mode = mode_arg != AXPY_PER_SLICE ? mode_arg : (ph == PH_START ? AXPY_INIT : AXPY_STEP);
   __shared__ double red[32];
   const float alpha = (float)st[s].alpha;
   const size_t base = (size_t)s * N;
@@ -1769,8 +1769,8 @@ __global__ void k_axpy_diag(int N, int mode_arg, const SliceState* __restrict__ 
   const int s = blockIdx.y;
   if (!slice_running(st, s)) return;
   const int ph = st[s].phase;
-  if (mode_arg == AXPY_PER_SLICE && ph == PH_END) return;
-  const int mode = mode_arg != AXPY_PER_SLICE ? mode_arg : (ph == PH_BOUNDARY ? AXPY_INIT : AXPY_STEP);
+  if (mode_arg == AXPY_PER_SLICE && !slice_working(ph)) return;
+  const int mode = mode_arg != AXPY_PER_SLICE ? mode_arg : (ph == PH_START ? AXPY_INIT : AXPY_STEP);
   __shared__ double red[32];
   const float alpha = (float)st[s].alpha;
   const size_t base = (size_t)s * N;
@@ -2079,7 +2079,7 @@ FI double sum_parts(const double* part, int s, int slot, int np) {
 }
 
 __global__ void k_state_init(int B, SliceState* st, const double* part, int np, const int* counts, int N,
-                             const float* lam, const float* lam_tv, float eps, int outer_max) {
+                             const float* lam, const float* lam_tv, float eps, int outer_max, int phase) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B) return;
   SliceState v;
@@ -2091,7 +2091,7 @@ __global__ void k_state_init(int B, SliceState* st, const double* part, int np, 
   v.rr0 = v.rhs2;
   v.relchg = 0.0;
   v.stall = 0;
-  v.phase = PH_BOUNDARY;
+  v.phase = phase;
   v.pcg_j = 0;
   v.outer_max = outer_max;
   for (int i = 0; i < MU_WINDOW; ++i) v.hist[i] = 0.f;
@@ -2112,24 +2112,30 @@ __global__ void k_state_init(int B, SliceState* st, const double* part, int np, 
 }
 
 void state_init(int batch, cudaStream_t s, SliceState* st, const double* part, int np, const int* counts,
-                int n, const float* lam, const float* lam_tv, float eps, int outer_max) {
+                int n, const float* lam, const float* lam_tv, float eps, int outer_max, int phase) {
   k_state_init<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np, counts, n * n, lam, lam_tv, eps,
-                                                   outer_max);
+                                                   outer_max, phase);
 }
 
-// The slices at the start of an outer step, as a copy of the state in which
-// every other slice reads as done: the weight and preconditioner set-up
-// kernels, which skip done slices and never write the state, then work on
-// exactly those slices.
-__global__ void k_boundary_view(int B, const SliceState* __restrict__ st, SliceState* __restrict__ view) {
+// The slices whose outer step is due (PH_BOUNDARY), as a copy of the state in
+// which every other slice reads as done: the weight and preconditioner
+// set-up kernels, which skip done slices and never write the state, then
+// work on exactly those slices.  The slices themselves move to PH_START (this
+// macro step's S apply and PCG update form their first residual, after the
+// set-up kernels have run).
+__global__ void k_boundary_view(int B, SliceState* __restrict__ st, SliceState* __restrict__ view) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B) return;
   SliceState v = st[s];
-  if (v.phase != PH_BOUNDARY) v.done = 1;
+  if (v.phase != PH_BOUNDARY) {
+    v.done = 1;
+  } else if (v.active && !v.done) {
+    st[s].phase = PH_START;
+  }
   view[s] = v;
 }
 
-void boundary_view(int batch, cudaStream_t s, const SliceState* st, SliceState* view) {
+void boundary_view(int batch, cudaStream_t s, SliceState* st, SliceState* view) {
   k_boundary_view<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, view);
 }
 
@@ -2151,7 +2157,7 @@ __global__ void k_pcg_scalars(int B, SliceState* st, const double* part, int np_
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B || !slice_running(st, s)) return;
   const int ph = st[s].phase;
-  const bool init = mode == SCALARS_INIT || (mode == SCALARS_PER_SLICE && ph == PH_BOUNDARY);
+  const bool init = mode == SCALARS_INIT || (mode == SCALARS_PER_SLICE && ph == PH_START);
   const bool step = mode == SCALARS_STEP || (mode == SCALARS_PER_SLICE && ph == PH_PCG);
   const double rz = sum_parts(part, s, SLOT_RZ, np_rz), rr = sum_parts(part, s, SLOT_RR, np_rr);
   if (init)

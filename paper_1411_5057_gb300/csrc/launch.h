@@ -134,14 +134,18 @@ enum ScalarsMode { SCALARS_INIT = 0, SCALARS_STEP = 1, SCALARS_PER_SLICE = -1 };
 void pcg_scalars(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts_rz, int nparts_rr,
                  int mode, const PcgSched& ps);
 // view = st with every slice not at the start of its outer step marked done
-void boundary_view(int batch, cudaStream_t s, const SliceState* st, SliceState* view);
+// (and the slices whose outer step is due move to PH_START)
+void boundary_view(int batch, cudaStream_t s, SliceState* st, SliceState* view);
 // x += dx (the outer step's accumulated update) with partial ||dx||^2 and
 // ||x||^2 (before the update) for the relative change.
 void outer_apply(int batch, int n, cudaStream_t s, const SliceState* st, float2* x, float2* dx,
                  double* part);
 void outer_end(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts,
                float outer_tol, int tol_kind, float stall_tol);
+// phase: PH_BOUNDARY for a solve (its first outer step is due), PH_START for
+// the single operator applications (no outer step)
 void state_init(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts_rhs,
-                const int* counts, int n, const float* lam, const float* lam_tv, float eps, int outer_max);
+                const int* counts, int n, const float* lam, const float* lam_tv, float eps, int outer_max,
+                int phase);
 
 }  // namespace firls

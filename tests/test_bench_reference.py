@@ -28,6 +28,7 @@ def test_reference_arm_line(procs):
     ours = bench.workload_config(type("A", (), {"queue": 608, "batch": 304, "outer": bench.OUTER,
                                                 "inner": bench.INNER, "inner_late": bench.INNER_LATE,
                                                 "outer_late": bench.OUTER_LATE,
+                                                "boundary_period": bench.BOUNDARY_PERIOD,
                                                 "outer_tol": bench.OUTER_TOL, "stall_tol": bench.STALL_TOL,
                                                 "steady": 0})(), 1)
     assert line["config"] == ours

@@ -70,3 +70,21 @@ def test_slices_with_different_inner_counts_are_independent(F):
         assert torch.equal(x1[0], xb[i]), i
         one.close()
     ctx.close()
+
+
+def test_boundary_period_changes_timing_not_results(F):
+    """Outer-step transitions every 4th macro step: slices wait for them, but
+    every slice computes exactly what it computes with a transition in every
+    macro step (same outer steps, same PCG steps, same x)."""
+    probs = [fs.make_problem(64, 0.2, 0.01, 95 + i, real=False, psi=fs.PSI_TV | fs.PSI_DB4, levels=3, lam=5e-4,
+                             lam_tv=1e-3) for i in range(3)]
+    ctx, b = _ctx(F, probs)
+    base = dict(lam=5e-4, lam_tv=1e-3, outer_tol=1e-4, stop_on_distance=False)
+    x1, s1 = ctx.solve(b, F.make_params(30, 15, **base), stats=True)
+    x1 = x1.clone()
+    _, od1, _, pc1 = ctx.slot_status(with_pcg=True)
+    x4, s4 = ctx.solve(b, F.make_params(30, 15, boundary_period=4, **base), stats=True)
+    _, od4, _, pc4 = ctx.slot_status(with_pcg=True)
+    assert od1 == od4 and pc1 == pc4
+    assert torch.equal(x1, x4)
+    ctx.close()
