@@ -300,6 +300,12 @@ def run_ours(args):
         print("[bench] PCG steps to 1e-6: " + json.dumps({k: v for k, v in pcg_iters.items()
                                                            if isinstance(v, dict)}), file=sys.stderr, flush=True)
 
+    # ---- the uneven batch (four sizes in one graph), untimed w.r.t. the main line ----
+    c4 = uneven_batch_run(F, torch, args) if args.uneven else None
+    if c4 is not None:
+        print(f"[bench] uneven batch: {c4['value']} recons/s ({c4['s_per_batch']} s per 64 slices), "
+              f"accuracy {json.dumps(c4['accuracy'])}", file=sys.stderr, flush=True)
+
     # ---- learned warm start (CNN trained on solver-generated pairs) ----
     learned = None
     if args.learned:
@@ -321,7 +327,7 @@ def run_ours(args):
                                "capped": int((steps >= args.outer).sum()),
                                "mean_pcg_steps": round(float(np.mean(pcg_counts)), 1),
                                "max_pcg_steps": int(np.max(pcg_counts))},
-               "accuracy": acc, "learned": learned, "pcg_iterations": pcg_iters}
+               "accuracy": acc, "learned": learned, "pcg_iterations": pcg_iters, "uneven_batch": c4}
         print(json.dumps(out), flush=True)
     ctx.close()
     if dist is not None:
@@ -426,9 +432,68 @@ def accuracy(xs, first_seed, steps=None):
     return out
 
 
+XSTAR_UNEVEN_DIR = os.path.join(ROOT, "tests", "golden", "xstar_uneven")
+
+
+def uneven_batch_run(F, torch, args, reps=2):
+    """The uneven batch: 64 slices, 16 each at 128^2, 192^2, 256^2 and 320^2
+    (TV + D4, per-slice lambdas and mask ratios, seeds 1000..1063), solved
+    together by firls_solve_multi (one context and stream per size, one
+    graph) with the bench schedule.  Reconstructions per second over the 64,
+    device-resident inputs, and the error of the slices that have a stored
+    oracle x*.  Untimed set-up; `reps` timed solves after one warm-up."""
+    import firls_synth as fs
+    groups = {}
+    for seed, p in zip(range(1000, 1064), fs.uneven_batch()):
+        groups.setdefault(p.n, []).append((seed, p))
+    sizes = sorted(groups)
+    streams = [torch.cuda.Stream() for _ in sizes]
+    ctxs, bs, ps, outs = [], [], [], []
+    for n, st in zip(sizes, streams):
+        probs = [p for _, p in groups[n]]
+        with torch.cuda.stream(st):
+            ctx = F.Context(n, batch=len(probs), stream=st)
+            ctx.set_operator(torch.from_numpy(np.stack([p.mask for p in probs])).cuda(), probs[0].psi, probs[0].levels)
+            b = torch.from_numpy(np.stack([p.b for p in probs]).astype(np.complex64)).cuda()
+        ctxs.append(ctx)
+        bs.append(b)
+        outs.append(torch.empty_like(b))
+        ps.append(F.make_params(args.outer, args.inner, lam_per_slice=[p.lam for p in probs],
+                                lam_tv_per_slice=[p.lam_tv for p in probs], outer_tol=args.outer_tol,
+                                stop_on_distance=True, stall_tol=args.stall_tol, pcg_late=args.inner_late,
+                                outer_late=args.outer_late))
+    torch.cuda.synchronize()
+    F.solve_multi(ctxs, bs, ps, outs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        stats = F.solve_multi(ctxs, bs, ps, outs, stats=True)
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / reps
+    outer = [s["outer_done"] for s in stats]
+    errs = {}
+    if os.path.isdir(XSTAR_UNEVEN_DIR):
+        for n, out in zip(sizes, outs):
+            for i, (seed, _) in enumerate(groups[n]):
+                f = os.path.join(XSTAR_UNEVEN_DIR, f"seed{seed}.npz")
+                if os.path.exists(f):
+                    xs = np.load(f)["x"].astype(np.complex128)
+                    x = out[i].cpu().numpy().astype(np.complex128)
+                    errs[seed] = float(np.linalg.norm(x - xs) / np.linalg.norm(xs))
+    for c in ctxs:
+        c.close()
+    return {"value": round(64 / sec, 3), "unit": UNIT, "s_per_batch": round(sec, 4),
+            "workload": "64 slices, 16 each at 128^2/192^2/256^2/320^2, TV + D4, per-slice lambda and mask",
+            "method": "firls_solve_multi: one graph over four contexts (one per size), bench schedule",
+            "max_outer_steps_per_size": dict(zip([str(n) for n in sizes], outer)),
+            "accuracy": {"n_checked": len(errs), "max_rel_err": max(errs.values()) if errs else None,
+                         "rel_err_by_seed": errs}}
+
+
 def precond_comparison(F, torch, stream, outer_steps=(1, 5, 20), tol=1e-6, cap=5000):
     """PCG steps to ||r|| <= tol ||A^H b|| with the proposed P, Jacobi and no
-    preconditioner (Sec. 5.2, Fig. 2 and the TV figure), from the iterates of
+    preconditioner (Sec. 5.2, Fig. 2 and the TV figure), and with TV also the
+    ILU(0) factors with updated pivots (Sec. 4.2's incomplete LU), from the iterates of
     the proposed PCG's own FIRLS trajectory (20 PCG steps per outer step) at
     the given outer steps; workload 1 (64^2 Haar l1, real) and one 256^2
     TV + D4 slice (seed 2).  Untimed."""
@@ -445,7 +510,7 @@ def precond_comparison(F, torch, stream, outer_steps=(1, 5, 20), tol=1e-6, cap=5
                 if k > 1:
                     x0 = ctx.solve(b, F.make_params(k - 1, 20, lam=p.lam, lam_tv=p.lam_tv)).clone()
                 row = {}
-                for pre in ("paper", "jacobi", "none"):
+                for pre in ("paper", "jacobi", "none") + (("ilu0",) if p.psi & fs.PSI_TV else ()):
                     _, st = ctx.solve(b, F.make_params(1, cap, lam=p.lam, lam_tv=p.lam_tv, pcg_tol=tol,
                                                        precond=pre), x0=x0, stats=True)
                     row[pre] = int(st["pcg_steps"])
@@ -600,6 +665,7 @@ def main(argv=None):
     ap.add_argument("--ref-procs", type=int, default=0,
                     help="reference arm: oracle instances run at once, one per host core (0: all cores)")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--uneven", type=int, default=1, help="also time the 64-slice uneven batch (1/0)")
     ap.add_argument("--precond-cmp", type=int, default=1,
                     help="report PCG steps to 1e-6 for the proposed, Jacobi and no preconditioner (1/0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

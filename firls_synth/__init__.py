@@ -27,6 +27,7 @@ PHANTOM, PHASE, MASK, NOISE, PARAMS = 0, 1, 2, 3, 4
 PSI_HAAR = 1
 PSI_DB4 = 2
 PSI_TV = 4
+PSI_TV_ANISO = 8   # l1 (anisotropic) TV
 
 
 def _rng(seed: int, stream: int) -> np.random.Generator:

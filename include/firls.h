@@ -54,10 +54,13 @@ typedef enum {
                                  slices it names hold invalid results        */
 } firls_status;
 
-/* Regulariser bitmask (psi_kind).  HAAR and DB4 are exclusive; TV may be
- * combined with either wavelet, in which case both terms enter S and the
- * TV preconditioner's diagonal gains lambda * diag(Phi^T W Phi). */
-enum { FIRLS_PSI_HAAR = 1, FIRLS_PSI_DB4 = 2, FIRLS_PSI_TV = 4 };
+/* Regulariser bitmask (psi_kind).  HAAR and DB4 are exclusive; TV
+ * (isotropic, Eq. iso) or TV_ANISO (l1 TV, Eq. l1: ||D1 x||_1 + ||D2 x||_1,
+ * weights W1 = (|D1 x|^2 + eps)^-1/2, W2 = (|D2 x|^2 + eps)^-1/2; Sec. 4.1
+ * derives it like the isotropic form) may be combined with either wavelet, in
+ * which case both terms enter S and the TV preconditioner's diagonal gains
+ * lambda * diag(Phi^T W Phi).  TV and TV_ANISO are exclusive. */
+enum { FIRLS_PSI_HAAR = 1, FIRLS_PSI_DB4 = 2, FIRLS_PSI_TV = 4, FIRLS_PSI_TV_ANISO = 8 };
 
 /* Context flags. FIRLS_REAL_X: the unknown x is real (A^T y = Re F^H R^T y);
  * buffers are still complex64 and their imaginary parts are ignored on
@@ -147,8 +150,12 @@ typedef struct {
  * and the TV figure).  PAPER: the proposed P (Eq. pog: Phi^T (abar I +
  * lambda G^T W G)^{-1} Phi without TV; Eq. ptv with the printed L U factors of
  * Sec. 4.2 with TV).  JACOBI: P = diag(S) = abar + lambda diag(Phi^T G^T W G
- * Phi) + lambda_tv diag(D1^T W D1 + D2^T W D2).  NONE: P = I (standard CG). */
-enum { FIRLS_PRECOND_PAPER = 0, FIRLS_PRECOND_JACOBI = 1, FIRLS_PRECOND_NONE = 2 };
+ * Phi) + lambda_tv diag(D1^T W D1 + D2^T W D2).  NONE: P = I (standard CG).
+ * ILU0 (TV only): the penta-diagonal P of Eq. ptv factored by the incomplete
+ * LU with zero fill and updated pivots, d_i = a_i - P_{i,i-1}^2 / d_{i-1}
+ * - P_{i,i-n}^2 / d_{i-n}, L = I + L_P diag(d)^{-1}, U = diag(d) + U_P (L U
+ * equals P on P's pattern; the printed factors keep d = a). */
+enum { FIRLS_PRECOND_PAPER = 0, FIRLS_PRECOND_JACOBI = 1, FIRLS_PRECOND_NONE = 2, FIRLS_PRECOND_ILU0 = 3 };
 
 typedef struct {
   int outer_done;            /* outer steps run (max over slices)             */
@@ -322,9 +329,10 @@ firls_status firls_warm_start_guard(firls_ctx* ctx, const void* b, const firls_p
                                     void* x0, int* chosen);
 
 /* Copy out the current per-coefficient wavelet weights diag(G^T W G)
- * (device float [batch][n][n]) and TV weights (device float [batch][n][n]);
- * either pointer may be NULL. */
-firls_status firls_get_weights(firls_ctx* ctx, float* w_wavelet, float* w_tv);
+ * (device float [batch][n][n]), the TV weights W (W1 for l1 TV) and, for l1
+ * TV only, W2 (device float [batch][n][n] each); any pointer may be NULL
+ * (w_tv2 must be NULL without FIRLS_PSI_TV_ANISO: FIRLS_E_STATE). */
+firls_status firls_get_weights(firls_ctx* ctx, float* w_wavelet, float* w_tv, float* w_tv2);
 
 /* Copy out the TV preconditioner's diagonal pieces of the last outer step
  * (Eq. ptv with the wavelet term of the combined TV + wavelet case):

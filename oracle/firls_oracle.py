@@ -47,7 +47,8 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spl
 
 EPS = 1e-10
-PSI_HAAR, PSI_DB4, PSI_TV = 1, 2, 4
+PSI_HAAR, PSI_DB4, PSI_TV, PSI_TV_ANISO = 1, 2, 4, 8
+PSI_ANY_TV = PSI_TV | PSI_TV_ANISO
 
 
 # ---------------------------------------------------------------------------
@@ -252,6 +253,37 @@ def tv_iso(x_flat, D1, D2, eps=0.0):
     return float(np.sum(np.sqrt(np.abs(g1) ** 2 + np.abs(g2) ** 2 + eps)))
 
 
+def tv_weights_aniso(x_flat, D1, D2, eps=EPS):
+    """l1 TV (Eq. l1): every entry of D1 x and of D2 x is its own group, so
+    W1_i = (|(D1 x)_i|^2 + eps)^(-1/2) and W2_i = (|(D2 x)_i|^2 + eps)^(-1/2)
+    (Sec. 4.1: the l1 form follows the isotropic derivation)."""
+    return (np.abs(D1 @ x_flat) ** 2 + eps) ** -0.5, (np.abs(D2 @ x_flat) ** 2 + eps) ** -0.5
+
+
+def tv_l1(x_flat, D1, D2, eps=0.0):
+    """||D1 x||_1 + ||D2 x||_1 (Eq. l1), eps-smoothed when eps > 0."""
+    return float(np.sum(np.sqrt(np.abs(D1 @ x_flat) ** 2 + eps)) + np.sum(np.sqrt(np.abs(D2 @ x_flat) ** 2 + eps)))
+
+
+def ilu0_pivots(P, n):
+    """Pivots d of the incomplete LU factorisation with zero fill, ILU(0), of
+    the penta-diagonal P (offsets 1 and n): d_i = a_i - sum over the lower
+    neighbours j in {i-1, i-n} of P_ij^2 / d_j, so that L U equals P on P's
+    sparsity pattern with L = I + L_P diag(d)^-1, U = diag(d) + U_P."""
+    P = sp.csr_matrix(P)
+    N = P.shape[0]
+    d = np.zeros(N)
+    for i in range(N):
+        di = P[i, i]
+        for j in (i - 1, i - n):
+            if j >= 0:
+                pij = P[i, j]
+                if pij != 0.0:
+                    di -= pij * pij / d[j]
+        d[i] = di
+    return d
+
+
 # ---------------------------------------------------------------------------
 # diag(Phi^T W Phi) for the combined preconditioner (exact diagonal)
 # ---------------------------------------------------------------------------
@@ -298,7 +330,7 @@ def wavelet_diag(w, n, kind, levels):
 # The system S and the preconditioners
 # ---------------------------------------------------------------------------
 
-PRECONDS = ("paper", "jacobi", "none")
+PRECONDS = ("paper", "jacobi", "none", "ilu0")
 
 
 class System:
@@ -308,12 +340,16 @@ class System:
     ``precond`` selects P for the comparison of Sec. 5.2 (Fig. 2 and the TV
     figure): "paper" is the proposed P (Eq. pog, Eq. ptv with the printed L
     U factors), "jacobi" is P = diag(S) (conventional Jacobi PCG), "none" is
-    P = I (standard CG).
+    P = I (standard CG), "ilu0" (TV only) factors the penta-diagonal P of
+    Eq. ptv by ILU(0) with updated pivots instead of the printed factors.
+    ``psi`` may hold PSI_TV (isotropic, Eq. iso) or PSI_TV_ANISO (l1, Eq. l1).
     """
 
     def __init__(self, mask, real, psi, levels, lam, lam_tv, groups=None, eps=EPS, precond="paper"):
         if precond not in PRECONDS:
             raise ValueError("unknown preconditioner")
+        if precond == "ilu0" and not (psi & PSI_ANY_TV):
+            raise ValueError("ILU(0) factors the TV preconditioner")
         self.precond = precond
         self.eps = float(eps)
         self.mask = np.asarray(mask).astype(np.float64)
@@ -324,13 +360,16 @@ class System:
         self.kind = wavelet_kind(psi)
         self.levels = int(levels)
         self.lam = float(lam)
-        self.lam_tv = float(lam_tv) if psi & PSI_TV else 0.0
+        self.tv = bool(psi & PSI_ANY_TV)
+        self.aniso = bool(psi & PSI_TV_ANISO)
+        self.lam_tv = float(lam_tv) if self.tv else 0.0
         self.abar = a_bar(mask)
         self.G, self.sizes = group_matrix(groups, self.N)
-        if psi & PSI_TV:
+        if self.tv:
             self.D1, self.D2 = tv_matrices(self.n)
         self.w = None        # diag(G^T W G) (wavelet part)
-        self.Wtv = None      # TV weights
+        self.Wtv = None      # TV weights (isotropic); W1, W2 below for both forms
+        self.W1 = self.W2 = None
         self.L = self.U = None
         self.pinv = None
 
@@ -341,9 +380,16 @@ class System:
             c = wavedec2(x, self.kind, self.levels).reshape(-1)
             Wg = group_weights(c, self.G, self.sizes, self.eps)
             self.w = gwg_diag(Wg, self.G, self.sizes)
-        if self.psi & PSI_TV:
+        if self.aniso:
+            self.W1, self.W2 = tv_weights_aniso(xf, self.D1, self.D2, self.eps)
+        elif self.tv:
             self.Wtv = tv_weights(xf, self.D1, self.D2, self.eps)
+            self.W1 = self.W2 = self.Wtv
         self._build_preconditioner()
+
+    def tv_term(self):
+        """D1^T W1 D1 + D2^T W2 D2 (W1 = W2 = W for isotropic TV, Eq. sub)."""
+        return self.D1.T @ sp.diags(self.W1) @ self.D1 + self.D2.T @ sp.diags(self.W2) @ self.D2
 
     def diag_S(self):
         """diag(S): abar (every diagonal entry of A^H A, Sec. 5.4) plus
@@ -351,9 +397,8 @@ class System:
         d = np.full(self.N, self.abar)
         if self.kind:
             d = d + self.lam * wavelet_diag(self.w, self.n, self.kind, self.levels).reshape(-1)
-        if self.psi & PSI_TV:
-            Wd = sp.diags(self.Wtv)
-            d = d + self.lam_tv * (self.D1.T @ Wd @ self.D1 + self.D2.T @ Wd @ self.D2).diagonal()
+        if self.tv:
+            d = d + self.lam_tv * self.tv_term().diagonal()
         return d
 
     def _build_preconditioner(self):
@@ -362,19 +407,18 @@ class System:
             return
         if self.precond == "none":
             return
-        if self.psi & PSI_TV:
+        if self.tv:
             # P = abar I + lam (D1^T W D1 + D2^T W D2)  (Eq. ptv), penta-diagonal
-            Wd = sp.diags(self.Wtv)
-            P = (self.abar * sp.identity(self.N)
-                 + self.lam_tv * (self.D1.T @ Wd @ self.D1 + self.D2.T @ Wd @ self.D2))
+            P = self.abar * sp.identity(self.N) + self.lam_tv * self.tv_term()
             P = sp.csr_matrix(P)
             if self.kind:
                 P = P + sp.diags(self.lam * wavelet_diag(self.w, self.n, self.kind, self.levels).reshape(-1))
             self.P = sp.csr_matrix(P)
-            a = self.P.diagonal()
+            # printed factors: L = I + L_P diag(a)^-1, U = diag(a) + U_P with
+            # a = diag(P); ILU(0) uses the updated pivots instead of a
+            a = ilu0_pivots(self.P, self.n) if self.precond == "ilu0" else self.P.diagonal()
             LP = sp.tril(self.P, -1)
             UP = sp.triu(self.P, 1)
-            # printed factors: L = I + L_P diag(a)^-1, U = diag(a) + U_P
             self.L = sp.csr_matrix(sp.identity(self.N) + LP @ sp.diags(1.0 / a))
             self.U = sp.csr_matrix(sp.diags(a) + UP)
         else:
@@ -390,10 +434,9 @@ class System:
         if self.kind:
             c = wavedec2(x, self.kind, self.levels)
             out = out + self.lam * waverec2(self.w.reshape(self.n, self.n) * c, self.kind, self.levels)
-        if self.psi & PSI_TV:
+        if self.tv:
             xf = x.reshape(-1)
-            Wd = sp.diags(self.Wtv)
-            t = self.D1.T @ (Wd @ (self.D1 @ xf)) + self.D2.T @ (Wd @ (self.D2 @ xf))
+            t = self.D1.T @ (self.W1 * (self.D1 @ xf)) + self.D2.T @ (self.W2 * (self.D2 @ xf))
             out = out + self.lam_tv * t.reshape(self.n, self.n)
         return out
 
@@ -402,7 +445,7 @@ class System:
             return (self.jacobi * np.asarray(r).reshape(-1)).reshape(self.n, self.n)
         if self.precond == "none":
             return np.array(r, copy=True)
-        if self.psi & PSI_TV:
+        if self.tv:
             rf = r.reshape(-1)
             y = spl.spsolve_triangular(self.L, rf, lower=True)
             z = spl.spsolve_triangular(self.U, y, lower=False)
@@ -458,7 +501,10 @@ def objective(x, b, mask, real, psi, levels, lam, lam_tv, groups=None, eps=0.0):
         G, sizes = group_matrix(groups, N)
         c = wavedec2(x, kind, levels).reshape(-1)
         val += lam * group_l21(c, G, sizes, eps)
-    if psi & PSI_TV:
+    if psi & PSI_TV_ANISO:
+        D1, D2 = tv_matrices(n)
+        val += lam_tv * tv_l1(np.asarray(x).reshape(-1), D1, D2, eps)
+    elif psi & PSI_TV:
         D1, D2 = tv_matrices(n)
         val += lam_tv * tv_iso(np.asarray(x).reshape(-1), D1, D2, eps)
     return val

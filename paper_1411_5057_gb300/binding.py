@@ -17,8 +17,8 @@ FIRLS_OK = 0
 STATUS = {0: "FIRLS_OK", 1: "FIRLS_E_INVALID_ARG", 2: "FIRLS_E_SHAPE", 3: "FIRLS_E_GROUPMAP",
           4: "FIRLS_E_CUDA", 5: "FIRLS_E_NOMEM", 6: "FIRLS_E_BREAKDOWN", 7: "FIRLS_E_STATE",
           8: "FIRLS_E_DEVICE_TIMEOUT"}
-PSI_HAAR, PSI_DB4, PSI_TV = 1, 2, 4
-PRECONDS = {"paper": 0, "jacobi": 1, "none": 2}
+PSI_HAAR, PSI_DB4, PSI_TV, PSI_TV_ANISO = 1, 2, 4, 8
+PRECONDS = {"paper": 0, "jacobi": 1, "none": 2, "ilu0": 3}
 REAL_X = 1
 
 EXPORTED = ["firls_size_supported", "firls_create", "firls_set_operator", "firls_solve", "firls_solve_multi",
@@ -86,7 +86,7 @@ def lib():
     L.firls_apply_Phi.argtypes = [vp, vp, vp]
     L.firls_apply_PhiT.argtypes = [vp, vp, vp]
     L.firls_apply_S_P.argtypes = [vp, ctypes.POINTER(Params), vp, vp, vp, vp, vp]
-    L.firls_get_weights.argtypes = [vp, vp, vp]
+    L.firls_get_weights.argtypes = [vp, vp, vp, vp]
     L.firls_get_precond.argtypes = [vp, vp, vp]
     L.firls_set_tuning.argtypes = [vp, i32, i32, i32]
     L.firls_get_inverse_map.argtypes = [vp, vp, vp]
@@ -299,8 +299,8 @@ class Context:
                     "warm_start_guard")
         return [bool(v) for v in ch]
 
-    def get_weights(self, w_wavelet=None, w_tv=None):
-        self._check(lib().firls_get_weights(self.h, _ptr(w_wavelet), _ptr(w_tv)), "get_weights")
+    def get_weights(self, w_wavelet=None, w_tv=None, w_tv2=None):
+        self._check(lib().firls_get_weights(self.h, _ptr(w_wavelet), _ptr(w_tv), _ptr(w_tv2)), "get_weights")
 
     def get_precond(self, wavelet_diag=None, inv_a=None):
         self._check(lib().firls_get_precond(self.h, _ptr(wavelet_diag), _ptr(inv_a)), "get_precond")

@@ -35,6 +35,7 @@ struct firls_ctx {
   // dx: the update of the current outer step, sum_j alpha_j d_j, accumulated
   // from zero by the PCG steps and added to x once at the end of the step
   float *ww = nullptr, *wtv = nullptr, *ia = nullptr, *wdiag = nullptr;
+  float* wtv2 = nullptr;  // l1 TV: the vertical weights W2 (wtv then holds W1)
   float* wg = nullptr;
   int *gidx = nullptr, *goff = nullptr, *inv_off = nullptr, *inv_ids = nullptr;
   int *gcounts = nullptr, *gcursor = nullptr, *gerr = nullptr;
@@ -166,7 +167,9 @@ FftArgs fft_args(firls_ctx* c) {
   return a;
 }
 
-bool has_tv(const firls_ctx* c) { return (c->psi & FIRLS_PSI_TV) != 0; }
+bool has_tv(const firls_ctx* c) { return (c->psi & (FIRLS_PSI_TV | FIRLS_PSI_TV_ANISO)) != 0; }
+bool is_aniso(const firls_ctx* c) { return (c->psi & FIRLS_PSI_TV_ANISO) != 0; }
+float* tv2_of(const firls_ctx* c) { return is_aniso(c) ? c->wtv2 : nullptr; }
 
 // ---- timing marks: an event pair around each launch group of a class ----
 cudaEvent_t next_event(firls_ctx* c) {
@@ -230,6 +233,7 @@ void enqueue_S(firls_ctx* c, int mode, const float2* zin, float2* din, float2* q
   }
   a.u = c->kind ? c->u : nullptr;
   a.wtv = has_tv(c) ? c->wtv : nullptr;
+  a.wtv2 = tv2_of(c);
   a.q = q;
   { TMark m(c, FIRLS_K_ROW_IFFT, 1); fft_row_inv(c->n, a); }
 }
@@ -251,9 +255,11 @@ void enqueue_weights(firls_ctx* c, const float2* x, int precond, const SliceStat
   }
   if (has_tv(c)) {
     // with TV, 1/a of the penta-diagonal P is also 1/diag(S) (the Jacobi scale)
-    tv_weights(B, n, c->stream, view, x, c->wtv);
+    tv_weights(B, n, c->stream, view, x, c->wtv, tv2_of(c));
     if (c->kind) wavelet_diag(B, n, c->levels, c->stream, view, c->ww, c->wdiag, c->sqtab, c->sqlen);
-    penta_setup(B, n, c->stream, view, c->wtv, c->kind ? c->wdiag : nullptr, c->ia);
+    penta_setup(B, n, c->stream, view, c->wtv, tv2_of(c), c->kind ? c->wdiag : nullptr, c->ia);
+    // ILU(0): the pivots of the incomplete factorisation replace 1/a
+    if (precond == FIRLS_PRECOND_ILU0) ilu0_pivots(B, n, c->stream, view, c->wtv, tv2_of(c), c->ia);
   } else if (precond == FIRLS_PRECOND_JACOBI) {
     wavelet_diag(B, n, c->levels, c->stream, view, c->ww, c->wdiag, c->sqtab, c->sqlen);
     jacobi_wavelet_setup(B, n, c->stream, view, c->wdiag, c->ia);
@@ -273,7 +279,8 @@ void enqueue_precond(firls_ctx* c, int mode, const firls_params& sc) {
   const bool init = mode == ILU_INIT;
   const int am = init ? AXPY_INIT : AXPY_PER_SLICE, sm = init ? SCALARS_INIT : SCALARS_PER_SLICE;
   const PcgSched ps = pcg_sched(sc);
-  if (sc.precond != FIRLS_PRECOND_PAPER) {  // Jacobi or none: one fused pass, then the FP64 scalars
+  if (sc.precond == FIRLS_PRECOND_JACOBI || sc.precond == FIRLS_PRECOND_NONE) {
+    // Jacobi or none: one fused pass, then the FP64 scalars
     {
       TMark m(c, FIRLS_K_AXPY, 1);
       axpy_diag_step(B, n, c->stream, c->st, c->part, am, c->dx, c->d, c->r, c->q, c->atb,
@@ -287,7 +294,7 @@ void enqueue_precond(firls_ctx* c, int mode, const firls_params& sc) {
     TMark m(c, FIRLS_K_ILU, 1);
     // the ILU CTA finishes rho (and beta) from its own sums
     ilu_step(B, n, c->stream, c->st, c->part, mode, c->dx, c->d, c->r, c->q, c->atb, c->u, c->z, c->ia, c->wtv,
-             c->tune_ilu, 1, ps, c->wait_test);
+             c->tune_ilu, 1, ps, c->wait_test, tv2_of(c));
     return;
   }
   {
@@ -348,8 +355,10 @@ firls_status check_params(firls_ctx* c, const firls_params* p) {
   if (p->outer_iters < 1 || p->pcg_iters < 1) return fail(c, FIRLS_E_INVALID_ARG, "iteration counts must be >= 1");
   if (!(p->pcg_tol >= 0.f) || !(p->outer_tol >= 0.f)) return fail(c, FIRLS_E_INVALID_ARG, "tolerances must be >= 0");
   if (p->outer_tol_kind != 0 && p->outer_tol_kind != 1) return fail(c, FIRLS_E_INVALID_ARG, "bad outer_tol_kind");
-  if (p->precond < FIRLS_PRECOND_PAPER || p->precond > FIRLS_PRECOND_NONE)
+  if (p->precond < FIRLS_PRECOND_PAPER || p->precond > FIRLS_PRECOND_ILU0)
     return fail(c, FIRLS_E_INVALID_ARG, "bad precond");
+  if (p->precond == FIRLS_PRECOND_ILU0 && !has_tv(c))
+    return fail(c, FIRLS_E_INVALID_ARG, "ILU(0) factors the TV preconditioner: needs FIRLS_PSI_TV or TV_ANISO");
   if (!(p->outer_stall_tol >= 0.f)) return fail(c, FIRLS_E_INVALID_ARG, "outer_stall_tol must be >= 0");
   if (p->pcg_tol_kind != 0 && p->pcg_tol_kind != 1) return fail(c, FIRLS_E_INVALID_ARG, "bad pcg_tol_kind");
   if (p->pcg_iters_late < 0 || p->outer_late < 0) return fail(c, FIRLS_E_INVALID_ARG, "bad late inner schedule");
@@ -433,11 +442,13 @@ firls_status macro_graph(firls_ctx* c, const firls_params& sc, int steps, cudaGr
   return FIRLS_OK;
 }
 
-bool all_done(firls_ctx* c, bool* ok) {
+// Every slice of c stopped?  Reads the state on `s` (default: c's stream).
+bool all_done(firls_ctx* c, bool* ok, cudaStream_t s = nullptr) {
+  if (!s) s = c->stream;
   std::vector<SliceState> hs(c->batch);
-  *ok = cudaMemcpyAsync(hs.data(), c->st, sizeof(SliceState) * c->batch, cudaMemcpyDeviceToHost, c->stream) ==
+  *ok = cudaMemcpyAsync(hs.data(), c->st, sizeof(SliceState) * c->batch, cudaMemcpyDeviceToHost, s) ==
             cudaSuccess &&
-        cudaStreamSynchronize(c->stream) == cudaSuccess;
+        cudaStreamSynchronize(s) == cudaSuccess;
   for (const SliceState& v : hs)
     if (v.active && !v.done) return false;
   return true;
@@ -465,7 +476,7 @@ firls_status run_macro(firls_ctx* c, const firls_params& sc, long total, int chu
   cudaGraphExec_t ex = nullptr, ex1 = nullptr;
   TRY(macro_graph(c, sc, chunk, &ex));
   const long full = total / chunk, rem = total % chunk;
-  const int kPoll = 16;
+  const int kPoll = 4;
   for (long k = 0; k < full; ++k) {
     CU(cudaGraphLaunch(ex, c->stream));
     if (poll && (k + 1) % kPoll == 0 && (k + 1 < full || rem)) {
@@ -573,7 +584,7 @@ extern "C" firls_status firls_create(firls_ctx** out, int n_rows, int n_cols, in
   for (float2** p : {&c->atb, &c->x, &c->r, &c->z, &c->d, &c->q, &c->t, &c->u, &c->cw, &c->dx}) A(p, BN);
   A(&c->tmpA, BH);
   A(&c->tmpB, BH);
-  for (float** p : {&c->ww, &c->wtv, &c->ia, &c->wdiag}) A(p, BN);
+  for (float** p : {&c->ww, &c->wtv, &c->ia, &c->wdiag, &c->wtv2}) A(p, BN);
   A(&c->st, (size_t)batch);
   A(&c->stw, (size_t)batch);
   A(&c->part, (size_t)batch * NSLOT * MAXPART);
@@ -610,8 +621,10 @@ extern "C" firls_status firls_set_operator(firls_ctx* c, const uint8_t* mask, un
   if (!mask) return fail(c, FIRLS_E_INVALID_ARG, "mask is null");
   const int n = c->n;
   const bool haar = psi_kind & FIRLS_PSI_HAAR, db4 = psi_kind & FIRLS_PSI_DB4;
-  if ((psi_kind & ~7u) || (haar && db4) || psi_kind == 0)
-    return fail(c, FIRLS_E_INVALID_ARG, "psi_kind must be HAAR or DB4, optionally with TV, or TV alone");
+  const bool both_tv = (psi_kind & FIRLS_PSI_TV) && (psi_kind & FIRLS_PSI_TV_ANISO);
+  if ((psi_kind & ~15u) || (haar && db4) || both_tv || psi_kind == 0)
+    return fail(c, FIRLS_E_INVALID_ARG,
+                "psi_kind must be HAAR or DB4, optionally with TV or TV_ANISO, or one TV form alone");
   const int kind = haar ? 1 : (db4 ? 2 : 0);
   if (kind) {
     if (wavelet_levels < 1 || (n % (1 << wavelet_levels)) || (n >> (wavelet_levels - 1)) < 2)
@@ -818,26 +831,45 @@ extern "C" firls_status firls_solve_multi(firls_ctx* const* ctxs, int n_ctx, con
       g_multi.ctxs.assign(ctxs, ctxs + n_ctx);
       g_multi.sched = *p;
     }
-    for (int k = 0; k < p->outer_iters; ++k) {
+    // replays of one outer step's worth of macro steps, then the remaining
+    // steps (the last one applies every context's last outer step); with
+    // tolerances, stop once every slice of every context has stopped
+    const long total = solve_steps(p), full = (total - 1) / chunk;
+    long rem = total - full * chunk;
+    const bool poll = has_tolerances(p);
+    for (long k = 0; k < full; ++k) {
       cudaError_t e = cudaGraphLaunch(g_multi.exec, c0->stream);
       if (e != cudaSuccess) {
         cleanup();
         return cuda_check(c0, e, "multi graph launch");
       }
+      if (poll && (k + 1) % 4 == 0) {
+        bool all = true, ok = true;
+        for (int i = 0; i < n_ctx && all; ++i) all = all_done(ctxs[i], &ok, c0->stream) && ok;
+        if (!ok) {
+          cleanup();
+          return fail(c0, FIRLS_E_CUDA, "state read-back failed");
+        }
+        if (all) {
+          rem = 0;
+          break;
+        }
+      }
     }
-    // the macro step that applies every context's last outer step
-    cudaEventRecord(fork, c0->stream);
-    for (int i = 0; i < n_ctx; ++i) {
-      firls_ctx* c = ctxs[i];
-      if (i > 0) cudaStreamWaitEvent(c->stream, fork, 0);
-      const bool t = c->timing;
-      c->timing = false;
-      enqueue_macro(c, *p);
-      c->timing = t;
-      c->marks_valid = t;
-      if (i > 0) {
-        cudaEventRecord(join[i], c->stream);
-        cudaStreamWaitEvent(c0->stream, join[i], 0);
+    if (rem > 0) {
+      cudaEventRecord(fork, c0->stream);
+      for (int i = 0; i < n_ctx; ++i) {
+        firls_ctx* c = ctxs[i];
+        if (i > 0) cudaStreamWaitEvent(c->stream, fork, 0);
+        const bool t = c->timing;
+        c->timing = false;
+        for (long k = 0; k < rem; ++k) enqueue_macro(c, *p);
+        c->timing = t;
+        c->marks_valid = t;
+        if (i > 0) {
+          cudaEventRecord(join[i], c->stream);
+          cudaStreamWaitEvent(c0->stream, join[i], 0);
+        }
       }
     }
   }
@@ -1002,7 +1034,7 @@ firls_status objective_parts(firls_ctx* c, const void* b, const firls_params* p,
     l21_sum(B, n, c->stream, c->cw, c->groups ? c->gidx : nullptr, c->goff, c->n_groups, c->gsize, eps, c->part,
             SLOT_RZ);
   }
-  if (has_tv(c)) tv_sum(B, n, c->stream, x, eps, c->part, SLOT_RR);
+  if (has_tv(c)) tv_sum(B, n, c->stream, x, eps, c->part, SLOT_RR, is_aniso(c) ? 1 : 0);
   return cuda_check(c, cudaGetLastError(), "objective");
 }
 
@@ -1185,7 +1217,7 @@ extern "C" firls_status firls_autotune(firls_ctx* c, const char* cache_path) {
     p.lambda_tv = 1e-3f;
     TRY(upload_params(c, &p));
     state_init(B, c->stream, c->st, c->part, 0, c->counts, n, c->lam_d, c->lamtv_d, 1e-10f, 1, PH_START);
-    if (has_tv(c)) penta_setup(B, n, c->stream, c->st, c->wtv, nullptr, c->ia);
+    if (has_tv(c)) penta_setup(B, n, c->stream, c->st, c->wtv, tv2_of(c), nullptr, c->ia);
     float best = 1e30f;
     if (c->kind) {
       for (int r : {1, 2, 4, 8, 16})
@@ -1206,10 +1238,10 @@ extern "C" firls_status firls_autotune(firls_ctx* c, const char* cache_path) {
     if (has_tv(c)) {
       best = 1e30f;
       for (int shape : {42, 43, 44, 22, 23, 24}) {
-        if (!ilu_shape_fits(n, shape)) continue;
+        if (!ilu_shape_fits(n, shape, is_aniso(c))) continue;
         const float t = time_ms(c, [&]() {
           ilu_step(B, n, c->stream, c->st, c->part, ILU_STEP, c->x, c->d, c->r, c->q, c->atb, c->u, c->z, c->ia,
-                   c->wtv, shape);
+                   c->wtv, shape, 0, PcgSched{0.f, 0, 1 << 30, 0, 0}, 0, tv2_of(c));
         }, 5);
         if (t < best) {
           best = t;
@@ -1238,7 +1270,7 @@ extern "C" firls_status firls_set_tuning(firls_ctx* c, int rows_per_cta, int coa
   if (!c) return FIRLS_E_INVALID_ARG;
   if (rows_per_cta < 0 || coarse_max < 0 || ilu_shape < 0)
     return fail(c, FIRLS_E_INVALID_ARG, "tile shapes must be >= 0 (0 = default)");
-  if (ilu_shape > 0 && !ilu_shape_fits(c->n, ilu_shape))
+  if (ilu_shape > 0 && !ilu_shape_fits(c->n, ilu_shape, is_aniso(c)))
     return fail(c, FIRLS_E_INVALID_ARG, "ILU shape does not fit this size");
   if ((rows_per_cta == 1 || rows_per_cta == 2) && c->kind && !wavelet_cluster_ctas(c->n, c->levels, c->kind, rows_per_cta))
     return fail(c, FIRLS_E_INVALID_ARG, "the one-launch cluster wavelet form does not fit this size");
@@ -1356,11 +1388,15 @@ extern "C" firls_status firls_warm_start_guard(firls_ctx* c, const void* b, cons
   return cuda_check(c, cudaGetLastError(), "warm_start_guard");
 }
 
-extern "C" firls_status firls_get_weights(firls_ctx* c, float* w_wavelet, float* w_tv) {
+extern "C" firls_status firls_get_weights(firls_ctx* c, float* w_wavelet, float* w_tv, float* w_tv2) {
   if (!c) return FIRLS_E_INVALID_ARG;
   const size_t bytes = sizeof(float) * (size_t)c->batch * c->n * c->n;
   if (w_wavelet) CU(cudaMemcpyAsync(w_wavelet, c->ww, bytes, cudaMemcpyDeviceToDevice, c->stream));
   if (w_tv) CU(cudaMemcpyAsync(w_tv, c->wtv, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  if (w_tv2) {
+    if (!is_aniso(c)) return fail(c, FIRLS_E_STATE, "W2 exists only with FIRLS_PSI_TV_ANISO");
+    CU(cudaMemcpyAsync(w_tv2, c->wtv2, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  }
   return FIRLS_OK;
 }
 

@@ -23,10 +23,12 @@ template <int N> __host__ __device__ constexpr int rows_per_cta() {
   return r;
 }
 
-template <int N> constexpr int row_smem_bytes(bool tv) {
+// tv: staged d rows and TV weight rows; aniso (l1 TV): a second weight array
+template <int N> constexpr int row_smem_bytes(bool tv, bool aniso = false) {
   constexpr int R = rows_per_cta<N>();
   int b = tw_bytes<N>() + R * 2 * fft_line_words<N>() * 4;
   if (tv) b += (R + 2) * N * 8 + (R + 1) * N * 4;
+  if (tv && aniso) b += (R + 1) * N * 4;
   return b;
 }
 
@@ -371,14 +373,15 @@ __global__ void __launch_bounds__(512) k_col_resid(const float2* __restrict__ tb
   if (threadIdx.x == 0) part[((size_t)s * NSLOT + slot) * MAXPART + blockIdx.x] = tot;
 }
 
-// q = (1/N) rowIFFT(t) [Re if real] + lam_tv (D1^T W D1 + D2^T W D2) d + lam u;
-// partial Re<d, q>.
+// q = (1/N) rowIFFT(t) [Re if real] + lam_tv (D1^T W1 D1 + D2^T W2 D2) d + lam u
+// (W1 = W2 = wtv for isotropic TV; wtv2 holds W2 for l1 TV); partial
+// Re<d, q>.
 template <int N>
 __global__ void __launch_bounds__(256) k_row_inv(const float2* __restrict__ tbuf, const float2* __restrict__ d,
                                                  const float2* __restrict__ u, const float* __restrict__ wtv,
                                                  float2* __restrict__ q, const SliceState* __restrict__ st,
                                                  double* __restrict__ part, int real,
-                                                 const float2* __restrict__ twg) {
+                                                 const float2* __restrict__ twg, const float* __restrict__ wtv2) {
   using C = FftCfg<N>;
   constexpr int R = rows_per_cta<N>(), E = C::E, T = C::T, LW = fft_line_words<N>();
   const int s = blockIdx.y;
@@ -389,9 +392,10 @@ __global__ void __launch_bounds__(256) k_row_inv(const float2* __restrict__ tbuf
   float* lines = reinterpret_cast<float*>(smem + tw_bytes<N>());
   float2* ds = reinterpret_cast<float2*>(smem + tw_bytes<N>() + R * 2 * LW * 4);  // rows r0-1 .. r0+R
   float* ws = reinterpret_cast<float*>(ds + (R + 2) * N);                 // rows r0 .. r0+R
+  float* ws2 = ws + (R + 1) * N;                                          // W2 rows (l1 TV)
   const int r0 = blockIdx.x * R;
   const size_t sbase = (size_t)s * N * N;
-  const bool tv = (wtv != nullptr);
+  const bool tv = (wtv != nullptr), aniso = tv && wtv2 != nullptr;
   if (tv) {
     // halo rows straight to shared memory, all copies in flight at once
     constexpr int NT = R * T, KD = (R + 2) * N / 2, KW = (R + 1) * N / 4;
@@ -409,6 +413,15 @@ __global__ void __launch_bounds__(256) k_row_inv(const float2* __restrict__ tbuf
         cp_async16_fft(ws + 4 * idx, wtv + sbase + (size_t)rr * N + cc);
       else
         *reinterpret_cast<float4*>(ws + 4 * idx) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (aniso) {
+      for (int idx = threadIdx.x; idx < KW; idx += NT) {
+        const int rr = r0 + (4 * idx) / N, cc = (4 * idx) % N;
+        if (rr < N)
+          cp_async16_fft(ws2 + 4 * idx, wtv2 + sbase + (size_t)rr * N + cc);
+        else
+          *reinterpret_cast<float4*>(ws2 + 4 * idx) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
@@ -441,9 +454,15 @@ __global__ void __launch_bounds__(256) k_row_inv(const float2* __restrict__ tbuf
       const float2 du = (ds + lr * N)[col];  // row - 1 (zero above the image)
       const float2 g1 = csub(dc, dl), g2 = csub(dc, du);
       const float wc = ws[lr * N + col];
-      float2 tvv = cscale(cadd(g1, g2), wc);
+      float2 tvv;
+      if (!aniso) {
+        tvv = cscale(cadd(g1, g2), wc);
+      } else {
+        tvv = cadd(cscale(g1, wc), cscale(g2, ws2[lr * N + col]));
+      }
+      const float* wv = aniso ? ws2 : ws;  // vertical couplings: W2 (W for isotropic TV)
       if (col < N - 1) tvv = csub(tvv, cscale(csub(dr[col + 1], dc), ws[lr * N + col + 1]));
-      if (row < N - 1) tvv = csub(tvv, cscale(csub((ds + (lr + 2) * N)[col], dc), ws[(lr + 1) * N + col]));
+      if (row < N - 1) tvv = csub(tvv, cscale(csub((ds + (lr + 2) * N)[col], dc), wv[(lr + 1) * N + col]));
       a = cfma(lam_tv, tvv, a);
     } else {
       dc = d[base + col];
@@ -465,7 +484,7 @@ template <int N> static void set_smem_attrs() {
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
     bool ok = cudaFuncSetAttribute(k_row_fwd<N>, A, row_smem_bytes<N>(false)) == cudaSuccess;
     ok = cudaFuncSetAttribute(k_row_ahb<N>, A, row_smem_bytes<N>(false)) == cudaSuccess && ok;
-    ok = cudaFuncSetAttribute(k_row_inv<N>, A, row_smem_bytes<N>(true)) == cudaSuccess && ok;
+    ok = cudaFuncSetAttribute(k_row_inv<N>, A, row_smem_bytes<N>(true, true)) == cudaSuccess && ok;
     ok = cudaFuncSetAttribute(k_col_mask<N>, A, col_smem_bytes<N>()) == cudaSuccess && ok;
     ok = cudaFuncSetAttribute(k_col_inv<N>, A, col_smem_bytes<N>()) == cudaSuccess && ok;
     ok = cudaFuncSetAttribute(k_col_resid<N>, A, col_smem_bytes<N>()) == cudaSuccess && ok;
@@ -508,8 +527,9 @@ template <int N> struct FftLaunch {
   }
   static void row_inv(const FftArgs& a) {
     set_smem_attrs<N>();
-    k_row_inv<N><<<dim3(N / R, a.batch), R * FftCfg<N>::T, row_smem_bytes<N>(a.wtv != nullptr), a.stream>>>(
-        a.t, a.d, a.u, a.wtv, a.q, a.st, a.part, a.real, a.tw);
+    k_row_inv<N><<<dim3(N / R, a.batch), R * FftCfg<N>::T,
+                   row_smem_bytes<N>(a.wtv != nullptr, a.wtv2 != nullptr), a.stream>>>(
+        a.t, a.d, a.u, a.wtv, a.q, a.st, a.part, a.real, a.tw, a.wtv2);
   }
 };
 

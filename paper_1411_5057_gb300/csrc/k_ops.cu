@@ -1011,9 +1011,11 @@ int wavelet_apply_launches(int n, int levels, int kind, int rb, int cmax) {
 
 // ================================================================== TV =====
 
-// W_i = (|grad_1 x_i|^2 + |grad_2 x_i|^2 + eps)^(-1/2), zero extension (Eq. wi)
+// Isotropic TV (wtv2 null): W_i = (|grad_1 x_i|^2 + |grad_2 x_i|^2 + eps)^(-1/2)
+// (Eq. wi).  l1 TV (Eq. l1): W1_i = (|grad_1 x_i|^2 + eps)^(-1/2) into wtv and
+// W2_i = (|grad_2 x_i|^2 + eps)^(-1/2) into wtv2.  Zero extension.
 __global__ void k_tv_weights(int n, const SliceState* __restrict__ st, const float2* __restrict__ x,
-                             float* __restrict__ wtv) {
+                             float* __restrict__ wtv, float* __restrict__ wtv2) {
   const int s = blockIdx.y;
   if (!slice_running(st, s)) return;
   const float eps = st[s].eps;
@@ -1023,14 +1025,19 @@ __global__ void k_tv_weights(int n, const SliceState* __restrict__ st, const flo
     const float2 xc = x[base + i];
     const float2 g1 = c > 0 ? csub(xc, x[base + i - 1]) : xc;
     const float2 g2 = r > 0 ? csub(xc, x[base + i - n]) : xc;
-    wtv[base + i] = rsqrtf(cabs2(g1) + cabs2(g2) + eps);
+    if (wtv2) {
+      wtv[base + i] = rsqrtf(cabs2(g1) + eps);
+      wtv2[base + i] = rsqrtf(cabs2(g2) + eps);
+    } else {
+      wtv[base + i] = rsqrtf(cabs2(g1) + cabs2(g2) + eps);
+    }
   }
 }
 
-void tv_weights(int batch, int n, cudaStream_t s, const SliceState* st, const float2* x, float* wtv) {
+void tv_weights(int batch, int n, cudaStream_t s, const SliceState* st, const float2* x, float* wtv, float* wtv2) {
   const int N = n * n;
   const int blocks = (N + 255) / 256 < 64 ? (N + 255) / 256 : 64;
-  k_tv_weights<<<dim3(blocks, batch), 256, 0, s>>>(n, st, x, wtv);
+  k_tv_weights<<<dim3(blocks, batch), 256, 0, s>>>(n, st, x, wtv, wtv2);
 }
 
 // Exact diag(Phi^T diag(w) Phi).  Each 2-D basis function of level l is an
@@ -1136,11 +1143,13 @@ void wavelet_diag(int batch, int n, int levels, cudaStream_t s, const SliceState
     k_wavelet_diag<0, 0><<<grid, 256, 2 * WD_PRMAX * n * 4, s>>>(n, levels, st, w, out, sqtab, sqlen);
 }
 
-// P = abar I + lam_tv (D1^T W D1 + D2^T W D2) [+ lam diag(Phi^T W Phi)] (Eq. ptv):
-// ia = 1 / a_i, the inverse diagonal.  The off-diagonals (-lam_tv W_{i+1},
-// -lam_tv W_{i+n}) are formed from W inside the ILU sweeps.
+// P = abar I + lam_tv (D1^T W1 D1 + D2^T W2 D2) [+ lam diag(Phi^T W Phi)]
+// (Eq. ptv; W1 = W2 = W for isotropic TV, wtv2 null): ia = 1 / a_i, the
+// inverse diagonal, a_i = abar + lam_tv (W1_i + W1_{i+1} + W2_i + W2_{i+n}).
+// The off-diagonals (-lam_tv W1_{i+1}, -lam_tv W2_{i+n}) are formed from the
+// weights inside the ILU sweeps.
 __global__ void k_penta(int n, const SliceState* __restrict__ st, const float* __restrict__ wtv,
-                        const float* __restrict__ wdiag, float* __restrict__ ia) {
+                        const float* __restrict__ wtv2, const float* __restrict__ wdiag, float* __restrict__ ia) {
   const int s = blockIdx.y;
   if (!slice_running(st, s)) return;
   const float abar = st[s].abar, lt = st[s].lam_tv, lw = st[s].lam;
@@ -1149,18 +1158,131 @@ __global__ void k_penta(int n, const SliceState* __restrict__ st, const float* _
     const int r = i / n, c = i % n;
     const float wc = wtv[base + i];
     const float wr = c < n - 1 ? wtv[base + i + 1] : 0.f;
-    const float wd = r < n - 1 ? wtv[base + i + n] : 0.f;
-    float a = abar + lt * (2.f * wc + wr + wd);
+    float a;
+    if (wtv2) {
+      const float wd = r < n - 1 ? wtv2[base + i + n] : 0.f;
+      a = abar + lt * (wc + wr + wtv2[base + i] + wd);
+    } else {
+      const float wd = r < n - 1 ? wtv[base + i + n] : 0.f;
+      a = abar + lt * (2.f * wc + wr + wd);
+    }
     if (wdiag) a = fmaf(lw, wdiag[base + i], a);
     ia[base + i] = 1.0f / a;
   }
 }
 
-void penta_setup(int batch, int n, cudaStream_t s, const SliceState* st, const float* wtv,
+void penta_setup(int batch, int n, cudaStream_t s, const SliceState* st, const float* wtv, const float* wtv2,
                  const float* wdiag, float* ia) {
   const int N = n * n;
   const int blocks = (N + 255) / 256 < 64 ? (N + 255) / 256 : 64;
-  k_penta<<<dim3(blocks, batch), 256, 0, s>>>(n, st, wtv, wdiag, ia);
+  k_penta<<<dim3(blocks, batch), 256, 0, s>>>(n, st, wtv, wtv2, wdiag, ia);
+}
+
+// ILU(0) pivots of the penta-diagonal P: d_i = a_i - (lam W1_i)^2 / d_{i-1}
+// [col > 0] - (lam W2_i)^2 / d_{i-n} [row > 0] (the incomplete LU with zero
+// fill of Sec. 4.2 with updated pivots; W1 = W2 = W for isotropic TV).
+// In: ia = 1/a; out: ia = 1/d in place.  One warp per slice, a row at a time:
+// with alpha_i = a_i - (lam W2_i)^2 / d_{i-n} the row recurrence
+// d_i = alpha_i - (lam W1_i)^2 / d_{i-1} is a Moebius map of d_{i-1}, i.e.
+// (p, q) -> M_i (p, q) with M_i = [[alpha_i, -(lam W1_i)^2], [1, 0]] and
+// d = p / q, so the row is a scan of 2 x 2 matrix products: each lane folds
+// its E columns, a warp shuffle scan combines the lanes (every product
+// scaled by its largest entry: only the ratio p / q matters), and each lane
+// then runs its own columns from the incoming ratio.
+template <int E>
+__global__ void __launch_bounds__(32) k_ilu0_pivots(int n, const SliceState* __restrict__ st,
+                                                     const float* __restrict__ wtv, const float* __restrict__ wtv2,
+                                                     float* __restrict__ ia) {
+  const int s = blockIdx.x;
+  if (!slice_running(st, s)) return;
+  const int lane = threadIdx.x;
+  const float lam = st[s].lam_tv;
+  const float* w2 = wtv2 ? wtv2 : wtv;
+  const size_t base = (size_t)s * n * n;
+  float dprev[E];  // d of the row above in this lane's columns
+#pragma unroll
+  for (int e = 0; e < E; ++e) dprev[e] = 1.f;
+  for (int r = 0; r < n; ++r) {
+    const size_t rb = base + (size_t)r * n;
+    float al[E], k2[E];
+    // this lane's segment as a 2 x 2 matrix T = M_{last} ... M_{first}
+    float t00 = 1.f, t01 = 0.f, t10 = 0.f, t11 = 1.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int c = lane * E + e;
+      al[e] = 1.f;
+      k2[e] = 0.f;
+      if (c < n) {
+        const float a = 1.0f / ia[rb + c];
+        const float kv = r > 0 ? lam * w2[rb + c] : 0.f;
+        const float kh = c > 0 ? lam * wtv[rb + c] : 0.f;
+        al[e] = a - kv * kv / dprev[e];
+        k2[e] = kh * kh;
+      }
+      // M_e * T
+      const float n00 = al[e] * t00 - k2[e] * t10, n01 = al[e] * t01 - k2[e] * t11;
+      t10 = t00;
+      t11 = t01;
+      t00 = n00;
+      t01 = n01;
+      const float m = fmaxf(fmaxf(fabsf(t00), fabsf(t01)), fmaxf(fabsf(t10), fabsf(t11)));
+      if (m > 0.f) {
+        const float im = 1.0f / m;
+        t00 *= im;
+        t01 *= im;
+        t10 *= im;
+        t11 *= im;
+      }
+    }
+    // inclusive scan over the lanes: P_L = T_L ... T_0
+    float p00 = t00, p01 = t01, p10 = t10, p11 = t11;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const float q00 = __shfl_up_sync(0xffffffffu, p00, off), q01 = __shfl_up_sync(0xffffffffu, p01, off);
+      const float q10 = __shfl_up_sync(0xffffffffu, p10, off), q11 = __shfl_up_sync(0xffffffffu, p11, off);
+      if (lane >= off) {  // P = P_mine * P_earlier
+        const float n00 = p00 * q00 + p01 * q10, n01 = p00 * q01 + p01 * q11;
+        const float n10 = p10 * q00 + p11 * q10, n11 = p10 * q01 + p11 * q11;
+        const float m = fmaxf(fmaxf(fabsf(n00), fabsf(n01)), fmaxf(fabsf(n10), fabsf(n11)));
+        const float im = m > 0.f ? 1.0f / m : 1.f;
+        p00 = n00 * im;
+        p01 = n01 * im;
+        p10 = n10 * im;
+        p11 = n11 * im;
+      }
+    }
+    // the ratio entering this lane: the previous lane's prefix applied to
+    // (1, 0) (no left neighbour for column 0)
+    const float e00 = __shfl_up_sync(0xffffffffu, p00, 1), e10 = __shfl_up_sync(0xffffffffu, p10, 1);
+    float d = lane == 0 ? 0.f : e00 / e10;  // lane 0: column 0 has k2 = 0, d_in unused
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int c = lane * E + e;
+      if (c < n) {
+        d = k2[e] > 0.f ? al[e] - k2[e] / d : al[e];
+        dprev[e] = d;
+        ia[rb + c] = 1.0f / d;
+      }
+    }
+  }
+}
+
+void ilu0_pivots(int batch, int n, cudaStream_t s, const SliceState* st, const float* wtv, const float* wtv2,
+                 float* ia) {
+  const int E = (n + 31) / 32;
+  switch (E) {
+    case 1: k_ilu0_pivots<1><<<batch, 32, 0, s>>>(n, st, wtv, wtv2, ia); break;
+    case 2: k_ilu0_pivots<2><<<batch, 32, 0, s>>>(n, st, wtv, wtv2, ia); break;
+    case 3: k_ilu0_pivots<3><<<batch, 32, 0, s>>>(n, st, wtv, wtv2, ia); break;
+    case 4: k_ilu0_pivots<4><<<batch, 32, 0, s>>>(n, st, wtv, wtv2, ia); break;
+    case 5: k_ilu0_pivots<5><<<batch, 32, 0, s>>>(n, st, wtv, wtv2, ia); break;
+    case 6: k_ilu0_pivots<6><<<batch, 32, 0, s>>>(n, st, wtv, wtv2, ia); break;
+    case 8: k_ilu0_pivots<8><<<batch, 32, 0, s>>>(n, st, wtv, wtv2, ia); break;
+    case 10: k_ilu0_pivots<10><<<batch, 32, 0, s>>>(n, st, wtv, wtv2, ia); break;
+    case 12: k_ilu0_pivots<12><<<batch, 32, 0, s>>>(n, st, wtv, wtv2, ia); break;
+    case 16: k_ilu0_pivots<16><<<batch, 32, 0, s>>>(n, st, wtv, wtv2, ia); break;
+    default: break;
+  }
 }
 
 // ------------------------------------------------ ILU solves (Sec. 4.2) -----
@@ -1304,12 +1426,13 @@ constexpr int IW_MAXCH = 3;                    // chunks of two columns per help
 constexpr int IW_MAXSTAGES = 8;
 
 static int iw_cols_per_lane(int n) { return (n + 31) / 32; }
-// Stage of G rows (bytes): R, Q, X, D (8nG each), W, IA (4nG each), then
-// SC: per row, float4 (t.x, t.y, h, g) per lane-major column slot.
+// Stage of G rows (bytes): R, Q, X, D (8nG each), W (W1 for l1 TV), IA
+// (4nG each), W2 (4nG, l1 TV only), then SC: per row, float4 (t.x, t.y, h, g)
+// per lane-major column slot.
 struct IwLayout {
-  int n, G, ns, oQ, oX, oD, oW, oIA, oSC, bytes;
+  int n, G, ns, oQ, oX, oD, oW, oIA, oW2, oSC, bytes;
 };
-static IwLayout iw_layout(int n, int G) {
+static IwLayout iw_layout(int n, int G, bool aniso = false) {
   IwLayout L;
   L.n = n;
   L.G = G;
@@ -1319,7 +1442,8 @@ static IwLayout iw_layout(int n, int G) {
   L.oD = 24 * n * G;
   L.oW = 32 * n * G;
   L.oIA = 36 * n * G;
-  L.oSC = 40 * n * G;
+  L.oW2 = 40 * n * G;
+  L.oSC = (aniso ? 44 : 40) * n * G;
   L.bytes = (L.oSC + 16 * L.ns * G + 127) / 128 * 128;
   return L;
 }
@@ -1347,7 +1471,7 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
           float2* __restrict__ x, const float2* __restrict__ d, float2* __restrict__ r,
           const float2* __restrict__ q, const float2* __restrict__ atb, float2* __restrict__ y,
           float2* __restrict__ z, const float* __restrict__ ia, const float* __restrict__ wtv, int fuse,
-          PcgSched ps, int wait_test) {
+          PcgSched ps, int wait_test, const float* __restrict__ wtv2) {
   const int s = blockIdx.x;
   if (!slice_running(st, s)) return;
   // ILU_PER_SLICE: the first residual for a slice at the start of its outer
@@ -1507,9 +1631,10 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
         }
         unsigned char* sp = smem + (size_t)pos.s * lay.bytes;
         uint64_t* bar = &bar_full[pos.s];
+        const unsigned cw2 = wtv2 ? c4 : 0u;
         if (g < NG) {
           const size_t go = base + (size_t)g * G * n;
-          mbar_arrive_tx(bar, init ? 2 * c8 + 2 * c4 : 4 * c8 + 2 * c4);
+          mbar_arrive_tx(bar, (init ? 2 * c8 + 2 * c4 : 4 * c8 + 2 * c4) + cw2);
           bulk_g2s(sp, rsrc + go, c8, bar);
           bulk_g2s(sp + lay.oQ, q + go, c8, bar);
           if (!init) {
@@ -1518,12 +1643,14 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
           }
           bulk_g2s(sp + lay.oW, wtv + go, c4, bar);
           bulk_g2s(sp + lay.oIA, ia + go, c4, bar);
+          if (wtv2) bulk_g2s(sp + lay.oW2, wtv2 + go, c4, bar);
         } else {
           const size_t go = base + (size_t)(n - (g - NG + 1) * G) * n;
-          mbar_arrive_tx(bar, c8 + 2 * c4);
+          mbar_arrive_tx(bar, c8 + 2 * c4 + cw2);
           bulk_g2s(sp, y + go, c8, bar);
           bulk_g2s(sp + lay.oW, wtv + go, c4, bar);
           bulk_g2s(sp + lay.oIA, ia + go, c4, bar);
+          if (wtv2) bulk_g2s(sp + lay.oW2, wtv2 + go, c4, bar);
         }
         pos.next(S);
       }
@@ -1584,9 +1711,17 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
               const float ial = c > 0 ? arow[c - 1] : 0.f;
               const float2 aab = prev[ch];  // ia of the row above
               const float lw0 = lam * w2.x, lw1 = lam * w2.y;
+              // vertical couplings use W2 (l1 TV), else W
+              float lv0 = lw0, lv1 = lw1;
+              if (wtv2) {
+                const float2 v2 = *reinterpret_cast<const float2*>(
+                    reinterpret_cast<const float*>(sp + lay.oW2 + i * nG4) + c);
+                lv0 = lam * v2.x;
+                lv1 = lam * v2.y;
+              }
               float4* sc = sc_row(pos.s, i);
-              sc[slot_of(c)] = make_float4(rn.x, rn.y, lw0 * aab.x, lw0 * ial);
-              sc[slot_of(c + 1)] = make_float4(rn.z, rn.w, lw1 * aab.y, lw1 * a2.x);
+              sc[slot_of(c)] = make_float4(rn.x, rn.y, lv0 * aab.x, lw0 * ial);
+              sc[slot_of(c + 1)] = make_float4(rn.z, rn.w, lv1 * aab.y, lw1 * a2.x);
               prev[ch] = a2;
             }
           }
@@ -1606,7 +1741,7 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
               const float2 w2 = *reinterpret_cast<const float2*>(wrow + c);
               const float2 a2 = *reinterpret_cast<const float2*>(arow + c);
               const float w3 = c + 2 < n ? wrow[c + 2] : 0.f;
-              const float2 wbl = prev[ch];  // W of the row below
+              const float2 wbl = prev[ch];  // W (W2 for l1 TV) of the row below
               const float la0 = lam * a2.x, la1 = lam * a2.y;
               const float2 t0 = make_float2(a2.x * y4.x, a2.x * y4.y), t1 = make_float2(a2.y * y4.z, a2.y * y4.w);
               rho = fmaf(t0.x, y4.x, fmaf(t0.y, y4.y, rho));
@@ -1614,7 +1749,9 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
               float4* sc = sc_row(pos.s, i);
               sc[slot_of(c)] = make_float4(t0.x, t0.y, la0 * wbl.x, la0 * w2.y);
               sc[slot_of(c + 1)] = make_float4(t1.x, t1.y, la1 * wbl.y, la1 * w3);
-              prev[ch] = w2;
+              prev[ch] = wtv2 ? *reinterpret_cast<const float2*>(
+                                    reinterpret_cast<const float*>(sp + lay.oW2 + o * nG4) + c)
+                              : w2;
             }
           }
         }
@@ -1646,7 +1783,7 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
 
 typedef void (*IluKernel)(int, int, int, IwLayout, SliceState*, double*, float2*, const float2*, float2*,
                           const float2*, const float2*, float2*, float2*, const float*, const float*, int, PcgSched,
-                          int);
+                          int, const float*);
 template <int G>
 static IluKernel ilu_kernel_g(int E) {
   switch (E) {
@@ -1683,33 +1820,35 @@ bool ilu_prepare() {
 // CTA per SM (batch <= 152) the ring takes 4-row stages, three of them as
 // long as they fit; with more CTAs per SM, 2-row stages in the shared
 // memory each CTA gets.
-int ilu_default_shape(int n, int batch) {
+int ilu_default_shape(int n, int batch, bool aniso) {
   int per_sm = (batch + 151) / 152;
   if (per_sm > 3) per_sm = 3;
   const int budget = per_sm == 1 ? ILU_SMEM_MAX : (224 * 1024) / per_sm - 2048;
   for (int G : {4, 2}) {
     if (per_sm > 1 && G == 4) continue;
-    int S = budget / iw_layout(n, G).bytes;
+    int S = budget / iw_layout(n, G, aniso).bytes;
     if (S > 4) S = 4;
     if (S >= 2) return 10 * G + S;
   }
   return 10 * 2 + 2;
 }
 
-bool ilu_shape_fits(int n, int shape) {
+bool ilu_shape_fits(int n, int shape, bool aniso) {
   const int G = shape / 10, S = shape % 10;
   if ((G != 2 && G != 4) || S < 2 || S > IW_MAXSTAGES || n % G) return false;
-  return (long)S * iw_layout(n, G).bytes <= ILU_SMEM_MAX;
+  return (long)S * iw_layout(n, G, aniso).bytes <= ILU_SMEM_MAX;
 }
 
 void ilu_step(int batch, int n, cudaStream_t s, SliceState* st, double* part, int mode, float2* x,
               const float2* d, float2* r, const float2* q, const float2* atb, float2* y, float2* z,
-              const float* ia, const float* wtv, int shape, int fuse_scalars, PcgSched ps, int wait_test) {
-  if (shape <= 0 || !ilu_shape_fits(n, shape)) shape = ilu_default_shape(n, batch);
+              const float* ia, const float* wtv, int shape, int fuse_scalars, PcgSched ps, int wait_test,
+              const float* wtv2) {
+  const bool aniso = wtv2 != nullptr;
+  if (shape <= 0 || !ilu_shape_fits(n, shape, aniso)) shape = ilu_default_shape(n, batch, aniso);
   const int G = shape / 10, S = shape % 10;
-  const IwLayout lay = iw_layout(n, G);
+  const IwLayout lay = iw_layout(n, G, aniso);
   ilu_kernel(n, G)<<<batch, IW_THREADS, (size_t)S * lay.bytes, s>>>(n, mode, S, lay, st, part, x, d, r, q, atb, y,
-                                                                     z, ia, wtv, fuse_scalars, ps, wait_test);
+                                                                     z, ia, wtv, fuse_scalars, ps, wait_test, wtv2);
 }
 
 // =========================================================== PCG vectors ==
@@ -2046,7 +2185,8 @@ void l21_sum(int batch, int n, cudaStream_t s, const float2* c, const int* gidx,
   k_l21_sum<<<dim3(axpy_ctas(n), batch), 256, 0, s>>>(n, c, gidx, goff, G, gsize, eps, part, slot);
 }
 
-__global__ void k_tv_sum(int n, const float2* __restrict__ x, float eps, double* __restrict__ part, int slot) {
+__global__ void k_tv_sum(int n, const float2* __restrict__ x, float eps, double* __restrict__ part, int slot,
+                         int aniso) {
   const int s = blockIdx.y;
   __shared__ double red[32];
   const size_t base = (size_t)s * n * n;
@@ -2059,14 +2199,14 @@ __global__ void k_tv_sum(int n, const float2* __restrict__ x, float eps, double*
     const float2 xc = x[base + i];
     const float2 g1 = cc > 0 ? csub(xc, x[base + i - 1]) : xc;
     const float2 g2 = r > 0 ? csub(xc, x[base + i - n]) : xc;
-    acc += sqrtf(cabs2(g1) + cabs2(g2) + eps);
+    acc += aniso ? sqrtf(cabs2(g1) + eps) + sqrtf(cabs2(g2) + eps) : sqrtf(cabs2(g1) + cabs2(g2) + eps);
   }
   const double tot = block_sum((double)acc, red);
   if (threadIdx.x == 0) part[((size_t)s * NSLOT + slot) * MAXPART + blockIdx.x] = tot;
 }
 
-void tv_sum(int batch, int n, cudaStream_t s, const float2* x, float eps, double* part, int slot) {
-  k_tv_sum<<<dim3(axpy_ctas(n), batch), 256, 0, s>>>(n, x, eps, part, slot);
+void tv_sum(int batch, int n, cudaStream_t s, const float2* x, float eps, double* part, int slot, int aniso) {
+  k_tv_sum<<<dim3(axpy_ctas(n), batch), 256, 0, s>>>(n, x, eps, part, slot, aniso);
 }
 
 // ========================================================== PCG scalars ===

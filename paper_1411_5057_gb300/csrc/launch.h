@@ -23,6 +23,7 @@ struct FftArgs {
   float2* x = nullptr;
   const float2* u = nullptr;
   const float* wtv = nullptr;
+  const float* wtv2 = nullptr;  // l1 TV: the vertical weights W2 (wtv then holds W1)
   float2* q = nullptr;
   const float2* xs = nullptr;   // row FFT, per-slice mode: x^k of slices starting an outer step
   int mode = 0;
@@ -76,11 +77,15 @@ int wavelet_apply_launches(int n, int levels, int kind, int rb, int coarse_max);
 void wav_prepare();
 
 // ---- TV, preconditioner, groups, PCG scalars ----
-void tv_weights(int batch, int n, cudaStream_t s, const SliceState* st, const float2* x, float* wtv);
+// wtv2 null: isotropic TV weights into wtv; else l1 TV: W1 into wtv, W2 into wtv2
+void tv_weights(int batch, int n, cudaStream_t s, const SliceState* st, const float2* x, float* wtv, float* wtv2);
 void wavelet_diag(int batch, int n, int levels, cudaStream_t s, const SliceState* st, const float* w,
                   float* out, const float* sqtab, const int* sqlen);
-void penta_setup(int batch, int n, cudaStream_t s, const SliceState* st, const float* wtv,
+void penta_setup(int batch, int n, cudaStream_t s, const SliceState* st, const float* wtv, const float* wtv2,
                  const float* wdiag, float* ia);
+// ia = 1/a -> 1/d, the ILU(0) pivots (updated pivots, zero fill)
+void ilu0_pivots(int batch, int n, cudaStream_t s, const SliceState* st, const float* wtv, const float* wtv2,
+                 float* ia);
 
 // In the PCG-step kernels below, `x` is the vector that receives alpha d: the
 // solver passes the outer step's update accumulator dx (added to the iterate
@@ -92,9 +97,10 @@ enum IluMode { ILU_INIT = 0, ILU_STEP = 1, ILU_LAST = 2, ILU_PER_SLICE = -1 };
 void ilu_step(int batch, int n, cudaStream_t s, SliceState* st, double* part, int mode,
               float2* x, const float2* d, float2* r, const float2* q, const float2* atb, float2* y,
               float2* z, const float* ia, const float* wtv, int shape, int fuse_scalars = 0,
-              PcgSched ps = PcgSched{0.f, 0, 1 << 30, 0, 0}, int wait_test = 0);
-int ilu_default_shape(int n, int batch);
-bool ilu_shape_fits(int n, int shape);
+              PcgSched ps = PcgSched{0.f, 0, 1 << 30, 0, 0}, int wait_test = 0, const float* wtv2 = nullptr);
+// aniso: the ring stages also hold the second weight array of l1 TV
+int ilu_default_shape(int n, int batch, bool aniso = false);
+bool ilu_shape_fits(int n, int shape, bool aniso = false);
 
 // AXPY_PER_SLICE (and ILU_PER_SLICE, SCALARS_PER_SLICE, mode < 0 of the row
 // FFT): each slice's own phase picks the first residual (PH_BOUNDARY) or a
@@ -126,7 +132,7 @@ void mask_popcount(int batch, int n, cudaStream_t s, const uint8_t* mask, int* c
 // and sum_i sqrt(|D1 x|_i^2 + |D2 x|_i^2 + eps).
 void l21_sum(int batch, int n, cudaStream_t s, const float2* c, const int* gidx, const int* goff, int n_groups,
              int gsize, float eps, double* part, int slot);
-void tv_sum(int batch, int n, cudaStream_t s, const float2* x, float eps, double* part, int slot);
+void tv_sum(int batch, int n, cudaStream_t s, const float2* x, float eps, double* part, int slot, int aniso);
 
 // PCG scalar updates (one thread per slice)
 void pcg_alpha(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts);

@@ -15,6 +15,8 @@ outer loop is memoryless), for instance to tighten an earlier run.
 One file per seed, ``xstar_tv_db4_256/seed<S>.npz``: x (complex64, full
 resolution), outer steps, the last relative change, mu and the estimated
 distance.  The GPU tests and the bench compare their results with these.
+--uneven writes ``xstar_uneven/seed<S>.npz`` for the first slice of each size
+of the uneven batch (128^2, 192^2, 256^2, 320^2 TV + D4, per-slice lambdas).
 
     python tests/golden/make_xstar.py [--procs P] [--resume] [seed ...]
     python tests/golden/make_xstar.py --steps-to [--procs P] [seed ...]
@@ -33,6 +35,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(HERE, "xstar_tv_db4_256")
+OUT_UNEVEN = os.path.join(HERE, "xstar_uneven")
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 DIST_TARGET = 1e-6
@@ -46,8 +49,20 @@ INNER = 60
 DEFAULT_SEEDS = [56, 12, 490, 79, 50] + [s for s in range(2, 18) if s != 12]
 
 
+# uneven batch (128^2 .. 320^2, seeds 1000..1063): the first slice of each size
+UNEVEN_SEEDS = [1000, 1016, 1032, 1048]
+
+
 def out_path(seed):
-    return os.path.join(OUT, f"seed{seed}.npz")
+    return os.path.join(OUT_UNEVEN if seed >= 1000 else OUT, f"seed{seed}.npz")
+
+
+def problem(seed):
+    """The 256^2 TV + D4 bench slice of a seed, or the uneven-batch slice."""
+    import firls_synth as fs
+    if seed >= 1000:
+        return next(p for p, s in zip(fs.uneven_batch(), range(1000, 1064)) if s == seed)
+    return fs.tv_db4_256(seed=seed)
 
 
 def contraction(rel):
@@ -60,9 +75,8 @@ def contraction(rel):
 def solve(args):
     seed, resume = args
     os.environ.setdefault("OMP_NUM_THREADS", "1")
-    import firls_synth as fs
     from oracle import firls_oracle as O
-    p = fs.tv_db4_256(seed=seed)
+    p = problem(seed)
     t0 = time.time()
     x, rel, done = None, [], 0
     if resume and os.path.exists(out_path(seed)):
@@ -85,12 +99,11 @@ def solve(args):
 
 def steps_to(seed, tol=1e-4):
     os.environ.setdefault("OMP_NUM_THREADS", "1")
-    import firls_synth as fs
     from oracle import firls_oracle as O
     t0 = time.time()
     z = dict(np.load(out_path(seed)))
     xstar = z["x"].astype(np.complex128)
-    p = fs.tv_db4_256(seed=seed)
+    p = problem(seed)
     x, k = None, 0
     while k < MAX_OUTER:
         x, _ = O.firls_problem(p, outer=1, inner=INNER, x_init=x)
@@ -107,10 +120,12 @@ def main():
     ap.add_argument("--procs", type=int, default=4)
     ap.add_argument("--resume", action="store_true", help="continue from the stored x* of each seed")
     ap.add_argument("--steps-to", action="store_true", help="record the oracle's outer steps to 1e-4 of x*")
+    ap.add_argument("--uneven", action="store_true", help="the first slice of each size of the uneven batch")
     ap.add_argument("seeds", type=int, nargs="*")
     a = ap.parse_args()
-    seeds = a.seeds or DEFAULT_SEEDS
+    seeds = a.seeds or (UNEVEN_SEEDS if a.uneven else DEFAULT_SEEDS)
     os.makedirs(OUT, exist_ok=True)
+    os.makedirs(OUT_UNEVEN, exist_ok=True)
     if a.steps_to:
         with mp.get_context("spawn").Pool(a.procs) as pool:
             for seed, k, sec in pool.imap_unordered(steps_to, seeds):

@@ -173,6 +173,25 @@ def test_wavelet_forms_S_Pinv_parity(F, name, n, cfg, form):
     _check_weights_S_Pinv(F, n, cfg, form)
 
 
+_TV_VARIANTS = [
+    ("tv_l1", 64, dict(real=False, psi=8, levels=0, lam=0.0, lam_tv=1e-3, groups=None)),
+    ("tv_l1_db4", 64, dict(real=False, psi=10, levels=4, lam=5e-4, lam_tv=1e-3, groups=None)),
+    ("tv_l1_haar_96", 96, dict(real=False, psi=9, levels=3, lam=5e-4, lam_tv=1e-3, groups=None)),
+    ("tv_l1_db4_256", 256, dict(real=False, psi=10, levels=4, lam=5e-4, lam_tv=1e-3, groups=None)),
+    ("tv", 64, dict(real=False, psi=4, levels=0, lam=0.0, lam_tv=1e-3, groups=None)),
+    ("tv_db4_256", 256, dict(real=False, psi=6, levels=4, lam=5e-4, lam_tv=1e-3, groups=None)),
+]
+
+
+@pytest.mark.parametrize("precond", ["paper", "ilu0"])
+@pytest.mark.parametrize("name,n,cfg", _TV_VARIANTS, ids=[c[0] for c in _TV_VARIANTS])
+def test_tv_variants_S_Pinv_parity(F, name, n, cfg, precond):
+    """l1 TV (Eq. l1, weights W1 and W2) and the TV preconditioner factored by
+    ILU(0) with updated pivots instead of the printed factors of Sec. 4.2:
+    weights, S d and P^-1 r against the oracle's."""
+    _check_weights_S_Pinv(F, n, cfg, precond=precond)
+
+
 @pytest.mark.parametrize("precond", ["jacobi", "none"])
 @pytest.mark.parametrize("name,n,cfg", _cases(), ids=[c[0] for c in _cases()])
 def test_precond_modes_S_Pinv_parity(F, name, n, cfg, precond):
@@ -203,7 +222,8 @@ def _check_weights_S_Pinv(F, n, cfg, form=None, precond="paper"):
     ctx.apply_S_P(p, c64(x[None]), c64(d[None]), q, c64(r[None]), z)
     ww = torch.empty(1, n, n, dtype=torch.float32, device="cuda")
     wt = torch.empty_like(ww)
-    ctx.get_weights(ww, wt)
+    wt2 = torch.empty_like(ww) if cfg["psi"] & 8 else None
+    ctx.get_weights(ww, wt, wt2)
     # w ~ 1/|c| magnifies the FP32 rounding of small coefficients, so the
     # weights are compared through the group norms 1/w (absolute error of a
     # FP32 norm: a few ulp of the largest norm).
@@ -213,6 +233,10 @@ def _check_weights_S_Pinv(F, n, cfg, form=None, precond="paper"):
     if cfg["psi"] & 4:
         g_gpu, g_ref = 1.0 / host(wt)[0].reshape(-1), 1.0 / sysm.Wtv
         assert np.max(np.abs(g_gpu - g_ref)) < TOL_OP * np.max(g_ref)
+    if cfg["psi"] & 8:  # l1 TV: W1 and W2
+        for got, want in ((wt, sysm.W1), (wt2, sysm.W2)):
+            g_gpu, g_ref = 1.0 / host(got)[0].reshape(-1), 1.0 / want
+            assert np.max(np.abs(g_gpu - g_ref)) < TOL_OP * np.max(g_ref)
     assert rel(host(q)[0], sysm.apply_S(d)) < 1e-4
     assert rel(host(z)[0], sysm.apply_Pinv(r)) < 1e-4
 

@@ -92,3 +92,36 @@ def test_pcg_iterations_to_tolerance(F, case):
     assert gpu["paper"] < gpu["jacobi"] and gpu["paper"] < gpu["none"], (case, gpu)
     assert ref["paper"] < ref["jacobi"] and ref["paper"] < ref["none"], (case, ref)
     ctx.close()
+
+
+@pytest.mark.parametrize("psi", [fs.PSI_TV, fs.PSI_TV_ANISO])
+@pytest.mark.parametrize("precond", ["paper", "ilu0"])
+def test_tv_forms_solve_parity(F, psi, precond):
+    """Isotropic and l1 TV at 96^2, 30 x 20, with the printed factors and with
+    ILU(0), against the oracle with the same regulariser and factors."""
+    p = fs.make_problem(96, 0.25, 0.01, 11, real=False, psi=psi, levels=0, lam=0.0, lam_tv=1e-3)
+    x_ref, _ = O.firls_problem(p, outer=30, inner=20, precond=precond)
+    ctx = _ctx(F, p)
+    x = ctx.solve(_b(p), F.make_params(30, 20, lam_tv=p.lam_tv, precond=precond))
+    assert _rel(x[0].cpu().numpy().astype(np.complex128), x_ref) < TOL_SOLVE
+    ctx.close()
+
+
+def test_ilu0_needs_fewer_pcg_steps_than_the_printed_factors(F):
+    """ILU(0) matches P on its whole pattern (the printed factors miss the
+    diagonal terms L_P D^-1 U_P), so PCG to 1e-6 takes fewer steps with it;
+    GPU counts against the oracle's from the same iterate."""
+    p = fs.make_problem(64, 0.25, 0.01, 2, real=False, psi=fs.PSI_TV, levels=0, lam=0.0, lam_tv=1e-3)
+    x4, _ = O.firls_problem(p, outer=4, inner=20)
+    ctx = _ctx(F, p)
+    x0 = torch.from_numpy(np.asarray(x4).astype(np.complex64)).cuda()[None]
+    gpu, ref = {}, {}
+    for pre in ("paper", "ilu0"):
+        _, info = O.firls_problem(p, outer=1, inner=5000, pcg_tol=1e-6, x_init=x4, precond=pre)
+        ref[pre] = info["pcg_steps"][0]
+        _, st = ctx.solve(_b(p), F.make_params(1, 5000, lam_tv=p.lam_tv, pcg_tol=1e-6, precond=pre), x0=x0,
+                          stats=True)
+        gpu[pre] = st["pcg_steps"]
+        assert 0.8 * ref[pre] - 5 <= gpu[pre] <= 1.25 * ref[pre] + 5, (pre, gpu, ref)
+    assert gpu["ilu0"] < gpu["paper"] and ref["ilu0"] < ref["paper"], (gpu, ref)
+    ctx.close()

@@ -398,12 +398,14 @@ def _system(n, psi, real=False, groups=None, levels=2, ratio=0.3, seed=0, precon
 
 
 @pytest.mark.parametrize("precond", O.PRECONDS)
-@pytest.mark.parametrize("psi", [O.PSI_HAAR, O.PSI_DB4, O.PSI_TV, O.PSI_TV | O.PSI_DB4])
+@pytest.mark.parametrize("psi", [O.PSI_HAAR, O.PSI_DB4, O.PSI_TV, O.PSI_TV | O.PSI_DB4, O.PSI_TV_ANISO])
 def test_pcg_matches_dense_direct_solve(psi, precond):
     """PCG with the proposed P, with Jacobi and without a preconditioner (plain
     CG) reaches the dense direct solve of S x = rhs (S Hermitian positive
     definite, so PCG with any SPD P converges in at most 2N real dimensions)."""
     n = 8
+    if precond == "ilu0" and not psi & O.PSI_ANY_TV:
+        pytest.skip("ILU(0) factors the TV preconditioner")
     s, mask = _system(n, psi, precond=precond)
     Sd = dense_op(s.apply_S, n)
     assert np.allclose(Sd, Sd.conj().T, atol=1e-12)        # Hermitian
@@ -431,6 +433,49 @@ def test_jacobi_preconditioner_is_the_dense_diagonal(psi, groups):
     s, _ = _system(n, psi, groups=gr, precond="none")
     r = crandn(rng(13), n, n)
     assert np.array_equal(s.apply_Pinv(r), r)
+
+
+@pytest.mark.parametrize("tv", [O.PSI_TV, O.PSI_TV_ANISO])
+def test_irls_system_is_the_gradient_of_F_eps(tv):
+    """S(W(x)) x - A^H b equals the gradient of the eps-smoothed objective at
+    x (central differences of F_eps alone): the weights of Eq. wi (or the l1
+    weights of Eq. l1) and the assembly of S agree with the objective."""
+    n = 6
+    p = fs.make_problem(n, 0.4, 0.01, 11, real=False, psi=tv | O.PSI_HAAR, levels=1, lam=5e-3, lam_tv=1e-2)
+    eps = 1e-4
+    x = fs.complex_phantom(n, 3) + 0.05 * crandn(rng(14), n, n)
+    s = O.System(p.mask, False, p.psi, p.levels, p.lam, p.lam_tv, None, eps)
+    s.update_weights(x)
+    g_irls = s.apply_S(x) - O.op_AH(p.b, p.mask.astype(float), False)
+    F = lambda z: O.objective(z, p.b, p.mask, False, p.psi, p.levels, p.lam, p.lam_tv, None, eps)
+    h = 1e-6
+    for i in range(n * n):
+        for e, part in ((1.0, "re"), (1j, "im")):
+            zp, zm = x.copy().reshape(-1), x.copy().reshape(-1)
+            zp[i] += h * e
+            zm[i] -= h * e
+            fd = (F(zp.reshape(n, n)) - F(zm.reshape(n, n))) / (2 * h)
+            got = g_irls.reshape(-1)[i]
+            got = got.real if part == "re" else got.imag
+            assert abs(fd - got) < 1e-5 * (1 + abs(fd)), (i, part, fd, got)
+
+
+@pytest.mark.parametrize("psi", [O.PSI_TV, O.PSI_TV_ANISO, O.PSI_TV | O.PSI_DB4, O.PSI_TV_ANISO | O.PSI_HAAR])
+def test_ilu0_reproduces_P_on_its_pattern(psi):
+    """ILU(0) (zero fill, updated pivots): L U equals P at every position of
+    P's sparsity pattern, the diagonal included, and differs only at the
+    fill positions; all pivots are positive (P is a diagonally dominant
+    M-matrix).  The printed factors of Sec. 4.2 differ on the diagonal."""
+    n = 6
+    s, _ = _system(n, psi, levels=1, precond="ilu0")
+    P = s.P.toarray()
+    LU = (s.L @ s.U).toarray()
+    pattern = P != 0
+    assert np.allclose(LU[pattern], P[pattern], rtol=1e-12, atol=1e-14)
+    assert np.all(s.U.diagonal() > 0)
+    printed, _ = _system(n, psi, levels=1, precond="paper")
+    LU_p = (printed.L @ printed.U).toarray()
+    assert not np.allclose(np.diag(LU_p), np.diag(P), rtol=1e-9)
 
 
 def test_S_is_gradient_of_quadratic_model():
@@ -469,7 +514,7 @@ def test_full_mask_wavelet_pcg_one_step():
 # ---------------------------------------------------------------- FIRLS ---
 
 @pytest.mark.parametrize("inner", [1, 3, 20])
-@pytest.mark.parametrize("which", ["haar_real", "tv_db4", "tree", "tv"])
+@pytest.mark.parametrize("which", ["haar_real", "tv_db4", "tree", "tv", "tv_l1", "tv_l1_db4_ilu0"])
 def test_theorem2_monotone_decrease(which, inner):
     if which == "haar_real":
         p = fs.make_problem(32, 0.25, 0.01, 1, real=True, psi=O.PSI_HAAR, levels=3, lam=1e-3)
@@ -477,9 +522,15 @@ def test_theorem2_monotone_decrease(which, inner):
         p = fs.make_problem(32, 0.2, 0.01, 2, real=False, psi=O.PSI_TV | O.PSI_DB4, levels=2, lam=5e-4, lam_tv=1e-3)
     elif which == "tree":
         p = fs.make_problem(32, 0.15, 0.005, 3, real=False, psi=O.PSI_DB4, levels=3, lam=2e-4, tree=True)
-    else:
+    elif which == "tv":
         p = fs.make_problem(32, 0.2, 0.01, 4, real=False, psi=O.PSI_TV, levels=0, lam=0.0, lam_tv=1e-3)
-    _, info = O.firls_problem(p, outer=8, inner=inner, record=True)
+    elif which == "tv_l1":
+        p = fs.make_problem(32, 0.2, 0.01, 4, real=False, psi=O.PSI_TV_ANISO, levels=0, lam=0.0, lam_tv=1e-3)
+    else:
+        p = fs.make_problem(32, 0.2, 0.01, 5, real=False, psi=O.PSI_TV_ANISO | O.PSI_DB4, levels=2, lam=5e-4,
+                            lam_tv=1e-3)
+    pre = "ilu0" if which == "tv_l1_db4_ilu0" else "paper"
+    _, info = O.firls_problem(p, outer=8, inner=inner, record=True, precond=pre)
     F = info["F_eps"]
     for k in range(len(F) - 1):
         assert F[k + 1] <= F[k] * (1 + 1e-12), (k, F[k], F[k + 1])
@@ -517,11 +568,13 @@ def test_soft_threshold_special_case():
     assert np.max(np.abs(c - soft)) < 10 * math.sqrt(O.EPS)
 
 
-def test_theorem3_stationarity_by_finite_differences():
+@pytest.mark.parametrize("tv", [O.PSI_TV, O.PSI_TV_ANISO])
+def test_theorem3_stationarity_by_finite_differences(tv):
     """At convergence the gradient of F_eps vanishes (Thm 3), checked with
-    central differences of the objective alone (forward operators only)."""
+    central differences of the objective alone (forward operators only), for
+    isotropic (Eq. iso) and l1 (Eq. l1) TV."""
     n = 6
-    p = fs.make_problem(n, 0.4, 0.01, 7, real=False, psi=O.PSI_TV | O.PSI_DB4, levels=1, lam=5e-3, lam_tv=1e-2)
+    p = fs.make_problem(n, 0.4, 0.01, 7, real=False, psi=tv | O.PSI_DB4, levels=1, lam=5e-3, lam_tv=1e-2)
     # eps = 1e-6 keeps the objective's curvature scale (sqrt eps) well above
     # the difference step, so central differences are accurate
     eps = 1e-6
