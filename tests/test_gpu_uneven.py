@@ -1,5 +1,5 @@
 """Slices of uneven size (128^2 .. 320^2, TV + D4, per-slice lambdas and mask
-ratios) solved together: one CUDA graph per outer step over four contexts."""
+ratios) solved together: one CUDA graph of macro steps over four contexts."""
 import numpy as np
 import pytest
 
@@ -52,21 +52,34 @@ def test_uneven_graph_matches_separate_solves(F):
             assert torch.equal(a, r)
 
 
-@pytest.mark.parametrize("gi", [0, 1, 2, 3], ids=["128", "192", "256", "320"])
-def test_uneven_one_step_parity(F, gi):
-    """One outer step from A^H b per size.  The tolerance is 1e-4, or five
-    times the error of an FP32-rounded run of the oracle on the same slice
-    where that is larger (some of these slices amplify FP32 rounding to
-    ~2e-3 within one PCG run; the GPU must stay within that band)."""
-    from fp32_emulation import one_outer_step_fp32_error
-    p = _groups()[gi][0]
-    ctx = _ctx(F, [p], torch.cuda.current_stream())
-    x = ctx.solve(torch.from_numpy(p.b[None]).to(torch.complex64).cuda(), _params(F, [p], 1, 20))
+def test_uneven_batch_reaches_converged_oracle(F):
+    """The first slice of each size (seeds 1000, 1016, 1032, 1048: 128^2 ..
+    320^2 TV + D4 with their own lambdas and masks), solved together by
+    solve_multi with the bench's schedule and per-slice stop, lands within
+    1e-4 of the FP64 oracle's converged x* (tests/golden/xstar_uneven,
+    written by tests/golden/make_xstar.py --uneven from the oracle alone)."""
+    import os
+    import bench
+    golden = os.path.join(os.path.dirname(__file__), "golden", "xstar_uneven")
+    seeds = (1000, 1016, 1032, 1048)
+    probs = {s: p for s, p in zip(range(1000, 1064), fs.uneven_batch()) if s in seeds}
+    groups = [[probs[s]] for s in seeds]
+    streams = [torch.cuda.Stream() for _ in groups]
+    ctxs = [_ctx(F, g, st) for g, st in zip(groups, streams)]
+    bs = [torch.from_numpy(np.stack([p.b for p in g])).to(torch.complex64).cuda() for g in groups]
+    ps = [F.make_params(bench.OUTER, bench.INNER, lam_per_slice=[p.lam for p in g],
+                        lam_tv_per_slice=[p.lam_tv for p in g], outer_tol=bench.OUTER_TOL, stop_on_distance=True,
+                        stall_tol=bench.STALL_TOL, pcg_late=bench.INNER_LATE, outer_late=bench.OUTER_LATE)
+          for g in groups]
+    outs = [torch.empty_like(b) for b in bs]
     torch.cuda.synchronize()
-    x_ref, _ = O.firls_problem(p, outer=1, inner=20)
-    got = x[0].cpu().numpy().astype(np.complex128)
-    tol = max(1e-4, 5 * one_outer_step_fp32_error(p, O.op_AH(p.b, p.mask, False), 20))
-    assert np.linalg.norm(got - x_ref) / np.linalg.norm(x_ref) < tol
+    F.solve_multi(ctxs, bs, ps, outs)
+    torch.cuda.synchronize()
+    for s, out in zip(seeds, outs):
+        xs = np.load(os.path.join(golden, f"seed{s}.npz"))["x"].astype(np.complex128)
+        got = out[0].cpu().numpy().astype(np.complex128)
+        err = np.linalg.norm(got - xs) / np.linalg.norm(xs)
+        assert err < 1e-4, (s, err)
 
 
 def test_autotune_picks_candidates_and_keeps_results(F, tmp_path):
