@@ -122,7 +122,12 @@ typedef struct {
                           relchg * mu / (1 - mu) with the contraction
                           mu = (relchg_k / relchg_{k-24})^(1/24), at most
                           0.999 (linear convergence), and the relative change
-                          are both <= outer_tol (after > 24 outer steps)      */
+                          are both <= outer_tol (after > 24 outer steps); with
+                          a late inner schedule (pcg_iters_late > 0), also
+                          once the relative change is <= outer_tol and has not
+                          fallen by 20 % over the 24 outer steps before, all
+                          taken from outer step outer_late on (the slice's
+                          FP32 floor)                                         */
   int precond;         /* FIRLS_PRECOND_*: the PCG preconditioner (0 = the
                           paper's)                                            */
   float outer_stall_tol; /* stop a slice once its relative change has stayed

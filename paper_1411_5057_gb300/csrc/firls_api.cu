@@ -326,7 +326,10 @@ void enqueue_macro(firls_ctx* c, const firls_params& sc, bool boundary_stage = t
     {
       TMark m(c, FIRLS_K_OTHER, 3);
       outer_apply(B, n, c->stream, c->st, c->x, c->dx, c->part);
-      outer_end(B, c->stream, c->st, c->part, axpy_ctas(n), sc.outer_tol, sc.outer_tol_kind, sc.outer_stall_tol);
+      // the plateau stop needs a whole contraction window of nearly exact inner solves
+      const int plateau_after = sc.pcg_iters_late > 0 ? sc.outer_late + MU_WINDOW : 1 << 30;
+      outer_end(B, c->stream, c->st, c->part, axpy_ctas(n), sc.outer_tol, sc.outer_tol_kind, sc.outer_stall_tol,
+                plateau_after);
       boundary_view(B, c->stream, c->st, c->stw);
     }
     enqueue_weights(c, c->x, sc.precond, c->stw);

@@ -2319,9 +2319,14 @@ void pcg_scalars(int batch, cudaStream_t s, SliceState* st, const double* part, 
 // 0.999 (a long window: the rate drifts early on and FP32 rounding jitters
 // single steps).  Either kind also stops a slice whose relative change has
 // stayed at or below stall_tol for STALL_STEPS consecutive steps: the FP32
-// rounding floor of the outer iteration, below which it cannot move.
+// rounding floor of the outer iteration, below which it cannot move.  Kind 1
+// stops a slice on a plateau too: from outer step plateau_after on (a whole
+// window in the phase of nearly exact inner solves, where the outer
+// iteration contracts by far more than 20 % over the window), a relative
+// change at or below tol that has not fallen by 20 % over the window is that
+// slice's FP32 floor, whatever its level.
 __global__ void k_outer_end(int B, SliceState* st, const double* part, int np, float tol, int kind,
-                            float stall_tol) {
+                            float stall_tol, int plateau_after) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B || !slice_running(st, s) || st[s].phase != PH_END) return;
   SliceState* v = st + s;
@@ -2344,6 +2349,7 @@ __global__ void k_outer_end(int B, SliceState* st, const double* part, int np, f
     } else if (k >= MU_WINDOW && old > 0.f) {
       const double mu = fmin(pow(rel / (double)old, 1.0 / MU_WINDOW), 0.999);
       if (rel * mu / (1.0 - mu) <= (double)tol && rel <= (double)tol) v->done = 1;
+      if (k >= plateau_after && rel <= (double)tol && rel >= 0.8 * (double)old) v->done = 1;
     }
   }
   if (v->outer_done >= v->outer_max) v->done = 1;
@@ -2351,8 +2357,8 @@ __global__ void k_outer_end(int B, SliceState* st, const double* part, int np, f
 }
 
 void outer_end(int batch, cudaStream_t s, SliceState* st, const double* part, int np, float tol, int kind,
-               float stall_tol) {
-  k_outer_end<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np, tol, kind, stall_tol);
+               float stall_tol, int plateau_after) {
+  k_outer_end<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np, tol, kind, stall_tol, plateau_after);
 }
 
 }  // namespace firls

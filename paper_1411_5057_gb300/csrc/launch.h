@@ -146,8 +146,9 @@ void boundary_view(int batch, cudaStream_t s, SliceState* st, SliceState* view);
 // ||x||^2 (before the update) for the relative change.
 void outer_apply(int batch, int n, cudaStream_t s, const SliceState* st, float2* x, float2* dx,
                  double* part);
+// plateau_after: first outer step at which kind 1 also stops on a plateau
 void outer_end(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts,
-               float outer_tol, int tol_kind, float stall_tol);
+               float outer_tol, int tol_kind, float stall_tol, int plateau_after);
 // phase: PH_BOUNDARY for a solve (its first outer step is due), PH_START for
 // the single operator applications (no outer step)
 void state_init(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts_rhs,
