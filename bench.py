@@ -76,10 +76,12 @@ ALG_BYTES_PER_PX = {
 }
 
 # DRAM bytes per pixel per launch (dram__bytes_read.sum + dram__bytes_write.sum)
-# from the ncu launch list of one 304-slice 256^2 outer step
-# (profiles/launch_list_tv_db4_256_b304.md), for the kernels as they are now.
+# of the dominant kernel, from a one-kernel ncu capture at 96 slots with the
+# bench's ILU ring shape (profiles/kernels_tv_db4_256_b96.md), scaled to the
+# bench's slots per pixel (the ILU moves the same bytes per slice at any
+# batch), for the kernel as it is now.
 MEASURED_TRAFFIC_PER_PX = {
-    "ilu": 84.5,
+    "ilu": 79.2,
 }
 
 
@@ -638,6 +640,29 @@ def run_reference(args):
     return out
 
 
+def profile_step(args):
+    """Profiling target (no timing, no JSON line): one outer step of 60 PCG
+    steps (61 macro steps) of the 256^2 TV + D4 workload on --profile-step
+    slices, run twice, with the given ILU ring shape (0: the default)."""
+    import torch
+    import paper_1411_5057_gb300 as F
+    B = args.profile_step
+    masks_h, b_h = make_batch(B, 2)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        masks = torch.from_numpy(masks_h).cuda()
+        b = torch.from_numpy(b_h).cuda()
+        ctx = F.Context(N, batch=B, stream=stream)
+        ctx.set_operator(masks, F.PSI_TV | F.PSI_DB4, LEVELS)
+        ctx.set_tuning(rows_per_cta=1, coarse_max=64, ilu_depth=args.profile_ilu_shape)
+        one = F.make_params(1, INNER, lam=LAM_W, lam_tv=LAM_TV)
+        for _ in range(2):
+            ctx.solve(b, one)
+    stream.synchronize()
+    ctx.close()
+    print(f"[bench] profile step: {B} slices, one outer step x2", file=sys.stderr)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -669,7 +694,12 @@ def main(argv=None):
     ap.add_argument("--precond-cmp", type=int, default=1,
                     help="report PCG steps to 1e-6 for the proposed, Jacobi and no preconditioner (1/0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-step", type=int, default=0,
+                    help="profiling target only: one outer step on this many slices, twice")
+    ap.add_argument("--profile-ilu-shape", type=int, default=0)
     args = ap.parse_args(argv)
+    if args.profile_step > 0:
+        return profile_step(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
