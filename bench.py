@@ -150,6 +150,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def rank_first_seed(rank, queue):
+    """First seed of a rank's queue: ranks serve disjoint, consecutive seed
+    ranges (replicas; no data is exchanged)."""
+    return 2 + rank * queue
+
+
+def max_over_ranks(value, dist, device):
+    """The largest value over the ranks (the step time every rank reports)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -168,7 +184,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     B, S = args.batch, args.queue
-    masks_h, b_h = make_batch(S, 2 + rank * S)
+    masks_h, b_h = make_batch(S, rank_first_seed(rank, S))
     stream = torch.cuda.Stream()
     params = F.make_params(args.outer, args.inner, lam=LAM_W, lam_tv=LAM_TV, outer_tol=args.outer_tol,
                            stop_on_distance=True, stall_tol=args.stall_tol, pcg_late=args.inner_late,
@@ -219,12 +235,9 @@ def run_ours(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     barrier()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     value = world * done_per_step / (ms / 1e3)
-    acc = accuracy(xlist, 2 + rank * S, steps)
+    acc = accuracy(xlist, rank_first_seed(rank, S), steps)
     if acc is not None:
         print(f"[bench] accuracy vs stored oracle x*: {acc['n_checked']} slices, max rel err {acc['max_rel_err']:.2e} "
               f"(seed {acc['worst_seed']}), median {acc['median_rel_err']:.2e}", file=sys.stderr, flush=True)
@@ -288,10 +301,7 @@ def run_ours(args):
                 xh.copy_(x, non_blocking=True)
             stream.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-        if dist is not None:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, dist, "cuda")
         e2e = {"value": world * done_per_step / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(bh.numel() * 8 + mh.numel()),
                "d2h_bytes_per_step": int(xh.numel() * 8)}
@@ -385,7 +395,7 @@ def run_learned(args, F, torch, stream, b, masks, B, S, plain_value, plain_steps
     ms = e0.elapsed_time(e1) / args.steps
     inf.close()
     prep.close()
-    lacc = accuracy(xs, 2 + rank * S, lsteps)
+    lacc = accuracy(xs, rank_first_seed(rank, S), lsteps)
     lsteps = np.asarray(lsteps)
     lsteps = lsteps[lsteps > 0]
     value = done_per_step / (ms / 1e3)
