@@ -178,6 +178,54 @@ def make_problem(n, ratio, sigma, seed, *, real, psi, levels, lam, lam_tv=0.0, t
                    meta=dict(ratio=ratio, sigma=sigma))
 
 
+# --- multi-contrast cross sections (joint sparsity / joint TV) --------------
+
+CONTRAST = 5   # substream of the per-contrast intensities
+
+
+def contrast_phantoms(n: int, contrasts: int, seed: int, n_ellipses: int = 10) -> list:
+    """Complex phantoms of one cross section seen with several contrasts: the
+    ellipse geometry (centres, semi-axes, angles) of ``seed`` is shared, the
+    intensity of every ellipse is drawn per contrast (U[0, 1], substream
+    CONTRAST, one draw per contrast and ellipse), and every contrast gets its
+    own smooth phase map (seed * 1000 + t)."""
+    geo = _rng(seed, PHANTOM)
+    shapes = []
+    for _ in range(n_ellipses):
+        cx, cy = geo.uniform(-0.7, 0.7, size=2)
+        ax, ay = geo.uniform(0.05, 0.45, size=2)
+        th = geo.uniform(0.0, math.pi)
+        geo.uniform(0.0, 1.0)  # the single-contrast intensity draw, unused here
+        shapes.append((cx, cy, ax, ay, th))
+    inten = _rng(seed, CONTRAST).uniform(0.0, 1.0, size=(contrasts, n_ellipses))
+    t = (2.0 * (np.arange(n) + 0.5) / n) - 1.0
+    v, u = np.meshgrid(t, t, indexing="ij")
+    out = []
+    for c in range(contrasts):
+        img = np.zeros((n, n))
+        for e, (cx, cy, ax, ay, th) in enumerate(shapes):
+            du, dv = u - cx, v - cy
+            ct, st = math.cos(th), math.sin(th)
+            inside = ((ct * du + st * dv) / ax) ** 2 + ((-st * du + ct * dv) / ay) ** 2 <= 1.0
+            img[inside] += inten[c, e]
+        out.append(img * np.exp(1j * smooth_phase(n, seed * 1000 + c)))
+    return out
+
+
+def multi_contrast(n: int, contrasts: int, ratio: float, sigma: float, seed: int, *, psi: int, levels: int,
+                   lam: float, lam_tv: float = 0.0) -> list:
+    """One multi-contrast cross section: a Problem per contrast with its own
+    variable-density mask and noise (seeds seed * 1000 + t)."""
+    out = []
+    for c, x0 in enumerate(contrast_phantoms(n, contrasts, seed)):
+        s = seed * 1000 + c
+        mask = vd_mask(n, ratio, s)
+        out.append(Problem(n=n, mask=mask, b=measurements(x0, mask, sigma, s), x0=x0, real=False, psi=psi,
+                           levels=levels, lam=lam, lam_tv=lam_tv, groups=None, seed=s,
+                           meta=dict(ratio=ratio, sigma=sigma, contrast=c)))
+    return out
+
+
 # --- the five workloads -----------------------------------------------------
 
 def haar_l1_64(seed: int = 1) -> Problem:

@@ -569,3 +569,138 @@ def inverse_group_map(groups, N):
     off = np.zeros(N + 1, dtype=np.int32)
     off[1:] = np.cumsum(counts)
     return off, gid[order].astype(np.int32)
+
+
+# ---------------------------------------------------------------------------
+# Multi-contrast reconstruction (Sec. 5.6: FIRLS_MT, FIRLS_JTV)
+# ---------------------------------------------------------------------------
+
+class JointSystem:
+    """T contrasts x_1..x_T of one cross section, each with its own sampling
+    mask, sharing the regulariser's weights (Sec. 5.6):
+
+    * wavelet joint sparsity (FIRLS_MT): the group of coefficient j holds
+      (Phi x_t)_j of every contrast, W_j = (sum_t |(Phi x_t)_j|^2 + eps)^(-1/2)
+      (Eq. gw with non-overlapping groups across contrasts);
+    * joint TV (FIRLS_JTV): W_i = (sum_t |grad_1 x_t,i|^2 + |grad_2 x_t,i|^2
+      + eps)^(-1/2) (Eq. wi summed over contrasts).
+
+    Given W the system is block diagonal: S = blockdiag_t(A_t^H A_t + lam
+    Phi^T W Phi + lam_TV (D1^T W D1 + D2^T W D2)), and so is P (each block
+    the single-contrast P of Eq. pog / Eq. ptv with that contrast's abar).
+    PCG runs on the stacked system (one alpha, beta, rho for all contrasts),
+    as Alg. 2 / Alg. 3 on the stacked unknown.
+    """
+
+    def __init__(self, masks, psi, levels, lam, lam_tv, eps=EPS):
+        self.T = len(masks)
+        self.eps = float(eps)
+        self.psi = int(psi)
+        self.kind = wavelet_kind(psi)
+        self.tv = bool(psi & PSI_TV)
+        if psi & PSI_TV_ANISO:
+            raise ValueError("joint TV is the isotropic form")
+        self.levels = int(levels)
+        self.lam = float(lam)
+        self.lam_tv = float(lam_tv) if self.tv else 0.0
+        self.parts = [System(m, False, psi, levels, lam, lam_tv, None, eps) for m in masks]
+
+    def update_weights(self, xs):
+        if self.kind:
+            sq = sum(np.abs(wavedec2(x, self.kind, self.levels).reshape(-1)) ** 2 for x in xs)
+            w = (sq + self.eps) ** -0.5
+            for p in self.parts:
+                p.w = w
+        if self.tv:
+            D1, D2 = self.parts[0].D1, self.parts[0].D2
+            sq = sum(np.abs(D1 @ x.reshape(-1)) ** 2 + np.abs(D2 @ x.reshape(-1)) ** 2 for x in xs)
+            W = (sq + self.eps) ** -0.5
+            for p in self.parts:
+                p.Wtv = W
+                p.W1 = p.W2 = W
+        for p in self.parts:
+            p._build_preconditioner()
+
+    def apply_S(self, xs):
+        return [p.apply_S(x) for p, x in zip(self.parts, xs)]
+
+    def apply_Pinv(self, rs):
+        return [p.apply_Pinv(r) for p, r in zip(self.parts, rs)]
+
+
+def rdot_joint(us, vs):
+    """Real inner product of stacked contrasts: sum_t Re <u_t, v_t>."""
+    return sum(rdot(u, v) for u, v in zip(us, vs))
+
+
+def pcg_joint(system, rhs, xs, inner, tol, rhs_norm):
+    """PCG (Saad, Alg. 9.1) on the stacked block system from the warm start xs."""
+    xs = [x.copy() for x in xs]
+    r = [b - s for b, s in zip(rhs, system.apply_S(xs))]
+    z = system.apply_Pinv(r)
+    d = [v.copy() for v in z]
+    rho = rdot_joint(r, z)
+    steps = 0
+    for j in range(inner):
+        q = system.apply_S(d)
+        alpha = rho / rdot_joint(d, q)
+        xs = [x + alpha * v for x, v in zip(xs, d)]
+        r = [a - alpha * v for a, v in zip(r, q)]
+        steps += 1
+        if tol > 0 and math.sqrt(rdot_joint(r, r)) <= tol * rhs_norm:
+            break
+        if j == inner - 1:
+            break
+        z = system.apply_Pinv(r)
+        rho_new = rdot_joint(r, z)
+        beta = rho_new / rho
+        d = [a + beta * v for a, v in zip(z, d)]
+        rho = rho_new
+    return xs, steps
+
+
+def objective_joint(xs, bs, masks, psi, levels, lam, lam_tv, eps=0.0):
+    """sum_t 1/2 ||A_t x_t - b_t||^2 + lam sum_j sqrt(sum_t |(Phi x_t)_j|^2 + eps)
+    + lam_TV sum_i sqrt(sum_t |grad x_t,i|^2 + eps)."""
+    val = 0.0
+    for x, b, m in zip(xs, bs, masks):
+        m = np.asarray(m).astype(np.float64)
+        val += 0.5 * float(np.sum(np.abs(op_A(x, m) - m * b) ** 2))
+    kind = wavelet_kind(psi)
+    if kind:
+        sq = sum(np.abs(wavedec2(x, kind, levels)) ** 2 for x in xs)
+        val += lam * float(np.sum(np.sqrt(sq + eps)))
+    if psi & PSI_TV:
+        n = np.asarray(masks[0]).shape[0]
+        D1, D2 = tv_matrices(n)
+        sq = sum(np.abs(D1 @ np.asarray(x).reshape(-1)) ** 2 + np.abs(D2 @ np.asarray(x).reshape(-1)) ** 2 for x in xs)
+        val += lam_tv * float(np.sum(np.sqrt(sq + eps)))
+    return val
+
+
+def firls_joint(bs, masks, *, psi, levels, lam, lam_tv=0.0, outer=50, inner=20, pcg_tol=0.0, outer_tol=0.0,
+                x_init=None, record=False, eps=EPS):
+    """FIRLS_MT / FIRLS_JTV (Sec. 5.6): Alg. 2 / Alg. 3 on the stacked
+    contrasts with joint weights.  Returns (list of x_t, info)."""
+    system = JointSystem(masks, psi, levels, lam, lam_tv, eps)
+    rhs = [op_AH(np.asarray(m) * b, np.asarray(m).astype(np.float64), False) for b, m in zip(bs, masks)]
+    rhs_norm = math.sqrt(rdot_joint(rhs, rhs))
+    xs = [r.copy() for r in rhs] if x_init is None else [np.array(x, copy=True) for x in x_init]
+    info = dict(pcg_steps=[], rel_change=[], F_eps=[], outer_done=0)
+    if record:
+        info["F_eps"].append(objective_joint(xs, bs, masks, psi, levels, lam, lam_tv, eps))
+    for k in range(outer):
+        system.update_weights(xs)
+        x_new, steps = pcg_joint(system, rhs, xs, inner, pcg_tol, rhs_norm)
+        dx = [a - b for a, b in zip(x_new, xs)]
+        nx = math.sqrt(rdot_joint(xs, xs))
+        rel = math.sqrt(rdot_joint(dx, dx)) / nx if nx > 0 else float("inf")
+        xs = x_new
+        info["pcg_steps"].append(steps)
+        info["rel_change"].append(rel)
+        info["outer_done"] = k + 1
+        if record:
+            info["F_eps"].append(objective_joint(xs, bs, masks, psi, levels, lam, lam_tv, eps))
+        if outer_tol > 0 and rel <= outer_tol:
+            break
+    return xs, info
