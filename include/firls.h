@@ -285,6 +285,24 @@ firls_status firls_slot_get(firls_ctx* ctx, int s, void* x_out);
  * firls_set_operator and before solving.  Synchronises the stream. */
 firls_status firls_autotune(firls_ctx* ctx, const char* cache_path);
 
+/* Multi-contrast images (Sec. 5.6, FIRLS_MT and FIRLS_JTV): with channels
+ * C > 1, every C consecutive slices of the batch are the contrasts x_1..x_C
+ * of one cross section, each with its own mask (set_operator) and k-space.
+ * They share the regulariser's weights: joint wavelet sparsity, W_j =
+ * (sum_t |(Phi x_t)_j|^2 + eps)^(-1/2) (non-overlapping groups across the
+ * contrasts, Eq. gw), and joint TV, W_i = (sum_t |grad_1 x_t,i|^2 +
+ * |grad_2 x_t,i|^2 + eps)^(-1/2).  Given W the system and P are block
+ * diagonal over the contrasts, and PCG runs on the stacked unknown: the inner
+ * products, the PCG stop, the relative change and the outer stop are sums
+ * over an image's contrasts, so its C slices move in lockstep (same outer
+ * and PCG counts).  firls_objective returns each image's F_eps for every one
+ * of its slices.  The contrasts of an image must share lambda and lambda_tv
+ * (FIRLS_E_INVALID_ARG from the solve otherwise).  Not with a group map or
+ * FIRLS_PSI_TV_ANISO, and not with the slot API (FIRLS_E_STATE from
+ * firls_slot_load).  channels must divide the batch; 1 (the default) is the
+ * single-contrast solver.  Call before solving; no device work. */
+firls_status firls_set_channels(firls_ctx* ctx, int channels);
+
 /* Failure-detection test hook (no counterpart in the paper).  With enable = 1
  * the TV preconditioner kernel (the ILU sweeps of Sec. 4.2) of every later
  * outer step runs in a test form: its producer issues no copy and every

@@ -24,7 +24,7 @@ REAL_X = 1
 EXPORTED = ["firls_size_supported", "firls_create", "firls_set_operator", "firls_solve", "firls_solve_multi",
             "firls_last_error", "firls_destroy", "firls_apply_AHA", "firls_apply_Phi", "firls_apply_PhiT",
             "firls_apply_S_P", "firls_get_weights", "firls_get_precond", "firls_get_inverse_map",
-            "firls_set_tuning", "firls_get_popcounts", "firls_set_wait_test",
+            "firls_set_tuning", "firls_get_popcounts", "firls_set_wait_test", "firls_set_channels",
             "firls_set_timing", "firls_get_timing", "firls_apply_AHA_noalloc",
             "firls_cnn_create", "firls_cnn_set_params", "firls_cnn_get_params", "firls_cnn_get_grads",
             "firls_cnn_forward", "firls_cnn_train_step", "firls_cnn_destroy", "firls_objective",
@@ -92,6 +92,7 @@ def lib():
     L.firls_get_inverse_map.argtypes = [vp, vp, vp]
     L.firls_get_popcounts.argtypes = [vp, vp]
     L.firls_set_wait_test.argtypes = [vp, i32]
+    L.firls_set_channels.argtypes = [vp, i32]
     L.firls_apply_AHA_noalloc.argtypes = [i32, i32, vp, vp, vp, vp]
     L.firls_objective.argtypes = [vp, vp, ctypes.POINTER(Params), vp, ctypes.POINTER(ctypes.c_double)]
     L.firls_adjoint.argtypes = [vp, vp, vp]
@@ -263,6 +264,11 @@ class Context:
         b = cur["coarse_max"] if coarse_max is None else coarse_max
         c = cur["ilu_depth"] if ilu_depth is None else ilu_depth
         self._check(lib().firls_set_tuning(self.h, a, b, c), "set_tuning")
+
+    def set_channels(self, channels):
+        """Multi-contrast images: every `channels` consecutive slices are the
+        contrasts of one image (joint weights, one PCG on the stacked unknown)."""
+        self._check(lib().firls_set_channels(self.h, int(channels)), "set_channels")
 
     def set_wait_test(self, enable=True):
         """Failure-detection test hook: the ILU kernel's bounded waits run out."""

@@ -26,6 +26,9 @@ struct firls_ctx {
   int levels = 0, kind = 0;
   int n_groups = 0, gsize = 0, gtotal = 0;
   bool groups = false;
+  // multi-contrast images (Sec. 5.6): C consecutive slices are the contrasts
+  // of one image, with joint weights and one set of PCG scalars
+  int channels = 1;
   // device workspace
   uint8_t* mask = nullptr;
   int* counts = nullptr;
@@ -245,7 +248,10 @@ void enqueue_weights(firls_ctx* c, const float2* x, int precond, const SliceStat
   TMark mk(c, FIRLS_K_WEIGHTS, 0);
   if (c->kind) {
     WavArgs w = wav_args(c, view);
-    if (!c->groups) {
+    if (c->channels > 1) {
+      wavelet_forward(w, x, c->cw, nullptr, WAV_RAW);
+      joint_wavelet_weights(B, n, c->channels, c->stream, view, c->cw, c->ww);
+    } else if (!c->groups) {
       wavelet_forward(w, x, c->cw, c->ww, WAV_SINGLETON_W);
     } else {
       wavelet_forward(w, x, c->cw, nullptr, WAV_RAW);
@@ -255,7 +261,7 @@ void enqueue_weights(firls_ctx* c, const float2* x, int precond, const SliceStat
   }
   if (has_tv(c)) {
     // with TV, 1/a of the penta-diagonal P is also 1/diag(S) (the Jacobi scale)
-    tv_weights(B, n, c->stream, view, x, c->wtv, tv2_of(c));
+    tv_weights(B, n, c->stream, view, x, c->wtv, tv2_of(c), c->channels);
     if (c->kind) wavelet_diag(B, n, c->levels, c->stream, view, c->ww, c->wdiag, c->sqtab, c->sqlen);
     penta_setup(B, n, c->stream, view, c->wtv, tv2_of(c), c->kind ? c->wdiag : nullptr, c->ia);
     // ILU(0): the pivots of the incomplete factorisation replace 1/a
@@ -287,14 +293,22 @@ void enqueue_precond(firls_ctx* c, int mode, const firls_params& sc) {
                      sc.precond == FIRLS_PRECOND_JACOBI ? c->ia : nullptr, c->z);
     }
     TMark m(c, FIRLS_K_SCALARS, 1);
-    pcg_scalars(B, c->stream, c->st, c->part, axpy_ctas(n), axpy_ctas(n), sm, ps);
+    pcg_scalars(B, c->stream, c->st, c->part, axpy_ctas(n), axpy_ctas(n), sm, ps, c->channels);
     return;
   }
   if (has_tv(c)) {
-    TMark m(c, FIRLS_K_ILU, 1);
-    // the ILU CTA finishes rho (and beta) from its own sums
-    ilu_step(B, n, c->stream, c->st, c->part, mode, c->dx, c->d, c->r, c->q, c->atb, c->u, c->z, c->ia, c->wtv,
-             c->tune_ilu, 1, ps, c->wait_test, tv2_of(c));
+    // the ILU CTA finishes rho (and beta) from its own sums, unless they are
+    // sums over the contrasts of an image
+    const bool fuse = c->channels == 1;
+    {
+      TMark m(c, FIRLS_K_ILU, 1);
+      ilu_step(B, n, c->stream, c->st, c->part, mode, c->dx, c->d, c->r, c->q, c->atb, c->u, c->z, c->ia, c->wtv,
+               c->tune_ilu, fuse ? 1 : 0, ps, c->wait_test, tv2_of(c));
+    }
+    if (!fuse) {
+      TMark m(c, FIRLS_K_SCALARS, 1);
+      pcg_scalars(B, c->stream, c->st, c->part, 1, 1, sm, ps, c->channels);
+    }
     return;
   }
   {
@@ -308,7 +322,7 @@ void enqueue_precond(firls_ctx* c, int mode, const firls_params& sc) {
   }
   TMark m(c, FIRLS_K_SCALARS, 1);
   const int np = wavelet_apply_ctas(n, c->levels, c->kind, c->tune_rb, c->tune_cmax);
-  pcg_scalars(B, c->stream, c->st, c->part, np, axpy_ctas(n), sm, ps);
+  pcg_scalars(B, c->stream, c->st, c->part, np, axpy_ctas(n), sm, ps, c->channels);
 }
 
 // One macro step: every slice advances by one step of its own outer step.
@@ -329,7 +343,7 @@ void enqueue_macro(firls_ctx* c, const firls_params& sc, bool boundary_stage = t
       // the plateau stop needs a whole contraction window of nearly exact inner solves
       const int plateau_after = sc.pcg_iters_late > 0 ? sc.outer_late + MU_WINDOW : 1 << 30;
       outer_end(B, c->stream, c->st, c->part, axpy_ctas(n), sc.outer_tol, sc.outer_tol_kind, sc.outer_stall_tol,
-                plateau_after);
+                plateau_after, c->channels);
       boundary_view(B, c->stream, c->st, c->stw);
     }
     enqueue_weights(c, c->x, sc.precond, c->stw);
@@ -337,7 +351,7 @@ void enqueue_macro(firls_ctx* c, const firls_params& sc, bool boundary_stage = t
   enqueue_S(c, -1, c->z, c->d, c->q);
   {
     TMark m(c, FIRLS_K_SCALARS, 1);
-    pcg_alpha(B, c->stream, c->st, c->part, fft_row_ctas(n));
+    pcg_alpha(B, c->stream, c->st, c->part, fft_row_ctas(n), c->channels);
   }
   enqueue_precond(c, ILU_PER_SLICE, sc);
 }
@@ -372,6 +386,13 @@ firls_status check_params(firls_ctx* c, const firls_params* p) {
     const float lt = p->lambda_tv_per_slice ? p->lambda_tv_per_slice[s] : p->lambda_tv;
     if (!(l >= 0.f) || !std::isfinite(l)) return fail(c, FIRLS_E_INVALID_ARG, "lambda must be finite and >= 0");
     if (!(lt >= 0.f) || !std::isfinite(lt)) return fail(c, FIRLS_E_INVALID_ARG, "lambda_tv must be finite and >= 0");
+    const int s0 = s - s % c->channels;
+    if (s != s0) {  // one regulariser per multi-contrast image
+      const float l0 = p->lambda_per_slice ? p->lambda_per_slice[s0] : p->lambda;
+      const float lt0 = p->lambda_tv_per_slice ? p->lambda_tv_per_slice[s0] : p->lambda_tv;
+      if (l != l0 || lt != lt0)
+        return fail(c, FIRLS_E_INVALID_ARG, "the contrasts of an image must share lambda and lambda_tv");
+    }
   }
   return FIRLS_OK;
 }
@@ -412,7 +433,7 @@ firls_status enqueue_setup(firls_ctx* c, const void* b, const firls_params* p, c
   }
   CU(cudaMemsetAsync(c->dx, 0, sizeof(float2) * (size_t)B * n * n, c->stream));
   state_init(B, c->stream, c->st, c->part, fft_col_ctas(n), c->counts, n, c->lam_d, c->lamtv_d, eps_of(p),
-             p->outer_iters, PH_BOUNDARY);
+             p->outer_iters, PH_BOUNDARY, c->channels);
   return cuda_check(c, cudaGetLastError(), "setup launch");
 }
 
@@ -634,6 +655,8 @@ extern "C" firls_status firls_set_operator(firls_ctx* c, const uint8_t* mask, un
       return fail(c, FIRLS_E_SHAPE, "n must be divisible by 2^levels, levels >= 1");
   }
   if (group_idx && !kind) return fail(c, FIRLS_E_INVALID_ARG, "groups need a wavelet");
+  if (c->channels > 1 && (group_idx || (psi_kind & FIRLS_PSI_TV_ANISO)))
+    return fail(c, FIRLS_E_INVALID_ARG, "multi-contrast images take singleton joint groups and isotropic joint TV");
   if (group_idx && (n_groups < 1 || (!group_off && group_size < 1)))
     return fail(c, FIRLS_E_INVALID_ARG, "bad group counts");
   const int B = c->batch;
@@ -1035,9 +1058,9 @@ firls_status objective_parts(firls_ctx* c, const void* b, const firls_params* p,
     WavArgs w = wav_args(c, nullptr);
     wavelet_forward(w, x, c->cw, nullptr, WAV_RAW);
     l21_sum(B, n, c->stream, c->cw, c->groups ? c->gidx : nullptr, c->goff, c->n_groups, c->gsize, eps, c->part,
-            SLOT_RZ);
+            SLOT_RZ, c->channels);
   }
-  if (has_tv(c)) tv_sum(B, n, c->stream, x, eps, c->part, SLOT_RR, is_aniso(c) ? 1 : 0);
+  if (has_tv(c)) tv_sum(B, n, c->stream, x, eps, c->part, SLOT_RR, is_aniso(c) ? 1 : 0, c->channels);
   return cuda_check(c, cudaGetLastError(), "objective");
 }
 
@@ -1060,6 +1083,14 @@ firls_status objective_read(firls_ctx* c, const firls_params* p, double* out) {
     if (has_tv(c)) f += lt * sum(SLOT_RR, nr);
     out[s] = f;
   }
+  // multi-contrast: F_eps of the whole image (the joint regularisers sit in
+  // its first slice's parts), the same value for each of its contrasts
+  const int C = c->channels;
+  for (int s0 = 0; C > 1 && s0 < B; s0 += C) {
+    double f = 0.0;
+    for (int t = 0; t < C; ++t) f += out[s0 + t];
+    for (int t = 0; t < C; ++t) out[s0 + t] = f;
+  }
   return FIRLS_OK;
 }
 
@@ -1073,6 +1104,7 @@ extern "C" firls_status firls_slot_load(firls_ctx* c, int s, const uint8_t* mask
   if (!c || !mask || !b) return FIRLS_E_INVALID_ARG;
   if (!c->op_set) return fail(c, FIRLS_E_STATE, "operator not set");
   if (s < 0 || s >= c->batch) return fail(c, FIRLS_E_INVALID_ARG, "slot out of range");
+  if (c->channels > 1) return fail(c, FIRLS_E_STATE, "slots hold single-contrast slices (channels is > 1)");
   if (!(lambda >= 0.f) || !(lambda_tv >= 0.f) || !std::isfinite(lambda) || !std::isfinite(lambda_tv))
     return fail(c, FIRLS_E_INVALID_ARG, "lambdas must be finite and >= 0");
   const int n = c->n;
@@ -1285,6 +1317,20 @@ extern "C" firls_status firls_set_tuning(firls_ctx* c, int rows_per_cta, int coa
     c->tune_ilu = ilu_shape;
     multi_forget(c);
     graphs_clear(c);  // the captured macro steps change shape
+  }
+  return FIRLS_OK;
+}
+
+extern "C" firls_status firls_set_channels(firls_ctx* c, int channels) {
+  if (!c) return FIRLS_E_INVALID_ARG;
+  if (channels < 1 || c->batch % channels)
+    return fail(c, FIRLS_E_INVALID_ARG, "channels must be >= 1 and divide the batch");
+  if (channels > 1 && c->op_set && (c->groups || (c->psi & FIRLS_PSI_TV_ANISO)))
+    return fail(c, FIRLS_E_INVALID_ARG, "multi-contrast images take singleton joint groups and isotropic joint TV");
+  if (channels != c->channels) {
+    c->channels = channels;
+    multi_forget(c);
+    graphs_clear(c);  // the captured macro steps change
   }
   return FIRLS_OK;
 }

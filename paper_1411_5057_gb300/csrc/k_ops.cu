@@ -1013,15 +1013,31 @@ int wavelet_apply_launches(int n, int levels, int kind, int rb, int cmax) {
 
 // Isotropic TV (wtv2 null): W_i = (|grad_1 x_i|^2 + |grad_2 x_i|^2 + eps)^(-1/2)
 // (Eq. wi).  l1 TV (Eq. l1): W1_i = (|grad_1 x_i|^2 + eps)^(-1/2) into wtv and
-// W2_i = (|grad_2 x_i|^2 + eps)^(-1/2) into wtv2.  Zero extension.
-__global__ void k_tv_weights(int n, const SliceState* __restrict__ st, const float2* __restrict__ x,
+// W2_i = (|grad_2 x_i|^2 + eps)^(-1/2) into wtv2.  Zero extension.  Joint TV
+// (Sec. 5.6, C > 1 contrasts in consecutive slices, isotropic only): the
+// squared gradients of all contrasts of the image are summed under the root,
+// and every contrast gets the same W.
+__global__ void k_tv_weights(int n, int C, const SliceState* __restrict__ st, const float2* __restrict__ x,
                              float* __restrict__ wtv, float* __restrict__ wtv2) {
   const int s = blockIdx.y;
   if (!slice_running(st, s)) return;
   const float eps = st[s].eps;
   const size_t base = (size_t)s * n * n;
+  const size_t img = (size_t)(s - s % C) * n * n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * n; i += gridDim.x * blockDim.x) {
     const int r = i / n, c = i % n;
+    if (C > 1) {
+      float g = 0.f;
+      for (int t = 0; t < C; ++t) {
+        const size_t bt = img + (size_t)t * n * n;
+        const float2 xc = x[bt + i];
+        const float2 g1 = c > 0 ? csub(xc, x[bt + i - 1]) : xc;
+        const float2 g2 = r > 0 ? csub(xc, x[bt + i - n]) : xc;
+        g += cabs2(g1) + cabs2(g2);
+      }
+      wtv[base + i] = rsqrtf(g + eps);
+      continue;
+    }
     const float2 xc = x[base + i];
     const float2 g1 = c > 0 ? csub(xc, x[base + i - 1]) : xc;
     const float2 g2 = r > 0 ? csub(xc, x[base + i - n]) : xc;
@@ -1034,10 +1050,35 @@ __global__ void k_tv_weights(int n, const SliceState* __restrict__ st, const flo
   }
 }
 
-void tv_weights(int batch, int n, cudaStream_t s, const SliceState* st, const float2* x, float* wtv, float* wtv2) {
+void tv_weights(int batch, int n, cudaStream_t s, const SliceState* st, const float2* x, float* wtv, float* wtv2,
+                int channels) {
   const int N = n * n;
   const int blocks = (N + 255) / 256 < 64 ? (N + 255) / 256 : 64;
-  k_tv_weights<<<dim3(blocks, batch), 256, 0, s>>>(n, st, x, wtv, wtv2);
+  k_tv_weights<<<dim3(blocks, batch), 256, 0, s>>>(n, channels, st, x, wtv, wtv2);
+}
+
+// Joint wavelet sparsity (Sec. 5.6, FIRLS_MT): coefficient j of the C
+// contrasts of an image forms one non-overlapping group, W_j = (sum_t
+// |(Phi x_t)_j|^2 + eps)^(-1/2) (Eq. gw), written to every contrast.  cw holds
+// the raw coefficients of all slices.
+__global__ void k_joint_wavelet_weights(int N, int C, const SliceState* __restrict__ st,
+                                        const float2* __restrict__ cw, float* __restrict__ ww) {
+  const int s = blockIdx.y;
+  if (!slice_running(st, s)) return;
+  const float eps = st[s].eps;
+  const size_t img = (size_t)(s - s % C) * N;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+    float g = 0.f;
+    for (int t = 0; t < C; ++t) g += cabs2(cw[img + (size_t)t * N + j]);
+    ww[(size_t)s * N + j] = rsqrtf(g + eps);
+  }
+}
+
+void joint_wavelet_weights(int batch, int n, int channels, cudaStream_t s, const SliceState* st, const float2* cw,
+                           float* ww) {
+  const int N = n * n;
+  const int blocks = (N + 255) / 256 < 64 ? (N + 255) / 256 : 64;
+  k_joint_wavelet_weights<<<dim3(blocks, batch), 256, 0, s>>>(N, channels, st, cw, ww);
 }
 
 // Exact diag(Phi^T diag(w) Phi).  Each 2-D basis function of level l is an
@@ -2154,19 +2195,27 @@ void mask_popcount(int batch, int n, cudaStream_t s, const uint8_t* mask, int* c
 
 // ======================================================== objective sums ===
 
-__global__ void k_l21_sum(int n, const float2* __restrict__ c, const int* __restrict__ gidx,
+// C > 1 (joint sparsity, no group map): the first slice of each image sums
+// sqrt(sum_t |c_tj|^2 + eps) over its C contrasts, the others contribute 0.
+__global__ void k_l21_sum(int n, int C, const float2* __restrict__ c, const int* __restrict__ gidx,
                           const int* __restrict__ goff, int G, int gsize, float eps, double* __restrict__ part,
                           int slot) {
   const int s = blockIdx.y;
   __shared__ double red[32];
-  const float2* cs = c + (size_t)s * n * n;
+  const size_t N = (size_t)n * n;
+  const float2* cs = c + (size_t)s * N;
   const int count = gidx ? G : n * n;
   const int chunk = (count + gridDim.x - 1) / gridDim.x;
   const int lo = blockIdx.x * chunk, hi = min(count, lo + chunk);
+  const int cc = s % C == 0 ? C : 0;
   float acc = 0.f;
   for (int g = lo + threadIdx.x; g < hi; g += blockDim.x) {
     float ss;
-    if (!gidx) {
+    if (C > 1) {
+      if (!cc) break;
+      ss = 0.f;
+      for (int t = 0; t < cc; ++t) ss += cabs2(cs[(size_t)t * N + g]);
+    } else if (!gidx) {
       ss = cabs2(cs[g]);
     } else {
       const int b = goff ? goff[g] : g * gsize;
@@ -2181,11 +2230,13 @@ __global__ void k_l21_sum(int n, const float2* __restrict__ c, const int* __rest
 }
 
 void l21_sum(int batch, int n, cudaStream_t s, const float2* c, const int* gidx, const int* goff, int G, int gsize,
-             float eps, double* part, int slot) {
-  k_l21_sum<<<dim3(axpy_ctas(n), batch), 256, 0, s>>>(n, c, gidx, goff, G, gsize, eps, part, slot);
+             float eps, double* part, int slot, int channels) {
+  k_l21_sum<<<dim3(axpy_ctas(n), batch), 256, 0, s>>>(n, channels, c, gidx, goff, G, gsize, eps, part, slot);
 }
 
-__global__ void k_tv_sum(int n, const float2* __restrict__ x, float eps, double* __restrict__ part, int slot,
+// C > 1 (joint TV): the first slice of each image sums sqrt(sum_t |grad
+// x_t,i|^2 + eps) over its C contrasts, the others contribute 0.
+__global__ void k_tv_sum(int n, int C, const float2* __restrict__ x, float eps, double* __restrict__ part, int slot,
                          int aniso) {
   const int s = blockIdx.y;
   __shared__ double red[32];
@@ -2193,20 +2244,28 @@ __global__ void k_tv_sum(int n, const float2* __restrict__ x, float eps, double*
   const int N = n * n;
   const int chunk = (N + gridDim.x - 1) / gridDim.x;
   const int lo = blockIdx.x * chunk, hi = min(N, lo + chunk);
+  const int cc = (C == 1 || s % C == 0) ? C : 0;
   float acc = 0.f;
-  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const int r = i / n, cc = i % n;
-    const float2 xc = x[base + i];
-    const float2 g1 = cc > 0 ? csub(xc, x[base + i - 1]) : xc;
-    const float2 g2 = r > 0 ? csub(xc, x[base + i - n]) : xc;
-    acc += aniso ? sqrtf(cabs2(g1) + eps) + sqrtf(cabs2(g2) + eps) : sqrtf(cabs2(g1) + cabs2(g2) + eps);
+  for (int i = lo + threadIdx.x; i < hi && cc; i += blockDim.x) {
+    const int r = i / n, col = i % n;
+    float g = 0.f, ga = 0.f;
+    for (int t = 0; t < cc; ++t) {
+      const size_t bt = base + (size_t)t * N;
+      const float2 xc = x[bt + i];
+      const float2 g1 = col > 0 ? csub(xc, x[bt + i - 1]) : xc;
+      const float2 g2 = r > 0 ? csub(xc, x[bt + i - n]) : xc;
+      g += cabs2(g1) + cabs2(g2);
+      if (aniso) ga = sqrtf(cabs2(g1) + eps) + sqrtf(cabs2(g2) + eps);
+    }
+    acc += aniso ? ga : sqrtf(g + eps);
   }
   const double tot = block_sum((double)acc, red);
   if (threadIdx.x == 0) part[((size_t)s * NSLOT + slot) * MAXPART + blockIdx.x] = tot;
 }
 
-void tv_sum(int batch, int n, cudaStream_t s, const float2* x, float eps, double* part, int slot, int aniso) {
-  k_tv_sum<<<dim3(axpy_ctas(n), batch), 256, 0, s>>>(n, x, eps, part, slot, aniso);
+void tv_sum(int batch, int n, cudaStream_t s, const float2* x, float eps, double* part, int slot, int aniso,
+            int channels) {
+  k_tv_sum<<<dim3(axpy_ctas(n), batch), 256, 0, s>>>(n, channels, x, eps, part, slot, aniso);
 }
 
 // ========================================================== PCG scalars ===
@@ -2218,15 +2277,28 @@ FI double sum_parts(const double* part, int s, int slot, int np) {
   return a;
 }
 
+// The sum over the C contrasts (consecutive slices) of the image that slice s
+// belongs to: multi-contrast PCG runs on the stacked unknown (Sec. 5.6), so
+// its inner products, and the relative change of the outer step, are sums
+// over the contrasts.  Every slice of the image sums in the same order and
+// takes the same scalars and the same phase transitions.
+FI double image_parts(const double* part, int s, int slot, int np, int C) {
+  if (C == 1) return sum_parts(part, s, slot, np);
+  const int s0 = s - s % C;
+  double a = 0.0;
+  for (int t = s0; t < s0 + C; ++t) a += sum_parts(part, t, slot, np);
+  return a;
+}
+
 __global__ void k_state_init(int B, SliceState* st, const double* part, int np, const int* counts, int N,
-                             const float* lam, const float* lam_tv, float eps, int outer_max, int phase) {
+                             const float* lam, const float* lam_tv, float eps, int outer_max, int phase, int C) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B) return;
   SliceState v;
   v.rho = 0.0;
   v.alpha = 0.0;
   v.beta = 0.0;
-  v.rhs2 = sum_parts(part, s, SLOT_RHS, np);
+  v.rhs2 = image_parts(part, s, SLOT_RHS, np, C);
   v.rr = v.rhs2;
   v.rr0 = v.rhs2;
   v.relchg = 0.0;
@@ -2252,9 +2324,9 @@ __global__ void k_state_init(int B, SliceState* st, const double* part, int np, 
 }
 
 void state_init(int batch, cudaStream_t s, SliceState* st, const double* part, int np, const int* counts,
-                int n, const float* lam, const float* lam_tv, float eps, int outer_max, int phase) {
+                int n, const float* lam, const float* lam_tv, float eps, int outer_max, int phase, int channels) {
   k_state_init<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np, counts, n * n, lam, lam_tv, eps,
-                                                   outer_max, phase);
+                                                   outer_max, phase, channels);
 }
 
 // The slices whose outer step is due (PH_BOUNDARY), as a copy of the state in
@@ -2279,27 +2351,27 @@ void boundary_view(int batch, cudaStream_t s, SliceState* st, SliceState* view) 
   k_boundary_view<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, view);
 }
 
-__global__ void k_alpha(int B, SliceState* st, const double* part, int np) {
+__global__ void k_alpha(int B, SliceState* st, const double* part, int np, int C) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B || !slice_in_pcg(st, s)) return;
-  pcg_alpha_from(st + s, sum_parts(part, s, SLOT_DQ, np));
+  pcg_alpha_from(st + s, image_parts(part, s, SLOT_DQ, np, C));
 }
 
-void pcg_alpha(int batch, cudaStream_t s, SliceState* st, const double* part, int np) {
-  k_alpha<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np);
+void pcg_alpha(int batch, cudaStream_t s, SliceState* st, const double* part, int np, int channels) {
+  k_alpha<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np, channels);
 }
 
 // After z = P^{-1} r: rho (first residual, slices at the start of an outer
 // step) or beta and the PCG stop (slices in PCG); mode INIT / STEP forces one
 // of them for every running slice.
 __global__ void k_pcg_scalars(int B, SliceState* st, const double* part, int np_rz, int np_rr, int mode,
-                              PcgSched ps) {
+                              PcgSched ps, int C) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= B || !slice_running(st, s)) return;
+  if (s >= B || !slice_running(st, s) || st[s].fault) return;
   const int ph = st[s].phase;
   const bool init = mode == SCALARS_INIT || (mode == SCALARS_PER_SLICE && ph == PH_START);
   const bool step = mode == SCALARS_STEP || (mode == SCALARS_PER_SLICE && ph == PH_PCG);
-  const double rz = sum_parts(part, s, SLOT_RZ, np_rz), rr = sum_parts(part, s, SLOT_RR, np_rr);
+  const double rz = image_parts(part, s, SLOT_RZ, np_rz, C), rr = image_parts(part, s, SLOT_RR, np_rr, C);
   if (init)
     pcg_rho_init_from(st + s, rz, rr);
   else if (step)
@@ -2307,8 +2379,8 @@ __global__ void k_pcg_scalars(int B, SliceState* st, const double* part, int np_
 }
 
 void pcg_scalars(int batch, cudaStream_t s, SliceState* st, const double* part, int np_rz, int np_rr, int mode,
-                 const PcgSched& ps) {
-  k_pcg_scalars<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np_rz, np_rr, mode, ps);
+                 const PcgSched& ps, int channels) {
+  k_pcg_scalars<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np_rz, np_rr, mode, ps, channels);
 }
 
 // Outer-loop stop.  kind 0: relative change <= tol.  kind 1: estimated
@@ -2326,12 +2398,12 @@ void pcg_scalars(int batch, cudaStream_t s, SliceState* st, const double* part, 
 // change at or below tol that has not fallen by 20 % over the window is that
 // slice's FP32 floor, whatever its level.
 __global__ void k_outer_end(int B, SliceState* st, const double* part, int np, float tol, int kind,
-                            float stall_tol, int plateau_after) {
+                            float stall_tol, int plateau_after, int C) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B || !slice_running(st, s) || st[s].phase != PH_END) return;
   SliceState* v = st + s;
-  const double dx = sum_parts(part, s, SLOT_DX, np);
-  const double xx = sum_parts(part, s, SLOT_XX, np);
+  const double dx = image_parts(part, s, SLOT_DX, np, C);
+  const double xx = image_parts(part, s, SLOT_XX, np, C);
   const double rel = xx > 0.0 ? sqrt(dx / xx) : INFINITY;
   const int k = v->outer_done;  // this step's index
   const float old = v->hist[k % MU_WINDOW];  // relchg of step k - MU_WINDOW
@@ -2357,8 +2429,9 @@ __global__ void k_outer_end(int B, SliceState* st, const double* part, int np, f
 }
 
 void outer_end(int batch, cudaStream_t s, SliceState* st, const double* part, int np, float tol, int kind,
-               float stall_tol, int plateau_after) {
-  k_outer_end<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np, tol, kind, stall_tol, plateau_after);
+               float stall_tol, int plateau_after, int channels) {
+  k_outer_end<<<(batch + 127) / 128, 128, 0, s>>>(batch, st, part, np, tol, kind, stall_tol, plateau_after,
+                                                  channels);
 }
 
 }  // namespace firls

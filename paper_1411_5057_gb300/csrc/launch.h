@@ -77,8 +77,15 @@ int wavelet_apply_launches(int n, int levels, int kind, int rb, int coarse_max);
 void wav_prepare();
 
 // ---- TV, preconditioner, groups, PCG scalars ----
-// wtv2 null: isotropic TV weights into wtv; else l1 TV: W1 into wtv, W2 into wtv2
-void tv_weights(int batch, int n, cudaStream_t s, const SliceState* st, const float2* x, float* wtv, float* wtv2);
+// wtv2 null: isotropic TV weights into wtv; else l1 TV: W1 into wtv, W2 into wtv2.
+// channels C > 1: joint TV weights of each image of C consecutive slices
+// (isotropic only), the same W into every contrast.
+void tv_weights(int batch, int n, cudaStream_t s, const SliceState* st, const float2* x, float* wtv, float* wtv2,
+                int channels = 1);
+// Joint wavelet-sparsity weights from the raw coefficients cw of every slice:
+// ww = (sum over the C contrasts of |c_j|^2 + eps)^(-1/2) for every contrast.
+void joint_wavelet_weights(int batch, int n, int channels, cudaStream_t s, const SliceState* st, const float2* cw,
+                           float* ww);
 void wavelet_diag(int batch, int n, int levels, cudaStream_t s, const SliceState* st, const float* w,
                   float* out, const float* sqtab, const int* sqlen);
 void penta_setup(int batch, int n, cudaStream_t s, const SliceState* st, const float* wtv, const float* wtv2,
@@ -129,16 +136,21 @@ void mask_popcount(int batch, int n, cudaStream_t s, const uint8_t* mask, int* c
 
 // Partial sums of the regularisers of F_eps (one slot each, axpy_ctas parts):
 // sum_j sqrt(|c_j|^2 + eps) (singleton groups) or sum_g sqrt(||c_g||^2 + eps),
-// and sum_i sqrt(|D1 x|_i^2 + |D2 x|_i^2 + eps).
+// and sum_i sqrt(|D1 x|_i^2 + |D2 x|_i^2 + eps).  channels C > 1: the joint
+// sums of each image in its first slice (the other slices' parts are 0).
 void l21_sum(int batch, int n, cudaStream_t s, const float2* c, const int* gidx, const int* goff, int n_groups,
-             int gsize, float eps, double* part, int slot);
-void tv_sum(int batch, int n, cudaStream_t s, const float2* x, float eps, double* part, int slot, int aniso);
+             int gsize, float eps, double* part, int slot, int channels = 1);
+void tv_sum(int batch, int n, cudaStream_t s, const float2* x, float eps, double* part, int slot, int aniso,
+            int channels = 1);
 
-// PCG scalar updates (one thread per slice)
-void pcg_alpha(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts);
+// PCG scalar updates (one thread per slice).  channels C > 1: the inner
+// products are summed over the C consecutive slices of a multi-contrast
+// image, whose slices then carry the same scalars (here, in outer_end and in
+// state_init's ||A^H b||^2).
+void pcg_alpha(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts, int channels = 1);
 enum ScalarsMode { SCALARS_INIT = 0, SCALARS_STEP = 1, SCALARS_PER_SLICE = -1 };
 void pcg_scalars(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts_rz, int nparts_rr,
-                 int mode, const PcgSched& ps);
+                 int mode, const PcgSched& ps, int channels = 1);
 // view = st with every slice not at the start of its outer step marked done
 // (and the slices whose outer step is due move to PH_START)
 void boundary_view(int batch, cudaStream_t s, SliceState* st, SliceState* view);
@@ -148,11 +160,11 @@ void outer_apply(int batch, int n, cudaStream_t s, const SliceState* st, float2*
                  double* part);
 // plateau_after: first outer step at which kind 1 also stops on a plateau
 void outer_end(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts,
-               float outer_tol, int tol_kind, float stall_tol, int plateau_after);
+               float outer_tol, int tol_kind, float stall_tol, int plateau_after, int channels = 1);
 // phase: PH_BOUNDARY for a solve (its first outer step is due), PH_START for
 // the single operator applications (no outer step)
 void state_init(int batch, cudaStream_t s, SliceState* st, const double* part, int nparts_rhs,
                 const int* counts, int n, const float* lam, const float* lam_tv, float eps, int outer_max,
-                int phase);
+                int phase, int channels = 1);
 
 }  // namespace firls
