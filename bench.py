@@ -318,6 +318,13 @@ def run_ours(args):
         print(f"[bench] uneven batch: {c4['value']} recons/s ({c4['s_per_batch']} s per 64 slices), "
               f"accuracy {json.dumps(c4['accuracy'])}", file=sys.stderr, flush=True)
 
+    # ---- multi-contrast cross sections (joint sparsity), untimed w.r.t. the main line ----
+    mt = multi_contrast_run(F, torch, args) if args.mt_sets > 0 else None
+    if mt is not None:
+        print(f"[bench] multi-contrast: {mt['value']} cross sections/s ({mt['s_per_batch']} s per "
+              f"{args.mt_sets}), accuracy {json.dumps(mt['accuracy_vs_oracle_same_schedule'])}, "
+              f"SNR {mt['snr_db_mean']} dB", file=sys.stderr, flush=True)
+
     # ---- learned warm start (CNN trained on solver-generated pairs) ----
     learned = None
     if args.learned:
@@ -339,7 +346,8 @@ def run_ours(args):
                                "capped": int((steps >= args.outer).sum()),
                                "mean_pcg_steps": round(float(np.mean(pcg_counts)), 1),
                                "max_pcg_steps": int(np.max(pcg_counts))},
-               "accuracy": acc, "learned": learned, "pcg_iterations": pcg_iters, "uneven_batch": c4}
+               "accuracy": acc, "learned": learned, "pcg_iterations": pcg_iters, "uneven_batch": c4,
+               "multi_contrast": mt}
         print(json.dumps(out), flush=True)
     ctx.close()
     if dist is not None:
@@ -445,6 +453,7 @@ def accuracy(xs, first_seed, steps=None):
 
 
 XSTAR_UNEVEN_DIR = os.path.join(ROOT, "tests", "golden", "xstar_uneven")
+XMT_DIR = os.path.join(ROOT, "tests", "golden", "xmt_db4_256")
 
 
 def uneven_batch_run(F, torch, args, reps=2):
@@ -500,6 +509,58 @@ def uneven_batch_run(F, torch, args, reps=2):
             "max_outer_steps_per_size": dict(zip([str(n) for n in sizes], outer)),
             "accuracy": {"n_checked": len(errs), "max_rel_err": max(errs.values()) if errs else None,
                          "rel_err_by_seed": errs}}
+
+
+MT_OUTER, MT_INNER = 100, 20
+
+
+def multi_contrast_run(F, torch, args, reps=2):
+    """Multi-contrast reconstruction with joint wavelet sparsity (FIRLS_MT,
+    Sec. 5.6): `args.mt_sets` cross sections of 3 contrasts at 256^2 (25 %
+    masks, one per contrast, joint 4-level D4, lambda 1e-3, seeds 1..), all
+    in one context with channels = 3, for the paper's budget of 100
+    iterations (20 PCG steps each).  Cross sections per second with
+    device-resident inputs; error against the FP64 oracle's result of the same
+    schedule for the seeds stored, and the SNR against the phantoms.  Untimed
+    set-up; `reps` timed solves after one warm-up."""
+    import firls_synth as fs
+    sets = args.mt_sets
+    probs = [p for seed in range(1, sets + 1) for p in fs.mt_db4_256(seed)]
+    p0 = probs[0]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = F.Context(p0.n, batch=len(probs), stream=stream)
+        ctx.set_channels(3)
+        ctx.set_operator(torch.from_numpy(np.stack([p.mask for p in probs])).cuda(), p0.psi, p0.levels)
+        b = torch.from_numpy(np.stack([p.b for p in probs]).astype(np.complex64)).cuda()
+        out = torch.empty_like(b)
+        prm = F.make_params(MT_OUTER, MT_INNER, lam=p0.lam)
+        ctx.solve(b, prm, out=out)
+    stream.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            ctx.solve(b, prm, out=out)
+    stream.synchronize()
+    sec = (time.perf_counter() - t0) / reps
+    x = out.cpu().numpy().astype(np.complex128)
+    snr = [20 * np.log10(np.linalg.norm(p.x0) / np.linalg.norm(x[i] - p.x0)) for i, p in enumerate(probs)]
+    errs = {}
+    for seed in range(1, sets + 1):
+        f = os.path.join(XMT_DIR, f"seed{seed}.npz")
+        if os.path.exists(f):
+            ref = np.load(f)["x"].astype(np.complex128)
+            got = x[3 * (seed - 1):3 * seed]
+            errs[seed] = max(float(np.linalg.norm(got[t] - ref[t]) / np.linalg.norm(ref[t])) for t in range(3))
+    ctx.close()
+    return {"value": round(sets / sec, 3), "unit": "cross sections/s (3 contrasts each)",
+            "images_per_s": round(3 * sets / sec, 3), "s_per_batch": round(sec, 4),
+            "workload": f"{sets} cross sections x 3 contrasts, 256^2, 25% masks, joint 4-level D4, lambda 1e-3",
+            "method": "one context, channels = 3: joint weights, PCG on the stacked contrasts",
+            "schedule": f"{MT_OUTER} outer x {MT_INNER} PCG (the paper's 100-iteration budget)",
+            "accuracy_vs_oracle_same_schedule": {"n_checked": len(errs),
+                                                 "max_rel_err": max(errs.values()) if errs else None},
+            "snr_db_mean": round(float(np.mean(snr)), 2), "paper_s_per_cross_section": 4.6}
 
 
 def precond_comparison(F, torch, stream, outer_steps=(1, 5, 20), tol=1e-6, cap=5000):
@@ -701,6 +762,8 @@ def main(argv=None):
                     help="reference arm: oracle instances run at once, one per host core (0: all cores)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--uneven", type=int, default=1, help="also time the 64-slice uneven batch (1/0)")
+    ap.add_argument("--mt-sets", type=int, default=100,
+                    help="multi-contrast cross sections timed beside the main line (0: none)")
     ap.add_argument("--precond-cmp", type=int, default=1,
                     help="report PCG steps to 1e-6 for the proposed, Jacobi and no preconditioner (1/0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -268,6 +268,13 @@ def uneven_batch(first_seed: int = 1000, per_size: int = 16) -> list[Problem]:
     return out
 
 
+def mt_db4_256(seed: int = 1, n: int = 256) -> list[Problem]:
+    """Multi-contrast cross section (joint sparsity, FIRLS_MT): 3 contrasts at
+    256x256, 25 % variable-density masks (one per contrast), sigma 0.01, joint
+    4-level Daubechies-4 sparsity, lambda 1e-3."""
+    return multi_contrast(n, 3, 0.25, 0.01, seed, psi=PSI_DB4, levels=4, lam=1e-3)
+
+
 # --- learned warm start: architecture and seeded initial weights ------------
 
 CNN_CHANNELS = (3, 32, 32, 32, 32, 32, 2)   # input: Re A^H b, Im A^H b, mask

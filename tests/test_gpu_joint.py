@@ -184,3 +184,22 @@ def test_channel_errors(F):
     x = ctx.solve(b, F.make_params(2, 2, lam=1e-3, lam_tv=1e-3))
     assert torch.isfinite(torch.view_as_real(x)).all()
     ctx.close()
+
+
+def test_mt_workload_matches_stored_oracle(F):
+    """The multi-contrast workload (3 contrasts at 256^2, joint D4) for the
+    paper's 100-iteration budget: each contrast against the FP64 oracle's
+    result of the same schedule (tests/golden/make_xmt.py)."""
+    import os
+    d = os.path.join(os.path.dirname(__file__), "golden", "xmt_db4_256")
+    seeds = [s for s in (1, 2) if os.path.exists(os.path.join(d, f"seed{s}.npz"))]
+    assert seeds, "no stored multi-contrast result"
+    probs = [p for s in seeds for p in fs.mt_db4_256(s)]
+    z0 = np.load(os.path.join(d, f"seed{seeds[0]}.npz"))
+    ctx, b = _ctx(F, probs, 3)
+    x = host(ctx.solve(b, F.make_params(int(z0["outer"]), int(z0["inner"]), lam=probs[0].lam)))
+    for i, s in enumerate(seeds):
+        ref = np.load(os.path.join(d, f"seed{s}.npz"))["x"].astype(np.complex128)
+        for t in range(3):
+            assert rel(x[3 * i + t], ref[t]) < TOL_SOLVE, (s, t, rel(x[3 * i + t], ref[t]))
+    ctx.close()
