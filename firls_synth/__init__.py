@@ -275,6 +275,37 @@ def mt_db4_256(seed: int = 1, n: int = 256) -> list[Problem]:
     return multi_contrast(n, 3, 0.25, 0.01, seed, psi=PSI_DB4, levels=4, lam=1e-3)
 
 
+# --- dense random projections (Sec. 5.2-5.3) ---------------------------------
+
+DENSE = 6
+
+
+@dataclass
+class DenseProblem:
+    """One sparse-recovery problem with a dense sensing matrix (inputs only)."""
+    A: np.ndarray               # float64 [M][N]
+    b: np.ndarray               # float64 [M]
+    x0: np.ndarray              # float64 [N], the sparse ground truth
+    lam: float
+    seed: int = 0
+
+
+def dense_l1(seed: int, N: int = 4000, M: int = 800, density: float = 0.1, sigma: float = 0.01,
+             lam: float = 0.05) -> DenseProblem:
+    """The 1-D random-projection workload of Sec. 5.3 (length 4000, 10 %
+    non-zeros, 800 measurements): A with i.i.d. N(0, 1/M) entries (substream
+    DENSE, row-major draws), round(density N) non-zeros at uniformly random
+    positions with N(0, 1) values (substream PHANTOM), b = A x0 + sigma e with
+    e ~ N(0, I) (substream NOISE)."""
+    A = _rng(seed, DENSE).standard_normal((M, N)) / math.sqrt(M)
+    g = _rng(seed, PHANTOM)
+    k = int(round(density * N))
+    x0 = np.zeros(N)
+    x0[g.choice(N, size=k, replace=False)] = g.standard_normal(k)
+    b = A @ x0 + sigma * _rng(seed, NOISE).standard_normal(M)
+    return DenseProblem(A=A, b=b, x0=x0, lam=lam, seed=seed)
+
+
 # --- learned warm start: architecture and seeded initial weights ------------
 
 CNN_CHANNELS = (3, 32, 32, 32, 32, 32, 2)   # input: Re A^H b, Im A^H b, mask
