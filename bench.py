@@ -216,6 +216,12 @@ def run_ours(args):
                            chunk=SERVE_CHUNK, pcg_steps=pcg_counts,
                            stop_after=S - B if args.steady else None, counters=counters)
 
+    def serve_queue(ml, bl, xl, pcg, x0s=None):
+        """Another queue through the same slots and schedule (drained)."""
+        with torch.cuda.stream(stream):
+            return F.serve(ctx, ml, bl, [LAM_W] * len(ml), [LAM_TV] * len(ml), params, xl, x0s=x0s,
+                           max_outer=args.outer, chunk=SERVE_CHUNK, pcg_steps=pcg)
+
     # ---- device-resident throughput: continuous batching over S slices ----
     for _ in range(args.warmup):
         steps = step()
@@ -272,15 +278,10 @@ def run_ours(args):
     for k in ALG_BYTES_PER_PX:  # op-apply bandwidth of every operator class, on algorithmic bytes
         if kt[k][0] > 0 and k in apps:
             kern[k]["alg_gbs"] = round(ALG_BYTES_PER_PX[k] * N * N * B / (kt[k][0] / apps[k] / 1e3) / 1e9, 1)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak, peak_source = hbm_peak()
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "peak_source": peak_source,
                 "alg_bytes_per_launch": alg, "launches_per_application": kt[dom][1] / apps[dom]}
 
     # ---- end to end through the public API with host buffers ----
@@ -325,10 +326,21 @@ def run_ours(args):
               f"{args.mt_sets}), accuracy {json.dumps(mt['accuracy_vs_oracle_same_schedule'])}, "
               f"SNR {mt['snr_db_mean']} dB", file=sys.stderr, flush=True)
 
+    # ---- dense random projections (Sec. 5.3), untimed w.r.t. the main line ----
+    dense = dense_run(F, torch, args) if args.dense_problems > 0 else None
+    if dense is not None:
+        print(f"[bench] dense A: {dense['value']} problems/s ({dense['us_per_pcg_step']} us per PCG step), rows "
+              f"{dense['roofline_rows']['achieved']} GB/s ({dense['roofline_rows']['frac']} of peak), accuracy "
+              f"{json.dumps(dense['accuracy_vs_oracle_same_schedule'])}", file=sys.stderr, flush=True)
+
     # ---- learned warm start (CNN trained on solver-generated pairs) ----
     learned = None
     if args.learned:
-        learned = run_learned(args, F, torch, stream, b, masks, B, S, value, steps, step, rank, done_per_step, xlist)
+        learned = run_learned(args, F, torch, stream, B, rank, world, dist, serve_queue)
+        print(f"[bench] learned vs plain on {learned['heldout_slices']} held-out slices: "
+              f"{learned['value']} vs {learned['plain_value']} recons/s ({learned['vs_plain']}x), "
+              f"PCG steps {learned['mean_pcg_steps']} vs {learned['plain_mean_pcg_steps']}", file=sys.stderr,
+              flush=True)
 
     out = None
     if rank == 0:
@@ -347,7 +359,7 @@ def run_ours(args):
                                "mean_pcg_steps": round(float(np.mean(pcg_counts)), 1),
                                "max_pcg_steps": int(np.max(pcg_counts))},
                "accuracy": acc, "learned": learned, "pcg_iterations": pcg_iters, "uneven_batch": c4,
-               "multi_contrast": mt}
+               "multi_contrast": mt, "dense_l1": dense}
         print(json.dumps(out), flush=True)
     ctx.close()
     if dist is not None:
@@ -355,14 +367,27 @@ def run_ours(args):
     return out
 
 
-def run_learned(args, F, torch, stream, b, masks, B, S, plain_value, plain_steps, step, rank, done_per_step, xs):
-    """Train the CNN (untimed) on pairs the solver generates, then time the
-    guarded learned start (CNN, data consistency, F_eps guard) plus the same
-    continuous-batching solve over the same slices."""
+HELDOUT_FIRST = 20000
+
+
+def run_learned(args, F, torch, stream, B, rank, world, dist, serve_queue):
+    """The learned warm start against the plain start (A^H b) on held-out
+    slices: the CNN is trained (untimed) on pairs the solver generates (seeds
+    10000..), then both starts serve the same `args.heldout` held-out 256^2
+    TV + D4 slices (seeds 20000.., never trained on) through the same slots
+    and stop rule.  Per start: wall time (the learned one including the CNN,
+    data consistency and F_eps guard), PCG and outer steps per slice, and the
+    error of the slices that have a stored oracle x*."""
     from paper_1411_5057_gb300 import learned as Lr
     import firls_synth as fs
+    H = args.heldout
+    first = HELDOUT_FIRST + rank * H
+    masks_h, b_h = make_batch(H, first)
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
+        masks = torch.from_numpy(masks_h).cuda()
+        b = torch.from_numpy(b_h).cuda()
+        x = torch.empty_like(b)
         seeds = list(range(10000 + rank * args.learned_train, 10000 + (rank + 1) * args.learned_train))
         atb_t, masks_t, xt = Lr.generate_pairs(N, seeds, 50, args.inner)
         net = F.Cnn(N, 16, stream=stream)
@@ -378,40 +403,54 @@ def run_learned(args, F, torch, stream, b, masks, B, S, plain_value, plain_steps
         one = F.make_params(1, 1, lam=LAM_W, lam_tv=LAM_TV)
     stream.synchronize()
     train_s = time.perf_counter() - t0
+    ml, bl, xl = list(masks), list(b), list(x)
     kept = [0]
+    pcg_plain, pcg_learned = [0] * H, [0] * H
+
+    def plain_step():
+        return serve_queue(ml, bl, xl, pcg_plain)
 
     def learned_step():
         kept[0] = 0
         with torch.cuda.stream(stream):
-            for i in range(0, S, B):
+            for i in range(0, H, B):
                 prep.set_operator(masks[i:i + B], F.PSI_TV | F.PSI_DB4, LEVELS)
                 atb = prep.adjoint(b[i:i + B])
                 xs, chosen = Lr.warm_start(prep, inf, b[i:i + B], atb, masks[i:i + B], one)
                 x0[i:i + B].copy_(xs)
                 kept[0] += int(sum(chosen))
-        return step(x0s=list(x0))
+        return serve_queue(ml, bl, xl, pcg_learned, x0s=list(x0))
 
-    for _ in range(max(1, args.warmup)):
-        lsteps = learned_step()
-    stream.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        lsteps = learned_step()
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    def timed(fn):
+        fn()  # warm-up
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.learned_steps):
+            st = fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.learned_steps, dist, "cuda")
+        acc = accuracy(xl, first, st)
+        st = np.asarray(st)
+        return ms, st, acc
+
+    ms_p, st_p, acc_p = timed(plain_step)
+    ms_l, st_l, acc_l = timed(learned_step)
     inf.close()
     prep.close()
-    lacc = accuracy(xs, rank_first_seed(rank, S), lsteps)
-    lsteps = np.asarray(lsteps)
-    lsteps = lsteps[lsteps > 0]
-    value = done_per_step / (ms / 1e3)
-    return {"value": round(value, 3), "unit": UNIT, "ms_per_step": round(ms, 3),
-            "mean_outer_steps": round(float(lsteps.mean()), 2), "plain_mean_outer_steps": round(float(plain_steps.mean()), 2),
-            "max_outer_steps": int(lsteps.max()), "kept_cnn_start": kept[0], "vs_plain": round(value / plain_value, 4),
-            "train_instances": args.learned_train, "train_epochs": args.learned_epochs, "setup_s": round(train_s, 1),
-            "accuracy": lacc}
+    v_p, v_l = world * H / (ms_p / 1e3), world * H / (ms_l / 1e3)
+    return {"value": round(v_l, 3), "plain_value": round(v_p, 3), "unit": UNIT, "vs_plain": round(v_l / v_p, 4),
+            "heldout_slices": H, "heldout_seeds": f"{first}..{first + H - 1}",
+            "ms_per_step": round(ms_l, 3), "plain_ms_per_step": round(ms_p, 3),
+            "mean_pcg_steps": round(float(np.mean(pcg_learned)), 1),
+            "plain_mean_pcg_steps": round(float(np.mean(pcg_plain)), 1),
+            "pcg_ratio": round(float(np.mean(pcg_learned)) / float(np.mean(pcg_plain)), 4),
+            "max_pcg_steps": int(np.max(pcg_learned)), "plain_max_pcg_steps": int(np.max(pcg_plain)),
+            "mean_outer_steps": round(float(st_l.mean()), 2), "plain_mean_outer_steps": round(float(st_p.mean()), 2),
+            "max_outer_steps": int(st_l.max()), "plain_max_outer_steps": int(st_p.max()),
+            "kept_cnn_start": kept[0], "train_instances": args.learned_train, "train_epochs": args.learned_epochs,
+            "setup_s": round(train_s, 1), "accuracy": acc_l, "plain_accuracy": acc_p}
 
 
 XSTAR_DIR = os.path.join(ROOT, "tests", "golden", "xstar_tv_db4_256")
@@ -561,6 +600,97 @@ def multi_contrast_run(F, torch, args, reps=2):
             "accuracy_vs_oracle_same_schedule": {"n_checked": len(errs),
                                                  "max_rel_err": max(errs.values()) if errs else None},
             "snr_db_mean": round(float(np.mean(snr)), 2), "paper_s_per_cross_section": 4.6}
+
+
+def hbm_peak():
+    """The measured HBM copy bandwidth (GB/s) of the GB300s, else the fallback."""
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(peaks["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+DENSE_OUTER, DENSE_INNER = 200, 30
+XDENSE_DIR = os.path.join(ROOT, "tests", "golden", "xdense_l1")
+
+
+def dense_run(F, torch, args, reps=2):
+    """The dense random-projection workload (Sec. 5.3: signals of length
+    4000 with 10 % non-zeros, 800 Gaussian measurements each, FIRLS_L1 with
+    30 PCG steps per outer step for 200 outer steps): `args.dense_problems`
+    problems, each with its own A (seeds 1..), in one context.  Problems per
+    second with device-resident inputs; the HBM roofline of the row kernel
+    (one pass over A per S d, timed through firls_dense_apply_AtA with CUDA
+    events); the error against the FP64 oracle's stored result of the same
+    schedule (seeds 1-2) and the MSE against the sparse truth.  Untimed
+    set-up; `reps` timed solves after one warm-up."""
+    import firls_synth as fs
+    P = args.dense_problems
+    M, Nd = 800, 4000
+    A = np.empty((P, M, Nd), np.float32)
+    bh = np.empty((P, M), np.float32)
+    x0 = []
+    for i in range(P):
+        p = fs.dense_l1(i + 1)
+        A[i], bh[i] = p.A, p.b
+        x0.append(p.x0)
+    lam = p.lam
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = F.DenseContext(M, Nd, P, stream=stream)
+        At = torch.from_numpy(A).cuda()
+        ctx.set_matrix(At)
+        del At
+        b = torch.from_numpy(bh).cuda()
+        out = torch.empty(P, Nd, dtype=torch.float32, device="cuda")
+        prm = F.make_params(DENSE_OUTER, DENSE_INNER, lam=lam)
+        ctx.solve(b, prm, out=out)
+    del A
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            ctx.solve(b, prm, out=out)
+    e1.record(stream)
+    e1.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3 / reps
+    # the row kernel alone: q = A^T A d over all problems (A is 12.8 MB per problem)
+    with torch.cuda.stream(stream):
+        d = torch.randn(P, Nd, device="cuda")
+        q = torch.empty_like(d)
+        for _ in range(3):
+            ctx.apply_AtA(d, q)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(20):
+            ctx.apply_AtA(d, q)
+    e1.record(stream)
+    e1.synchronize()
+    t_apply = e0.elapsed_time(e1) / 1e3 / 20
+    abytes = P * M * Nd * 4
+    x = out.cpu().numpy().astype(np.float64)
+    errs = {}
+    for seed in (1, 2):
+        f = os.path.join(XDENSE_DIR, f"seed{seed}.npz")
+        if seed <= P and os.path.exists(f):
+            ref = np.load(f)["x"]
+            errs[seed] = float(np.linalg.norm(x[seed - 1] - ref) / np.linalg.norm(ref))
+    mse = float(np.mean([np.mean((x[i] - x0[i]) ** 2) for i in range(P)]))
+    ctx.close()
+    steps = DENSE_OUTER * (DENSE_INNER + 1)
+    return {"value": round(P / sec, 3), "unit": "problems/s", "s_per_batch": round(sec, 4),
+            "workload": f"{P} problems, A 800 x 4000 Gaussian (own A each), 10% non-zeros, lambda {lam}",
+            "schedule": f"{DENSE_OUTER} outer x {DENSE_INNER} PCG (the paper's 30 PCG steps, converged in 200)",
+            "us_per_pcg_step": round(sec / steps * 1e6, 1),
+            "roofline_rows": {"bound": "hbm", "kernel": "k_dense_rows (+ k_dense_reduce)",
+                              "achieved": round(abytes / t_apply / 1e9, 1), "peak": hbm_peak()[0], "unit": "GB/s",
+                              "frac": round(abytes / t_apply / 1e9 / hbm_peak()[0], 3),
+                              "algorithmic_bytes": abytes, "us_per_apply": round(t_apply * 1e6, 1)},
+            "accuracy_vs_oracle_same_schedule": {"n_checked": len(errs),
+                                                 "max_rel_err": max(errs.values()) if errs else None},
+            "mse_vs_truth_mean": round(mse, 4), "paper_mse": "0.0427-0.0481 (FIRLS_L1, Table 1)"}
 
 
 def precond_comparison(F, torch, stream, outer_steps=(1, 5, 20), tol=1e-6, cap=5000):
@@ -756,12 +886,16 @@ def main(argv=None):
     ap.add_argument("--learned", type=int, default=1, help="also time the learned warm start (1/0)")
     ap.add_argument("--learned-train", type=int, default=4000, help="training instances solved by the method")
     ap.add_argument("--learned-epochs", type=int, default=10)
+    ap.add_argument("--heldout", type=int, default=512, help="held-out slices of the learned comparison")
+    ap.add_argument("--learned-steps", type=int, default=2, help="timed passes per start over the held-out slices")
     ap.add_argument("--ref-outer", type=int, default=1, help="oracle outer steps per sample")
     ap.add_argument("--ref-inner", type=int, default=ORACLE_INNER, help="oracle PCG steps per outer step")
     ap.add_argument("--ref-procs", type=int, default=0,
                     help="reference arm: oracle instances run at once, one per host core (0: all cores)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--uneven", type=int, default=1, help="also time the 64-slice uneven batch (1/0)")
+    ap.add_argument("--dense-problems", type=int, default=152,
+                    help="dense random-projection problems timed beside the main line (0: none)")
     ap.add_argument("--mt-sets", type=int, default=100,
                     help="multi-contrast cross sections timed beside the main line (0: none)")
     ap.add_argument("--precond-cmp", type=int, default=1,

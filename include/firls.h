@@ -473,6 +473,52 @@ void firls_cnn_destroy(firls_cnn* net);
 firls_status firls_apply_AHA_noalloc(int n, int batch, const uint8_t* mask, const void* d, void* q,
                                      void* cuda_stream);
 
+/* ---- Dense sensing matrix (Sec. 5.2-5.3: random projections) -----------
+ *
+ * FIRLS_L1 with a dense real A in place of the partial Fourier operator:
+ *     min_x 1/2 ||A x - b||^2 + lambda ||x||_1,  A in R^{M x N}, x in R^N
+ * (Eq. anapro with Phi = I and singleton groups).  Alg. 2 with W =
+ * diag((x_i^2 + eps)^(-1/2)) (Eq. gw), S = A^T A + lambda W (Eq. subprob) and
+ * the proposed preconditioner P = abar I + lambda W, abar = tr(A^T A) / N, the
+ * mean diagonal entry of A^T A (Eq. ps, Eq. pog with Phi = I); Jacobi PCG
+ * uses P = diag(A^T A) + lambda W and plain CG P = I (Sec. 5.2).
+ *
+ * A context holds `problems` independent problems of one shape.  With
+ * shared_matrix = 0 every problem has its own A (A device float
+ * [problems][M][N]); with 1 all problems share one A ([M][N]) and differ in b
+ * (several signals measured by one projection).  Vectors are device float:
+ * b [problems][M], x [problems][N].  Constraints: 1 <= M, 4 <= N <= 8192 with
+ * N % 4 == 0 (rows are read as 16-byte vectors; A 16-byte aligned),
+ * problems >= 1 (FIRLS_E_SHAPE otherwise).  Operators run in FP32; the PCG
+ * inner products, alpha, beta, rho, the residual norms and the relative change
+ * in FP64.  Each step S d = A^T (A d) + lambda W d streams A once: a row's
+ * product with d is formed and immediately scattered back along the row. */
+typedef struct firls_dense_ctx firls_dense_ctx;
+
+firls_status firls_dense_create(firls_dense_ctx** out, int M, int N, int problems, int shared_matrix,
+                                void* cuda_stream);
+/* Copy A (device float, see above; the context keeps its own copy) and
+ * compute diag(A^T A) and abar per matrix.  Synchronises the stream. */
+firls_status firls_dense_set_matrix(firls_dense_ctx* ctx, const float* A);
+/* abar per matrix (host double [shared_matrix ? 1 : problems]).  Synchronises. */
+firls_status firls_dense_abar(firls_dense_ctx* ctx, double* out);
+/* q = A^T A d per problem (device float [problems][N] each; q may not alias
+ * d).  The operator-level entry point of the parity tests and the bandwidth
+ * measurement. */
+firls_status firls_dense_apply_AtA(firls_dense_ctx* ctx, const float* d, float* q);
+/* Run FIRLS_L1 on every problem from x^1 = A^T b (x0 NULL) or x0.  Uses
+ * params->outer_iters, pcg_iters, pcg_tol (relative to ||A^T b||),
+ * outer_tol (relative change), lambda / lambda_per_slice, eps and precond
+ * (PAPER, JACOBI or NONE); every other field must be 0 (FIRLS_E_INVALID_ARG).
+ * Problems advance independently (each stops on its own tolerance).  Returns
+ * FIRLS_E_BREAKDOWN if a problem broke down (x_out holds its last iterate);
+ * a problem whose A^T b is not finite is not iterated and counts as one.
+ * stats (host, may be NULL) as for firls_solve.  Synchronises the stream. */
+firls_status firls_dense_solve(firls_dense_ctx* ctx, const float* b, const firls_params* params, const float* x0,
+                               float* x_out, firls_stats* stats);
+const char* firls_dense_last_error(const firls_dense_ctx* ctx);
+firls_status firls_dense_destroy(firls_dense_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

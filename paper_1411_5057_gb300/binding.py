@@ -24,7 +24,9 @@ REAL_X = 1
 EXPORTED = ["firls_size_supported", "firls_create", "firls_set_operator", "firls_solve", "firls_solve_multi",
             "firls_last_error", "firls_destroy", "firls_apply_AHA", "firls_apply_Phi", "firls_apply_PhiT",
             "firls_apply_S_P", "firls_get_weights", "firls_get_precond", "firls_get_inverse_map",
-            "firls_set_tuning", "firls_get_popcounts", "firls_set_wait_test", "firls_set_channels",
+            "firls_set_tuning", "firls_get_popcounts", "firls_set_wait_test", "firls_set_channels", "firls_dense_create",
+            "firls_dense_set_matrix", "firls_dense_abar", "firls_dense_apply_AtA", "firls_dense_solve",
+            "firls_dense_last_error", "firls_dense_destroy",
             "firls_set_timing", "firls_get_timing", "firls_apply_AHA_noalloc",
             "firls_cnn_create", "firls_cnn_set_params", "firls_cnn_get_params", "firls_cnn_get_grads",
             "firls_cnn_forward", "firls_cnn_train_step", "firls_cnn_destroy", "firls_objective",
@@ -119,6 +121,14 @@ def lib():
     L.firls_set_timing.argtypes = [vp, i32]
     L.firls_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_int)]
+    L.firls_dense_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, i32, vp]
+    L.firls_dense_set_matrix.argtypes = [vp, vp]
+    L.firls_dense_abar.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.firls_dense_apply_AtA.argtypes = [vp, vp, vp]
+    L.firls_dense_solve.argtypes = [vp, vp, ctypes.POINTER(Params), vp, vp, ctypes.POINTER(Stats)]
+    L.firls_dense_last_error.argtypes = [vp]
+    L.firls_dense_last_error.restype = ctypes.c_char_p
+    L.firls_dense_destroy.argtypes = [vp]
     _lib = L
     return L
 
@@ -158,6 +168,61 @@ def make_params(outer, pcg, lam=0.0, lam_tv=0.0, pcg_tol=0.0, outer_tol=0.0, eps
         p.lambda_tv_per_slice = ctypes.cast(a, ctypes.POINTER(ctypes.c_float))
     p._keep = keep
     return p
+
+
+class DenseContext:
+    """`problems` sparse-recovery problems with a dense M x N sensing matrix
+    (own matrix per problem, or one shared), float32 device tensors."""
+
+    def __init__(self, M, N, problems=1, shared=False, stream=None):
+        import torch
+        self.M, self.N, self.problems, self.shared = int(M), int(N), int(problems), bool(shared)
+        self._torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = lib().firls_dense_create(ctypes.byref(h), self.M, self.N, self.problems, 1 if shared else 0,
+                                      ctypes.c_void_p(self.stream.cuda_stream))
+        if st != FIRLS_OK:
+            raise FirlsError(st, f"firls_dense_create(M={M}, N={N}, problems={problems})")
+        self.h = h
+
+    def _check(self, st, what):
+        if st != FIRLS_OK:
+            msg = lib().firls_dense_last_error(self.h)
+            raise FirlsError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().firls_dense_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_matrix(self, A):
+        """A: float32 CUDA [problems, M, N] (or [M, N] when shared)."""
+        self._check(lib().firls_dense_set_matrix(self.h, _ptr(A)), "set_matrix")
+
+    def abar(self):
+        out = (ctypes.c_double * (1 if self.shared else self.problems))()
+        self._check(lib().firls_dense_abar(self.h, out), "abar")
+        return list(out)
+
+    def apply_AtA(self, d, q):
+        self._check(lib().firls_dense_apply_AtA(self.h, _ptr(d), _ptr(q)), "apply_AtA")
+
+    def solve(self, b, params, x0=None, out=None, stats=False):
+        torch = self._torch
+        if out is None:
+            out = torch.empty((self.problems, self.N), dtype=torch.float32, device=b.device)
+        s = Stats() if stats else None
+        st = lib().firls_dense_solve(self.h, _ptr(b), ctypes.byref(params), _ptr(x0), _ptr(out),
+                                     ctypes.byref(s) if s is not None else None)
+        self._check(st, "dense_solve")
+        return (out, s.as_dict()) if stats else out
 
 
 class Context:

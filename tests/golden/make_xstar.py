@@ -16,7 +16,9 @@ One file per seed, ``xstar_tv_db4_256/seed<S>.npz``: x (complex64, full
 resolution), outer steps, the last relative change, mu and the estimated
 distance.  The GPU tests and the bench compare their results with these.
 --uneven writes ``xstar_uneven/seed<S>.npz`` for the first slice of each size
-of the uneven batch (128^2, 192^2, 256^2, 320^2 TV + D4, per-slice lambdas).
+of the uneven batch (128^2, 192^2, 256^2, 320^2 TV + D4, per-slice lambdas);
+--heldout the first four of the 512 held-out slices (seeds 20000..20511) of
+the learned warm start's comparison.
 
     python tests/golden/make_xstar.py [--procs P] [--resume] [seed ...]
     python tests/golden/make_xstar.py --steps-to [--procs P] [seed ...]
@@ -51,16 +53,23 @@ DEFAULT_SEEDS = [56, 12, 490, 79, 50] + [s for s in range(2, 18) if s != 12]
 
 # uneven batch (128^2 .. 320^2, seeds 1000..1063): the first slice of each size
 UNEVEN_SEEDS = [1000, 1016, 1032, 1048]
+# the first slices of the 512 held-out 256^2 TV + D4 slices (seeds 20000..20511)
+# on which the learned warm start is compared with the plain start
+HELDOUT_SEEDS = [20000, 20001, 20002, 20003]
+
+
+def uneven(seed):
+    return 1000 <= seed < 1064
 
 
 def out_path(seed):
-    return os.path.join(OUT_UNEVEN if seed >= 1000 else OUT, f"seed{seed}.npz")
+    return os.path.join(OUT_UNEVEN if uneven(seed) else OUT, f"seed{seed}.npz")
 
 
 def problem(seed):
-    """The 256^2 TV + D4 bench slice of a seed, or the uneven-batch slice."""
+    """The 256^2 TV + D4 slice of a seed, or the uneven-batch slice."""
     import firls_synth as fs
-    if seed >= 1000:
+    if uneven(seed):
         return next(p for p, s in zip(fs.uneven_batch(), range(1000, 1064)) if s == seed)
     return fs.tv_db4_256(seed=seed)
 
@@ -121,9 +130,10 @@ def main():
     ap.add_argument("--resume", action="store_true", help="continue from the stored x* of each seed")
     ap.add_argument("--steps-to", action="store_true", help="record the oracle's outer steps to 1e-4 of x*")
     ap.add_argument("--uneven", action="store_true", help="the first slice of each size of the uneven batch")
+    ap.add_argument("--heldout", action="store_true", help="the first held-out slices of the learned comparison")
     ap.add_argument("seeds", type=int, nargs="*")
     a = ap.parse_args()
-    seeds = a.seeds or (UNEVEN_SEEDS if a.uneven else DEFAULT_SEEDS)
+    seeds = a.seeds or (UNEVEN_SEEDS if a.uneven else HELDOUT_SEEDS if a.heldout else DEFAULT_SEEDS)
     os.makedirs(OUT, exist_ok=True)
     os.makedirs(OUT_UNEVEN, exist_ok=True)
     if a.steps_to:
