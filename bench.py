@@ -25,6 +25,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import math
 import subprocess
 import sys
 import threading
@@ -396,9 +397,11 @@ def run_learned(args, F, torch, stream, B, rank, world, dist, serve_queue):
         prm = net.get_params()
         net.close()
         del atb_t, masks_t, xt
-        inf = F.Cnn(N, B, stream=stream)
+        # the CNN start runs in chunks of the largest divisor of H up to B slices
+        Bc = max(k for k in range(1, B + 1) if H % k == 0)
+        inf = F.Cnn(N, Bc, stream=stream)
         inf.set_params(prm)
-        prep = F.Context(N, batch=B, stream=stream)
+        prep = F.Context(N, batch=Bc, stream=stream)
         x0 = torch.empty_like(b)
         one = F.make_params(1, 1, lam=LAM_W, lam_tv=LAM_TV)
     stream.synchronize()
@@ -413,11 +416,11 @@ def run_learned(args, F, torch, stream, B, rank, world, dist, serve_queue):
     def learned_step():
         kept[0] = 0
         with torch.cuda.stream(stream):
-            for i in range(0, H, B):
-                prep.set_operator(masks[i:i + B], F.PSI_TV | F.PSI_DB4, LEVELS)
-                atb = prep.adjoint(b[i:i + B])
-                xs, chosen = Lr.warm_start(prep, inf, b[i:i + B], atb, masks[i:i + B], one)
-                x0[i:i + B].copy_(xs)
+            for i in range(0, H, Bc):
+                prep.set_operator(masks[i:i + Bc], F.PSI_TV | F.PSI_DB4, LEVELS)
+                atb = prep.adjoint(b[i:i + Bc])
+                xs, chosen = Lr.warm_start(prep, inf, b[i:i + Bc], atb, masks[i:i + Bc], one)
+                x0[i:i + Bc].copy_(xs)
                 kept[0] += int(sum(chosen))
         return serve_queue(ml, bl, xl, pcg_learned, x0s=list(x0))
 
@@ -864,6 +867,30 @@ def profile_step(args):
     print(f"[bench] profile step: {B} slices, one outer step x2", file=sys.stderr)
 
 
+def profile_dense(args):
+    """Profiling target (no timing, no JSON line): q = A^T A d on
+    --profile-dense problems of the dense workload's shape (800 x 4000, own A
+    each, seeded device draws), five applications."""
+    import torch
+    import paper_1411_5057_gb300 as F
+    P, M, Nd = args.profile_dense, 800, 4000
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        A = torch.randn(P, M, Nd, device="cuda", generator=g) / math.sqrt(M)
+        ctx = F.DenseContext(M, Nd, P, stream=stream)
+        ctx.set_matrix(A)
+        del A
+        d = torch.randn(P, Nd, device="cuda", generator=g)
+        q = torch.empty_like(d)
+        for _ in range(5):
+            ctx.apply_AtA(d, q)
+    stream.synchronize()
+    ctx.close()
+    print(f"[bench] profile dense: {P} problems, five applications", file=sys.stderr)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -904,9 +931,13 @@ def main(argv=None):
     ap.add_argument("--profile-step", type=int, default=0,
                     help="profiling target only: one outer step on this many slices, twice")
     ap.add_argument("--profile-ilu-shape", type=int, default=0)
+    ap.add_argument("--profile-dense", type=int, default=0,
+                    help="profiling target: q = A^T A d on this many dense problems, no timing")
     args = ap.parse_args(argv)
     if args.profile_step > 0:
         return profile_step(args)
+    if args.profile_dense > 0:
+        return profile_dense(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

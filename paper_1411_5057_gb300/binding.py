@@ -133,6 +133,16 @@ def lib():
     return L
 
 
+def _need(t, numel, what):
+    """Reject a CUDA tensor that does not hold `numel` contiguous elements
+    (the library reads and writes exactly that many)."""
+    if t is None:
+        return
+    if not t.is_cuda or not t.is_contiguous() or t.numel() != numel:
+        raise FirlsError(1, f"{what}: expected a contiguous CUDA tensor of {numel} elements, got "
+                            f"{tuple(t.shape)} on {t.device}")
+
+
 def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
@@ -204,6 +214,7 @@ class DenseContext:
 
     def set_matrix(self, A):
         """A: float32 CUDA [problems, M, N] (or [M, N] when shared)."""
+        _need(A, (1 if self.shared else self.problems) * self.M * self.N, "A")
         self._check(lib().firls_dense_set_matrix(self.h, _ptr(A)), "set_matrix")
 
     def abar(self):
@@ -218,6 +229,9 @@ class DenseContext:
         torch = self._torch
         if out is None:
             out = torch.empty((self.problems, self.N), dtype=torch.float32, device=b.device)
+        _need(b, self.problems * self.M, "b")
+        _need(x0, self.problems * self.N, "x0")
+        _need(out, self.problems * self.N, "out")
         s = Stats() if stats else None
         st = lib().firls_dense_solve(self.h, _ptr(b), ctypes.byref(params), _ptr(x0), _ptr(out),
                                      ctypes.byref(s) if s is not None else None)
@@ -258,6 +272,7 @@ class Context:
 
     def set_operator(self, mask, psi, levels=0, groups=None, group_off=None, group_size=0):
         """mask: uint8 [batch, n, n] CUDA; groups: int32 CUDA ([G, g] or flat with group_off)."""
+        _need(mask, self.batch * self.n * self.n, "mask")
         n_groups = 0
         if groups is not None:
             if group_off is not None:
@@ -271,6 +286,10 @@ class Context:
         torch = self._torch
         if out is None:
             out = torch.empty((self.batch, self.n, self.n), dtype=torch.complex64, device=b.device)
+        nn = self.batch * self.n * self.n
+        _need(b, nn, "b")
+        _need(x0, nn, "x0")
+        _need(out, nn, "out")
         s = Stats() if stats else None
         st = lib().firls_solve(self.h, _ptr(b), ctypes.byref(params), _ptr(x0), _ptr(out),
                                ctypes.byref(s) if s is not None else None)
