@@ -327,6 +327,13 @@ def run_ours(args):
               f"{args.mt_sets}), accuracy {json.dumps(mt['accuracy_vs_oracle_same_schedule'])}, "
               f"SNR {mt['snr_db_mean']} dB", file=sys.stderr, flush=True)
 
+    # ---- overlapping tree groups at 512^2, untimed w.r.t. the main line ----
+    tree = tree_run(F, torch, args) if args.tree_slices > 0 else None
+    if tree is not None:
+        print(f"[bench] tree groups 512^2: {tree['value']} recons/s ({tree['s_per_batch']} s per "
+              f"{args.tree_slices}), accuracy {json.dumps(tree['accuracy_vs_oracle_same_schedule'])}, "
+              f"SNR {tree['snr_db_mean']} dB", file=sys.stderr, flush=True)
+
     # ---- dense random projections (Sec. 5.3), untimed w.r.t. the main line ----
     dense = dense_run(F, torch, args) if args.dense_problems > 0 else None
     if dense is not None:
@@ -360,7 +367,7 @@ def run_ours(args):
                                "mean_pcg_steps": round(float(np.mean(pcg_counts)), 1),
                                "max_pcg_steps": int(np.max(pcg_counts))},
                "accuracy": acc, "learned": learned, "pcg_iterations": pcg_iters, "uneven_batch": c4,
-               "multi_contrast": mt, "dense_l1": dense}
+               "multi_contrast": mt, "dense_l1": dense, "tree_512": tree}
         print(json.dumps(out), flush=True)
     ctx.close()
     if dist is not None:
@@ -612,6 +619,58 @@ def hbm_peak():
         return float(peaks["hbm_gbs"]), "measured"
     except (OSError, ValueError, KeyError):
         return 6800.0, "fallback"
+
+
+TREE_OUTER, TREE_INNER = 100, 20
+XTREE_DIR = os.path.join(ROOT, "tests", "golden", "xtree_db4_512")
+
+
+def tree_run(F, torch, args, reps=2):
+    """Overlapping group sparsity at 512^2 (5-level D4, parent-child tree
+    groups of size 2, 15 % mask, sigma 0.005, lambda 2e-4; FIRLS_OG):
+    `args.tree_slices` slices (seeds 3..) in one context for the paper's
+    budget of 100 iterations (20 PCG steps each).  Reconstructions per second
+    with device-resident inputs, the error against the FP64 oracle's stored
+    result of the same schedule (seeds 3-4, tests/golden/make_xtree.py) and
+    the mean SNR against the phantoms.  Untimed set-up; `reps` timed solves
+    after one warm-up."""
+    import firls_synth as fs
+    S = args.tree_slices
+    probs = [fs.tree_db4_512(seed=3 + i) for i in range(S)]
+    p0 = probs[0]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = F.Context(p0.n, batch=S, stream=stream)
+        ctx.set_operator(torch.from_numpy(np.stack([p.mask for p in probs])).cuda(), p0.psi, p0.levels,
+                         torch.from_numpy(p0.groups).cuda())
+        b = torch.from_numpy(np.stack([p.b for p in probs]).astype(np.complex64)).cuda()
+        out = torch.empty_like(b)
+        prm = F.make_params(TREE_OUTER, TREE_INNER, lam=p0.lam)
+        ctx.solve(b, prm, out=out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            ctx.solve(b, prm, out=out)
+    e1.record(stream)
+    e1.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3 / reps
+    x = out.cpu().numpy().astype(np.complex128)
+    snr = [20 * np.log10(np.linalg.norm(p.x0) / np.linalg.norm(x[i] - p.x0)) for i, p in enumerate(probs)]
+    errs = {}
+    for i in range(min(S, 2)):
+        f = os.path.join(XTREE_DIR, f"seed{3 + i}.npz")
+        if os.path.exists(f):
+            ref = np.load(f)["x"].astype(np.complex128)
+            errs[3 + i] = float(np.linalg.norm(x[i] - ref) / np.linalg.norm(ref))
+    ctx.close()
+    return {"value": round(S / sec, 3), "unit": UNIT, "s_per_batch": round(sec, 4),
+            "workload": f"{S} slices 512^2, 5-level D4, parent-child tree groups (overlapping), lambda 2e-4",
+            "schedule": f"{TREE_OUTER} outer x {TREE_INNER} PCG (the paper's 100-iteration budget)",
+            "accuracy_vs_oracle_same_schedule": {"n_checked": len(errs),
+                                                 "max_rel_err": max(errs.values()) if errs else None},
+            "snr_db_mean": round(float(np.mean(snr)), 2)}
 
 
 DENSE_OUTER, DENSE_INNER = 200, 30
@@ -921,6 +980,8 @@ def main(argv=None):
                     help="reference arm: oracle instances run at once, one per host core (0: all cores)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--uneven", type=int, default=1, help="also time the 64-slice uneven batch (1/0)")
+    ap.add_argument("--tree-slices", type=int, default=32,
+                    help="512^2 tree-group slices timed beside the main line (0: none)")
     ap.add_argument("--dense-problems", type=int, default=152,
                     help="dense random-projection problems timed beside the main line (0: none)")
     ap.add_argument("--mt-sets", type=int, default=100,

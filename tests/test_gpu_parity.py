@@ -521,3 +521,19 @@ def test_set_tuning_shapes(F):
     with pytest.raises(F.FirlsError):
         big.set_tuning(rows_per_cta=1)  # a 512^2 slice does not fit one cluster's shared memory
     big.set_tuning(rows_per_cta=16)
+
+
+def test_tree_512_workload_matches_stored_oracle(F):
+    """The 512^2 overlapping-group workload (5-level D4 tree groups) for the
+    paper's 100-iteration budget (20 PCG steps each): against the FP64
+    oracle's stored result of the same schedule (tests/golden/make_xtree.py)."""
+    import os
+    d = os.path.join(os.path.dirname(__file__), "golden", "xtree_db4_512")
+    seeds = [s for s in (3, 4) if os.path.exists(os.path.join(d, f"seed{s}.npz"))]
+    assert seeds, "no stored tree-group result"
+    probs = [fs.tree_db4_512(seed=s) for s in seeds]
+    z0 = np.load(os.path.join(d, f"seed{seeds[0]}.npz"))
+    x = _gpu_solve(F, probs, int(z0["outer"]), int(z0["inner"]))
+    for i, s in enumerate(seeds):
+        ref = np.load(os.path.join(d, f"seed{s}.npz"))["x"].astype(np.complex128)
+        assert rel(x[i], ref) < TOL_SOLVE, (s, rel(x[i], ref))
