@@ -60,6 +60,9 @@ RATIO, SIGMA, LAM_TV, LAM_W, LEVELS = 0.20, 0.01, 1e-3, 5e-4, 4
 # tests/test_gpu_parity.py::test_bench_workload_reaches_converged_oracle and
 # reported per result in the bench line ("accuracy").
 OUTER, INNER, INNER_LATE, OUTER_LATE, OUTER_TOL, STALL_TOL = 800, 60, 240, 60, 3e-5, 6e-7
+# the ILU(0) variant's late inner schedule (its subproblems are solved in fewer
+# PCG steps, and a shorter late schedule is the faster one for it)
+ILU0_INNER_LATE = 160
 SERVE_CHUNK = 64   # macro steps between polls of the slots
 BOUNDARY_PERIOD = 4  # outer-step transitions (and their weight updates) every 4th macro step
 REF_OUTER_PER_RECON = 43   # FP64 oracle outer steps (x 60 PCG) to 1e-4 of x* on seed 2
@@ -189,7 +192,8 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     params = F.make_params(args.outer, args.inner, lam=LAM_W, lam_tv=LAM_TV, outer_tol=args.outer_tol,
                            stop_on_distance=True, stall_tol=args.stall_tol, pcg_late=args.inner_late,
-                           outer_late=args.outer_late, boundary_period=args.boundary_period)
+                           outer_late=args.outer_late, boundary_period=args.boundary_period,
+                           precond=args.precond)
     lams, lam_tvs = [LAM_W] * S, [LAM_TV] * S
     with torch.cuda.stream(stream):
         masks = torch.from_numpy(masks_h).cuda()
@@ -257,7 +261,7 @@ def run_ours(args):
 
     # ---- per-kernel timing of one outer step over all B slots ----
     ctx.set_timing(True)
-    one = F.make_params(1, args.inner, lam=LAM_W, lam_tv=LAM_TV)
+    one = F.make_params(1, args.inner, lam=LAM_W, lam_tv=LAM_TV, precond=args.precond)
     with torch.cuda.stream(stream):
         ctx.solve(b[:B], one, out=x[:B])
         ctx.solve(b[:B], one, out=x[:B])
@@ -307,6 +311,40 @@ def run_ours(args):
         e2e = {"value": world * done_per_step / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(bh.numel() * 8 + mh.numel()),
                "d2h_bytes_per_step": int(xh.numel() * 8)}
+
+    # ---- the same queue with the ILU(0) variant of the TV preconditioner ----
+    ilu0 = None
+    if args.ilu0_variant and args.precond == "paper":
+        p_ilu = F.make_params(args.outer, args.inner, lam=LAM_W, lam_tv=LAM_TV, outer_tol=args.outer_tol,
+                              stop_on_distance=True, stall_tol=args.stall_tol, pcg_late=ILU0_INNER_LATE,
+                              outer_late=args.outer_late, boundary_period=args.boundary_period, precond="ilu0")
+        pcg_ilu = [0] * S
+
+        def ilu_step():
+            with torch.cuda.stream(stream):
+                return F.serve(ctx, mlist, blist, lams, lam_tvs, p_ilu, xlist, max_outer=args.outer,
+                               chunk=SERVE_CHUNK, pcg_steps=pcg_ilu)
+
+        ilu_step()
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(args.ilu0_variant):
+            ist = ilu_step()
+        e1.record(stream)
+        e1.synchronize()
+        ims = max_over_ranks(e0.elapsed_time(e1) / args.ilu0_variant, dist, "cuda")
+        iacc = accuracy(xlist, rank_first_seed(rank, S), ist)
+        ist = np.asarray(ist)
+        ilu0 = {"value": round(world * done_per_step / (ims / 1e3), 3), "unit": UNIT, "ms_per_step": round(ims, 3),
+                "vs_paper": round(ms / ims, 4), "timed_steps": args.ilu0_variant, "warmup": 1,
+                "precond": "ilu0 (Sec. 4.2's incomplete LU with updated pivots)", "inner": args.inner,
+                "inner_late": ILU0_INNER_LATE, "outer_late": args.outer_late,
+                "mean_outer_steps": round(float(ist.mean()), 2), "max_outer_steps": int(ist.max()),
+                "mean_pcg_steps": round(float(np.mean(pcg_ilu)), 1), "max_pcg_steps": int(np.max(pcg_ilu)),
+                "accuracy": iacc}
+        print(f"[bench] ILU(0) variant: {ilu0['value']} recons/s ({ilu0['vs_paper']}x), PCG steps mean "
+              f"{ilu0['mean_pcg_steps']}, accuracy max {iacc['max_rel_err'] if iacc else None}", file=sys.stderr,
+              flush=True)
 
     # ---- preconditioner comparison (PCG iteration counts, untimed) ----
     pcg_iters = precond_comparison(F, torch, stream) if args.precond_cmp else None
@@ -367,7 +405,7 @@ def run_ours(args):
                                "mean_pcg_steps": round(float(np.mean(pcg_counts)), 1),
                                "max_pcg_steps": int(np.max(pcg_counts))},
                "accuracy": acc, "learned": learned, "pcg_iterations": pcg_iters, "uneven_batch": c4,
-               "multi_contrast": mt, "dense_l1": dense, "tree_512": tree}
+               "multi_contrast": mt, "dense_l1": dense, "tree_512": tree, "ilu0_variant": ilu0}
         print(json.dumps(out), flush=True)
     ctx.close()
     if dist is not None:
@@ -790,7 +828,7 @@ def workload_config(args, world, done_per_step=None):
     return {"workload": f"firls_tv_db4_{N}", "n": N, "slices_per_step_per_gpu": args.queue, "slots": args.batch,
             "outer_max": args.outer, "inner": args.inner, "inner_late": args.inner_late,
             "outer_late": args.outer_late, "outer_tol": args.outer_tol, "stall_tol": args.stall_tol,
-            "boundary_period": args.boundary_period,
+            "boundary_period": args.boundary_period, "precond": args.precond,
             "mask_ratio": RATIO, "sigma": SIGMA, "lambda_tv": LAM_TV, "lambda_w": LAM_W,
             "wavelet": "db4", "levels": LEVELS, "batching": "continuous (slots refilled on convergence)",
             "completions_per_step": args.queue if done_per_step is None else done_per_step,
@@ -968,6 +1006,8 @@ def main(argv=None):
     ap.add_argument("--boundary-period", type=int, default=BOUNDARY_PERIOD,
                     help="macro steps between outer-step transitions of the served slots")
     ap.add_argument("--stall-tol", type=float, default=STALL_TOL)
+    ap.add_argument("--precond", default="paper", choices=["paper", "ilu0", "jacobi", "none"],
+                    help="PCG preconditioner of the served queue (paper: the printed L U factors of Sec. 4.2)")
     ap.add_argument("--autotune", type=int, default=1, help="autotune tile shapes before timing (1/0)")
     ap.add_argument("--learned", type=int, default=1, help="also time the learned warm start (1/0)")
     ap.add_argument("--learned-train", type=int, default=4000, help="training instances solved by the method")
@@ -980,6 +1020,8 @@ def main(argv=None):
                     help="reference arm: oracle instances run at once, one per host core (0: all cores)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--uneven", type=int, default=1, help="also time the 64-slice uneven batch (1/0)")
+    ap.add_argument("--ilu0-variant", type=int, default=1,
+                    help="timed passes of the queue with the ILU(0) preconditioner after one warm-up (0: none)")
     ap.add_argument("--tree-slices", type=int, default=32,
                     help="512^2 tree-group slices timed beside the main line (0: none)")
     ap.add_argument("--dense-problems", type=int, default=152,
