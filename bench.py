@@ -396,9 +396,10 @@ def run_ours(args):
                "vs_baseline": None, "dtype": "f32 (FP64 PCG scalars)", "data": "synthetic",
                "config": workload_config(args, world, done_per_step),
                "roofline": roofline, "kernels_per_outer_step": kern,
-               # kernels per macro step x macro steps run, plus 4 kernels per slot load and 1 per retire
+               # kernels per macro step x macro steps run, plus 4 kernels per slot load and 1 per
+               # retire or slot move
                "gpu_launches": int(launches_per_outer / (args.inner + 1) * served["runs"] * SERVE_CHUNK
-                                   + 4 * served["loads"] + served["retires"]),
+                                   + 4 * served["loads"] + served["retires"] + served.get("moves", 0)),
                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
                "solve_stats": {"mean_outer_steps": round(float(steps.mean()), 2), "max_outer_steps": int(steps.max()),
                                "capped": int((steps >= args.outer).sum()),

@@ -271,6 +271,19 @@ firls_status firls_slot_status(firls_ctx* ctx, int* done, int* outer_done, doubl
 firls_status firls_slot_retire(firls_ctx* ctx, int s);
 firls_status firls_slot_get(firls_ctx* ctx, int s, void* x_out);
 
+/* Slot compaction for the end of a queue, when few slots still run and most
+ * launched blocks would find their slot idle (no counterpart in the paper).
+ * firls_slot_move: slot `from` continues in slot `to` (every per-slice array
+ *   and its state are copied on the stream; `from` is retired).  `to` must
+ *   not hold a running slice (it is overwritten).  Results are bit for bit
+ *   those of the unmoved slice.
+ * firls_set_active_slots: firls_run_steps and firls_run launch only slots
+ *   [0, k) (k = 0 or batch: all); slots >= k must not hold a running slice
+ *   (they are left as they are).  The other entry points always cover the
+ *   whole batch.  FIRLS_E_INVALID_ARG for k outside [0, batch]. */
+firls_status firls_slot_move(firls_ctx* ctx, int from, int to);
+firls_status firls_set_active_slots(firls_ctx* ctx, int k);
+
 /* Autotuner: time the tile-shape choices of this context's size, batch and
  * regulariser on its own buffers (CUDA events on its stream) and keep the
  * fastest: the wavelet form (1, 2: every level of a slice in one launch on a

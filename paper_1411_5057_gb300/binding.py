@@ -32,7 +32,7 @@ EXPORTED = ["firls_size_supported", "firls_create", "firls_set_operator", "firls
             "firls_cnn_forward", "firls_cnn_train_step", "firls_cnn_destroy", "firls_objective",
             "firls_warm_start_guard", "firls_adjoint", "firls_data_consistency", "firls_autotune",
             "firls_get_tuning", "firls_slot_load", "firls_run", "firls_run_steps", "firls_slot_status",
-            "firls_slot_retire",
+            "firls_slot_retire", "firls_slot_move", "firls_set_active_slots",
             "firls_slot_get"]
 KERNEL_CLASSES = ["row_fft", "col_fft_mask", "wavelet_S", "wavelet_Pinv", "row_ifft_combine", "ilu", "axpy",
                   "scalars", "weights", "other"]
@@ -105,6 +105,8 @@ def lib():
     L.firls_slot_status.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(i32)]
     L.firls_slot_retire.argtypes = [vp, i32]
+    L.firls_slot_move.argtypes = [vp, i32, i32]
+    L.firls_set_active_slots.argtypes = [vp, i32]
     L.firls_slot_get.argtypes = [vp, i32, vp]
     L.firls_get_tuning.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.firls_data_consistency.argtypes = [vp, vp, vp, vp]
@@ -333,6 +335,14 @@ class Context:
     def slot_retire(self, s):
         self._check(lib().firls_slot_retire(self.h, int(s)), "slot_retire")
 
+    def slot_move(self, src, dst):
+        """Slot src continues in slot dst (src is retired)."""
+        self._check(lib().firls_slot_move(self.h, int(src), int(dst)), "slot_move")
+
+    def set_active_slots(self, k):
+        """run / run_steps launch only slots [0, k) (0: all)."""
+        self._check(lib().firls_set_active_slots(self.h, int(k)), "set_active_slots")
+
     def slot_get(self, s, out):
         self._check(lib().firls_slot_get(self.h, int(s), _ptr(out)), "slot_get")
 
@@ -507,8 +517,16 @@ class Cnn:
             pass
 
 
+def _bucket(batch, active):
+    """Smallest slot count of the form ceil(batch / 2^j) that holds `active`."""
+    k = batch
+    while k > 1 and (k + 1) // 2 >= active:
+        k = (k + 1) // 2
+    return k
+
+
 def serve(ctx, masks, bs, lams, lam_tvs, params, outs, x0s=None, chunk=64, max_outer=400, stop_after=None,
-          counters=None, pcg_steps=None):
+          counters=None, pcg_steps=None, compact=True):
     """Continuous batching over a queue of slices with ctx.batch slots.
 
     masks/bs/outs: per-slice device tensors ([n][n]); lams/lam_tvs: floats;
@@ -519,13 +537,18 @@ def serve(ctx, masks, bs, lams, lam_tvs, params, outs, x0s=None, chunk=64, max_o
     returns once that many slices have completed and retires the slices still
     in flight (their entry in the result stays 0).  Returns the outer steps
     of every slice.  counters (a dict, optional) receives "runs" (calls of
-    ctx.run_steps, each one graph of `chunk` macro steps), "loads" and
-    "retires"; pcg_steps (a list of len(bs), optional) receives the PCG steps
-    of every slice.
+    ctx.run_steps, each one graph of `chunk` macro steps), "loads",
+    "retires" and "moves"; pcg_steps (a list of len(bs), optional) receives
+    the PCG steps of every slice.  With compact, once the queue is empty and
+    at most half of the launched slots still run, the running slices move to
+    the lowest slots and only those are launched (a halving bucket of slots);
+    a slice's results do not depend on its slot.
     """
     cnt = counters if counters is not None else {}
-    for k in ("runs", "loads", "retires"):
+    for k in ("runs", "loads", "retires", "moves"):
         cnt.setdefault(k, 0)
+    ctx.set_active_slots(0)
+    launched = ctx.batch
     q = len(bs)
     steps = [0] * q
     slot_of = [-1] * ctx.batch
@@ -573,4 +596,17 @@ def serve(ctx, masks, bs, lams, lam_tvs, params, outs, x0s=None, chunk=64, max_o
                 cnt["retires"] += 1
                 slot_of[s] = -1
                 active -= 1
+        if compact and nxt >= q and active:
+            k = _bucket(ctx.batch, active)
+            if k < launched:
+                free = [t for t in range(k) if slot_of[t] < 0]
+                for src in range(k, launched):
+                    if slot_of[src] >= 0:
+                        dst = free.pop()
+                        ctx.slot_move(src, dst)
+                        cnt["moves"] += 1
+                        slot_of[dst], slot_of[src] = slot_of[src], -1
+                launched = k
+                ctx.set_active_slots(k)
+    ctx.set_active_slots(0)
     return steps

@@ -29,6 +29,10 @@ struct firls_ctx {
   // multi-contrast images (Sec. 5.6): C consecutive slices are the contrasts
   // of one image, with joint weights and one set of PCG scalars
   int channels = 1;
+  // slot mode (firls_run_steps / firls_run): only slots [0, active_slots) are
+  // launched (0: all); cur_batch is the batch the launch helpers use (0: all)
+  int active_slots = 0;
+  int cur_batch = 0;
   // device workspace
   uint8_t* mask = nullptr;
   int* counts = nullptr;
@@ -66,6 +70,7 @@ struct firls_ctx {
   struct CachedGraph {
     firls_params sched;
     int steps;
+    int batch;  // slots launched
     cudaGraphExec_t exec;
   };
   std::vector<CachedGraph> graphs;
@@ -143,9 +148,13 @@ void basis_tables(int n, int levels, int kind, std::vector<float>& tab, std::vec
   }
 }
 
+// The slots the macro-step launches cover: all of them, or in slot mode the
+// first active_slots (the others hold no running slice).
+int run_batch(const firls_ctx* c) { return c->cur_batch > 0 ? c->cur_batch : c->batch; }
+
 WavArgs wav_args(firls_ctx* c, const SliceState* st) {
   WavArgs a;
-  a.batch = c->batch;
+  a.batch = run_batch(c);
   a.n = c->n;
   a.levels = c->levels;
   a.kind = c->kind;
@@ -161,7 +170,7 @@ WavArgs wav_args(firls_ctx* c, const SliceState* st) {
 
 FftArgs fft_args(firls_ctx* c) {
   FftArgs a;
-  a.batch = c->batch;
+  a.batch = run_batch(c);
   a.stream = c->stream;
   a.tw = c->tw;
   a.st = c->st;
@@ -244,7 +253,7 @@ void enqueue_S(firls_ctx* c, int mode, const float2* zin, float2* din, float2* q
 // Update W^k and P from x (Alg. 2/3, first two lines of the loop body) for
 // the slices that `view` shows running (its other slices read as done).
 void enqueue_weights(firls_ctx* c, const float2* x, int precond, const SliceState* view) {
-  const int B = c->batch, n = c->n;
+  const int B = run_batch(c), n = c->n;
   TMark mk(c, FIRLS_K_WEIGHTS, 0);
   if (c->kind) {
     WavArgs w = wav_args(c, view);
@@ -280,7 +289,7 @@ PcgSched pcg_sched(const firls_params& sc) {
 // PCG stop.  mode ILU_INIT: the first residual r = A^H b - q for every
 // running slice; ILU_PER_SLICE: each slice by its phase.  x updates go to dx.
 void enqueue_precond(firls_ctx* c, int mode, const firls_params& sc) {
-  const int B = c->batch, n = c->n;
+  const int B = run_batch(c), n = c->n;
   const int real = (c->flags & FIRLS_REAL_X) ? 1 : 0;
   const bool init = mode == ILU_INIT;
   const int am = init ? AXPY_INIT : AXPY_PER_SLICE, sm = init ? SCALARS_INIT : SCALARS_PER_SLICE;
@@ -302,8 +311,11 @@ void enqueue_precond(firls_ctx* c, int mode, const firls_params& sc) {
     const bool fuse = c->channels == 1;
     {
       TMark m(c, FIRLS_K_ILU, 1);
+      // the tuned ring shape for the whole batch, the default one for the
+      // fewer slots of a compacted launch (every shape gives the same sums)
+      const int shape = (c->tune_ilu && B == c->batch) ? c->tune_ilu : ilu_default_shape(n, B, is_aniso(c));
       ilu_step(B, n, c->stream, c->st, c->part, mode, c->dx, c->d, c->r, c->q, c->atb, c->u, c->z, c->ia, c->wtv,
-               c->tune_ilu, fuse ? 1 : 0, ps, c->wait_test, tv2_of(c));
+               shape, fuse ? 1 : 0, ps, c->wait_test, tv2_of(c));
     }
     if (!fuse) {
       TMark m(c, FIRLS_K_SCALARS, 1);
@@ -335,7 +347,7 @@ void enqueue_precond(firls_ctx* c, int mode, const firls_params& sc) {
 // J + 1 macro steps; with one every P macro steps a slice waits at most
 // P - 1 macro steps per outer step.
 void enqueue_macro(firls_ctx* c, const firls_params& sc, bool boundary_stage = true) {
-  const int B = c->batch, n = c->n;
+  const int B = run_batch(c), n = c->n;
   if (boundary_stage) {
     {
       TMark m(c, FIRLS_K_OTHER, 3);
@@ -447,7 +459,7 @@ void graphs_clear(firls_ctx* c) {
 // with timing on, the marks of its last capture are the ones read back).
 firls_status macro_graph(firls_ctx* c, const firls_params& sc, int steps, cudaGraphExec_t* out) {
   for (auto& g : c->graphs)
-    if (g.steps == steps && same_schedule(g.sched, sc)) {
+    if (g.steps == steps && g.batch == run_batch(c) && same_schedule(g.sched, sc)) {
       *out = g.exec;
       return FIRLS_OK;
     }
@@ -461,7 +473,7 @@ firls_status macro_graph(firls_ctx* c, const firls_params& sc, int steps, cudaGr
   e = cudaGraphInstantiate(&ex, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_check(c, e, "graph instantiate");
-  c->graphs.push_back({sc, steps, ex});
+  c->graphs.push_back({sc, steps, run_batch(c), ex});
   *out = ex;
   return FIRLS_OK;
 }
@@ -1152,7 +1164,10 @@ extern "C" firls_status firls_run_steps(firls_ctx* c, const firls_params* p, int
   q.outer_iters = 1;  // the per-slot limits come from firls_slot_load
   TRY(check_params(c, &q));
   // one graph of all the steps: the caller polls with firls_slot_status
-  return run_macro(c, q, macro_steps, macro_steps, false);
+  c->cur_batch = c->active_slots;
+  const firls_status st = run_macro(c, q, macro_steps, macro_steps, false);
+  c->cur_batch = 0;
+  return st;
 }
 
 extern "C" firls_status firls_run(firls_ctx* c, const firls_params* p) {
@@ -1162,7 +1177,10 @@ extern "C" firls_status firls_run(firls_ctx* c, const firls_params* p) {
   firls_params q = *p;
   q.outer_iters = 1;
   TRY(check_params(c, &q));
-  return run_macro(c, q, solve_steps(p), p->pcg_iters + 1, false);
+  c->cur_batch = c->active_slots;
+  const firls_status st = run_macro(c, q, solve_steps(p), p->pcg_iters + 1, false);
+  c->cur_batch = 0;
+  return st;
 }
 
 extern "C" firls_status firls_slot_status(firls_ctx* c, int* done, int* outer_done, double* rel_change,
@@ -1185,6 +1203,37 @@ extern "C" firls_status firls_slot_retire(firls_ctx* c, int s) {
   if (!c || s < 0 || s >= c->batch) return FIRLS_E_INVALID_ARG;
   k_slot_retire<<<1, 1, 0, c->stream>>>(c->st + s);
   return cuda_check(c, cudaGetLastError(), "slot_retire");
+}
+
+extern "C" firls_status firls_set_active_slots(firls_ctx* c, int k) {
+  if (!c) return FIRLS_E_INVALID_ARG;
+  if (k < 0 || k > c->batch) return fail(c, FIRLS_E_INVALID_ARG, "active slots out of range");
+  c->active_slots = k == c->batch ? 0 : k;
+  return FIRLS_OK;
+}
+
+extern "C" firls_status firls_slot_move(firls_ctx* c, int from, int to) {
+  if (!c) return FIRLS_E_INVALID_ARG;
+  if (from < 0 || from >= c->batch || to < 0 || to >= c->batch || from == to)
+    return fail(c, FIRLS_E_INVALID_ARG, "bad slot pair");
+  if (!c->op_set) return fail(c, FIRLS_E_STATE, "operator not set");
+  const size_t N = (size_t)c->n * c->n;
+  auto mv = [&](auto* base, size_t per) -> cudaError_t {
+    return cudaMemcpyAsync(base + (size_t)to * per, base + (size_t)from * per, sizeof(*base) * per,
+                           cudaMemcpyDeviceToDevice, c->stream);
+  };
+  CU(mv(c->mask, N));
+  CU(mv(c->counts, 1));
+  for (float2* v : {c->atb, c->x, c->r, c->z, c->d, c->q, c->t, c->u, c->cw, c->dx}) CU(mv(v, N));
+  for (float* v : {c->ww, c->wtv, c->ia, c->wdiag, c->wtv2}) CU(mv(v, N));
+  if (c->groups) CU(mv(c->wg, (size_t)c->n_groups));
+  CU(mv(c->st, 1));
+  CU(mv(c->stw, 1));
+  CU(mv(c->part, (size_t)NSLOT * MAXPART));
+  CU(mv(c->lam_d, 1));
+  CU(mv(c->lamtv_d, 1));
+  k_slot_retire<<<1, 1, 0, c->stream>>>(c->st + from);
+  return cuda_check(c, cudaGetLastError(), "slot_move");
 }
 
 extern "C" firls_status firls_slot_get(firls_ctx* c, int s, void* x_out) {

@@ -1701,6 +1701,11 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
     // ============================================================== helpers
     const int hh = t - 64;
     float2 prev[IW_MAXCH];  // ia of the row above (forward) / W of the row below (backward)
+    // sums per column chunk: each chunk meets its rows in the same order for
+    // every ring shape, so the totals do not depend on G or S
+    float rr_c[IW_MAXCH], rho_c[IW_MAXCH];
+#pragma unroll
+    for (int c = 0; c < IW_MAXCH; ++c) rr_c[c] = rho_c[c] = 0.f;
 #pragma unroll
     for (int c = 0; c < IW_MAXCH; ++c) prev[c] = make_float2(0.f, 0.f);
     bool ok = true;
@@ -1744,7 +1749,7 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
                                 fmaf(alpha, d4.w, x4.w));
               }
               *reinterpret_cast<float4*>(r + g0) = rn;
-              rr += rn.x * rn.x + rn.y * rn.y + rn.z * rn.z + rn.w * rn.w;
+              rr_c[ch] += rn.x * rn.x + rn.y * rn.y + rn.z * rn.z + rn.w * rn.w;
               const float* wrow = reinterpret_cast<const float*>(sp + lay.oW + i * nG4);
               const float* arow = reinterpret_cast<const float*>(sp + lay.oIA + i * nG4);
               const float2 w2 = *reinterpret_cast<const float2*>(wrow + c);
@@ -1785,8 +1790,8 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
               const float2 wbl = prev[ch];  // W (W2 for l1 TV) of the row below
               const float la0 = lam * a2.x, la1 = lam * a2.y;
               const float2 t0 = make_float2(a2.x * y4.x, a2.x * y4.y), t1 = make_float2(a2.y * y4.z, a2.y * y4.w);
-              rho = fmaf(t0.x, y4.x, fmaf(t0.y, y4.y, rho));
-              rho = fmaf(t1.x, y4.z, fmaf(t1.y, y4.w, rho));
+              rho_c[ch] = fmaf(t0.x, y4.x, fmaf(t0.y, y4.y, rho_c[ch]));
+              rho_c[ch] = fmaf(t1.x, y4.z, fmaf(t1.y, y4.w, rho_c[ch]));
               float4* sc = sc_row(pos.s, i);
               sc[slot_of(c)] = make_float4(t0.x, t0.y, la0 * wbl.x, la0 * w2.y);
               sc[slot_of(c + 1)] = make_float4(t1.x, t1.y, la1 * wbl.y, la1 * w3);
@@ -1805,6 +1810,11 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
       pos.next(S);
     }
     if (!ok) fault();
+#pragma unroll
+    for (int c = 0; c < IW_MAXCH; ++c) {
+      rr += rr_c[c];
+      rho += rho_c[c];
+    }
   }
   __syncthreads();
   const double trz = block_sum((double)rho, red);

@@ -88,3 +88,63 @@ def test_boundary_period_changes_timing_not_results(F):
     assert od1 == od4 and pc1 == pc4
     assert torch.equal(x1, x4)
     ctx.close()
+
+
+def _serve_probs():
+    return [fs.make_problem(64, 0.15 + 0.02 * (i % 5), 0.01, 300 + i, real=False, psi=fs.PSI_TV | fs.PSI_DB4,
+                            levels=3, lam=4e-4, lam_tv=1e-3) for i in range(10)]
+
+
+def test_slot_move_continues_bit_for_bit(F):
+    """A slice moved to another slot mid-solve continues exactly as it would
+    have in its own slot (every per-slice array and its state move)."""
+    p = _serve_probs()[0]
+    prm = F.make_params(1, 20, lam=p.lam, lam_tv=p.lam_tv, outer_tol=1e-4, stop_on_distance=True)
+    mask = torch.from_numpy(p.mask).cuda()
+    b = torch.from_numpy(p.b.astype(np.complex64)).cuda()
+    outs = []
+    for move in (False, True):
+        ctx = F.Context(64, batch=3)
+        ctx.set_operator(mask[None].expand(3, 64, 64).contiguous(), p.psi, p.levels)
+        for s in range(3):
+            ctx.slot_retire(s)
+        ctx.slot_load(0, mask, b, p.lam, p.lam_tv)
+        ctx.run_steps(prm, 37)
+        src = 0
+        if move:
+            ctx.slot_move(0, 2)
+            src = 2
+        ctx.run_steps(prm, 50)
+        x = torch.empty(64, 64, dtype=torch.complex64, device="cuda")
+        ctx.slot_get(src, x)
+        _, od, rel, pc = ctx.slot_status(with_pcg=True)
+        outs.append((x, od[src], rel[src], pc[src]))
+        ctx.close()
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert outs[0][1:] == outs[1][1:]
+
+
+def test_serve_compaction_is_bit_exact(F):
+    """The serving loop's compaction at the end of the queue (running slices
+    moved to the lowest slots, fewer slots launched) changes no result."""
+    probs = _serve_probs()
+    masks = [torch.from_numpy(p.mask).cuda() for p in probs]
+    bs = [torch.from_numpy(p.b.astype(np.complex64)).cuda() for p in probs]
+    prm = F.make_params(300, 20, lam=4e-4, lam_tv=1e-3, outer_tol=3e-5, stop_on_distance=True, stall_tol=6e-7,
+                        pcg_late=60, outer_late=20, boundary_period=4)
+    res = []
+    for compact in (False, True):
+        ctx = F.Context(64, batch=4)
+        ctx.set_operator(torch.stack(masks[:4]), probs[0].psi, probs[0].levels)
+        outs = [torch.zeros(64, 64, dtype=torch.complex64, device="cuda") for _ in probs]
+        pcg = [0] * len(probs)
+        cnt = {}
+        steps = F.serve(ctx, masks, bs, [p.lam for p in probs], [p.lam_tv for p in probs], prm, outs, chunk=8,
+                        max_outer=300, counters=cnt, pcg_steps=pcg, compact=compact)
+        res.append((outs, steps, pcg, cnt))
+        ctx.close()
+    (o0, s0, p0, c0), (o1, s1, p1, c1) = res
+    assert c0["moves"] == 0 and c1["moves"] > 0
+    assert s0 == s1 and p0 == p1
+    for a, b in zip(o0, o1):
+        assert torch.equal(a, b)
