@@ -30,7 +30,7 @@ def test_reference_arm_line(procs):
                                                 "outer_late": bench.OUTER_LATE,
                                                 "boundary_period": bench.BOUNDARY_PERIOD,
                                                 "outer_tol": bench.OUTER_TOL, "stall_tol": bench.STALL_TOL,
-                                                "steady": 0})(), 1)
+                                                "steady": 0, "precond": "paper"})(), 1)
     assert line["config"] == ours
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == procs
     assert line["cpu_baseline"]["value"] == line["value"]
