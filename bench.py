@@ -64,7 +64,7 @@ OUTER, INNER, INNER_LATE, OUTER_LATE, OUTER_TOL, STALL_TOL = 800, 60, 240, 60, 3
 # PCG steps, and a shorter late schedule is the faster one for it)
 ILU0_INNER_LATE = 160
 SERVE_CHUNK = 64   # macro steps between polls of the slots
-BOUNDARY_PERIOD = 4  # outer-step transitions (and their weight updates) every 4th macro step
+BOUNDARY_PERIOD = 8  # outer-step transitions (and their weight updates) every 8th macro step
 REF_OUTER_PER_RECON = 43   # FP64 oracle outer steps (x 60 PCG) to 1e-4 of x* on seed 2
 
 # Algorithmic bytes per pixel per launch of each kernel class: every distinct

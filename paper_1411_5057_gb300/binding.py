@@ -518,10 +518,14 @@ class Cnn:
 
 
 def _bucket(batch, active):
-    """Smallest slot count of the form ceil(batch / 2^j) that holds `active`."""
+    """Smallest slot count of the sequence batch, ceil(3/4 batch), ... that
+    holds `active`."""
     k = batch
-    while k > 1 and (k + 1) // 2 >= active:
-        k = (k + 1) // 2
+    while k > 1:
+        nxt = max(1, min(k - 1, (3 * k + 3) // 4))
+        if nxt < active:
+            break
+        k = nxt
     return k
 
 
@@ -540,8 +544,8 @@ def serve(ctx, masks, bs, lams, lam_tvs, params, outs, x0s=None, chunk=64, max_o
     ctx.run_steps, each one graph of `chunk` macro steps), "loads",
     "retires" and "moves"; pcg_steps (a list of len(bs), optional) receives
     the PCG steps of every slice.  With compact, once the queue is empty and
-    at most half of the launched slots still run, the running slices move to
-    the lowest slots and only those are launched (a halving bucket of slots);
+    fewer slots than a smaller bucket holds still run, the running slices move to
+    the lowest slots and only those are launched (buckets shrinking by 3/4);
     a slice's results do not depend on its slot.
     """
     cnt = counters if counters is not None else {}

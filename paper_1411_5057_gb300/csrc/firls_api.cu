@@ -285,6 +285,13 @@ PcgSched pcg_sched(const firls_params& sc) {
   return PcgSched{sc.pcg_tol, sc.pcg_tol_kind, sc.pcg_iters, sc.pcg_iters_late, sc.outer_late};
 }
 
+// alpha inside the ILU kernel (one launch fewer per macro step): the TV
+// preconditioners with one contrast per image
+bool alpha_in_ilu(const firls_ctx* c, const firls_params& sc) {
+  return has_tv(c) && c->channels == 1 &&
+         (sc.precond == FIRLS_PRECOND_PAPER || sc.precond == FIRLS_PRECOND_ILU0);
+}
+
 // Residual update and z = P^{-1} r, then rho (first residual) or beta and the
 // PCG stop.  mode ILU_INIT: the first residual r = A^H b - q for every
 // running slice; ILU_PER_SLICE: each slice by its phase.  x updates go to dx.
@@ -314,8 +321,9 @@ void enqueue_precond(firls_ctx* c, int mode, const firls_params& sc) {
       // the tuned ring shape for the whole batch, the default one for the
       // fewer slots of a compacted launch (every shape gives the same sums)
       const int shape = (c->tune_ilu && B == c->batch) ? c->tune_ilu : ilu_default_shape(n, B, is_aniso(c));
+      const int alpha_np = (mode == ILU_PER_SLICE && alpha_in_ilu(c, sc)) ? fft_row_ctas(n) : 0;
       ilu_step(B, n, c->stream, c->st, c->part, mode, c->dx, c->d, c->r, c->q, c->atb, c->u, c->z, c->ia, c->wtv,
-               shape, fuse ? 1 : 0, ps, c->wait_test, tv2_of(c));
+               shape, fuse ? 1 : 0, ps, c->wait_test, tv2_of(c), alpha_np);
     }
     if (!fuse) {
       TMark m(c, FIRLS_K_SCALARS, 1);
@@ -361,7 +369,7 @@ void enqueue_macro(firls_ctx* c, const firls_params& sc, bool boundary_stage = t
     enqueue_weights(c, c->x, sc.precond, c->stw);
   }
   enqueue_S(c, -1, c->z, c->d, c->q);
-  {
+  if (!alpha_in_ilu(c, sc)) {
     TMark m(c, FIRLS_K_SCALARS, 1);
     pcg_alpha(B, c->stream, c->st, c->part, fft_row_ctas(n), c->channels);
   }

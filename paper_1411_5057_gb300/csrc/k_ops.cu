@@ -1512,12 +1512,28 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
           float2* __restrict__ x, const float2* __restrict__ d, float2* __restrict__ r,
           const float2* __restrict__ q, const float2* __restrict__ atb, float2* __restrict__ y,
           float2* __restrict__ z, const float* __restrict__ ia, const float* __restrict__ wtv, int fuse,
-          PcgSched ps, int wait_test, const float* __restrict__ wtv2) {
+          PcgSched ps, int wait_test, const float* __restrict__ wtv2, int alpha_np) {
   const int s = blockIdx.x;
   if (!slice_running(st, s)) return;
   // ILU_PER_SLICE: the first residual for a slice at the start of its outer
   // step, a PCG step otherwise
-  const int ph = st[s].phase;
+  int ph = st[s].phase;
+  if (alpha_np > 0 && mode_arg == ILU_PER_SLICE && ph == PH_PCG) {
+    // alpha = rho / <d, S d> from the S apply's alpha_np partial sums, as the
+    // scalar kernel forms it (same order); a slice that stops here (rho = 0
+    // or a breakdown) does nothing more in this macro step
+    __shared__ int ph_alpha;
+    if (threadIdx.x == 0) {
+      const double* pp = part + ((size_t)s * NSLOT + SLOT_DQ) * MAXPART;
+      double dq = 0.0;
+      for (int i = 0; i < alpha_np; ++i) dq += pp[i];
+      pcg_alpha_from(st + s, dq);
+      ph_alpha = st[s].done ? -1 : st[s].phase;
+    }
+    __syncthreads();
+    if (ph_alpha < 0) return;
+    ph = ph_alpha;
+  }
   if (mode_arg == ILU_PER_SLICE && !slice_working(ph)) return;
   const int mode = mode_arg != ILU_PER_SLICE ? mode_arg : (ph == PH_START ? ILU_INIT : ILU_STEP);
   // wait_test (failure-detection test only): the producer issues no copy and
@@ -1834,7 +1850,7 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
 
 typedef void (*IluKernel)(int, int, int, IwLayout, SliceState*, double*, float2*, const float2*, float2*,
                           const float2*, const float2*, float2*, float2*, const float*, const float*, int, PcgSched,
-                          int, const float*);
+                          int, const float*, int);
 template <int G>
 static IluKernel ilu_kernel_g(int E) {
   switch (E) {
@@ -1893,13 +1909,14 @@ bool ilu_shape_fits(int n, int shape, bool aniso) {
 void ilu_step(int batch, int n, cudaStream_t s, SliceState* st, double* part, int mode, float2* x,
               const float2* d, float2* r, const float2* q, const float2* atb, float2* y, float2* z,
               const float* ia, const float* wtv, int shape, int fuse_scalars, PcgSched ps, int wait_test,
-              const float* wtv2) {
+              const float* wtv2, int alpha_np) {
   const bool aniso = wtv2 != nullptr;
   if (shape <= 0 || !ilu_shape_fits(n, shape, aniso)) shape = ilu_default_shape(n, batch, aniso);
   const int G = shape / 10, S = shape % 10;
   const IwLayout lay = iw_layout(n, G, aniso);
   ilu_kernel(n, G)<<<batch, IW_THREADS, (size_t)S * lay.bytes, s>>>(n, mode, S, lay, st, part, x, d, r, q, atb, y,
-                                                                     z, ia, wtv, fuse_scalars, ps, wait_test, wtv2);
+                                                                     z, ia, wtv, fuse_scalars, ps, wait_test, wtv2,
+                                                                     alpha_np);
 }
 
 // =========================================================== PCG vectors ==

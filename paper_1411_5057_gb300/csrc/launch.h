@@ -101,10 +101,13 @@ enum IluMode { ILU_INIT = 0, ILU_STEP = 1, ILU_LAST = 2, ILU_PER_SLICE = -1 };
 // shape: shared-memory ring, 10 * rows per stage + stages (0: chosen from n and batch)
 // fuse_scalars: the CTA finishes the PCG scalars itself from its sums (rho
 // at ILU_INIT; rr, the residual test against pcg_tol, beta and rho at ILU_STEP)
+// alpha_np > 0 (ILU_PER_SLICE): the CTA of a slice in PCG first forms alpha
+// from the S apply's alpha_np partial sums of <d, S d> (pcg_alpha's work)
 void ilu_step(int batch, int n, cudaStream_t s, SliceState* st, double* part, int mode,
               float2* x, const float2* d, float2* r, const float2* q, const float2* atb, float2* y,
               float2* z, const float* ia, const float* wtv, int shape, int fuse_scalars = 0,
-              PcgSched ps = PcgSched{0.f, 0, 1 << 30, 0, 0}, int wait_test = 0, const float* wtv2 = nullptr);
+              PcgSched ps = PcgSched{0.f, 0, 1 << 30, 0, 0}, int wait_test = 0, const float* wtv2 = nullptr,
+              int alpha_np = 0);
 // aniso: the ring stages also hold the second weight array of l1 TV
 int ilu_default_shape(int n, int batch, bool aniso = false);
 bool ilu_shape_fits(int n, int shape, bool aniso = false);
