@@ -221,11 +221,12 @@ def run_ours(args):
                            chunk=SERVE_CHUNK, pcg_steps=pcg_counts,
                            stop_after=S - B if args.steady else None, counters=counters)
 
-    def serve_queue(ml, bl, xl, pcg, x0s=None):
-        """Another queue through the same slots and schedule (drained)."""
+    def serve_queue(ml, bl, xl, pcg, x0s=None, stop_after=None):
+        """Another queue through the same slots and schedule (drained, or
+        stopped after `stop_after` completions)."""
         with torch.cuda.stream(stream):
             return F.serve(ctx, ml, bl, [LAM_W] * len(ml), [LAM_TV] * len(ml), params, xl, x0s=x0s,
-                           max_outer=args.outer, chunk=SERVE_CHUNK, pcg_steps=pcg)
+                           max_outer=args.outer, chunk=SERVE_CHUNK, pcg_steps=pcg, stop_after=stop_after)
 
     # ---- device-resident throughput: continuous batching over S slices ----
     for _ in range(args.warmup):
@@ -385,8 +386,9 @@ def run_ours(args):
         learned = run_learned(args, F, torch, stream, B, rank, world, dist, serve_queue)
         print(f"[bench] learned vs plain on {learned['heldout_slices']} held-out slices: "
               f"{learned['value']} vs {learned['plain_value']} recons/s ({learned['vs_plain']}x), "
-              f"PCG steps {learned['mean_pcg_steps']} vs {learned['plain_mean_pcg_steps']}", file=sys.stderr,
-              flush=True)
+              f"PCG steps {learned['mean_pcg_steps']} vs {learned['plain_mean_pcg_steps']}; steady state "
+              f"{learned['steady']['value']} vs {learned['steady']['plain_value']} ({learned['steady']['vs_plain']}x)",
+              file=sys.stderr, flush=True)
 
     out = None
     if rank == 0:
@@ -456,10 +458,10 @@ def run_learned(args, F, torch, stream, B, rank, world, dist, serve_queue):
     kept = [0]
     pcg_plain, pcg_learned = [0] * H, [0] * H
 
-    def plain_step():
-        return serve_queue(ml, bl, xl, pcg_plain)
+    def plain_step(stop_after=None):
+        return serve_queue(ml, bl, xl, pcg_plain, stop_after=stop_after)
 
-    def learned_step():
+    def learned_step(stop_after=None):
         kept[0] = 0
         with torch.cuda.stream(stream):
             for i in range(0, H, Bc):
@@ -468,7 +470,7 @@ def run_learned(args, F, torch, stream, B, rank, world, dist, serve_queue):
                 xs, chosen = Lr.warm_start(prep, inf, b[i:i + Bc], atb, masks[i:i + Bc], one)
                 x0[i:i + Bc].copy_(xs)
                 kept[0] += int(sum(chosen))
-        return serve_queue(ml, bl, xl, pcg_learned, x0s=list(x0))
+        return serve_queue(ml, bl, xl, pcg_learned, x0s=list(x0), stop_after=stop_after)
 
     def timed(fn):
         fn()  # warm-up
@@ -486,6 +488,19 @@ def run_learned(args, F, torch, stream, B, rank, world, dist, serve_queue):
 
     ms_p, st_p, acc_p = timed(plain_step)
     ms_l, st_l, acc_l = timed(learned_step)
+
+    # steady state: the completions while the queue still refills every slot
+    # (the learned pass includes the CNN start of all H slices)
+    def steady(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        fn(stop_after=H - B)
+        e1.record(stream)
+        e1.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+
+    sms_p, sms_l = steady(plain_step), steady(learned_step)
     inf.close()
     prep.close()
     v_p, v_l = world * H / (ms_p / 1e3), world * H / (ms_l / 1e3)
@@ -499,7 +514,10 @@ def run_learned(args, F, torch, stream, B, rank, world, dist, serve_queue):
             "mean_outer_steps": round(float(st_l.mean()), 2), "plain_mean_outer_steps": round(float(st_p.mean()), 2),
             "max_outer_steps": int(st_l.max()), "plain_max_outer_steps": int(st_p.max()),
             "kept_cnn_start": kept[0], "train_instances": args.learned_train, "train_epochs": args.learned_epochs,
-            "setup_s": round(train_s, 1), "accuracy": acc_l, "plain_accuracy": acc_p}
+            "setup_s": round(train_s, 1), "accuracy": acc_l, "plain_accuracy": acc_p,
+            "steady": {"completions": H - B, "value": round(world * (H - B) / (sms_l / 1e3), 3),
+                       "plain_value": round(world * (H - B) / (sms_p / 1e3), 3), "vs_plain": round(sms_p / sms_l, 4),
+                       "counted": "slices completed while the queue refills every slot (one pass each)"}}
 
 
 XSTAR_DIR = os.path.join(ROOT, "tests", "golden", "xstar_tv_db4_256")
