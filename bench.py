@@ -315,7 +315,10 @@ def run_ours(args):
 
     # ---- the same queue with the ILU(0) variant of the TV preconditioner ----
     ilu0 = None
-    if args.ilu0_variant and args.precond == "paper":
+    # the measurements beside the main line run at N = 1 (the scaling runs time
+    # the main line only)
+    aux = world == 1
+    if aux and args.ilu0_variant and args.precond == "paper":
         p_ilu = F.make_params(args.outer, args.inner, lam=LAM_W, lam_tv=LAM_TV, outer_tol=args.outer_tol,
                               stop_on_distance=True, stall_tol=args.stall_tol, pcg_late=ILU0_INNER_LATE,
                               outer_late=args.outer_late, boundary_period=args.boundary_period, precond="ilu0")
@@ -348,33 +351,33 @@ def run_ours(args):
               flush=True)
 
     # ---- preconditioner comparison (PCG iteration counts, untimed) ----
-    pcg_iters = precond_comparison(F, torch, stream) if args.precond_cmp else None
+    pcg_iters = precond_comparison(F, torch, stream) if aux and args.precond_cmp else None
     if pcg_iters is not None:
         print("[bench] PCG steps to 1e-6: " + json.dumps({k: v for k, v in pcg_iters.items()
                                                            if isinstance(v, dict)}), file=sys.stderr, flush=True)
 
     # ---- the uneven batch (four sizes in one graph), untimed w.r.t. the main line ----
-    c4 = uneven_batch_run(F, torch, args) if args.uneven else None
+    c4 = uneven_batch_run(F, torch, args) if aux and args.uneven else None
     if c4 is not None:
         print(f"[bench] uneven batch: {c4['value']} recons/s ({c4['s_per_batch']} s per 64 slices), "
               f"accuracy {json.dumps(c4['accuracy'])}", file=sys.stderr, flush=True)
 
     # ---- multi-contrast cross sections (joint sparsity), untimed w.r.t. the main line ----
-    mt = multi_contrast_run(F, torch, args) if args.mt_sets > 0 else None
+    mt = multi_contrast_run(F, torch, args) if aux and args.mt_sets > 0 else None
     if mt is not None:
         print(f"[bench] multi-contrast: {mt['value']} cross sections/s ({mt['s_per_batch']} s per "
               f"{args.mt_sets}), accuracy {json.dumps(mt['accuracy_vs_oracle_same_schedule'])}, "
               f"SNR {mt['snr_db_mean']} dB", file=sys.stderr, flush=True)
 
     # ---- overlapping tree groups at 512^2, untimed w.r.t. the main line ----
-    tree = tree_run(F, torch, args) if args.tree_slices > 0 else None
+    tree = tree_run(F, torch, args) if aux and args.tree_slices > 0 else None
     if tree is not None:
         print(f"[bench] tree groups 512^2: {tree['value']} recons/s ({tree['s_per_batch']} s per "
               f"{args.tree_slices}), accuracy {json.dumps(tree['accuracy_vs_oracle_same_schedule'])}, "
               f"SNR {tree['snr_db_mean']} dB", file=sys.stderr, flush=True)
 
     # ---- dense random projections (Sec. 5.3), untimed w.r.t. the main line ----
-    dense = dense_run(F, torch, args) if args.dense_problems > 0 else None
+    dense = dense_run(F, torch, args) if aux and args.dense_problems > 0 else None
     if dense is not None:
         print(f"[bench] dense A: {dense['value']} problems/s ({dense['us_per_pcg_step']} us per PCG step), rows "
               f"{dense['roofline_rows']['achieved']} GB/s ({dense['roofline_rows']['frac']} of peak), accuracy "
@@ -382,7 +385,7 @@ def run_ours(args):
 
     # ---- learned warm start (CNN trained on solver-generated pairs) ----
     learned = None
-    if args.learned:
+    if aux and args.learned:
         learned = run_learned(args, F, torch, stream, B, rank, world, dist, serve_queue)
         print(f"[bench] learned vs plain on {learned['heldout_slices']} held-out slices: "
               f"{learned['value']} vs {learned['plain_value']} recons/s ({learned['vs_plain']}x), "
