@@ -591,7 +591,7 @@ def uneven_batch_run(F, torch, args, reps=2):
         ps.append(F.make_params(args.outer, args.inner, lam_per_slice=[p.lam for p in probs],
                                 lam_tv_per_slice=[p.lam_tv for p in probs], outer_tol=args.outer_tol,
                                 stop_on_distance=True, stall_tol=args.stall_tol, pcg_late=args.inner_late,
-                                outer_late=args.outer_late))
+                                outer_late=args.outer_late, boundary_period=args.boundary_period))
     torch.cuda.synchronize()
     F.solve_multi(ctxs, bs, ps, outs)
     torch.cuda.synchronize()

@@ -204,8 +204,10 @@ firls_status firls_solve(firls_ctx* ctx, const void* b, const firls_params* para
  * together: one outer step of every context is captured as ONE CUDA graph
  * (forked from ctxs[0]'s stream onto each context's own stream and joined
  * back) and replayed outer_iters times on ctxs[0]'s stream.  Arrays have
- * n_ctx entries, params included (per-context lambdas); the schedule and
- * tolerances must be equal in all of them (boundary_period 0 or 1).  Contexts must have distinct,
+ * n_ctx entries, params included (per-context lambdas); the schedule,
+ * tolerances and boundary_period must be equal in all of them (with
+ * boundary_period P > 1 the captured outer step holds a boundary stage every
+ * P-th macro step, as in firls_solve).  Contexts must have distinct,
  * non-default streams for the graph; otherwise the steps are enqueued
  * directly.  Same buffer rules as firls_solve; results are ordered on
  * ctxs[0]'s stream.  stats (host, may be NULL) has n_ctx entries. */

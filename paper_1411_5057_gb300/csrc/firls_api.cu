@@ -805,7 +805,6 @@ extern "C" firls_status firls_solve_multi(firls_ctx* const* ctxs, int n_ctx, con
     TRY(check_params(c, &pa[i]));
     if (pa[i].outer_iters != p->outer_iters || !same_schedule(pa[i], *p))
       return fail(c, FIRLS_E_INVALID_ARG, "solve_multi: contexts must share the schedule and tolerances");
-    if (period_of(pa[i]) != 1) return fail(c, FIRLS_E_INVALID_ARG, "solve_multi: boundary_period must be 0 or 1");
     if (!c->stream || !c->use_graph) graphable = false;
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == c || (ctxs[j]->stream == c->stream && c->stream)) graphable = false;
@@ -834,7 +833,7 @@ extern "C" firls_status firls_solve_multi(firls_ctx* const* ctxs, int n_ctx, con
   if (!graphable) {
     const long total = solve_steps(p);
     for (long k = 0; k < total; ++k)
-      for (int i = 0; i < n_ctx; ++i) enqueue_macro(ctxs[i], *p);
+      for (int i = 0; i < n_ctx; ++i) enqueue_macro(ctxs[i], *p, k % period_of(*p) == 0);
   } else {
     const bool same = g_multi.exec && same_schedule(g_multi.sched, *p) && (int)g_multi.ctxs.size() == n_ctx &&
                       std::equal(g_multi.ctxs.begin(), g_multi.ctxs.end(), ctxs);
@@ -856,7 +855,7 @@ extern "C" firls_status firls_solve_multi(firls_ctx* const* ctxs, int n_ctx, con
       for (int i = 1; i < n_ctx; ++i) cudaStreamWaitEvent(ctxs[i]->stream, fork, 0);
       for (int i = 0; i < n_ctx; ++i) {
         if (ctxs[i]->timing) marks_reset(ctxs[i]);
-        for (int k = 0; k < chunk; ++k) enqueue_macro(ctxs[i], *p);
+        for (int k = 0; k < chunk; ++k) enqueue_macro(ctxs[i], *p, k % period_of(*p) == 0);
       }
       for (int i = 1; i < n_ctx; ++i) {
         cudaEventRecord(join[i], ctxs[i]->stream);
@@ -909,7 +908,7 @@ extern "C" firls_status firls_solve_multi(firls_ctx* const* ctxs, int n_ctx, con
         if (i > 0) cudaStreamWaitEvent(c->stream, fork, 0);
         const bool t = c->timing;
         c->timing = false;
-        for (long k = 0; k < rem; ++k) enqueue_macro(c, *p);
+        for (long k = 0; k < rem; ++k) enqueue_macro(c, *p);  // each with its boundary stage
         c->timing = t;
         c->marks_valid = t;
         if (i > 0) {

@@ -52,6 +52,28 @@ def test_uneven_graph_matches_separate_solves(F):
             assert torch.equal(a, r)
 
 
+def test_uneven_graph_with_boundary_period(F):
+    """Outer-step transitions every 8th macro step in the multi-context
+    graph: every slice computes what it computes when each context is solved
+    alone with a transition in every macro step (same x, bit for bit)."""
+    groups = _groups()
+    ctxs = [_ctx(F, probs, torch.cuda.Stream()) for probs in groups]
+    bs = [torch.from_numpy(np.stack([p.b for p in probs])).to(torch.complex64).cuda() for probs in groups]
+
+    def prm(probs, period):
+        return F.make_params(30, 20, lam_per_slice=[p.lam for p in probs], lam_tv_per_slice=[p.lam_tv for p in probs],
+                             outer_tol=1e-4, stop_on_distance=False, boundary_period=period)
+
+    torch.cuda.synchronize()
+    ref = [c.solve(b, prm(g, 1)).clone() for c, b, g in zip(ctxs, bs, groups)]
+    torch.cuda.synchronize()
+    outs = [torch.empty_like(b) for b in bs]
+    F.solve_multi(ctxs, bs, [prm(g, 8) for g in groups], outs)
+    torch.cuda.synchronize()
+    for a, r in zip(outs, ref):
+        assert torch.equal(a, r)
+
+
 def test_uneven_batch_reaches_converged_oracle(F):
     """The first slice of each size (seeds 1000, 1016, 1032, 1048: 128^2 ..
     320^2 TV + D4 with their own lambdas and masks), solved together by
@@ -69,7 +91,8 @@ def test_uneven_batch_reaches_converged_oracle(F):
     bs = [torch.from_numpy(np.stack([p.b for p in g])).to(torch.complex64).cuda() for g in groups]
     ps = [F.make_params(bench.OUTER, bench.INNER, lam_per_slice=[p.lam for p in g],
                         lam_tv_per_slice=[p.lam_tv for p in g], outer_tol=bench.OUTER_TOL, stop_on_distance=True,
-                        stall_tol=bench.STALL_TOL, pcg_late=bench.INNER_LATE, outer_late=bench.OUTER_LATE)
+                        stall_tol=bench.STALL_TOL, pcg_late=bench.INNER_LATE, outer_late=bench.OUTER_LATE,
+                        boundary_period=bench.BOUNDARY_PERIOD)
           for g in groups]
     outs = [torch.empty_like(b) for b in bs]
     torch.cuda.synchronize()
