@@ -570,47 +570,49 @@ def serve(ctx, masks, bs, lams, lam_tvs, params, outs, x0s=None, chunk=64, max_o
     run.outer_iters = 1
     active = sum(1 for v in slot_of if v >= 0)
     completed = 0
-    while active:
-        if stop_after is not None and completed >= stop_after:
+    try:
+        while active:
+            if stop_after is not None and completed >= stop_after:
+                for s in range(ctx.batch):
+                    if slot_of[s] >= 0:
+                        ctx.slot_retire(s)
+                        cnt["retires"] += 1
+                        slot_of[s] = -1
+                break
+            ctx.run_steps(run, chunk)
+            cnt["runs"] += 1
+            done, od, _, pc = ctx.slot_status(with_pcg=True)
             for s in range(ctx.batch):
-                if slot_of[s] >= 0:
+                i = slot_of[s]
+                if i < 0 or not (done[s] or od[s] >= max_outer):
+                    continue
+                ctx.slot_get(s, outs[i])
+                steps[i] = od[s]
+                if pcg_steps is not None:
+                    pcg_steps[i] = pc[s]
+                completed += 1
+                if nxt < q:
+                    ctx.slot_load(s, masks[nxt], bs[nxt], lams[nxt], lam_tvs[nxt], None if x0s is None else x0s[nxt])
+                    cnt["loads"] += 1
+                    slot_of[s] = nxt
+                    nxt += 1
+                else:
                     ctx.slot_retire(s)
                     cnt["retires"] += 1
                     slot_of[s] = -1
-            break
-        ctx.run_steps(run, chunk)
-        cnt["runs"] += 1
-        done, od, _, pc = ctx.slot_status(with_pcg=True)
-        for s in range(ctx.batch):
-            i = slot_of[s]
-            if i < 0 or not (done[s] or od[s] >= max_outer):
-                continue
-            ctx.slot_get(s, outs[i])
-            steps[i] = od[s]
-            if pcg_steps is not None:
-                pcg_steps[i] = pc[s]
-            completed += 1
-            if nxt < q:
-                ctx.slot_load(s, masks[nxt], bs[nxt], lams[nxt], lam_tvs[nxt], None if x0s is None else x0s[nxt])
-                cnt["loads"] += 1
-                slot_of[s] = nxt
-                nxt += 1
-            else:
-                ctx.slot_retire(s)
-                cnt["retires"] += 1
-                slot_of[s] = -1
-                active -= 1
-        if compact and nxt >= q and active:
-            k = _bucket(ctx.batch, active)
-            if k < launched:
-                free = [t for t in range(k) if slot_of[t] < 0]
-                for src in range(k, launched):
-                    if slot_of[src] >= 0:
-                        dst = free.pop()
-                        ctx.slot_move(src, dst)
-                        cnt["moves"] += 1
-                        slot_of[dst], slot_of[src] = slot_of[src], -1
-                launched = k
-                ctx.set_active_slots(k)
-    ctx.set_active_slots(0)
+                    active -= 1
+            if compact and nxt >= q and active:
+                k = _bucket(ctx.batch, active)
+                if k < launched:
+                    free = [t for t in range(k) if slot_of[t] < 0]
+                    for src in range(k, launched):
+                        if slot_of[src] >= 0:
+                            dst = free.pop()
+                            ctx.slot_move(src, dst)
+                            cnt["moves"] += 1
+                            slot_of[dst], slot_of[src] = slot_of[src], -1
+                    launched = k
+                    ctx.set_active_slots(k)
+    finally:
+        ctx.set_active_slots(0)
     return steps
