@@ -10,6 +10,7 @@
 // next direction), including the end of the outer step.  FP32 operators,
 // FP64 inner products and PCG scalars (the SliceState helpers shared with the
 // Fourier path).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -333,10 +334,142 @@ __global__ void k_dense_abar(int N, const float* __restrict__ dAtA, float* __res
   }
 }
 
+// ---- shared matrix: S d for all problems as two register-tiled GEMMs ----
+// With one A for every problem, A^T A d_p for all p is T = D A^T (P x M)
+// then Q = T A (P x N): dense contractions in which a loaded tile of A serves
+// 64 problems.  C[m][n] = sum_k X[m][k] Y(k, n) over one split of K, X
+// row-major with K contiguous; Y(k, n) = B[n ldb + k] (YT) or B[k ldb + n].
+// A CTA computes a 64 x 128 tile (each thread 4 x 8 outputs) from 16-deep
+// slabs staged in shared memory, the next slab's loads in flight while the
+// current one is used.  FP32 throughout; the split partials are summed in
+// split order by the next stage.
+constexpr int GM = 64, GN = 128, GK = 16, GT = 256;
+constexpr int kGemmCtasPerSm = 4;  // splits of K until each product has about this many CTAs per SM
+
+template <bool YT>
+__global__ void __launch_bounds__(GT) k_dense_gemm(int Mg, int Ng, int K, int kper, const float* __restrict__ X,
+                                                   int ldx, const float* __restrict__ B, int ldb,
+                                                   float* __restrict__ C, int ldc, size_t split_stride) {
+  __shared__ __align__(16) float Xs[2][GK][GM + 4];
+  __shared__ __align__(16) float Ys[2][GK][GN + 4];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int bm = blockIdx.y * GM, bn = blockIdx.x * GN, sp = blockIdx.z;
+  const int k0 = sp * kper, k1 = min(K, k0 + kper);
+  float acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  float4 px, py[2];
+  // X slab: 64 rows x 16 k, one float4 (4 k) per thread
+  auto load_x = [&](int k) {
+    const int row = tid / 4, kq = (tid % 4) * 4;
+    px = (bm + row < Mg && k + kq < k1) ? *reinterpret_cast<const float4*>(X + (size_t)(bm + row) * ldx + k + kq)
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  auto store_x = [&](int buf) {
+    const int row = tid / 4, kq = (tid % 4) * 4;
+    Xs[buf][kq][row] = px.x;
+    Xs[buf][kq + 1][row] = px.y;
+    Xs[buf][kq + 2][row] = px.z;
+    Xs[buf][kq + 3][row] = px.w;
+  };
+  // Y slab: 16 k x 128 n, two float4 per thread
+  auto load_y = [&](int k) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int idx = tid + GT * h;
+      if (YT) {
+        const int n = idx / 4, kq = (idx % 4) * 4;
+        py[h] = (bn + n < Ng && k + kq < k1) ? *reinterpret_cast<const float4*>(B + (size_t)(bn + n) * ldb + k + kq)
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        const int kk = idx / 32, nq = (idx % 32) * 4;
+        py[h] = (k + kk < k1 && bn + nq < Ng) ? *reinterpret_cast<const float4*>(B + (size_t)(k + kk) * ldb + bn + nq)
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  };
+  auto store_y = [&](int buf) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int idx = tid + GT * h;
+      if (YT) {
+        const int n = idx / 4, kq = (idx % 4) * 4;
+        Ys[buf][kq][n] = py[h].x;
+        Ys[buf][kq + 1][n] = py[h].y;
+        Ys[buf][kq + 2][n] = py[h].z;
+        Ys[buf][kq + 3][n] = py[h].w;
+      } else {
+        const int kk = idx / 32, nq = (idx % 32) * 4;
+        *reinterpret_cast<float4*>(&Ys[buf][kk][nq]) = py[h];
+      }
+    }
+  };
+  int buf = 0;
+  if (k0 < k1) {
+    load_x(k0);
+    load_y(k0);
+    store_x(0);
+    store_y(0);
+  }
+  __syncthreads();
+  for (int k = k0; k < k1; k += GK) {
+    const bool more = k + GK < k1;
+    if (more) {  // the next slab's loads fly while this one is multiplied
+      load_x(k + GK);
+      load_y(k + GK);
+    }
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      const float4 a = *reinterpret_cast<const float4*>(&Xs[buf][kk][ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Ys[buf][kk][tx * 8]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Ys[buf][kk][tx * 8 + 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (more) {
+      store_x(buf ^ 1);
+      store_y(buf ^ 1);
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+  float* Cs = C + (size_t)sp * split_stride;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = bm + ty * 4 + i;
+    if (m >= Mg) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int n = bn + tx * 8 + j;
+      if (n < Ng) Cs[(size_t)m * ldc + n] = acc[i][j];
+    }
+  }
+}
+
+// T[p][i] = sum over the splits of Tpart[s][p][i] (split order).
+__global__ void k_dense_sum_splits(int count, int S, const float* __restrict__ part, float* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    float a = 0.f;
+    for (int sp = 0; sp < S; ++sp) a += part[(size_t)sp * count + i];
+    out[i] = a;
+  }
+}
+
 }  // namespace
 
 struct firls_dense_ctx {
   int M = 0, N = 0, P = 0, shared = 0, nA = 0, CH = 1;
+  // shared matrix with M % 4 == 0: the GEMM form (S1 splits of K = N in the
+  // first product; CH splits of K = M in the second, the partials of q)
+  bool gemm = false;
+  int S1 = 1;
+  float *tpart = nullptr, *tmat = nullptr;
   cudaStream_t stream = nullptr;
   bool matrix_set = false;
   float *A = nullptr, *dAtA = nullptr, *abar = nullptr;
@@ -389,9 +522,31 @@ int chunks_for(int M, int P) {
   return want < 1 ? 1 : (want > cap ? cap : want);
 }
 
+// q partials of A^T A v (or A^T b) per problem.  The GEMM form computes them
+// for every problem (the PCG kernel reads only the problems it serves).
 void launch_rows(firls_dense_ctx* c, int mode, const float* v, const float* b) {
-  rows_kernel(c->N)<<<dim3(c->CH, c->P), RT, 0, c->stream>>>(c->M, c->N, c->CH, c->shared, mode, c->st, c->A, v,
-                                                               b, c->qpart);
+  if (!c->gemm) {
+    rows_kernel(c->N)<<<dim3(c->CH, c->P), RT, 0, c->stream>>>(c->M, c->N, c->CH, c->shared, mode, c->st, c->A,
+                                                                 v, b, c->qpart);
+    return;
+  }
+  const int M = c->M, N = c->N, P = c->P;
+  const float* t = c->tmat;
+  if (mode == DR_ATB) {
+    cudaMemcpyAsync(c->tmat, b, sizeof(float) * (size_t)P * M, cudaMemcpyDeviceToDevice, c->stream);
+  } else {
+    // T = V A^T over S1 splits of N, then their sum
+    const int kper1 = ((N + c->S1 - 1) / c->S1 + GK - 1) / GK * GK;
+    k_dense_gemm<true><<<dim3((M + GN - 1) / GN, (P + GM - 1) / GM, c->S1), GT, 0, c->stream>>>(
+        P, M, N, kper1, v, N, c->A, N, c->tpart, M, (size_t)P * M);
+    const int cnt = P * M;
+    k_dense_sum_splits<<<(cnt + 255) / 256 < 1024 ? (cnt + 255) / 256 : 1024, 256, 0, c->stream>>>(cnt, c->S1,
+                                                                                                    c->tpart, c->tmat);
+  }
+  // q partials = T A over CH splits of M: partial s of problem p at qpart[(p CH + s) N]
+  const int kper2 = ((M + c->CH - 1) / c->CH + GK - 1) / GK * GK;
+  k_dense_gemm<false><<<dim3((N + GN - 1) / GN, (P + GM - 1) / GM, c->CH), GT, 0, c->stream>>>(
+      P, N, M, kper2, t, M, c->A, N, c->qpart, c->CH * N, (size_t)N);
 }
 
 void launch_pcg(firls_dense_ctx* c, int mode, int precond, const PcgSched& ps, float outer_tol) {
@@ -441,6 +596,15 @@ extern "C" firls_status firls_dense_create(firls_dense_ctx** out, int M, int N, 
   c->nA = c->shared ? 1 : problems;
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   c->CH = chunks_for(M, problems);
+  c->gemm = c->shared && M % 4 == 0;
+  if (c->gemm) {  // enough CTAs in both products: splits of K
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int tiles1 = ((M + GN - 1) / GN) * ((problems + GM - 1) / GM);
+    const int tiles2 = ((N + GN - 1) / GN) * ((problems + GM - 1) / GM);
+    c->S1 = std::max(1, std::min((kGemmCtasPerSm * sms + tiles1 - 1) / tiles1, std::max(1, N / (4 * GK))));
+    c->CH = std::max(1, std::min((kGemmCtasPerSm * sms + tiles2 - 1) / tiles2, std::max(1, M / (4 * GK))));
+  }
   const size_t PN = (size_t)problems * N;
   firls_status s = FIRLS_OK;
   auto al = [&](auto** p, size_t n) {
@@ -452,6 +616,10 @@ extern "C" firls_status firls_dense_create(firls_dense_ctx** out, int M, int N, 
   al(&c->abar64, (size_t)c->nA);
   for (float** v : {&c->atb, &c->x, &c->dx, &c->r, &c->z, &c->d, &c->q, &c->w, &c->pinv}) al(v, PN);
   al(&c->qpart, PN * c->CH);
+  if (c->gemm) {
+    al(&c->tpart, (size_t)c->S1 * problems * M);
+    al(&c->tmat, (size_t)problems * M);
+  }
   al(&c->lam, (size_t)problems);
   al(&c->st, (size_t)problems);
   if (s != FIRLS_OK) {
