@@ -339,71 +339,62 @@ __global__ void k_dense_abar(int N, const float* __restrict__ dAtA, float* __res
 // then Q = T A (P x N): dense contractions in which a loaded tile of A serves
 // 64 problems.  C[m][n] = sum_k X[m][k] Y(k, n) over one split of K, X
 // row-major with K contiguous; Y(k, n) = B[n ldb + k] (YT) or B[k ldb + n].
-// A CTA computes a 64 x 128 tile (each thread 4 x 8 outputs) from 16-deep
+// A CTA computes a 128 x 128 tile (each thread 8 x 8 outputs) from 8-deep
 // slabs staged in shared memory, the next slab's loads in flight while the
 // current one is used.  FP32 throughout; the split partials are summed in
 // split order by the next stage.
-constexpr int GM = 64, GN = 128, GK = 16, GT = 256;
+constexpr int GM = 128, GN = 128, GK = 8, GT = 256;
 constexpr int kGemmCtasPerSm = 4;  // splits of K until each product has about this many CTAs per SM
 
 template <bool YT>
-__global__ void __launch_bounds__(GT) k_dense_gemm(int Mg, int Ng, int K, int kper, const float* __restrict__ X,
-                                                   int ldx, const float* __restrict__ B, int ldb,
-                                                   float* __restrict__ C, int ldc, size_t split_stride) {
+__global__ void __launch_bounds__(GT, 2) k_dense_gemm(int Mg, int Ng, int K, int kper, const float* __restrict__ X,
+                                                      int ldx, const float* __restrict__ B, int ldb,
+                                                      float* __restrict__ C, int ldc, size_t split_stride) {
   __shared__ __align__(16) float Xs[2][GK][GM + 4];
   __shared__ __align__(16) float Ys[2][GK][GN + 4];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   const int bm = blockIdx.y * GM, bn = blockIdx.x * GN, sp = blockIdx.z;
   const int k0 = sp * kper, k1 = min(K, k0 + kper);
-  float acc[4][8];
+  float acc[8][8];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-  float4 px, py[2];
-  // X slab: 64 rows x 16 k, one float4 (4 k) per thread
+  float4 px, py;
+  // X slab: 128 rows x 8 k, one float4 (4 k) per thread
+  const int xr = tid / 2, xk = (tid % 2) * 4;
   auto load_x = [&](int k) {
-    const int row = tid / 4, kq = (tid % 4) * 4;
-    px = (bm + row < Mg && k + kq < k1) ? *reinterpret_cast<const float4*>(X + (size_t)(bm + row) * ldx + k + kq)
-                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+    px = (bm + xr < Mg && k + xk < k1) ? *reinterpret_cast<const float4*>(X + (size_t)(bm + xr) * ldx + k + xk)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
   };
   auto store_x = [&](int buf) {
-    const int row = tid / 4, kq = (tid % 4) * 4;
-    Xs[buf][kq][row] = px.x;
-    Xs[buf][kq + 1][row] = px.y;
-    Xs[buf][kq + 2][row] = px.z;
-    Xs[buf][kq + 3][row] = px.w;
+    Xs[buf][xk][xr] = px.x;
+    Xs[buf][xk + 1][xr] = px.y;
+    Xs[buf][xk + 2][xr] = px.z;
+    Xs[buf][xk + 3][xr] = px.w;
   };
-  // Y slab: 16 k x 128 n, two float4 per thread
+  // Y slab: 8 k x 128 n, one float4 per thread
   auto load_y = [&](int k) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int idx = tid + GT * h;
-      if (YT) {
-        const int n = idx / 4, kq = (idx % 4) * 4;
-        py[h] = (bn + n < Ng && k + kq < k1) ? *reinterpret_cast<const float4*>(B + (size_t)(bn + n) * ldb + k + kq)
-                                             : make_float4(0.f, 0.f, 0.f, 0.f);
-      } else {
-        const int kk = idx / 32, nq = (idx % 32) * 4;
-        py[h] = (k + kk < k1 && bn + nq < Ng) ? *reinterpret_cast<const float4*>(B + (size_t)(k + kk) * ldb + bn + nq)
-                                              : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
+    if (YT) {
+      const int n = tid / 2, kq = (tid % 2) * 4;
+      py = (bn + n < Ng && k + kq < k1) ? *reinterpret_cast<const float4*>(B + (size_t)(bn + n) * ldb + k + kq)
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      const int kk = tid / 32, nq = (tid % 32) * 4;
+      py = (k + kk < k1 && bn + nq < Ng) ? *reinterpret_cast<const float4*>(B + (size_t)(k + kk) * ldb + bn + nq)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   };
   auto store_y = [&](int buf) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int idx = tid + GT * h;
-      if (YT) {
-        const int n = idx / 4, kq = (idx % 4) * 4;
-        Ys[buf][kq][n] = py[h].x;
-        Ys[buf][kq + 1][n] = py[h].y;
-        Ys[buf][kq + 2][n] = py[h].z;
-        Ys[buf][kq + 3][n] = py[h].w;
-      } else {
-        const int kk = idx / 32, nq = (idx % 32) * 4;
-        *reinterpret_cast<float4*>(&Ys[buf][kk][nq]) = py[h];
-      }
+    if (YT) {
+      const int n = tid / 2, kq = (tid % 2) * 4;
+      Ys[buf][kq][n] = py.x;
+      Ys[buf][kq + 1][n] = py.y;
+      Ys[buf][kq + 2][n] = py.z;
+      Ys[buf][kq + 3][n] = py.w;
+    } else {
+      const int kk = tid / 32, nq = (tid % 32) * 4;
+      *reinterpret_cast<float4*>(&Ys[buf][kk][nq]) = py;
     }
   };
   int buf = 0;
@@ -422,13 +413,14 @@ __global__ void __launch_bounds__(GT) k_dense_gemm(int Mg, int Ng, int K, int kp
     }
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
-      const float4 a = *reinterpret_cast<const float4*>(&Xs[buf][kk][ty * 4]);
+      const float4 a0 = *reinterpret_cast<const float4*>(&Xs[buf][kk][ty * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&Xs[buf][kk][ty * 8 + 4]);
       const float4 b0 = *reinterpret_cast<const float4*>(&Ys[buf][kk][tx * 8]);
       const float4 b1 = *reinterpret_cast<const float4*>(&Ys[buf][kk][tx * 8 + 4]);
-      const float av[4] = {a.x, a.y, a.z, a.w};
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
@@ -441,8 +433,8 @@ __global__ void __launch_bounds__(GT) k_dense_gemm(int Mg, int Ng, int K, int kp
   }
   float* Cs = C + (size_t)sp * split_stride;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int m = bm + ty * 4 + i;
+  for (int i = 0; i < 8; ++i) {
+    const int m = bm + ty * 8 + i;
     if (m >= Mg) continue;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
