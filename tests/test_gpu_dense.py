@@ -186,3 +186,23 @@ def test_dense_errors(F):
     x = ctx.solve(b, F.make_params(2, 2, lam=0.1))                 # b = 0: x = 0 exactly
     assert torch.count_nonzero(x) == 0
     ctx.close()
+
+
+def test_shared_matrix_gemm_ragged_tiles(F):
+    """A shared matrix whose sizes leave ragged tiles in every dimension of
+    both products (200 problems over 128-row tiles, M = 260 and N = 1000 over
+    128-column tiles, K split unevenly): A^T A d against FP64."""
+    P, M, N = 200, 260, 1000
+    rng = np.random.default_rng(21)
+    A = (rng.standard_normal((M, N)) / math.sqrt(M)).astype(np.float32)
+    d = rng.standard_normal((P, N)).astype(np.float32)
+    ctx = F.DenseContext(M, N, P, shared=True)
+    ctx.set_matrix(f32(A))
+    q = torch.empty(P, N, dtype=torch.float32, device="cuda")
+    ctx.apply_AtA(f32(d), q)
+    A64 = A.astype(np.float64)
+    want = (d.astype(np.float64) @ A64.T) @ A64
+    got = q.cpu().numpy().astype(np.float64)
+    for p in range(P):
+        assert rel(got[p], want[p]) < 2e-5, (p, rel(got[p], want[p]))
+    ctx.close()
