@@ -137,3 +137,32 @@ def test_bounded_wait_running_out_is_reported(F):
         x_ref, _ = O.firls_problem(probs[s], outer=2, inner=5)
         assert _rel(x_again[s].cpu().numpy().astype(np.complex128), x_ref) < TOL_SOLVE
     ctx.close()
+
+
+def test_slot_and_dense_arguments_rejected(F):
+    """Slot compaction and the dense solver reject bad arguments before any
+    launch: launched-slot counts outside [0, batch], a slot moved onto
+    itself or out of range, a dense matrix that is not 16-byte aligned, and
+    tensors of the wrong size."""
+    p = _problems(n=32, seeds=(41,))[0]
+    ctx = F.Context(32, batch=3)
+    ctx.set_operator(torch.from_numpy(np.stack([p.mask] * 3)).cuda(), p.psi, p.levels)
+    for k in (-1, 4):
+        with pytest.raises(F.FirlsError):
+            ctx.set_active_slots(k)
+    for a, b in ((1, 1), (0, 3), (-1, 0)):
+        with pytest.raises(F.FirlsError):
+            ctx.slot_move(a, b)
+    ctx.set_active_slots(3)
+    ctx.set_active_slots(0)
+    with pytest.raises(F.FirlsError):   # two slices' worth of k-space for three slots
+        ctx.solve(torch.zeros(2, 32, 32, dtype=torch.complex64, device="cuda"), F.make_params(1, 1, lam=1e-3))
+    ctx.close()
+    dc = F.DenseContext(8, 16, 2)
+    A = torch.randn(2 * 8 * 16 + 1, device="cuda")
+    with pytest.raises(F.FirlsError):
+        dc.set_matrix(A[1:].view(2, 8, 16))      # 4 bytes past an aligned start
+    dc.set_matrix(A[:-1].view(2, 8, 16))
+    with pytest.raises(F.FirlsError):
+        dc.solve(torch.zeros(2, 7, device="cuda"), F.make_params(1, 1, lam=0.1))
+    dc.close()
