@@ -1404,6 +1404,30 @@ FI void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// The same with an L2 eviction policy (a hint: what the ILU reads again in
+// its backward sweep stays, what it streams through goes first).
+FI void bulk_g2s_hint(void* dst, const void* src, unsigned bytes, uint64_t* bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;\n" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+FI uint64_t l2_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+FI uint64_t l2_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+FI void st_hint_f4(float2* dst, float4 v, uint64_t policy) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;\n" ::"l"(dst), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w), "l"(policy)
+               : "memory");
+}
 FI void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;\n" ::: "memory"); }
 FI int ld_acquire(const int* p) {
   int v;
@@ -1446,13 +1470,14 @@ FI float2 warp_affine_exclusive(float A, float2 B) {
   return make_float2(bx, by);
 }
 
-// Store E consecutive complex values of one lane (columns c0 .. c0+E-1 < n).
+// Store E consecutive complex values of one lane (columns c0 .. c0+E-1 < n),
+// with an L2 eviction policy.
 template <int E>
-FI void store_lane_row(float2* dst, int c0, int n, const float2 (&v)[E]) {
+FI void store_lane_row(float2* dst, int c0, int n, const float2 (&v)[E], uint64_t policy) {
   if ((E & 1) == 0 && c0 + E <= n) {
 #pragma unroll
     for (int e = 0; e < E; e += 2)
-      *reinterpret_cast<float4*>(dst + c0 + e) = make_float4(v[e].x, v[e].y, v[e + 1].x, v[e + 1].y);
+      st_hint_f4(dst + c0 + e, make_float4(v[e].x, v[e].y, v[e + 1].x, v[e + 1].y), policy);
   } else {
 #pragma unroll
     for (int e = 0; e < E; ++e)
@@ -1552,6 +1577,9 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
   const float lam = st[s].lam_tv;
   const float alpha = (float)st[s].alpha;
   const size_t base = (size_t)s * n * n;
+  // L2 policies: y, W and 1/a are read again by the backward sweep; the
+  // rest passes through once
+  const uint64_t pol_keep = l2_evict_last(), pol_stream = l2_evict_first();
   if (t == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(&bar_full[i], 1);
@@ -1642,7 +1670,7 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
               v = make_float2(fmaf(cur[e].w, v.x, tv[e].x), fmaf(cur[e].w, v.y, tv[e].y));
               vab[e] = v;
             }
-            store_lane_row<E>(y + base + (size_t)(gg * G + i) * n, E * lane, n, vab);
+            store_lane_row<E>(y + base + (size_t)(gg * G + i) * n, E * lane, n, vab, pol_keep);
           } else {
 #pragma unroll
             for (int e = E - 1; e >= 0; --e) {
@@ -1656,7 +1684,7 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
               v = make_float2(fmaf(cur[e].w, v.x, tv[e].x), fmaf(cur[e].w, v.y, tv[e].y));
               vab[e] = v;
             }
-            store_lane_row<E>(z + base + (size_t)(n - 1 - gg * G - i) * n, E * lane, n, vab);
+            store_lane_row<E>(z + base + (size_t)(n - 1 - gg * G - i) * n, E * lane, n, vab, pol_stream);
           }
         }
         pos.next(S);
@@ -1692,22 +1720,24 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
         if (g < NG) {
           const size_t go = base + (size_t)g * G * n;
           mbar_arrive_tx(bar, (init ? 2 * c8 + 2 * c4 : 4 * c8 + 2 * c4) + cw2);
-          bulk_g2s(sp, rsrc + go, c8, bar);
-          bulk_g2s(sp + lay.oQ, q + go, c8, bar);
+          // streamed once: r, q, x, d; read again by the backward sweep: W, 1/a
+          bulk_g2s_hint(sp, rsrc + go, c8, bar, pol_stream);
+          bulk_g2s_hint(sp + lay.oQ, q + go, c8, bar, pol_stream);
           if (!init) {
-            bulk_g2s(sp + lay.oX, x + go, c8, bar);
-            bulk_g2s(sp + lay.oD, d + go, c8, bar);
+            bulk_g2s_hint(sp + lay.oX, x + go, c8, bar, pol_stream);
+            bulk_g2s_hint(sp + lay.oD, d + go, c8, bar, pol_stream);
           }
-          bulk_g2s(sp + lay.oW, wtv + go, c4, bar);
-          bulk_g2s(sp + lay.oIA, ia + go, c4, bar);
-          if (wtv2) bulk_g2s(sp + lay.oW2, wtv2 + go, c4, bar);
+          bulk_g2s_hint(sp + lay.oW, wtv + go, c4, bar, pol_keep);
+          bulk_g2s_hint(sp + lay.oIA, ia + go, c4, bar, pol_keep);
+          if (wtv2) bulk_g2s_hint(sp + lay.oW2, wtv2 + go, c4, bar, pol_keep);
         } else {
           const size_t go = base + (size_t)(n - (g - NG + 1) * G) * n;
           mbar_arrive_tx(bar, c8 + 2 * c4 + cw2);
-          bulk_g2s(sp, y + go, c8, bar);
-          bulk_g2s(sp + lay.oW, wtv + go, c4, bar);
-          bulk_g2s(sp + lay.oIA, ia + go, c4, bar);
-          if (wtv2) bulk_g2s(sp + lay.oW2, wtv2 + go, c4, bar);
+          // last uses
+          bulk_g2s_hint(sp, y + go, c8, bar, pol_stream);
+          bulk_g2s_hint(sp + lay.oW, wtv + go, c4, bar, pol_stream);
+          bulk_g2s_hint(sp + lay.oIA, ia + go, c4, bar, pol_stream);
+          if (wtv2) bulk_g2s_hint(sp + lay.oW2, wtv2 + go, c4, bar, pol_stream);
         }
         pos.next(S);
       }
@@ -1760,11 +1790,12 @@ __global__ void __launch_bounds__(IW_THREADS, (G == 2 && E <= 10) ? 3 : 1)
                 const float4 d4 = *reinterpret_cast<const float4*>(rowp + lay.oD + 16 * j);
                 rn = make_float4(fmaf(-alpha, q4.x, r4.x), fmaf(-alpha, q4.y, r4.y), fmaf(-alpha, q4.z, r4.z),
                                  fmaf(-alpha, q4.w, r4.w));
-                *reinterpret_cast<float4*>(x + g0) =
-                    make_float4(fmaf(alpha, d4.x, x4.x), fmaf(alpha, d4.y, x4.y), fmaf(alpha, d4.z, x4.z),
-                                fmaf(alpha, d4.w, x4.w));
+                st_hint_f4(x + g0,
+                           make_float4(fmaf(alpha, d4.x, x4.x), fmaf(alpha, d4.y, x4.y), fmaf(alpha, d4.z, x4.z),
+                                       fmaf(alpha, d4.w, x4.w)),
+                           pol_stream);
               }
-              *reinterpret_cast<float4*>(r + g0) = rn;
+              st_hint_f4(r + g0, rn, pol_stream);
               rr_c[ch] += rn.x * rn.x + rn.y * rn.y + rn.z * rn.z + rn.w * rn.w;
               const float* wrow = reinterpret_cast<const float*>(sp + lay.oW + i * nG4);
               const float* arow = reinterpret_cast<const float*>(sp + lay.oIA + i * nG4);
