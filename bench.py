@@ -80,13 +80,10 @@ ALG_BYTES_PER_PX = {
 }
 
 # DRAM bytes per pixel per launch (dram__bytes_read.sum + dram__bytes_write.sum)
-# of the dominant kernel, from a one-kernel ncu capture at 96 slots with the
-# bench's ILU ring shape (profiles/kernels_tv_db4_256_b96.md), scaled to the
-# bench's slots per pixel (the ILU moves the same bytes per slice at any
-# batch), for the kernel as it is now.
-MEASURED_TRAFFIC_PER_PX = {
-    "ilu": 79.2,
-}
+# of the dominant kernel, from a one-pass ncu capture of those two counters on
+# the bench's 304 slots with its ILU ring shape (profiles/kernels_tv_db4_256_b96.md
+# gives the command), for the kernel as it is now: 1.634 GB per launch.
+MEASURED_TRAFFIC_PER_PX = {"ilu": 82.0}
 
 
 def problem(seed):
