@@ -80,10 +80,12 @@ ALG_BYTES_PER_PX = {
 }
 
 # DRAM bytes per pixel per launch (dram__bytes_read.sum + dram__bytes_write.sum)
-# of the dominant kernel, from a one-pass ncu capture of those two counters on
-# the bench's 304 slots with its ILU ring shape (profiles/kernels_tv_db4_256_b96.md
-# gives the command), for the kernel as it is now: 1.634 GB per launch.
-MEASURED_TRAFFIC_PER_PX = {"ilu": 82.0}
+# of the dominant kernel at the bench's 304 slots of 256^2, by the ILU ring
+# shape the autotuner picks, from one-pass ncu captures of those two counters
+# (profiles/kernels_tv_db4_256_b96.md gives the commands), for the kernel as
+# it is now: 1.634 GB per launch with ring 22, 1.618 GB with ring 42.  Other
+# shapes: not measured (traffic null).
+MEASURED_TRAFFIC_PER_PX = {("ilu", 22): 82.0, ("ilu", 42): 81.2}
 
 
 def problem(seed):
@@ -277,7 +279,9 @@ def run_ours(args):
     per_app_s = kt[dom][0] / apps[dom] / 1e3
     alg = ALG_BYTES_PER_PX[dom] * N * N * B
     achieved = alg / per_app_s / 1e9
-    traffic = MEASURED_TRAFFIC_PER_PX[dom] * N * N * B if dom in MEASURED_TRAFFIC_PER_PX and N == 256 else None
+    tkey = (dom, tuning.get("ilu_depth"))
+    traffic = MEASURED_TRAFFIC_PER_PX[tkey] * N * N * B if tkey in MEASURED_TRAFFIC_PER_PX and N == 256 and B == 304 \
+        else None
     for k in ALG_BYTES_PER_PX:  # op-apply bandwidth of every operator class, on algorithmic bytes
         if kt[k][0] > 0 and k in apps:
             kern[k]["alg_gbs"] = round(ALG_BYTES_PER_PX[k] * N * N * B / (kt[k][0] / apps[k] / 1e3) / 1e9, 1)
