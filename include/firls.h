@@ -506,8 +506,10 @@ firls_status firls_apply_AHA_noalloc(int n, int batch, const uint8_t* mask, cons
  * N % 4 == 0 (rows are read as 16-byte vectors; A 16-byte aligned),
  * problems >= 1 (FIRLS_E_SHAPE otherwise).  Operators run in FP32; the PCG
  * inner products, alpha, beta, rho, the residual norms and the relative change
- * in FP64.  Each step S d = A^T (A d) + lambda W d streams A once: a row's
- * product with d is formed and immediately scattered back along the row. */
+ * in FP64.  With a matrix per problem each step S d = A^T (A d) + lambda W d
+ * streams A once (a row's product with d is formed and immediately scattered
+ * back along the row); with a shared matrix and M % 4 == 0, A^T A d for all
+ * problems is two register-tiled GEMMs, T = D A^T and Q = T A. */
 typedef struct firls_dense_ctx firls_dense_ctx;
 
 firls_status firls_dense_create(firls_dense_ctx** out, int M, int N, int problems, int shared_matrix,
