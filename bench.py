@@ -990,7 +990,8 @@ def profile_step(args):
 def profile_dense(args):
     """Profiling target (no timing, no JSON line): q = A^T A d on
     --profile-dense problems of the dense workload's shape (800 x 4000, own A
-    each, seeded device draws), five applications."""
+    each, or one shared A with --profile-dense-shared; seeded device draws),
+    five applications."""
     import torch
     import paper_1411_5057_gb300 as F
     P, M, Nd = args.profile_dense, 800, 4000
@@ -998,8 +999,9 @@ def profile_dense(args):
     g.manual_seed(0)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        A = torch.randn(P, M, Nd, device="cuda", generator=g) / math.sqrt(M)
-        ctx = F.DenseContext(M, Nd, P, stream=stream)
+        shared = bool(args.profile_dense_shared)
+        A = torch.randn(1 if shared else P, M, Nd, device="cuda", generator=g) / math.sqrt(M)
+        ctx = F.DenseContext(M, Nd, P, shared=shared, stream=stream)
         ctx.set_matrix(A)
         del A
         d = torch.randn(P, Nd, device="cuda", generator=g)
@@ -1008,7 +1010,8 @@ def profile_dense(args):
             ctx.apply_AtA(d, q)
     stream.synchronize()
     ctx.close()
-    print(f"[bench] profile dense: {P} problems, five applications", file=sys.stderr)
+    print(f"[bench] profile dense: {P} problems ({'shared' if shared else 'own'} A), five applications",
+          file=sys.stderr)
 
 
 def main(argv=None):
@@ -1059,6 +1062,7 @@ def main(argv=None):
     ap.add_argument("--profile-ilu-shape", type=int, default=0)
     ap.add_argument("--profile-dense", type=int, default=0,
                     help="profiling target: q = A^T A d on this many dense problems, no timing")
+    ap.add_argument("--profile-dense-shared", type=int, default=0, help="1: one A shared by the profiled problems")
     args = ap.parse_args(argv)
     if args.profile_step > 0:
         return profile_step(args)

@@ -339,12 +339,13 @@ __global__ void k_dense_abar(int N, const float* __restrict__ dAtA, float* __res
 // then Q = T A (P x N): dense contractions in which a loaded tile of A serves
 // 64 problems.  C[m][n] = sum_k X[m][k] Y(k, n) over one split of K, X
 // row-major with K contiguous; Y(k, n) = B[n ldb + k] (YT) or B[k ldb + n].
-// A CTA computes a 128 x 128 tile (each thread 8 x 8 outputs) from 8-deep
-// slabs staged in shared memory, the next slab's loads in flight while the
-// current one is used.  FP32 throughout; the split partials are summed in
-// split order by the next stage.
+// A CTA computes a 128 x 128 tile (each thread 8 rows x 8 columns: columns
+// 4 tx .. 4 tx + 3 and 64 + 4 tx .. 64 + 4 tx + 3, so that the eight threads
+// of a quarter warp read 128 consecutive bytes of the Y slab, free of bank
+// conflicts) from 8-deep slabs staged in shared memory, the next slab's loads
+// in flight while the current one is used.  FP32 throughout; the split
+// partials are summed in split order by the next stage.
 constexpr int GM = 128, GN = 128, GK = 8, GT = 256;
-constexpr int kGemmCtasPerSm = 4;  // splits of K until each product has about this many CTAs per SM
 
 template <bool YT>
 __global__ void __launch_bounds__(GT, 2) k_dense_gemm(int Mg, int Ng, int K, int kper, const float* __restrict__ X,
@@ -415,8 +416,8 @@ __global__ void __launch_bounds__(GT, 2) k_dense_gemm(int Mg, int Ng, int K, int
     for (int kk = 0; kk < GK; ++kk) {
       const float4 a0 = *reinterpret_cast<const float4*>(&Xs[buf][kk][ty * 8]);
       const float4 a1 = *reinterpret_cast<const float4*>(&Xs[buf][kk][ty * 8 + 4]);
-      const float4 b0 = *reinterpret_cast<const float4*>(&Ys[buf][kk][tx * 8]);
-      const float4 b1 = *reinterpret_cast<const float4*>(&Ys[buf][kk][tx * 8 + 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Ys[buf][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Ys[buf][kk][64 + tx * 4]);
       const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -431,17 +432,40 @@ __global__ void __launch_bounds__(GT, 2) k_dense_gemm(int Mg, int Ng, int K, int
     __syncthreads();
     buf ^= 1;
   }
+  // Ng, ldc and split_stride are multiples of 4 (M % 4 = N % 4 = 0 on this
+  // path), so each group of four columns is one aligned float4, whole or out.
   float* Cs = C + (size_t)sp * split_stride;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int m = bm + ty * 8 + i;
     if (m >= Mg) continue;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int n = bn + tx * 8 + j;
-      if (n < Ng) Cs[(size_t)m * ldc + n] = acc[i][j];
+    for (int h = 0; h < 2; ++h) {
+      const int n = bn + h * 64 + tx * 4;
+      if (n < Ng)
+        *reinterpret_cast<float4*>(Cs + (size_t)m * ldc + n) =
+            make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
     }
   }
+}
+
+// Splits of K for a product of `tiles` output tiles with `slots` resident
+// CTAs on the device: the count that minimises (waves of CTAs) x (slabs per
+// CTA + 2), the 2 standing for a CTA's epilogue and the partial its split
+// adds to the sum; at least 4 slabs per split, fewest splits on ties.
+int gemm_splits(int tiles, int K, int slots) {
+  int best = 1;
+  long best_cost = -1;
+  for (int S = 1; S <= std::max(1, K / (4 * GK)); ++S) {
+    const int kper = ((K + S - 1) / S + GK - 1) / GK * GK;
+    const long waves = ((long)tiles * S + slots - 1) / slots;
+    const long cost = waves * (kper / GK + 2);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = S;
+    }
+  }
+  return best;
 }
 
 // T[p][i] = sum over the splits of Tpart[s][p][i] (split order).
@@ -589,13 +613,20 @@ extern "C" firls_status firls_dense_create(firls_dense_ctx** out, int M, int N, 
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   c->CH = chunks_for(M, problems);
   c->gemm = c->shared && M % 4 == 0;
-  if (c->gemm) {  // enough CTAs in both products: splits of K
-    int dev = 0, sms = 152;
+  if (c->gemm) {  // splits of K sized to whole waves of resident CTAs
+    int dev = 0, sms = 152, per_sm = 2;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm2 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_gemm<true>, GT, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_dense_gemm<false>, GT, 0) != cudaSuccess) {
+      cudaGetLastError();
+      per_sm = per_sm2 = 1;
+    }
+    per_sm = std::max(1, std::min(per_sm, per_sm2));
     const int tiles1 = ((M + GN - 1) / GN) * ((problems + GM - 1) / GM);
     const int tiles2 = ((N + GN - 1) / GN) * ((problems + GM - 1) / GM);
-    c->S1 = std::max(1, std::min((kGemmCtasPerSm * sms + tiles1 - 1) / tiles1, std::max(1, N / (4 * GK))));
-    c->CH = std::max(1, std::min((kGemmCtasPerSm * sms + tiles2 - 1) / tiles2, std::max(1, M / (4 * GK))));
+    c->S1 = gemm_splits(tiles1, N, per_sm * sms);
+    c->CH = gemm_splits(tiles2, M, per_sm * sms);
   }
   const size_t PN = (size_t)problems * N;
   firls_status s = FIRLS_OK;
