@@ -813,7 +813,71 @@ def dense_run(F, torch, args, reps=2):
                               "algorithmic_bytes": abytes, "us_per_apply": round(t_apply * 1e6, 1)},
             "accuracy_vs_oracle_same_schedule": {"n_checked": len(errs),
                                                  "max_rel_err": max(errs.values()) if errs else None},
-            "mse_vs_truth_mean": round(mse, 4), "paper_mse": "0.0427-0.0481 (FIRLS_L1, Table 1)"}
+            "mse_vs_truth_mean": round(mse, 4), "paper_mse": "0.0427-0.0481 (FIRLS_L1, Table 1)",
+            "shared_matrix": dense_shared_run(F, torch, args) if args.dense_shared_problems > 0 else None}
+
+
+def dense_shared_run(F, torch, args, reps=2):
+    """The same workload with one A shared by `args.dense_shared_problems`
+    signals (firls_synth.dense_l1_shared(1, P): problem 0 is dense_l1(1)),
+    where S d for all problems is two FP32 GEMMs (T = D A^T, Q = T A).
+    Problems per second for the 200 x 30 schedule with device-resident
+    inputs; the GEMM pair's FLOP rate against the FP32 FMA peak of the SMs
+    (SMs x 128 lanes x 2 flops x 2.07 GHz), timed through
+    firls_dense_apply_AtA with CUDA events; problem 0 against the FP64
+    oracle's stored result of dense_l1(1); the MSE against the truth."""
+    import firls_synth as fs
+    P = args.dense_shared_problems
+    M, Nd = 800, 4000
+    A, B, X0, lam = fs.dense_l1_shared(1, P)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = F.DenseContext(M, Nd, P, shared=True, stream=stream)
+        ctx.set_matrix(torch.from_numpy(A.astype(np.float32)).cuda())
+        b = torch.from_numpy(B.astype(np.float32)).cuda()
+        out = torch.empty(P, Nd, dtype=torch.float32, device="cuda")
+        prm = F.make_params(DENSE_OUTER, DENSE_INNER, lam=lam)
+        ctx.solve(b, prm, out=out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            ctx.solve(b, prm, out=out)
+    e1.record(stream)
+    e1.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3 / reps
+    with torch.cuda.stream(stream):
+        d = torch.randn(P, Nd, device="cuda")
+        q = torch.empty_like(d)
+        for _ in range(3):
+            ctx.apply_AtA(d, q)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(20):
+            ctx.apply_AtA(d, q)
+    e1.record(stream)
+    e1.synchronize()
+    t_apply = e0.elapsed_time(e1) / 1e3 / 20
+    flops = 4.0 * P * M * Nd
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 128 * 2 * 2.07e9 / 1e12
+    x = out.cpu().numpy().astype(np.float64)
+    ctx.close()
+    f = os.path.join(XDENSE_DIR, "seed1.npz")
+    err = None
+    if os.path.exists(f):
+        ref = np.load(f)["x"]
+        err = float(np.linalg.norm(x[0] - ref) / np.linalg.norm(ref))
+    return {"value": round(P / sec, 3), "unit": "problems/s", "s_per_batch": round(sec, 4),
+            "workload": f"{P} signals, one A 800 x 4000 Gaussian, 10% non-zeros each, lambda {lam}",
+            "roofline_gemm": {"bound": "alu", "kernel": "k_dense_gemm (x2) + k_dense_sum_splits",
+                              "achieved": round(flops / t_apply / 1e12, 2), "peak": round(peak, 1),
+                              "unit": "TFLOP/s", "frac": round(flops / t_apply / 1e12 / peak, 3),
+                              "peak_derivation": f"{sms} SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
+                              "us_per_apply": round(t_apply * 1e6, 1)},
+            "accuracy_vs_oracle_same_schedule": {"n_checked": 0 if err is None else 1, "max_rel_err": err},
+            "mse_vs_truth_mean": round(float(np.mean((x - X0) ** 2)), 4)}
 
 
 def precond_comparison(F, torch, stream, outer_steps=(1, 5, 20), tol=1e-6, cap=5000):
@@ -1050,6 +1114,8 @@ def main(argv=None):
                     help="timed passes of the queue with the ILU(0) preconditioner after one warm-up (0: none)")
     ap.add_argument("--tree-slices", type=int, default=32,
                     help="512^2 tree-group slices timed beside the main line (0: none)")
+    ap.add_argument("--dense-shared-problems", type=int, default=256,
+                    help="signals sharing one A in the dense measurement (0: skip)")
     ap.add_argument("--dense-problems", type=int, default=152,
                     help="dense random-projection problems timed beside the main line (0: none)")
     ap.add_argument("--mt-sets", type=int, default=100,

@@ -306,6 +306,24 @@ def dense_l1(seed: int, N: int = 4000, M: int = 800, density: float = 0.1, sigma
     return DenseProblem(A=A, b=b, x0=x0, lam=lam, seed=seed)
 
 
+def dense_l1_shared(seed: int, problems: int, N: int = 4000, M: int = 800, density: float = 0.1,
+                    sigma: float = 0.01, lam: float = 0.05):
+    """Several signals measured by one projection (the workload of Sec. 5.3
+    with A shared): A as in ``dense_l1(seed)``; signal p has the non-zeros and
+    the noise of ``dense_l1(seed + p)`` (substreams PHANTOM and NOISE of
+    seed + p), so problem 0 is ``dense_l1(seed)`` itself.  Returns
+    (A [M][N], B [problems][M], X0 [problems][N], lam), float64."""
+    A = _rng(seed, DENSE).standard_normal((M, N)) / math.sqrt(M)
+    k = int(round(density * N))
+    X0 = np.zeros((problems, N))
+    B = np.empty((problems, M))
+    for p in range(problems):
+        g = _rng(seed + p, PHANTOM)
+        X0[p, g.choice(N, size=k, replace=False)] = g.standard_normal(k)
+        B[p] = A @ X0[p] + sigma * _rng(seed + p, NOISE).standard_normal(M)
+    return A, B, X0, lam
+
+
 # --- learned warm start: architecture and seeded initial weights ------------
 
 CNN_CHANNELS = (3, 32, 32, 32, 32, 32, 2)   # input: Re A^H b, Im A^H b, mask

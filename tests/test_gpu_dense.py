@@ -122,6 +122,24 @@ def test_paper_workload_matches_stored_oracle(F):
     ctx.close()
 
 
+def test_shared_paper_workload_matches_stored_oracle(F):
+    """The Sec. 5.3 workload with one A shared by several signals (the GEMM
+    form of S d): problem 0 of firls_synth.dense_l1_shared(1, P) is
+    dense_l1(1), so after 200 x 30 it matches the FP64 oracle's stored
+    result of seed 1; every problem lands near its sparse truth."""
+    f = os.path.join(os.path.dirname(__file__), "golden", "xdense_l1", "seed1.npz")
+    assert os.path.exists(f), "no stored dense result"
+    z = np.load(f)
+    A, B, X0, lam = fs.dense_l1_shared(1, 5)
+    ctx = F.DenseContext(800, 4000, 5, shared=True)
+    ctx.set_matrix(f32(A))
+    x = ctx.solve(f32(B), F.make_params(int(z["outer"]), int(z["inner"]), lam=lam)).cpu().numpy()
+    assert rel(x[0].astype(np.float64), z["x"]) < TOL_SOLVE, rel(x[0], z["x"])
+    for p in range(5):
+        assert np.mean((x[p] - X0[p]) ** 2) < 2 * float(z["mse"]) + 0.02, p
+    ctx.close()
+
+
 def test_tolerance_stops_and_independence(F):
     """Problems with different lambdas stop on their own outer tolerance and
     PCG tolerance; each equals that problem solved beside other problems

@@ -119,3 +119,19 @@ def test_dense_generator_shapes():
     assert np.count_nonzero(p.x0) == 50
     q = fs.dense_l1(3, N=500, M=100)
     assert np.array_equal(p.A, q.A) and np.array_equal(p.b, q.b)
+
+
+def test_dense_shared_generator():
+    """One projection for every signal; problem p takes the signal and noise
+    of dense_l1(seed + p), so problem 0 is dense_l1(seed) bit for bit."""
+    A, B, X0, lam = fs.dense_l1_shared(3, 3, N=500, M=100)
+    assert A.shape == (100, 500) and B.shape == (3, 100) and X0.shape == (3, 500)
+    for p in range(3):
+        one = fs.dense_l1(3 + p, N=500, M=100)
+        assert np.array_equal(X0[p], one.x0)
+        assert np.count_nonzero(X0[p]) == 50
+        if p == 0:
+            assert np.array_equal(A, one.A) and np.array_equal(B[0], one.b) and lam == one.lam
+        else:
+            assert not np.array_equal(A, one.A)
+            assert np.allclose(B[p], A @ X0[p], atol=0.1)
