@@ -255,6 +255,89 @@ def _conv_backward_unflipped(a, w, dz):
 _orig_conv_bwd = C.conv3x3_backward
 
 
+def _idwt1_shift(a, d, h, g, axis):
+    """Synthesis with the taps rolled the wrong way (not the adjoint)."""
+    shape = list(a.shape)
+    shape[axis] *= 2
+    ua = np.zeros(shape, dtype=np.result_type(a, d))
+    ud = np.zeros(shape, dtype=np.result_type(a, d))
+    idx = [slice(None)] * len(shape)
+    idx[axis] = slice(0, shape[axis], 2)
+    ua[tuple(idx)] = a
+    ud[tuple(idx)] = d
+    x = 0
+    for t in range(len(h)):
+        x = x + h[t] * np.roll(ua, -t, axis=axis) + g[t] * np.roll(ud, -t, axis=axis)
+    return x
+
+
+def _inverse_map_descending(groups, N):
+    """Coefficient -> groups map with each coefficient's groups in descending order."""
+    groups = np.asarray(groups)
+    s, g = groups.shape
+    coef = groups.reshape(-1)
+    gid = np.repeat(np.arange(s), g)
+    order = np.lexsort((-gid, coef))
+    off = np.zeros(N + 1, dtype=np.int32)
+    off[1:] = np.cumsum(np.bincount(coef, minlength=N))
+    return off, gid[order].astype(np.int32)
+
+
+def _wavelet_diag_no_LL(w, n, kind, levels):
+    """diag(Phi^T W Phi) without the coarsest scaling band."""
+    S, V = O._analysis_matrices_1d(n, kind, levels)
+    w = np.asarray(w, dtype=np.float64).reshape(n, n)
+    out = np.zeros((n, n))
+    for l in range(1, levels + 1):
+        h = n >> l
+        for (br, bc) in ((0, 1), (1, 0), (1, 1)):
+            R = (S[l] if br == 0 else V[l]) ** 2
+            Cm = (S[l] if bc == 0 else V[l]) ** 2
+            out += R.T @ w[br * h:(br + 1) * h, bc * h:(bc + 1) * h] @ Cm
+    return out
+
+
+def _objective_joint_unsummed(xs, bs, masks, psi, levels, lam, lam_tv, eps=0.0):
+    """Joint F with the wavelet norm taken per contrast (no sum under the root)."""
+    val = 0.0
+    for x, b, m in zip(xs, bs, masks):
+        m = np.asarray(m).astype(np.float64)
+        val += 0.5 * float(np.sum(np.abs(O.op_A(x, m) - m * b) ** 2))
+    kind = O.wavelet_kind(psi)
+    if kind:
+        val += lam * sum(float(np.sum(np.sqrt(np.abs(O.wavedec2(x, kind, levels)) ** 2 + eps))) for x in xs)
+    if psi & O.PSI_TV:
+        n = np.asarray(masks[0]).shape[0]
+        D1, D2 = O.tv_matrices(n)
+        sq = sum(np.abs(D1 @ np.asarray(x).reshape(-1)) ** 2 + np.abs(D2 @ np.asarray(x).reshape(-1)) ** 2
+                 for x in xs)
+        val += lam_tv * float(np.sum(np.sqrt(sq + eps)))
+    return val
+
+
+def _forward_relu_last(params, inp):
+    """The CNN with ReLU on its last layer too."""
+    acts = [inp]
+    a = inp
+    for w, b in params:
+        a = np.maximum(C.conv3x3(a, w, b), 0.0)
+        acts.append(a)
+    return acts
+
+
+def _adam_no_bias_correction(params, grads, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    state["t"] += 1
+    out = []
+    for i, ((w, b), (gw, gb)) in enumerate(zip(params, grads)):
+        new = []
+        for j, (p, g) in enumerate(((w, gw), (b, gb))):
+            m = state["m"][2 * i + j] = beta1 * state["m"][2 * i + j] + (1 - beta1) * g
+            v = state["v"][2 * i + j] = beta2 * state["v"][2 * i + j] + (1 - beta2) * g * g
+            new.append(p - lr * m / (np.sqrt(v) + eps))
+        out.append(tuple(new))
+    return out
+
+
 # (target, attribute, replacement, pins that must catch it, invariant pins it passes)
 CASES = {
     "dft_unnormalised": [(O, "fft2u", lambda x: np.fft.fft2(x)), (O, "ifft2u", lambda y: np.fft.ifft2(y))],
@@ -299,7 +382,20 @@ CASES = {
         self, "w", (np.asarray(x, dtype=np.float64) ** 2 + self.eps) ** -1.0))],
     "cnn_kernel_flipped": [(C, "conv3x3", _conv_flipped)],
     "cnn_backward_unflipped": [(C, "conv3x3_backward", _conv_backward_unflipped)],
+    "synthesis_taps_rolled_back": [(O, "idwt1", _idwt1_shift)],
+    "inverse_map_descending": [(O, "inverse_group_map", _inverse_map_descending)],
+    "wavelet_diag_no_LL": [(O, "wavelet_diag", _wavelet_diag_no_LL)],
+    "l1_tv_weights_swapped": [(O, "tv_weights_aniso", lambda x, D1, D2, eps=O.EPS: tuple(reversed(
+        _orig_aniso(x, D1, D2, eps))))],
+    "joint_objective_unsummed": [(O, "objective_joint", _objective_joint_unsummed)],
+    "dense_objective_no_half": [(D, "objective", lambda x, A, b, lam, eps=0.0: 2.0 * _orig_dense_obj(
+        x, A, b, lam, eps) - lam * float(np.sum(np.sqrt(np.asarray(x, dtype=np.float64) ** 2 + eps))))],
+    "cnn_relu_on_output": [(C, "forward", _forward_relu_last)],
+    "adam_no_bias_correction": [(C, "adam_step", _adam_no_bias_correction)],
 }
+
+_orig_aniso = O.tv_weights_aniso
+_orig_dense_obj = D.objective
 
 _filters = O.wavelet_filters
 _orig_p_diag = D.DenseSystem.p_diag
@@ -374,6 +470,15 @@ PINS = {
     "dense_weights_no_sqrt": [TD.test_system_is_gradient_of_F_eps],
     "cnn_kernel_flipped": [TC.test_conv_matches_bruteforce],
     "cnn_backward_unflipped": [TC.test_conv_backward_is_the_adjoint],
+    "synthesis_taps_rolled_back": [lambda: TO.test_wavelet_orthogonal_dense(O.PSI_DB4, 1)],
+    "inverse_map_descending": [TO.test_inverse_group_map_bruteforce],
+    "wavelet_diag_no_LL": [lambda: TO.test_wavelet_diag_bruteforce(O.PSI_HAAR, 2)],
+    "l1_tv_weights_swapped": [lambda: TO.test_irls_system_is_the_gradient_of_F_eps(O.PSI_TV_ANISO)],
+    "joint_objective_unsummed": [lambda: TJ.test_joint_system_is_the_gradient_of_joint_F_eps(O.PSI_HAAR, 5e-3,
+                                                                                              0.0)],
+    "dense_objective_no_half": [TD.test_system_is_gradient_of_F_eps],
+    "cnn_relu_on_output": [TC.test_network_gradients_by_finite_differences],
+    "adam_no_bias_correction": [TC.test_adam_matches_closed_form_first_step],
 }
 
 # slips that keep an invariant: the invariant's pin passes, the other pins fail
