@@ -352,34 +352,34 @@ def run_ours(args):
               flush=True)
 
     # ---- preconditioner comparison (PCG iteration counts, untimed) ----
-    pcg_iters = precond_comparison(F, torch, stream) if aux and args.precond_cmp else None
-    if pcg_iters is not None:
+    pcg_iters = _aux(precond_comparison, F, torch, stream) if aux and args.precond_cmp else None
+    if _ok(pcg_iters):
         print("[bench] PCG steps to 1e-6: " + json.dumps({k: v for k, v in pcg_iters.items()
                                                            if isinstance(v, dict)}), file=sys.stderr, flush=True)
 
     # ---- the uneven batch (four sizes in one graph), untimed w.r.t. the main line ----
-    c4 = uneven_batch_run(F, torch, args) if aux and args.uneven else None
-    if c4 is not None:
+    c4 = _aux(uneven_batch_run, F, torch, args) if aux and args.uneven else None
+    if _ok(c4):
         print(f"[bench] uneven batch: {c4['value']} recons/s ({c4['s_per_batch']} s per 64 slices), "
               f"accuracy {json.dumps(c4['accuracy'])}", file=sys.stderr, flush=True)
 
     # ---- multi-contrast cross sections (joint sparsity), untimed w.r.t. the main line ----
-    mt = multi_contrast_run(F, torch, args) if aux and args.mt_sets > 0 else None
-    if mt is not None:
+    mt = _aux(multi_contrast_run, F, torch, args) if aux and args.mt_sets > 0 else None
+    if _ok(mt):
         print(f"[bench] multi-contrast: {mt['value']} cross sections/s ({mt['s_per_batch']} s per "
               f"{args.mt_sets}), accuracy {json.dumps(mt['accuracy_vs_oracle_same_schedule'])}, "
               f"SNR {mt['snr_db_mean']} dB", file=sys.stderr, flush=True)
 
     # ---- overlapping tree groups at 512^2, untimed w.r.t. the main line ----
-    tree = tree_run(F, torch, args) if aux and args.tree_slices > 0 else None
-    if tree is not None:
+    tree = _aux(tree_run, F, torch, args) if aux and args.tree_slices > 0 else None
+    if _ok(tree):
         print(f"[bench] tree groups 512^2: {tree['value']} recons/s ({tree['s_per_batch']} s per "
               f"{args.tree_slices}), accuracy {json.dumps(tree['accuracy_vs_oracle_same_schedule'])}, "
               f"SNR {tree['snr_db_mean']} dB", file=sys.stderr, flush=True)
 
     # ---- dense random projections (Sec. 5.3), untimed w.r.t. the main line ----
-    dense = dense_run(F, torch, args) if aux and args.dense_problems > 0 else None
-    if dense is not None:
+    dense = _aux(dense_run, F, torch, args) if aux and args.dense_problems > 0 else None
+    if _ok(dense):
         print(f"[bench] dense A: {dense['value']} problems/s ({dense['us_per_pcg_step']} us per PCG step), rows "
               f"{dense['roofline_rows']['achieved']} GB/s ({dense['roofline_rows']['frac']} of peak), accuracy "
               f"{json.dumps(dense['accuracy_vs_oracle_same_schedule'])}", file=sys.stderr, flush=True)
@@ -387,7 +387,8 @@ def run_ours(args):
     # ---- learned warm start (CNN trained on solver-generated pairs) ----
     learned = None
     if aux and args.learned:
-        learned = run_learned(args, F, torch, stream, B, rank, world, dist, serve_queue)
+        learned = _aux(run_learned, args, F, torch, stream, B, rank, world, dist, serve_queue)
+    if _ok(learned):
         print(f"[bench] learned vs plain on {learned['heldout_slices']} held-out slices: "
               f"{learned['value']} vs {learned['plain_value']} recons/s ({learned['vs_plain']}x), "
               f"PCG steps {learned['mean_pcg_steps']} vs {learned['plain_mean_pcg_steps']}; steady state "
@@ -671,6 +672,22 @@ def multi_contrast_run(F, torch, args, reps=2):
             "accuracy_vs_oracle_same_schedule": {"n_checked": len(errs),
                                                  "max_rel_err": max(errs.values()) if errs else None},
             "snr_db_mean": round(float(np.mean(snr)), 2), "paper_s_per_cross_section": 4.6}
+
+
+def _aux(fn, *a):
+    """Run one measurement beside the main line; an exception in it is
+    reported in its JSON key (and its traceback on stderr) instead of ending
+    the run before the main line prints."""
+    try:
+        return fn(*a)
+    except Exception as e:  # noqa: BLE001 - reported, not hidden
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
+def _ok(r):
+    return r is not None and "error" not in r
 
 
 def hbm_peak():

@@ -36,3 +36,15 @@ def test_reference_arm_line(procs):
     assert line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_auxiliary_measurement_failure_is_reported_not_fatal(capsys):
+    """A measurement beside the main line that raises leaves an error entry
+    in its key; the main line still prints."""
+    def boom(x):
+        raise KeyError(x)
+    r = bench._aux(boom, "missing")
+    assert r == {"error": "KeyError: 'missing'"} and not bench._ok(r)
+    assert "KeyError" in capsys.readouterr().err
+    assert bench._aux(lambda a, b: {"value": a + b}, 1, 2) == {"value": 3} and bench._ok({"value": 3})
+    assert not bench._ok(None)
