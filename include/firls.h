@@ -504,7 +504,8 @@ firls_status firls_apply_AHA_noalloc(int n, int batch, const uint8_t* mask, cons
  * (several signals measured by one projection).  Vectors are device float:
  * b [problems][M], x [problems][N].  Constraints: 1 <= M, 4 <= N <= 8192 with
  * N % 4 == 0 (rows are read as 16-byte vectors; A 16-byte aligned),
- * problems >= 1 (FIRLS_E_SHAPE otherwise).  Operators run in FP32; the PCG
+ * 1 <= problems <= 65535 with problems * M and problems * N below 2^31
+ * (FIRLS_E_SHAPE otherwise).  Operators run in FP32; the PCG
  * inner products, alpha, beta, rho, the residual norms and the relative change
  * in FP64.  With a matrix per problem each step S d = A^T (A d) + lambda W d
  * streams A once (a row's product with d is formed and immediately scattered

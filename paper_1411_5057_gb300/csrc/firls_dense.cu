@@ -11,6 +11,7 @@
 // FP64 inner products and PCG scalars (the SliceState helpers shared with the
 // Fourier path).
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -337,7 +338,7 @@ __global__ void k_dense_abar(int N, const float* __restrict__ dAtA, float* __res
 // ---- shared matrix: S d for all problems as two register-tiled GEMMs ----
 // With one A for every problem, A^T A d_p for all p is T = D A^T (P x M)
 // then Q = T A (P x N): dense contractions in which a loaded tile of A serves
-// 64 problems.  C[m][n] = sum_k X[m][k] Y(k, n) over one split of K, X
+// 128 problems.  C[m][n] = sum_k X[m][k] Y(k, n) over one split of K, X
 // row-major with K contiguous; Y(k, n) = B[n ldb + k] (YT) or B[k ldb + n].
 // A CTA computes a 128 x 128 tile (each thread 8 rows x 8 columns: columns
 // 4 tx .. 4 tx + 3 and 64 + 4 tx .. 64 + 4 tx + 3, so that the eight threads
@@ -603,7 +604,10 @@ extern "C" firls_status firls_dense_create(firls_dense_ctx** out, int M, int N, 
                                            void* cuda_stream) {
   if (!out) return FIRLS_E_INVALID_ARG;
   *out = nullptr;
-  if (M < 1 || N < 4 || N > 8192 || N % 4 || problems < 1) return FIRLS_E_SHAPE;
+  // problems index a grid dimension (<= 65535); P M and P N stay int-sized
+  if (M < 1 || N < 4 || N > 8192 || N % 4 || problems < 1 || problems > 65535 ||
+      (long long)problems * M > INT_MAX || (long long)problems * N > INT_MAX)
+    return FIRLS_E_SHAPE;
   firls_dense_ctx* c = new firls_dense_ctx();
   c->M = M;
   c->N = N;

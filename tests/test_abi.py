@@ -59,3 +59,18 @@ def test_invalid_shapes_rejected_without_device_work(lib):
     assert f(ctypes.byref(h), 64, 64, 0, 0, None) == 1        # empty batch
     assert f(None, 64, 64, 1, 0, None) == 1
     assert h.value is None
+
+
+def test_dense_shapes_rejected_without_device_work(lib):
+    """firls_dense_create checks its shape before any CUDA call: N a multiple
+    of 4 in [4, 8192], M >= 1, 1 <= problems <= 65535 and P M int-sized."""
+    h = ctypes.c_void_p()
+    f = lib.firls_dense_create
+    f.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                  ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    for M, N, P in ((0, 8, 1), (10, 6, 1), (10, 0, 1), (10, 8196, 1), (10, 8, 0), (10, 8, 65536),
+                    (40000, 8, 60000)):
+        assert f(ctypes.byref(h), M, N, P, 1, None) == 2, (M, N, P)      # FIRLS_E_SHAPE
+        assert h.value is None
+    assert f(None, 10, 8, 1, 0, None) == 1                              # FIRLS_E_INVALID_ARG
