@@ -135,14 +135,17 @@ def lib():
     return L
 
 
-def _need(t, numel, what):
+def _need(t, numel, what, dtype=None):
     """Reject a CUDA tensor that does not hold `numel` contiguous elements
-    (the library reads and writes exactly that many)."""
+    (the library reads and writes exactly that many), or, with `dtype`, whose
+    element type differs."""
     if t is None:
         return
     if not t.is_cuda or not t.is_contiguous() or t.numel() != numel:
         raise FirlsError(1, f"{what}: expected a contiguous CUDA tensor of {numel} elements, got "
                             f"{tuple(t.shape)} on {t.device}")
+    if dtype is not None and t.dtype != dtype:
+        raise FirlsError(1, f"{what}: expected {dtype}, got {t.dtype}")
 
 
 def _ptr(t):
@@ -216,7 +219,7 @@ class DenseContext:
 
     def set_matrix(self, A):
         """A: float32 CUDA [problems, M, N] (or [M, N] when shared)."""
-        _need(A, (1 if self.shared else self.problems) * self.M * self.N, "A")
+        _need(A, (1 if self.shared else self.problems) * self.M * self.N, "A", self._torch.float32)
         self._check(lib().firls_dense_set_matrix(self.h, _ptr(A)), "set_matrix")
 
     def abar(self):
@@ -225,15 +228,20 @@ class DenseContext:
         return list(out)
 
     def apply_AtA(self, d, q):
+        """q = A^T A d for every problem: float32 CUDA [problems, N] each."""
+        f32 = self._torch.float32
+        _need(d, self.problems * self.N, "d", f32)
+        _need(q, self.problems * self.N, "q", f32)
         self._check(lib().firls_dense_apply_AtA(self.h, _ptr(d), _ptr(q)), "apply_AtA")
 
     def solve(self, b, params, x0=None, out=None, stats=False):
         torch = self._torch
         if out is None:
             out = torch.empty((self.problems, self.N), dtype=torch.float32, device=b.device)
-        _need(b, self.problems * self.M, "b")
-        _need(x0, self.problems * self.N, "x0")
-        _need(out, self.problems * self.N, "out")
+        f32 = torch.float32
+        _need(b, self.problems * self.M, "b", f32)
+        _need(x0, self.problems * self.N, "x0", f32)
+        _need(out, self.problems * self.N, "out", f32)
         s = Stats() if stats else None
         st = lib().firls_dense_solve(self.h, _ptr(b), ctypes.byref(params), _ptr(x0), _ptr(out),
                                      ctypes.byref(s) if s is not None else None)

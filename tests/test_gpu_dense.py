@@ -203,6 +203,13 @@ def test_dense_errors(F):
         ctx.solve(b, F.make_params(1, 1, lam=-1.0))
     x = ctx.solve(b, F.make_params(2, 2, lam=0.1))                 # b = 0: x = 0 exactly
     assert torch.count_nonzero(x) == 0
+    q = torch.empty(2, 16, device="cuda")
+    for bad in (torch.zeros(2, 16, dtype=torch.float64, device="cuda"), torch.zeros(2, 15, device="cuda"),
+                torch.zeros(16, 2, device="cuda").t()):
+        with pytest.raises(F.FirlsError):                                # wrong type, size or layout
+            ctx.apply_AtA(bad, q)
+    with pytest.raises(F.FirlsError):
+        ctx.solve(b.double(), F.make_params(1, 1, lam=0.1))
     ctx.close()
 
 
