@@ -152,6 +152,10 @@ def test_tolerance_stops_and_independence(F):
     ctx.set_matrix(f32(np.stack(As)))
     x, st = ctx.solve(f32(np.stack(bs)), prm(lams), stats=True)
     assert st["outer_done"] < 300
+    # each side stops where its own relative change first falls to 1e-4 (and
+    # its PCG where its own residual falls to 1e-5): FP32 and FP64 can take
+    # those decisions one step apart, so the iterates agree to the stopping
+    # tolerances' scale, not to the fixed-schedule 1e-4 of the tests above
     for p in range(P):
         want, info = D.firls_l1(As[p], bs[p], lams[p], outer=300, inner=40, pcg_tol=1e-5, outer_tol=1e-4)
         assert rel(x[p].cpu().numpy().astype(np.float64), want) < 1e-3, p
