@@ -1095,7 +1095,7 @@ def profile_dense(args):
           file=sys.stderr)
 
 
-def main(argv=None):
+def build_parser():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -1146,7 +1146,11 @@ def main(argv=None):
     ap.add_argument("--profile-dense", type=int, default=0,
                     help="profiling target: q = A^T A d on this many dense problems, no timing")
     ap.add_argument("--profile-dense-shared", type=int, default=0, help="1: one A shared by the profiled problems")
-    args = ap.parse_args(argv)
+    return ap
+
+
+def main(argv=None):
+    args = build_parser().parse_args(argv)
     if args.profile_step > 0:
         return profile_step(args)
     if args.profile_dense > 0:
