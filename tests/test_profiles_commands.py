@@ -70,3 +70,13 @@ def test_commands_run_committed_files_only():
         for w in shlex.split(cmd.replace("$k", "k_ilu")):
             if w.endswith(".py"):
                 assert os.path.exists(os.path.join(ROOT, w)), (f, w)
+
+
+def test_referenced_summaries_exist():
+    """Every profiles/*.md that the notes, the README or bench.py names exists."""
+    for name in ("DESIGN.md", "README.md", "BASELINE.md", "bench.py"):
+        path = os.path.join(ROOT, name)
+        if not os.path.exists(path):
+            continue
+        for ref in re.findall(r"profiles/[A-Za-z0-9_.-]+\.md", open(path).read()):
+            assert os.path.exists(os.path.join(ROOT, ref)), (name, ref)
