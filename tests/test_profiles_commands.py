@@ -73,10 +73,7 @@ def test_commands_run_committed_files_only():
 
 
 def test_referenced_summaries_exist():
-    """Every profiles/*.md that the notes, the README or bench.py names exists."""
-    for name in ("DESIGN.md", "README.md", "BASELINE.md", "bench.py"):
-        path = os.path.join(ROOT, name)
-        if not os.path.exists(path):
-            continue
+    """Every profiles/*.md that a top-level document or bench.py names exists."""
+    for path in sorted(glob.glob(os.path.join(ROOT, "*.md"))) + [os.path.join(ROOT, "bench.py")]:
         for ref in re.findall(r"profiles/[A-Za-z0-9_.-]+\.md", open(path).read()):
-            assert os.path.exists(os.path.join(ROOT, ref)), (name, ref)
+            assert os.path.exists(os.path.join(ROOT, ref)), (os.path.basename(path), ref)
